@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of the Panorama exact-refinement search on GB300.
+
+A step is one whole search of a batch of synthetic queries through the
+library's C-ABI (query transform, coarse probe, work inversion, level-wise
+verification with pruning, exact re-ranking, top-k) with the index and the
+queries resident in HBM.  The default workload is the 960-d IVF workload:
+N = 1,000,000 FP32 vectors from a 1,024-cluster Gaussian mixture (eigen-decay
+exp(-0.01 i)), nlist = 1024, nprobe = 32, 10,000 queries, 16 levels x 60
+dims, k = 10.
+
+Printed (rank 0, one JSON line): candidates verified per second (query,
+candidate pairs resolved per second over all GPUs), QPS, the same through
+host buffers (e2e), the plain FP32 full-distance scan of the same candidate
+sets as the comparator, the roofline of the dominant kernel, the CPU oracle
+baseline and the SM clocks seen during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 2]
+  python bench.py --impl reference ...   # the CPU oracle as the reference arm
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("candidates verified/sec and QPS at oracle-exact top-k: "
+          "pruned BF16/FP8 vs plain FP32")
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS, FALLBACK_BF16_TFS = 6800.0, 1900.0
+KERNELS_PER_SEARCH = 13  # see the launch list in profiles/
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--config", type=int, default=2)
+    p.add_argument("--impl", default="panorama", choices=["panorama", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--scan-steps", type=int, default=3)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_name(s):
+    return (f"{s.name}: N={s.n:,} d={s.d} {s.precision.upper()}, nlist={s.nlist}, "
+            f"nprobe={s.nprobe}, {s.n_queries:,} queries, {s.n_levels}x{s.d // s.n_levels}"
+            f" levels, k={s.k}")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock / throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            j = json.load(f)
+        return j, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "bf16_tflops": FALLBACK_BF16_TFS,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_baseline(X, Q, C, s, sample_queries):
+    """The oracle (as it stands) on the host cores: FP64 brute force over each
+    sampled query's candidate set after its own FP64 list assignment."""
+    import numpy as np
+    import oracle
+    lists, _ = oracle.assign(X, C)
+    ptr, rows = oracle.ivf_lists(lists, C.shape[0])
+    qs = Q[:sample_queries]
+    t0 = time.perf_counter()
+    probes, _ = oracle.probe(qs, C, s.nprobe)
+    ids, _ = oracle.ivf_topk(X, qs, ptr, rows, probes, np.full(len(qs), s.k))
+    dt = time.perf_counter() - t0
+    pairs = sum(int(ptr[p + 1].sum() - ptr[p].sum()) for p in probes)
+    return {"value": pairs / dt, "unit": "candidates/s", "cores": os.cpu_count(),
+            "kind": "oracle", "qps": len(qs) / dt,
+            "sample": f"{len(qs)} queries of the workload (probe + FP64 brute force "
+                      f"over their candidate sets; list assignment untimed)",
+            "seconds": dt}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, on the host cores, on bounded samples."""
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    import numpy as np
+    import torch
+    import synth
+    s = synth.spec(args.config)
+    w = synth.generate(s, device="cpu")
+    X, Q = w.X.numpy(), w.Q.numpy()
+    import oracle
+    g = np.random.default_rng(3000 + s.cfg)
+    C = X[np.sort(g.choice(len(X), s.nlist, replace=False))].astype(np.float32)
+    lists, _ = oracle.assign(X, C)
+    ptr, rows = oracle.ivf_lists(lists, s.nlist)
+    per_step = 24
+    def step(i):
+        qs = Q[(i * per_step) % len(Q):][:per_step]
+        probes, _ = oracle.probe(qs, C, s.nprobe)
+        oracle.ivf_topk(X, qs, ptr, rows, probes, np.full(len(qs), s.k))
+        return sum(int(ptr[p + 1].sum() - ptr[p].sum()) for p in probes)
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    pairs = 0
+    for i in range(args.steps):
+        pairs += step(args.warmup + i)
+    dt = time.perf_counter() - t0
+    v = pairs / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "candidates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(s),
+                       "step": f"{per_step} queries (bounded sample of the workload)"},
+            "qps": per_step * args.steps / dt,
+            "cpu_baseline": {"value": v, "unit": "candidates/s", "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"{per_step} queries per step, FP64 brute force"},
+            "e2e": {"value": v, "unit": "candidates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2510_00566_gb300 as pano
+    import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2510_00566_gb300 import _build
+    if rank == 0 or not os.path.exists(pano.library_path):
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    pano.lib()
+
+    s = synth.spec(args.config)
+    # every rank holds a replica of the index and verifies its own query batch
+    w = synth.generate(s, device=dev)
+    if rank > 0:
+        import dataclasses
+        sq = dataclasses.replace(s, cfg=s.cfg + 100 * rank)
+        w.Q = synth.generate(sq, device=dev, queries_only=True).Q
+    X, Q = w.X, w.Q
+    t = pano.panorama_fit_transform(X[:65536], n_levels=s.n_levels)
+    idx = pano.panorama_build_ivf(t, X, nlist=s.nlist, n_levels=s.n_levels, seed=3000 + s.cfg)
+    nq = Q.shape[0]
+    k = s.k if isinstance(s.k, int) else max(s.k)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > L2
+
+    def step(mode=0, timing=False):
+        return idx.search(Q, s.nprobe, k, mode=mode, collect_timing=timing)
+
+    # counters (one instrumented search, outside the timed region)
+    step(0)
+    idx.search(Q, s.nprobe, k, collect_stats=True)
+    st = pano.last_stats().as_dict()
+
+    def timed(mode, steps, warmup, timing=True):
+        for _ in range(warmup):
+            step(mode)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        total, verify_ms = 0.0, []
+        clk = Clocks(local)
+        clk.start()
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(mode, timing)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+            if timing:
+                sm = pano.last_stats().stage_ms
+                verify_ms.append((sm[3], sm[4], list(sm)))
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        t_all = torch.tensor([total], device=dev)
+        if world > 1:
+            dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+        return t_all.item(), verify_ms, clocks
+
+    total_ms, vms, clocks = timed(0, args.steps, args.warmup)
+    ms_per_step = total_ms / args.steps
+    pairs = st["pairs"]
+    value = pairs * world / (ms_per_step / 1e3)
+    qps = nq * world / (ms_per_step / 1e3)
+
+    # comparator: plain FP32 full-distance scan of the same candidate sets
+    scan_ms, _, _ = timed(1, args.scan_steps, 1, timing=False)
+    scan_per = scan_ms / args.scan_steps
+
+    # e2e: through the public API with host buffers (pinned H2D + D2H)
+    qh = Q.cpu().pin_memory()
+    ids_h = torch.empty((nq, k), dtype=torch.int64).pin_memory()
+    d_h = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+    qd = torch.empty_like(Q)
+    for _ in range(2):
+        qd.copy_(qh, non_blocking=True)
+        a, b = idx.search(qd, s.nprobe, k)
+        ids_h.copy_(a, non_blocking=True)
+        d_h.copy_(b, non_blocking=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e2e_total = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        qd.copy_(qh, non_blocking=True)
+        a, b = idx.search(qd, s.nprobe, k)
+        ids_h.copy_(a, non_blocking=True)
+        d_h.copy_(b, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_total += e0.elapsed_time(e1)
+    t_e2e = torch.tensor([e2e_total], device=dev)
+    if world > 1:
+        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+    e2e_per = t_e2e.item() / args.steps
+
+    # roofline of the dominant kernel (verify phase B), measured live above
+    pk, pk_kind = peaks()
+    va = float(np.median([v[0] for v in vms]))
+    vb = float(np.median([v[1] for v in vms]))
+    stage = {n: float(np.median([v[2][i] for v in vms])) for i, n in
+             enumerate(("transform", "probe", "inversion", "verify_a", "verify_b", "decode"))}
+    verify_ms = va + vb
+    flops = 2.0 * st["dims_scanned"]
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA pipes
+    achieved = flops / (verify_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "kernel": "verify_fp32 (phases A+B)",
+            "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": None,
+            "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
+                           f"(max clock from MEASURED_PEAKS.json, {pk_kind})",
+            "slice_bytes_per_step": st["slice_bytes"],
+            "slice_GBps": st["slice_bytes"] / (verify_ms / 1e3) / 1e9,
+            "hbm_peak_GBps": pk.get("hbm_gbs"), "verify_ms": verify_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        Xh, Qh = X.cpu().numpy(), Q.cpu().numpy()
+        cpu = cpu_baseline(Xh, Qh, idx.centroids(), s, sample_queries=48)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if s.precision == "fp32" else s.precision, "data": "synthetic",
+            "config": {"workload": workload_name(s),
+                       "l2": "256 MB buffer written between timed steps (L2 flushed)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "qps": qps,
+            "fp32_scan": {"value": pairs * world / (scan_per / 1e3), "qps": nq * world / (scan_per / 1e3),
+                          "ms_per_step": scan_per, "speedup_of_pruned": scan_per / ms_per_step},
+            "e2e": {"value": pairs * world / (e2e_per / 1e3), "unit": "candidates/s",
+                    "qps": nq * world / (e2e_per / 1e3), "ms_per_step": e2e_per,
+                    "h2d_bytes_per_step": Q.numel() * 4, "d2h_bytes_per_step": nq * k * 12},
+            "gpu_launches": KERNELS_PER_SEARCH * args.steps,
+            "roofline": roof,
+            "stage_ms": stage,
+            "search_stats": {kk: st[kk] for kk in ("pairs", "pair_levels", "dims_scanned",
+                                                     "tile_levels", "slice_bytes", "reranked",
+                                                     "work_items")},
+            "dims_scanned_frac": st["dims_scanned"] / max(1, pairs * s.d),
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,234 @@
+/*
+ * panorama.h -- C-ABI of a GB300 (sm_103a) library for exact, level-wise
+ * verification of approximate-nearest-neighbour candidates in the manner of
+ * "Panorama: Fast-Track Nearest Neighbors" (arXiv 2510.00566).
+ *
+ * What the library computes (paper sections in brackets):
+ *   * an orthogonal PCA transform T and centre mu fit in closed form
+ *     [Section 4.1]; vectors are compared in the rotated space T(x - mu),
+ *     where squared distances are unchanged [Eq. 1];
+ *   * an IVF index: k-means centroids, lists of vectors [Section 6.1], each
+ *     list stored level-major (the L slices of a chunk of vectors follow one
+ *     another) together with per-vector cumulative tail norms [Section 6.5];
+ *   * search: for every query the nprobe nearest lists form the candidate set
+ *     Gamma [Problem 2]; candidates are refined level by level with the
+ *     Cauchy-Schwarz lower bound of Eq. 3 and discarded as soon as it exceeds
+ *     the running k-th distance [Algorithm 1, epsilon = 1], so the answer is
+ *     the exact k nearest candidates [Problem 1].
+ *
+ * Conventions shared by every entry point:
+ *   * Return value: PANO_OK (0) or a negative PANO_E* code.  The calling
+ *     thread's last error message is available from panorama_last_error().
+ *   * Matrices are row-major, FP32, one vector per row.
+ *   * "device" pointers are CUDA device (or managed) memory of the current
+ *     device; "host" pointers are ordinary process memory.  Entry points that
+ *     accept either detect the kind with cudaPointerGetAttributes.
+ *   * `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; temporary device memory is allocated
+ *     and freed stream-ordered on it (cudaMallocAsync / cudaFreeAsync).
+ *   * Squared Euclidean distances in the ORIGINAL space are reported.
+ *   * Result rows are sorted ascending by (distance, id); a row with fewer
+ *     than k candidates is padded with id -1 and distance +infinity.
+ *   * Objects (pano_transform, pano_index) are owned by the library and freed
+ *     with the matching panorama_free_* call; the caller owns every array it
+ *     passes in.  An index may be searched from several host threads at once
+ *     (searches only read it).
+ */
+#ifndef PANORAMA_H
+#define PANORAMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ error codes */
+#define PANO_OK 0
+#define PANO_EINVAL (-1)   /* invalid argument (shape, range, null pointer)  */
+#define PANO_ENOMEM (-2)   /* host or device allocation failed               */
+#define PANO_ECUDA (-3)    /* a CUDA call failed (message has the cause)     */
+#define PANO_ETIMEOUT (-4) /* a bounded device-side wait gave up             */
+#define PANO_ECORRUPT (-5) /* index file malformed or checksum mismatch      */
+#define PANO_ENODEV (-6)   /* no usable sm_103 device                        */
+
+/* ------------------------------------------------------ storage precision */
+#define PANO_FP32 0 /* level slices in FP32, SIMT partial products          */
+#define PANO_BF16 1 /* level slices in BF16, tensor-core partial products   */
+#define PANO_FP8 2  /* level slices in FP8 E4M3 with a per-vector scale     */
+
+typedef struct pano_transform pano_transform; /* opaque, library-owned */
+typedef struct pano_index pano_index;         /* opaque, library-owned */
+
+/* Build-time options.  Zero-initialise and set what you need; zero fields
+ * take the documented defaults. */
+typedef struct {
+  int32_t n_levels;            /* L >= 1 (default 8; clamped to d)           */
+  const int32_t* level_widths; /* host, L entries summing to d; NULL = equal
+                                  widths (d must then be divisible by L)     */
+  int32_t precision;           /* PANO_FP32 / PANO_BF16 / PANO_FP8           */
+  int64_t fit_sample;          /* rows used for the PCA covariance
+                                  (default min(n, 65536))                    */
+  uint64_t seed;               /* k-means sampling / initialisation seed     */
+  int32_t kmeans_iters;        /* Lloyd iterations (default 20)              */
+  int64_t kmeans_sample;       /* training rows (default min(n, 256 nlist))  */
+  int32_t identity_transform;  /* 1 = T = I, mu = 0 (raw axes)              */
+  const float* centroids;      /* optional host nlist x d original-space
+                                  centroids; when set k-means is skipped     */
+} pano_build_opts;
+
+/* Search-time options (pass NULL for the defaults). */
+typedef struct {
+  int32_t mode;        /* 0 = Panorama pruning (default); 1 = plain scan:
+                          every candidate's full distance, no early pruning */
+  int32_t synchronize; /* 1 (default when opts == NULL) = wait for the
+                          search and report device-side errors; 0 = return
+                          after enqueueing (errors surface on the next call
+                          or via panorama_search_stats)                     */
+  int32_t collect_stats; /* 1 = count pairs / levels / reranks (slower)     */
+  int32_t query_group; /* max queries sharing one tile (0 = automatic)      */
+  int32_t collect_timing; /* 1 = record CUDA events around each stage on
+                             `stream` (stage_ms in the stats; implies a wait) */
+} pano_search_opts;
+
+/* Counters of the most recent search through this index from this thread
+ * (filled when collect_stats = 1). */
+typedef struct {
+  int64_t n_queries;
+  int64_t pairs;          /* (query, candidate) pairs in all Gamma(q)        */
+  int64_t pair_levels;    /* sum over pairs of levels whose partial product
+                             was computed (dims scanned = sum of widths)     */
+  int64_t dims_scanned;   /* sum over pairs of coordinates read            */
+  int64_t tile_levels;    /* (query group, chunk, level) steps executed      */
+  int64_t slice_bytes;    /* level-slice bytes staged into shared memory     */
+  int64_t reranked;       /* pairs whose exact distance was computed         */
+  int64_t work_items;     /* (list, query group, segment) work items         */
+  int32_t device_error;   /* nonzero: a bounded wait or check failed         */
+  int32_t pad_;
+  /* device time per stage in ms (collect_timing = 1), measured with CUDA
+   * events on the search stream: [0] transform + norms, [1] coarse probe,
+   * [2] work inversion, [3] verify phase A (each query's nearest list),
+   * [4] verify phase B (remaining lists), [5] result decode */
+  float stage_ms[6];
+  float pad2_[2];
+} pano_search_stats;
+
+/* Description of a built index. */
+typedef struct {
+  int64_t n;
+  int32_t d;
+  int32_t nlist;
+  int32_t n_levels;
+  int32_t precision;
+  int32_t chunk;        /* vectors per level-major chunk                     */
+  int32_t max_level_width;
+  int64_t n_chunks;
+  int64_t device_bytes; /* device memory held by the index                   */
+  double eta;           /* ||T~^T T~ - I||_F of the FP32 transform            */
+} pano_index_info;
+
+/* ---------------------------------------------------------------- transform
+ * panorama_fit_transform -- PCA basis of a sample [Section 4.1].
+ *   X: host or device, n x d FP32.  The first min(n, fit_sample) rows are
+ *      used (pass a random subset if the rows are ordered).
+ *   The covariance (1/n normalisation) and its eigen-decomposition are
+ *   computed on the host in FP64; rows of T are eigenvectors ordered by
+ *   eigenvalue descending, each with its largest-magnitude entry positive.
+ *   opts may be NULL.  *out receives a new object.
+ * Errors: PANO_EINVAL (n < 1, d < 1, null pointers), PANO_ENOMEM,
+ *         PANO_ECUDA (copy of a device X failed). */
+int panorama_fit_transform(const float* X, int64_t n, int32_t d,
+                           const pano_build_opts* opts, pano_transform** out);
+
+/* Copies the fitted transform out (any pointer may be NULL):
+ *   T: d x d FP64 row-major, mu: d FP64, eigenvalues: d FP64 (descending). */
+int panorama_transform_export(const pano_transform* t, double* T, double* mu,
+                              double* eigenvalues);
+int panorama_transform_dim(const pano_transform* t);
+void panorama_free_transform(pano_transform* t);
+
+/* ------------------------------------------------------------------- build
+ * panorama_build_ivf -- IVF index with level-major lists [Section 6.1, 6.5].
+ *   t:     transform from panorama_fit_transform (the index keeps a copy).
+ *   X:     host or device, n x d FP32; vector i gets id i.
+ *   nlist: number of lists (1 = flat index, every vector in one list).
+ *   opts:  level split, precision, k-means settings (may be NULL).
+ *   Steps (all on `stream`'s device): k-means (unless opts->centroids),
+ *   nearest-centroid assignment (ties -> lower list id), transform of every
+ *   vector, per-vector tail norms and rounding-error bounds, level-major
+ *   packing in chunks, and an FP32 copy of the original rows for the exact
+ *   re-ranking step.  Blocks until the index is complete.
+ * Errors: PANO_EINVAL (d mismatch, nlist < 1 or > n, bad level split,
+ *         unknown precision), PANO_ENOMEM, PANO_ECUDA, PANO_ENODEV. */
+int panorama_build_ivf(const pano_transform* t, const float* X, int64_t n,
+                       int32_t nlist, const pano_build_opts* opts,
+                       void* stream, pano_index** out);
+
+/* ------------------------------------------------------------------ search
+ * panorama_search -- exact k nearest neighbours over each query's IVF
+ * candidate set [Problems 1-2, Algorithm 1 with epsilon = 1].
+ *   queries:  device, nq x d FP32.
+ *   nprobe:   device, nq int32 (each in [1, nlist]); or NULL with
+ *             nprobe_scalar in [1, nlist] for every query.
+ *   k:        device, nq int32 (each in [0, k_max]); or NULL with k_scalar.
+ *   k_max:    row stride of the outputs, 1..1024.
+ *   out_ids:  device, nq x k_max int64; out_dists: device, nq x k_max FP32.
+ *   Columns >= k of a row are filled with (-1, +inf).
+ *   Every candidate whose exact distance can still be among the k smallest
+ *   survives pruning (the bounds carry a rigorous rounding-error margin), and
+ *   survivors are re-ranked with exact FP32 distances on the original rows,
+ *   so ids equal those of an exact search except where two distances are
+ *   within FP32 rounding of each other.
+ * Errors: PANO_EINVAL (bad sizes, nprobe or k out of range when scalar),
+ *         PANO_ENOMEM, PANO_ECUDA, PANO_ETIMEOUT (device wait gave up);
+ *         out-of-range per-query nprobe/k values are clamped on the device.
+ */
+int panorama_search(const pano_index* idx, const float* queries, int64_t nq,
+                    const int32_t* nprobe, int32_t nprobe_scalar,
+                    const int32_t* k, int32_t k_scalar, int32_t k_max,
+                    int64_t* out_ids, float* out_dists, void* stream);
+
+/* panorama_search with options (opts may be NULL).  mode = 1 runs the plain
+ * FP32 full-distance scan over the same candidate sets (the comparator). */
+int panorama_search_ex(const pano_index* idx, const float* queries,
+                       int64_t nq, const int32_t* nprobe,
+                       int32_t nprobe_scalar, const int32_t* k,
+                       int32_t k_scalar, int32_t k_max, int64_t* out_ids,
+                       float* out_dists, void* stream,
+                       const pano_search_opts* opts);
+
+/* Counters of this thread's last search_ex with collect_stats = 1. */
+int panorama_search_stats(pano_search_stats* out);
+
+/* panorama_probe -- the coarse step alone: the nprobe nearest lists of each
+ * query by (original-space squared distance, list id) [Section 6.1].
+ *   queries: device nq x d; out_lists: device nq x nprobe int32, ascending. */
+int panorama_probe(const pano_index* idx, const float* queries, int64_t nq,
+                   int32_t nprobe, int32_t* out_lists, void* stream);
+
+/* ------------------------------------------------------ index inspection */
+int panorama_index_info(const pano_index* idx, pano_index_info* out);
+/* host nlist x d FP32 original-space centroids */
+int panorama_index_centroids(const pano_index* idx, float* out);
+/* host n int32: the list of every vector id */
+int panorama_index_assignment(const pano_index* idx, int32_t* out);
+
+/* ------------------------------------------------------ persistence
+ * panorama_save writes a versioned little-endian file with an FNV-1a 64-bit
+ * checksum; panorama_load rebuilds the index on the current device.
+ * Errors: PANO_EINVAL, PANO_ENOMEM, PANO_ECUDA, PANO_ECORRUPT (bad magic,
+ *         version, sizes or checksum), and I/O failures as PANO_EINVAL. */
+int panorama_save(const pano_index* idx, const char* path);
+int panorama_load(const char* path, pano_index** out);
+void panorama_free_index(pano_index* idx);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* panorama_last_error(void);
+/* Library version string. */
+const char* panorama_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PANORAMA_H */

@@ -1,0 +1,312 @@
+"""Python binding of libpanorama (GB300 / sm_103a), argument marshalling only.
+
+Every computation runs in the library's CUDA kernels behind the C-ABI of
+``include/panorama.h``; this module converts torch tensors / numpy arrays to
+pointers and sizes.  Importing the package does not load the library;
+``lib()`` does, and raises if the library was not built (there is no CPU
+fallback).  Build it with ``paper_2510_00566_gb300._build.build()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+__all__ = ["lib", "LibraryError", "Transform", "Index", "SearchStats",
+           "panorama_fit_transform", "panorama_build_ivf", "panorama_search",
+           "panorama_search_ex", "panorama_probe", "panorama_save",
+           "panorama_load", "PANO_FP32", "PANO_BF16", "PANO_FP8",
+           "library_path"]
+
+PANO_FP32, PANO_BF16, PANO_FP8 = 0, 1, 2
+_ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT",
+           -5: "ECORRUPT", -6: "ENODEV"}
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "lib", "libpanorama.so")
+_lib = None
+
+
+class LibraryError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"panorama error {code} ({_ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_int32),
+                ("level_widths", ctypes.POINTER(ctypes.c_int32)),
+                ("precision", ctypes.c_int32),
+                ("fit_sample", ctypes.c_int64),
+                ("seed", ctypes.c_uint64),
+                ("kmeans_iters", ctypes.c_int32),
+                ("kmeans_sample", ctypes.c_int64),
+                ("identity_transform", ctypes.c_int32),
+                ("centroids", ctypes.c_void_p)]
+
+
+class SearchOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("synchronize", ctypes.c_int32),
+                ("collect_stats", ctypes.c_int32),
+                ("query_group", ctypes.c_int32),
+                ("collect_timing", ctypes.c_int32)]
+
+
+class SearchStats(ctypes.Structure):
+    _fields_ = [("n_queries", ctypes.c_int64), ("pairs", ctypes.c_int64),
+                ("pair_levels", ctypes.c_int64),
+                ("dims_scanned", ctypes.c_int64),
+                ("tile_levels", ctypes.c_int64),
+                ("slice_bytes", ctypes.c_int64),
+                ("reranked", ctypes.c_int64), ("work_items", ctypes.c_int64),
+                ("device_error", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("stage_ms", ctypes.c_float * 6), ("pad2_", ctypes.c_float * 2)]
+
+    STAGES = ("transform", "probe", "inversion", "verify_a", "verify_b",
+              "decode")
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_
+             if not f.startswith("pad") and f != "stage_ms"}
+        d["stage_ms"] = dict(zip(self.STAGES, list(self.stage_ms)))
+        return d
+
+
+class IndexInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32),
+                ("nlist", ctypes.c_int32), ("n_levels", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("max_level_width", ctypes.c_int32),
+                ("n_chunks", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("eta", ctypes.c_double)]
+
+
+# name -> (restype, argtypes); the exported C-ABI (include/panorama.h)
+_P, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+SIGNATURES = {
+    "panorama_fit_transform": (ctypes.c_int, [_P, _I64, _I32, _P, _P]),
+    "panorama_transform_export": (ctypes.c_int, [_P, _P, _P, _P]),
+    "panorama_transform_dim": (ctypes.c_int, [_P]),
+    "panorama_free_transform": (None, [_P]),
+    "panorama_build_ivf": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _P]),
+    "panorama_search": (ctypes.c_int, [_P, _P, _I64, _P, _I32, _P, _I32,
+                                       _I32, _P, _P, _P]),
+    "panorama_search_ex": (ctypes.c_int, [_P, _P, _I64, _P, _I32, _P, _I32,
+                                          _I32, _P, _P, _P, _P]),
+    "panorama_search_stats": (ctypes.c_int, [_P]),
+    "panorama_probe": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P]),
+    "panorama_index_info": (ctypes.c_int, [_P, _P]),
+    "panorama_index_centroids": (ctypes.c_int, [_P, _P]),
+    "panorama_index_assignment": (ctypes.c_int, [_P, _P]),
+    "panorama_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "panorama_load": (ctypes.c_int, [ctypes.c_char_p, _P]),
+    "panorama_free_index": (None, [_P]),
+    "panorama_last_error": (ctypes.c_char_p, []),
+    "panorama_version": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """Load libpanorama.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(library_path):
+            raise RuntimeError(
+                f"{library_path} is missing: build it with "
+                "paper_2510_00566_gb300._build.build() (no CPU fallback)")
+        L = ctypes.CDLL(library_path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise LibraryError(rc, lib().panorama_last_error().decode())
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _host_f32(a):
+    import numpy as np
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda:
+            return a.contiguous(), a.contiguous().data_ptr()
+        a = a.numpy()
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data
+
+
+# ------------------------------------------------------------------ C names
+def panorama_fit_transform(X, n_levels=8, fit_sample=0, identity=False):
+    """PCA transform of the rows of X (host numpy / torch, or CUDA tensor)."""
+    keep, ptr = _host_f32(X)
+    n, d = keep.shape
+    opts = BuildOpts(n_levels=n_levels, fit_sample=fit_sample,
+                     identity_transform=1 if identity else 0)
+    out = ctypes.c_void_p()
+    _check(lib().panorama_fit_transform(ptr, n, d, ctypes.byref(opts),
+                                        ctypes.byref(out)))
+    return Transform(out.value, d)
+
+
+def panorama_build_ivf(t: "Transform", X, nlist: int, n_levels=8,
+                       level_widths=None, precision=PANO_FP32, seed=1234,
+                       kmeans_iters=20, kmeans_sample=0, centroids=None,
+                       stream=None):
+    """IVF index of X (CUDA tensor or host array); see panorama_build_ivf."""
+    import numpy as np
+    keep, ptr = _host_f32(X)
+    n, d = keep.shape
+    widths = None
+    if level_widths is not None:
+        widths = (ctypes.c_int32 * len(level_widths))(*level_widths)
+        n_levels = len(level_widths)
+    cent_keep = None
+    opts = BuildOpts(n_levels=n_levels, level_widths=widths,
+                     precision=precision, seed=seed,
+                     kmeans_iters=kmeans_iters, kmeans_sample=kmeans_sample)
+    if centroids is not None:
+        cent_keep = np.ascontiguousarray(
+            centroids.cpu().numpy() if hasattr(centroids, "cpu") else centroids,
+            dtype=np.float32)
+        opts.centroids = cent_keep.ctypes.data
+    out = ctypes.c_void_p()
+    _check(lib().panorama_build_ivf(t.handle, ptr, n, nlist, ctypes.byref(opts),
+                                    _stream_ptr(stream), ctypes.byref(out)))
+    del cent_keep
+    return Index(out.value)
+
+
+def panorama_search_ex(idx: "Index", queries, nprobe, k, k_max=None,
+                       mode=0, collect_stats=False, synchronize=True,
+                       stream=None, out=None, collect_timing=False):
+    """Returns (ids int64 [nq, k_max], dists float32 [nq, k_max]) on the GPU.
+
+    nprobe / k: python ints, or CUDA int32 tensors with one value per query.
+    """
+    import torch
+    q = queries.contiguous()
+    assert q.is_cuda and q.dtype == torch.float32
+    nq = q.shape[0]
+    np_ptr, np_scalar = None, 0
+    if isinstance(nprobe, torch.Tensor):
+        nprobe = nprobe.to(device=q.device, dtype=torch.int32).contiguous()
+        np_ptr, np_scalar = nprobe.data_ptr(), int(nprobe.max()) if nq else 1
+    else:
+        np_scalar = int(nprobe)
+    k_ptr, k_scalar = None, 0
+    if isinstance(k, torch.Tensor):
+        k = k.to(device=q.device, dtype=torch.int32).contiguous()
+        k_ptr = k.data_ptr()
+        if k_max is None:
+            k_max = int(k.max()) if nq else 1
+    else:
+        k_scalar = int(k)
+        if k_max is None:
+            k_max = max(1, k_scalar)
+    if out is None:
+        ids = torch.empty((nq, k_max), dtype=torch.int64, device=q.device)
+        dists = torch.empty((nq, k_max), dtype=torch.float32, device=q.device)
+    else:
+        ids, dists = out
+    opts = SearchOpts(mode=mode, synchronize=1 if synchronize else 0,
+                      collect_stats=1 if collect_stats else 0,
+                      collect_timing=1 if collect_timing else 0)
+    _check(lib().panorama_search_ex(idx.handle, q.data_ptr(), nq, np_ptr,
+                                    np_scalar, k_ptr, k_scalar, k_max,
+                                    ids.data_ptr(), dists.data_ptr(),
+                                    _stream_ptr(stream), ctypes.byref(opts)))
+    return ids, dists
+
+
+def panorama_search(idx, queries, nprobe, k, k_max=None, stream=None):
+    return panorama_search_ex(idx, queries, nprobe, k, k_max, stream=stream)
+
+
+def panorama_probe(idx: "Index", queries, nprobe: int, stream=None):
+    import torch
+    q = queries.contiguous()
+    out = torch.empty((q.shape[0], nprobe), dtype=torch.int32, device=q.device)
+    _check(lib().panorama_probe(idx.handle, q.data_ptr(), q.shape[0], nprobe,
+                                out.data_ptr(), _stream_ptr(stream)))
+    return out
+
+
+def panorama_save(idx: "Index", path: str):
+    _check(lib().panorama_save(idx.handle, path.encode()))
+
+
+def panorama_load(path: str) -> "Index":
+    out = ctypes.c_void_p()
+    _check(lib().panorama_load(path.encode(), ctypes.byref(out)))
+    return Index(out.value)
+
+
+def last_stats() -> SearchStats:
+    s = SearchStats()
+    _check(lib().panorama_search_stats(ctypes.byref(s)))
+    return s
+
+
+# ------------------------------------------------------------ thin objects
+class Transform:
+    def __init__(self, handle: int, d: int):
+        self.handle = handle
+        self.d = d
+
+    def export(self):
+        import numpy as np
+        T = np.empty((self.d, self.d), dtype=np.float64)
+        mu = np.empty(self.d, dtype=np.float64)
+        ev = np.empty(self.d, dtype=np.float64)
+        _check(lib().panorama_transform_export(self.handle, T.ctypes.data,
+                                               mu.ctypes.data, ev.ctypes.data))
+        return T, mu, ev
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.panorama_free_transform(self.handle)
+            self.handle = None
+
+
+class Index:
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def info(self) -> IndexInfo:
+        i = IndexInfo()
+        _check(lib().panorama_index_info(self.handle, ctypes.byref(i)))
+        return i
+
+    def centroids(self):
+        import numpy as np
+        i = self.info()
+        out = np.empty((i.nlist, i.d), dtype=np.float32)
+        _check(lib().panorama_index_centroids(self.handle, out.ctypes.data))
+        return out
+
+    def assignment(self):
+        import numpy as np
+        out = np.empty(self.info().n, dtype=np.int32)
+        _check(lib().panorama_index_assignment(self.handle, out.ctypes.data))
+        return out
+
+    def search(self, queries, nprobe, k, k_max=None, **kw):
+        return panorama_search_ex(self, queries, nprobe, k, k_max, **kw)
+
+    def free(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.panorama_free_index(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.free()

@@ -1,0 +1,121 @@
+// Device helpers shared by the library's kernels: bulk-async (TMA engine)
+// copies with mbarrier completion, bounded waits, (distance, id) keys and the
+// lock-free k-smallest insertion used for the running top-k.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pano {
+
+// Error bits written into the per-call device status word.
+enum : int {
+  kErrTimeout = 1,   // a bounded wait gave up
+  kErrOverflow = 2,  // a capacity bound was exceeded (result still valid)
+  kErrBadInput = 4,  // an out-of-range per-query value was clamped
+};
+
+// Roughly one second of spinning at GB300 clocks before a wait gives up.
+constexpr long long kWaitCycles = 2000000000LL;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(count));
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+// One bulk-async copy global -> shared completing on `bar` (TMA engine,
+// non-tensor form).  dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of `bar`; false after ~kWaitCycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+// ------------------------------------------------------- (dist, id) keys
+// Non-negative FP32 distances order like their bit patterns, so a 64-bit key
+// (dist bits << 32 | id) orders by (distance, id).  The empty key is ~0.
+constexpr unsigned long long kEmptyKey = ~0ULL;
+
+__device__ __forceinline__ unsigned long long make_key(float dist, int32_t id) {
+  dist = fmaxf(dist, 0.0f);
+  return (static_cast<unsigned long long>(__float_as_uint(dist)) << 32) |
+         static_cast<uint32_t>(id);
+}
+__device__ __forceinline__ float key_dist(unsigned long long k) {
+  return __uint_as_float(static_cast<uint32_t>(k >> 32));
+}
+__device__ __forceinline__ int32_t key_id(unsigned long long k) {
+  return static_cast<int32_t>(static_cast<uint32_t>(k & 0xffffffffULL));
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+// Insert `key` into the ascending k-slot array `slots` shared by concurrent
+// inserters.  Each step is an atomic compare-exchange between the carried
+// key and one slot (atomicMin keeps the smaller, the larger moves on), so
+// once all inserts have finished the slots hold the k smallest keys ever
+// inserted, in ascending order.  A slot whose current value is already below
+// the carried key would keep it, so those steps are skipped.
+__device__ __forceinline__ void topk_insert(unsigned long long* slots, int k,
+                                            unsigned long long key) {
+  int j = 0;
+  while (j < k && ld_volatile_u64(slots + j) < key) ++j;
+  for (; j < k; ++j) {
+    unsigned long long old = atomicMin(slots + j, key);
+    if (old == kEmptyKey) return;
+    key = old > key ? old : key;
+  }
+}
+
+// Order-preserving map of any FP32 value to uint32.
+__device__ __forceinline__ uint32_t float_ordered(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+}  // namespace pano

@@ -1,0 +1,105 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <functional>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/panorama.h"
+
+namespace pano {
+
+// ------------------------------------------------------------ error state
+void set_error(const std::string& msg);
+void clear_error();
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define PANO_CUDA(expr)                                   \
+  do {                                                    \
+    cudaError_t e_ = (expr);                              \
+    if (e_ != cudaSuccess) return ::pano::cuda_fail(e_, #expr); \
+  } while (0)
+
+#define PANO_CHECK(cond, code, msg)          \
+  do {                                       \
+    if (!(cond)) return ::pano::fail(code, msg); \
+  } while (0)
+
+// ------------------------------------------------ rounding-error constants
+// Unit roundoff of FP32 (round to nearest).
+constexpr double kU32 = 5.9604644775390625e-08;  // 2^-24
+// gamma_n = n u / (1 - n u): bound on the relative error of an n-term
+// floating-point sum/product chain (standard a priori analysis).
+inline double gamma_n(double n) { return n * kU32 / (1.0 - n * kU32); }
+
+// The SIMT GEMM accumulates each K-tile of GEMM_KT products in a fresh
+// register and then adds the tile sums, so every product passes through at
+// most GEMM_KT + ceil(K / GEMM_KT) + 1 roundings.
+constexpr int GEMM_KT = 16;
+inline double gemm_rounds(int K) { return GEMM_KT + (K + GEMM_KT - 1) / GEMM_KT + 1; }
+
+// ------------------------------------------------------------ host helpers
+void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& fn);
+int fit_pca(const float* X, int64_t n, int d, std::vector<double>& mu,
+            std::vector<double>& T, std::vector<double>& lam, std::string& err);
+double orthogonality_defect(const float* A, int d);
+
+// Device allocation owned by an index (freed in the destructor).
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int alloc(size_t n);
+  void release();
+  template <class T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+  ~DevBuf() { release(); }
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+};
+
+}  // namespace pano
+
+struct pano_transform {
+  int32_t d = 0;
+  int32_t identity = 0;
+  std::vector<double> T, mu, lam;  // FP64 fit
+  std::vector<float> T32, mu32;    // what the device uses (T~, mu~)
+  double eta = 0.0;                // ||T~^T T~ - I||_F (bounds sigma(T~))
+};
+
+struct pano_index {
+  int device = 0;
+  int64_t n = 0;
+  int32_t d = 0, nlist = 0, L = 0, precision = 0, chunk = 64;
+  int32_t max_w = 0;
+  std::vector<int32_t> widths, offs;  // offs[l] = m_l, l = 0..L
+  int64_t n_chunks = 0;
+  double eta = 0.0;     // orthogonality defect of T~
+  double c_trans = 0.0; // e(v) <= c_trans * ||v - mu~|| for the FP32 transform
+  float cmax = 0.f;     // max centroid norm (probe rounding band)
+  pano_transform tf;
+  // host copies
+  std::vector<float> centroids;         // nlist x d, original space
+  std::vector<int32_t> assign;          // n: list of each vector
+  std::vector<int64_t> list_chunk_off;  // nlist + 1
+  std::vector<int32_t> list_size;       // nlist
+  // device arrays
+  pano::DevBuf T32, mu32;        // d x d, d
+  pano::DevBuf cent, cent_n2;    // nlist x d, nlist   (original space)
+  pano::DevBuf chunk_off_d;      // nlist + 1 int64
+  pano::DevBuf list_size_d;      // nlist int32
+  pano::DevBuf level_off_d;      // L + 1 int32 (m_l)
+  pano::DevBuf slices;   // FP32: [chunk][d][64] level-major, dims-major slices
+  pano::DevBuf tails;    // [chunk][L+1][CH] sqrt tail energy, rounded up
+  pano::DevBuf xn2;      // [chunk][CH] ||x~||^2
+  pano::DevBuf ex;       // [chunk][CH] bound on ||x~ - T~(x - mu~)||
+  pano::DevBuf ids;      // [chunk][CH] int32 original id, -1 = padding
+  pano::DevBuf rows;     // [chunk * CH][d] original FP32 rows (re-ranking)
+  size_t device_bytes() const;
+};

@@ -1,0 +1,957 @@
+// panorama_search: the device hot path.
+//
+//   a1 transform_queries   q~ = T~(q - mu~) (FP32 GEMM) + per-query norms,
+//                          rounded-up tail norms sqrt(R_q^{(l,d)}) and the
+//                          transform-error bound e_q                  [Alg. 1]
+//   a2 probe + select      original-space expansion distances to every
+//                          centroid, radix select of the nprobe-th, exact
+//                          re-score of the boundary band    [Section 6.1]
+//   a3 work inversion      probes -> per-list query buckets -> work items
+//                          (list, segment, query group); rank-0 probes (each
+//                          query's nearest list) form phase A, the rest B
+//   a4-a8 verify           level-wise partial products, bound update,
+//                          pruning and survivor compaction   [Eq. 2-3, Alg. 1]
+//   a9 re-rank             survivors' exact distances on the original rows
+//   a10 top-k              lock-free k-smallest insertion per query; its k-th
+//                          key is the running threshold d_k      [Alg. 1]
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "gemm.h"
+#include "internal.h"
+#include "kernels_common.cuh"
+#include "search.h"
+
+namespace pano {
+
+namespace {
+
+constexpr int CH = 64;
+constexpr int SEG_CHUNKS = 32;  // chunks per work-item segment
+constexpr int NT = 256;
+
+__device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// --------------------------------------------------------------- a1: norms
+__global__ void query_norms_kernel(const float* __restrict__ q, const float* __restrict__ qt,
+                                   int64_t nq, int d, int L, const int32_t* __restrict__ level_off,
+                                   const float* __restrict__ mu, double c_trans,
+                                   float4* __restrict__ qinfo, float* __restrict__ qtail,
+                                   float* __restrict__ qn2) {
+  int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (row >= nq) return;
+  const int lane = threadIdx.x & 31;
+  const float* x = qt + row * d;
+  double suffix = 0.0;
+  for (int l = L - 1; l >= 0; --l) {
+    double e = 0.0;
+    for (int j = level_off[l] + lane; j < level_off[l + 1]; j += 32) {
+      double v = x[j];
+      e += v * v;
+    }
+    suffix += warp_sum_f64(e);
+    if (lane == 0)
+      qtail[row * (L + 1) + l] = __double2float_ru(sqrt(suffix * (1.0 + 1e-12)));
+  }
+  double dev = 0.0, on = 0.0;
+  for (int j = lane; j < d; j += 32) {
+    double v = q[row * d + j];
+    double w = v - (double)mu[j];
+    dev += w * w;
+    on += v * v;
+  }
+  dev = warp_sum_f64(dev);
+  on = warp_sum_f64(on);
+  if (lane == 0) {
+    qtail[row * (L + 1) + L] = 0.f;
+    float nqf = (float)suffix;
+    qinfo[row] = make_float4(nqf, sqrtf(nqf), __double2float_ru(c_trans * sqrt(dev) * (1.0 + 1e-9)), 0.f);
+    qn2[row] = (float)on;
+  }
+}
+
+// FP32 squared norms of rows (accumulated in FP64, rounded once).
+__global__ void row_sqnorm_kernel(const float* __restrict__ X, int64_t m, int d,
+                                  float* __restrict__ out) {
+  int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (row >= m) return;
+  double s = 0.0;
+  for (int j = threadIdx.x & 31; j < d; j += 32) {
+    double v = X[row * d + j];
+    s += v * v;
+  }
+  s = warp_sum_f64(s);
+  if ((threadIdx.x & 31) == 0) out[row] = (float)s;
+}
+
+// nprobe / k per query, clamped to [1, nlist] and [0, k_max].
+__global__ void prep_kernel(int64_t nq, const int32_t* __restrict__ nprobe, int nprobe_scalar,
+                            int nprobe_cap, const int32_t* __restrict__ k, int k_scalar,
+                            int k_max, int32_t* __restrict__ npq, int32_t* __restrict__ kq,
+                            int* __restrict__ err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  int np = nprobe ? nprobe[i] : nprobe_scalar;
+  int kk = k ? k[i] : k_scalar;
+  if (np < 1 || np > nprobe_cap || kk < 0 || kk > k_max) atomicOr(err, kErrBadInput);
+  npq[i] = min(max(np, 1), nprobe_cap);
+  kq[i] = min(max(kk, 0), k_max);
+}
+
+// ------------------------------------------------------ a2: probe selection
+// One CTA per query.  The nprobe-th smallest expansion distance v is found by
+// an 8-bit radix select on order-preserving keys; every centroid whose
+// expansion distance is within twice the expansion's rounding bound of v (or
+// below) is re-scored with the compensated difference form and the first
+// nprobe by (exact distance, list id) are written in ascending order.
+constexpr int kBandCap = 1024;
+
+__global__ void __launch_bounds__(NT) probe_select_kernel(
+    const float* __restrict__ pdist, int nlist, const float* __restrict__ q,
+    const float* __restrict__ cent, int d, const float* __restrict__ qn2, float cmax,
+    float gerr, const int32_t* __restrict__ npq, int nprobe_stride,
+    int32_t* __restrict__ probes, int* __restrict__ err) {
+  extern __shared__ uint32_t keys[];  // nlist
+  __shared__ int hist[256];
+  __shared__ int s_bin, s_below;
+  __shared__ int band_n;
+  __shared__ int band_id[kBandCap];
+  __shared__ float band_d[kBandCap];
+  const int64_t row = blockIdx.x;
+  const int m = npq[row];
+  const float* pd = pdist + row * (int64_t)nlist;
+  for (int i = threadIdx.x; i < nlist; i += NT) keys[i] = float_ordered(pd[i]);
+  if (threadIdx.x == 0) band_n = 0;
+  uint32_t prefix = 0, mask = 0;
+  int remaining = m;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int i = threadIdx.x; i < 256; i += NT) hist[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nlist; i += NT) {
+      uint32_t k = keys[i];
+      if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int acc = 0, b = 0;
+      for (; b < 256; ++b) {
+        if (acc + hist[b] >= remaining) break;
+        acc += hist[b];
+      }
+      s_bin = b;
+      s_below = acc;
+    }
+    __syncthreads();
+    prefix |= (uint32_t)s_bin << shift;
+    mask |= 255u << shift;
+    remaining -= s_below;
+    __syncthreads();
+  }
+  // decode v and form the band
+  uint32_t u = (prefix & 0x80000000u) ? (prefix & 0x7fffffffu) : ~prefix;
+  float v = __uint_as_float(u);
+  float s = sqrtf(qn2[row]) + cmax;
+  float hi = v + 2.f * gerr * s * s;
+  for (int i = threadIdx.x; i < nlist; i += NT) {
+    if (pd[i] <= hi) {
+      int pos = atomicAdd(&band_n, 1);
+      if (pos < kBandCap) band_id[pos] = i;
+    }
+  }
+  __syncthreads();
+  const int nb = min(band_n, kBandCap);
+  if (threadIdx.x == 0 && band_n > kBandCap) atomicOr(err, kErrOverflow);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  for (int b = warp; b < nb; b += NT / 32) {
+    float e = exact_sqdist_warp(q + row * d, cent + (int64_t)band_id[b] * d, d);
+    if (lane == 0) band_d[b] = e;
+  }
+  __syncthreads();
+  int32_t* out = probes + row * (int64_t)nprobe_stride;
+  for (int b = threadIdx.x; b < nb; b += NT) {
+    float db = band_d[b];
+    int ib = band_id[b];
+    int rank = 0;
+    for (int o = 0; o < nb; ++o) {
+      float dd = band_d[o];
+      rank += (dd < db) || (dd == db && band_id[o] < ib);
+    }
+    if (rank < m) out[rank] = ib;
+  }
+  for (int r = nb + threadIdx.x; r < m; r += NT) out[r] = -1;  // unreachable unless nlist < m
+}
+
+// ------------------------------------------------------- a3: work inversion
+__global__ void inv_count_kernel(int64_t nq, const int32_t* __restrict__ probes, int stride,
+                                 const int32_t* __restrict__ npq, int* __restrict__ cnt,
+                                 int nlist) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nq * stride) return;
+  int64_t qi = e / stride;
+  int r = (int)(e % stride);
+  if (r >= npq[qi]) return;
+  int c = probes[e];
+  if (c < 0) return;
+  atomicAdd(&cnt[(r == 0 ? 0 : nlist) + c], 1);
+}
+
+// Single CTA: exclusive scans of bucket sizes and of work items per list for
+// both phases.  items(c) = ceil(cnt / QB_phase) * nseg(c).
+__global__ void __launch_bounds__(1024) inv_scan_kernel(const int* __restrict__ cnt, int nlist,
+                                                        const int64_t* __restrict__ chunk_off,
+                                                        int qbA, int qbB, int* __restrict__ boff,
+                                                        int* __restrict__ ioff,
+                                                        int* __restrict__ totals) {
+  __shared__ int part_b[1024], part_i[1024];
+  for (int ph = 0; ph < 2; ++ph) {
+    const int* cn = cnt + ph * nlist;
+    const int qb = ph == 0 ? qbA : qbB;
+    int per = (nlist + 1023) / 1024;
+    int b0 = threadIdx.x * per, b1 = min(nlist, b0 + per);
+    int sb = 0, si = 0;
+    for (int c = b0; c < b1; ++c) {
+      int nch = (int)(chunk_off[c + 1] - chunk_off[c]);
+      int nseg = (nch + SEG_CHUNKS - 1) / SEG_CHUNKS;
+      sb += cn[c];
+      si += ((cn[c] + qb - 1) / qb) * nseg;
+    }
+    part_b[threadIdx.x] = sb;
+    part_i[threadIdx.x] = si;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int ab = 0, ai = 0;
+      for (int t = 0; t < 1024; ++t) {
+        int xb = part_b[t], xi = part_i[t];
+        part_b[t] = ab;
+        part_i[t] = ai;
+        ab += xb;
+        ai += xi;
+      }
+      totals[2 * ph] = ab;
+      totals[2 * ph + 1] = ai;
+    }
+    __syncthreads();
+    int ab = part_b[threadIdx.x], ai = part_i[threadIdx.x];
+    for (int c = b0; c < b1; ++c) {
+      int nch = (int)(chunk_off[c + 1] - chunk_off[c]);
+      int nseg = (nch + SEG_CHUNKS - 1) / SEG_CHUNKS;
+      boff[ph * (nlist + 1) + c] = ab;
+      ioff[ph * (nlist + 1) + c] = ai;
+      ab += cn[c];
+      ai += ((cn[c] + qb - 1) / qb) * nseg;
+    }
+    if (threadIdx.x == 1023) {
+      boff[ph * (nlist + 1) + nlist] = ab;
+      ioff[ph * (nlist + 1) + nlist] = ai;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void inv_scatter_kernel(int64_t nq, const int32_t* __restrict__ probes, int stride,
+                                   const int32_t* __restrict__ npq, const int* __restrict__ boff,
+                                   const int* __restrict__ totals, int* __restrict__ fill,
+                                   int nlist, int32_t* __restrict__ bucket) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nq * stride) return;
+  int64_t qi = e / stride;
+  int r = (int)(e % stride);
+  if (r >= npq[qi]) return;
+  int c = probes[e];
+  if (c < 0) return;
+  int ph = r == 0 ? 0 : 1;
+  int base = ph == 1 ? totals[0] : 0;  // phase-B buckets follow the phase-A ones
+  int pos = base + boff[ph * (nlist + 1) + c] + atomicAdd(&fill[ph * nlist + c], 1);
+  bucket[pos] = (int32_t)qi;
+}
+
+// Work item i of a phase -> (list, segment, bucket offset, group size).
+__global__ void inv_emit_kernel(int ph, const int* __restrict__ cnt, int nlist,
+                                const int64_t* __restrict__ chunk_off, int qb,
+                                const int* __restrict__ boff, const int* __restrict__ ioff,
+                                const int* __restrict__ totals, int64_t cap,
+                                int4* __restrict__ items, int* __restrict__ err) {
+  const int n_items = totals[2 * ph + 1];
+  const int* io = ioff + ph * (nlist + 1);
+  const int* bo = boff + ph * (nlist + 1);
+  if (n_items > cap && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, kErrOverflow);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < imin64(n_items, cap);
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nlist;  // largest c with io[c] <= i
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (io[mid] <= i) lo = mid;
+      else hi = mid;
+    }
+    int c = lo;
+    while (c + 1 < nlist && io[c + 1] <= i) ++c;  // skip empty lists
+    int local = (int)(i - io[c]);
+    int nch = (int)(chunk_off[c + 1] - chunk_off[c]);
+    int nseg = (nch + SEG_CHUNKS - 1) / SEG_CHUNKS;
+    int g = local / nseg, s = local % nseg;
+    int n_in = cnt[ph * nlist + c];
+    int base = (ph == 1 ? totals[0] : 0) + bo[c] + g * qb;
+    items[i] = make_int4(c, s, base, min(qb, n_in - g * qb));
+  }
+}
+
+// ------------------------------------------------------------ a4-a10 verify
+struct VerifyArgs {
+  const float* slices;
+  const float* tails;
+  const float* xn2;
+  const float* ex;
+  const int32_t* ids;
+  const float* rows;
+  const int64_t* chunk_off;
+  const float* qt;
+  const float* qorig;
+  const float4* qinfo;
+  const float* qtail;
+  const int32_t* kq;
+  const int4* items;
+  const int* n_items;  // device count
+  int* counter;
+  const int32_t* bucket;
+  unsigned long long* topk;
+  int* err;
+  unsigned long long* stats;  // 8 counters (see pano_search_stats order)
+  int64_t items_cap;
+  int d, L, max_w, k_max;
+  float gslack;    // slack factor: |computed - exact| <= gslack (|q~|+|x~|)^2
+  float lb_scale;  // (1 - 8u) / (1 + eta): lower bound in T~ space -> original
+  int prune;       // 0: plain scan (prune only after the last level)
+  int collect;
+  int32_t level_off[65];
+};
+
+struct Smem {
+  // sizes depend on (QB, CB, max_w, L); carved at run time
+  static size_t bytes(int QB, int CB, int max_w, int L) {
+    size_t s = 0;
+    s += (size_t)CB * max_w * 4;          // xs
+    s += (size_t)max_w * (QB + 4) * 4;    // qs
+    s += (size_t)CB * (L + 1) * 4;        // candidate tails
+    s += (size_t)QB * (L + 1) * 4;        // query tails
+    s += (size_t)CB * 4 * 4;              // xn2, rx, ex, ids
+    s += (size_t)QB * 6 * 4;              // qid, nq, rq, eq, tau, k
+    s += (size_t)QB * CB * 2;             // survivors
+    return s + 64;
+  }
+};
+
+template <int QB, int CB>
+__global__ void __launch_bounds__(NT) verify_fp32_kernel(const VerifyArgs a) {
+  constexpr int NCH = CB / CH;
+  constexpr int TQ = QB / 4;
+  static_assert(TQ * (CB / 4) == NT, "4x4 register tile per thread");
+  static_assert(TQ <= 32 && (32 % TQ) == 0, "query blocks of a candidate block share a warp");
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int L = a.L, d = a.d, max_w = a.max_w;
+  float* xs = reinterpret_cast<float*>(smem);               // [NCH][max_w][CH]
+  float* qs = xs + (size_t)CB * max_w;                       // [max_w][QB+4]
+  float* ctl = qs + (size_t)max_w * (QB + 4);               // [NCH][L+1][CH]
+  float* qtl = ctl + (size_t)CB * (L + 1);                   // [QB][L+1]
+  float* xn2s = qtl + (size_t)QB * (L + 1);                  // [CB]
+  float* rxs = xn2s + CB;
+  float* exs = rxs + CB;
+  int32_t* ids_s = reinterpret_cast<int32_t*>(exs + CB);
+  int32_t* qid = ids_s + CB;                                 // [QB]
+  float* qnq = reinterpret_cast<float*>(qid + QB);
+  float* qrq = qnq + QB;
+  float* qeq = qrq + QB;
+  float* qtau = qeq + QB;
+  int32_t* qk = reinterpret_cast<int32_t*>(qtau + QB);
+  uint16_t* surv = reinterpret_cast<uint16_t*>(qk + QB);    // [QB*CB]
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_item, s_nsurv;
+  __shared__ int chunk_live[NCH];
+
+  const int tid = threadIdx.x;
+  const int tq = tid % TQ, tc = tid / TQ;
+  const int warp = tid / 32, lane = tid & 31;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  if (tid < NCH) chunk_live[tid] = 0;
+  if (tid == 0) s_nsurv = 0;
+  __syncthreads();
+  uint32_t phase = 0;
+  unsigned long long st_pair_levels = 0, st_dims = 0, st_tile_levels = 0, st_bytes = 0,
+                     st_rerank = 0;
+  bool failed = false;
+
+  while (true) {
+    if (tid == 0) s_item = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    const int n_items = (int)imin64(*a.n_items, a.items_cap);
+    if (item >= n_items || failed) break;
+    const int4 it = a.items[item];
+    const int64_t ch0 = a.chunk_off[it.x] + (int64_t)it.y * SEG_CHUNKS;
+    const int64_t ch1 = imin64(a.chunk_off[it.x + 1], ch0 + SEG_CHUNKS);
+    const int G = it.w;
+    for (int g = tid; g < QB; g += NT) {
+      if (g < G) {
+        int q = a.bucket[it.z + g];
+        qid[g] = q;
+        float4 inf = a.qinfo[q];
+        qnq[g] = inf.x;
+        qrq[g] = inf.y;
+        qeq[g] = inf.z;
+        qk[g] = a.kq[q];
+      } else {
+        qid[g] = -1;
+        qnq[g] = qrq[g] = qeq[g] = 0.f;
+        qk[g] = 0;
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < QB * (L + 1); e += NT) {
+      int g = e / (L + 1), l = e % (L + 1);
+      qtl[e] = g < G ? a.qtail[(int64_t)qid[g] * (L + 1) + l] : 0.f;
+    }
+
+    for (int64_t tile = ch0; tile < ch1; tile += NCH) {
+      const int nch = (int)imin64(NCH, ch1 - tile);
+      // running threshold: k-th key of the query's top-k (rounded up)
+      for (int g = tid; g < QB; g += NT) {
+        float tau = -1.f;  // k == 0: nothing can enter
+        if (g < G && qk[g] > 0) {
+          unsigned long long kk = ld_volatile_u64(a.topk + (int64_t)qid[g] * a.k_max + qk[g] - 1);
+          tau = kk == kEmptyKey ? INFINITY : __fmul_ru(key_dist(kk), 1.000001f);
+        }
+        qtau[g] = tau;
+      }
+      for (int e = tid; e < CB; e += NT) {
+        int ch = e / CH, i = e % CH;
+        if (ch < nch) {
+          int64_t slot = (tile + ch) * CH + i;
+          float nx = a.xn2[slot];
+          xn2s[e] = nx;
+          rxs[e] = sqrtf(nx);
+          exs[e] = a.ex[slot];
+          ids_s[e] = a.ids[slot];
+        } else {
+          xn2s[e] = rxs[e] = exs[e] = 0.f;
+          ids_s[e] = -1;
+        }
+      }
+      for (int e = tid; e < nch * (L + 1) * CH; e += NT) {
+        int ch = e / ((L + 1) * CH);
+        int r = e % ((L + 1) * CH);
+        ctl[e] = a.tails[(tile + ch) * (L + 1) * CH + r];
+      }
+      __syncthreads();
+
+      uint32_t alive = 0;  // bit 4*ai + bi: pair (query 4tq+ai, cand 4tc+bi)
+#pragma unroll
+      for (int ai = 0; ai < 4; ++ai)
+#pragma unroll
+        for (int bi = 0; bi < 4; ++bi) {
+          int g = 4 * tq + ai, e = 4 * tc + bi;
+          if (g < G && qk[g] > 0 && ids_s[e] >= 0) alive |= 1u << (4 * ai + bi);
+        }
+      float p[4][4];
+#pragma unroll
+      for (int ai = 0; ai < 4; ++ai)
+#pragma unroll
+        for (int bi = 0; bi < 4; ++bi) p[ai][bi] = 0.f;
+      const int my_ch = (4 * tc) / CH, my_i = (4 * tc) % CH;
+      bool completed = true;
+
+      for (int l = 0; l < L; ++l) {
+        // candidate-level liveness (any query of the group) -> live chunks
+        uint32_t cm = alive;
+#pragma unroll
+        for (int off = 1; off < TQ; off <<= 1) cm |= __shfl_xor_sync(0xffffffffu, cm, off);
+        if (tq == 0 && cm) chunk_live[my_ch] = 1;
+        const int any = __syncthreads_or(alive != 0);
+        if (!any) {
+          completed = false;
+          break;
+        }
+        const int m = a.level_off[l], w = a.level_off[l + 1] - m;
+        if (tid == 0) {
+          uint32_t bytes = 0;
+          for (int c = 0; c < nch; ++c)
+            if (chunk_live[c]) bytes += (uint32_t)w * CH * 4;
+          mbar_arrive_expect_tx(&bar, bytes);
+          for (int c = 0; c < nch; ++c)
+            if (chunk_live[c])
+              bulk_g2s(xs + (size_t)c * max_w * CH, a.slices + ((tile + c) * d + m) * CH,
+                       (uint32_t)w * CH * 4, &bar);
+          st_bytes += bytes;
+          st_tile_levels += 1;
+        }
+        for (int e = tid; e < QB * w; e += NT) {
+          int g = e / w, j = e % w;
+          qs[j * (QB + 4) + g] = g < G ? a.qt[(int64_t)qid[g] * d + m + j] : 0.f;
+        }
+        __syncthreads();
+        if (tid < NCH) chunk_live[tid] = 0;  // read by thread 0 above
+        if (!mbar_wait_bounded(&bar, phase)) {
+          if (tid == 0) atomicOr(a.err, kErrTimeout);
+          failed = true;
+        }
+        phase ^= 1;
+        if (__syncthreads_or(failed)) {
+          failed = true;
+          completed = false;
+          break;
+        }
+        if (cm != 0) {
+          float acc[4][4];
+#pragma unroll
+          for (int ai = 0; ai < 4; ++ai)
+#pragma unroll
+            for (int bi = 0; bi < 4; ++bi) acc[ai][bi] = 0.f;
+          const float* xb = xs + (size_t)my_ch * max_w * CH + my_i;
+          const float* qb = qs + 4 * tq;
+#pragma unroll 4
+          for (int j = 0; j < w; ++j) {
+            float4 qa = *reinterpret_cast<const float4*>(qb + j * (QB + 4));
+            float4 xv = *reinterpret_cast<const float4*>(xb + j * CH);
+            float qv[4] = {qa.x, qa.y, qa.z, qa.w};
+            float xx[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+            for (int ai = 0; ai < 4; ++ai)
+#pragma unroll
+              for (int bi = 0; bi < 4; ++bi) acc[ai][bi] = fmaf(qv[ai], xx[bi], acc[ai][bi]);
+          }
+#pragma unroll
+          for (int ai = 0; ai < 4; ++ai)
+#pragma unroll
+            for (int bi = 0; bi < 4; ++bi) p[ai][bi] += acc[ai][bi];
+          if (a.collect) {
+            st_pair_levels += __popc(alive);
+            st_dims += (unsigned long long)__popc(alive) * w;
+          }
+          // bound update and pruning (Eq. 3 with rounding margins)
+          const bool test = a.prune || (l == L - 1);
+          if (test) {
+#pragma unroll
+            for (int ai = 0; ai < 4; ++ai) {
+              const int g = 4 * tq + ai;
+              const float nq = qnq[g], rq = qrq[g], eq = qeq[g], tau = qtau[g];
+              const float sq = qtl[g * (L + 1) + l + 1];
+#pragma unroll
+              for (int bi = 0; bi < 4; ++bi) {
+                const uint32_t bit = 1u << (4 * ai + bi);
+                if (!(alive & bit)) continue;
+                const int e = 4 * tc + bi;
+                const float nx = xn2s[e], rx = rxs[e];
+                const float sx = ctl[((size_t)my_ch * (L + 1) + l + 1) * CH + my_i + bi];
+                const float A = nq + nx - 2.f * p[ai][bi];
+                const float C = sq * sx;
+                const float S = rq + rx;
+                const float lbs = A - 2.f * C - a.gslack * S * S;
+                const float r = sqrtf(fmaxf(lbs, 0.f)) - (eq + exs[e]);
+                const float LB = r > 0.f ? r * r * a.lb_scale : 0.f;
+                if (LB > tau) alive &= ~bit;
+              }
+            }
+          }
+        }
+        __syncthreads();  // xs / qs are overwritten by the next level
+      }
+      // survivors of all L levels: exact re-rank and top-k insertion
+      if (completed && alive) {
+#pragma unroll
+        for (int ai = 0; ai < 4; ++ai)
+#pragma unroll
+          for (int bi = 0; bi < 4; ++bi)
+            if (alive & (1u << (4 * ai + bi))) {
+              int pos = atomicAdd(&s_nsurv, 1);
+              surv[pos] = (uint16_t)(((4 * tq + ai) << 8) | (4 * tc + bi));
+            }
+      }
+      __syncthreads();
+      const int ns = s_nsurv;
+      for (int s = warp; s < ns; s += NT / 32) {
+        const int g = surv[s] >> 8, e = surv[s] & 255;
+        const int q = qid[g];
+        const int64_t slot = (tile + e / CH) * CH + (e % CH);
+        float dist = exact_sqdist_warp(a.qorig + (int64_t)q * d, a.rows + slot * d, d);
+        if (lane == 0) topk_insert(a.topk + (int64_t)q * a.k_max, qk[g], make_key(dist, ids_s[e]));
+      }
+      st_rerank += (tid == 0) ? ns : 0;
+      __syncthreads();
+      if (tid == 0) s_nsurv = 0;
+    }
+    __syncthreads();
+  }
+  if (a.collect) {
+    unsigned long long v = st_pair_levels;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) atomicAdd(&a.stats[0], v);
+    unsigned long long dv = st_dims;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) dv += __shfl_xor_sync(0xffffffffu, dv, off);
+    if (lane == 0) atomicAdd(&a.stats[5], dv);
+    if (tid == 0) {
+      atomicAdd(&a.stats[1], st_tile_levels);
+      atomicAdd(&a.stats[2], st_bytes);
+      atomicAdd(&a.stats[3], st_rerank);
+    }
+  }
+}
+
+__global__ void decode_kernel(int64_t nq, int k_max, const int32_t* __restrict__ kq,
+                              const unsigned long long* __restrict__ topk,
+                              int64_t* __restrict__ out_ids, float* __restrict__ out_d) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nq * k_max) return;
+  int64_t qi = e / k_max;
+  int j = (int)(e % k_max);
+  unsigned long long key = j < kq[qi] ? topk[e] : kEmptyKey;
+  if (key == kEmptyKey) {
+    out_ids[e] = -1;
+    out_d[e] = INFINITY;
+  } else {
+    out_ids[e] = key_id(key);
+    out_d[e] = key_dist(key);
+  }
+}
+
+// Pairs in all candidate sets (stats): sum over (q, r < nprobe_q) of list sizes.
+__global__ void pair_count_kernel(int64_t nq, const int32_t* __restrict__ probes, int stride,
+                                  const int32_t* __restrict__ npq, const int32_t* __restrict__ lsz,
+                                  unsigned long long* __restrict__ out) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long v = 0;
+  if (e < nq * stride) {
+    int64_t qi = e / stride;
+    int r = (int)(e % stride);
+    if (r < npq[qi] && probes[e] >= 0) v = lsz[probes[e]];
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+}
+
+// Lets `kern` use all the dynamic shared memory the device allows next to its
+// static shared memory.
+cudaError_t allow_dynamic_smem(const void* kern) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes);
+}
+
+template <int QB, int CB>
+int launch_verify(const VerifyArgs& a, size_t smem, cudaStream_t st) {
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  auto kern = verify_fp32_kernel<QB, CB>;
+  std::call_once(once, [&] { attr_err = allow_dynamic_smem((const void*)kern); });
+  PANO_CUDA(attr_err);
+  int bps = 0;
+  PANO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, NT, smem));
+  if (bps < 1) return fail(PANO_EINVAL, "verify tile does not fit in shared memory");
+  int dev = 0, sms = 0;
+  PANO_CUDA(cudaGetDevice(&dev));
+  PANO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  kern<<<sms * bps, NT, smem, st>>>(a);
+  PANO_CUDA(cudaGetLastError());
+  return PANO_OK;
+}
+
+// Carves one stream-ordered allocation into aligned pieces.
+struct Carver {
+  size_t off = 0;
+  template <class T>
+  size_t take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    size_t at = off;
+    off += count * sizeof(T);
+    return at;
+  }
+};
+
+thread_local pano_search_stats t_stats;
+
+}  // namespace
+
+int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t* nprobe,
+           int32_t nprobe_scalar, const int32_t* k, int32_t k_scalar, int32_t k_max,
+           int64_t* out_ids, float* out_dists, cudaStream_t st, const pano_search_opts* opts) {
+  PANO_CHECK(ip, PANO_EINVAL, "null index");
+  const pano_index& I = *ip;
+  PANO_CHECK(nq >= 0 && nq < (1LL << 31), PANO_EINVAL, "nq out of range");
+  PANO_CHECK(nq == 0 || (queries && out_ids && out_dists), PANO_EINVAL, "null argument");
+  PANO_CHECK(k_max >= 1 && k_max <= 1024, PANO_EINVAL, "k_max must be in [1, 1024]");
+  if (!nprobe)
+    PANO_CHECK(nprobe_scalar >= 1 && nprobe_scalar <= I.nlist, PANO_EINVAL,
+               "nprobe must be in [1, nlist]");
+  if (!k) PANO_CHECK(k_scalar >= 0 && k_scalar <= k_max, PANO_EINVAL, "k must be in [0, k_max]");
+  const int mode = opts ? opts->mode : 0;
+  const bool timing = opts ? opts->collect_timing != 0 : false;
+  const bool sync = (opts ? opts->synchronize != 0 : true) || timing;
+  const bool collect = opts ? opts->collect_stats != 0 : false;
+  std::memset(&t_stats, 0, sizeof(t_stats));
+  t_stats.n_queries = nq;
+  if (nq == 0) return PANO_OK;
+  int cur = 0;
+  PANO_CUDA(cudaGetDevice(&cur));
+  PANO_CHECK(cur == I.device, PANO_EINVAL, "current device differs from the index's device");
+
+  const int d = I.d, L = I.L, nlist = I.nlist;
+  const int np_cap = nprobe ? ((nprobe_scalar >= 1) ? std::min(nprobe_scalar, nlist) : nlist)
+                            : nprobe_scalar;
+  const int stride = np_cap;
+  constexpr int QBA = 16, CBA = 256, QBB = 64, CBB = 64;
+  // work-item capacity: groups x segments, plus one partial group per list
+  int64_t max_seg = 1, tot_seg = 0;
+  for (int c = 0; c < nlist; ++c) {
+    int64_t nch = I.list_chunk_off[c + 1] - I.list_chunk_off[c];
+    int64_t s = (nch + SEG_CHUNKS - 1) / SEG_CHUNKS;
+    max_seg = std::max(max_seg, s);
+    tot_seg += s;
+  }
+  const int64_t capA = ((nq + QBA - 1) / QBA) * max_seg + tot_seg;
+  const int64_t capB = ((nq * std::max(0, stride - 1) + QBB - 1) / QBB) * max_seg + tot_seg;
+
+  Carver cv;
+  size_t o_qt = cv.take<float>((size_t)nq * d);
+  size_t o_qinfo = cv.take<float4>(nq);
+  size_t o_qtail = cv.take<float>((size_t)nq * (L + 1));
+  size_t o_qn2 = cv.take<float>(nq);
+  size_t o_pd = nlist > 1 ? cv.take<float>((size_t)nq * nlist) : 0;
+  size_t o_pr = cv.take<int32_t>((size_t)nq * stride);
+  size_t o_npq = cv.take<int32_t>(nq);
+  size_t o_kq = cv.take<int32_t>(nq);
+  size_t o_cnt = cv.take<int>(2 * (size_t)nlist);
+  size_t o_fill = cv.take<int>(2 * (size_t)nlist);
+  size_t o_boff = cv.take<int>(2 * (size_t)(nlist + 1));
+  size_t o_ioff = cv.take<int>(2 * (size_t)(nlist + 1));
+  size_t o_tot = cv.take<int>(8);
+  size_t o_bucket = cv.take<int32_t>((size_t)nq * stride);
+  size_t o_itA = cv.take<int4>(capA);
+  size_t o_itB = cv.take<int4>(std::max<int64_t>(capB, 1));
+  size_t o_topk = cv.take<unsigned long long>((size_t)nq * k_max);
+  size_t o_err = cv.take<int>(4);
+  size_t o_stats = cv.take<unsigned long long>(8);
+  void* ws = nullptr;
+  PANO_CUDA(cudaMallocAsync(&ws, cv.off, st));
+  char* W = static_cast<char*>(ws);
+  auto P = [&](size_t o) { return (void*)(W + o); };
+  float* qt = (float*)P(o_qt);
+  float4* qinfo = (float4*)P(o_qinfo);
+  float* qtail = (float*)P(o_qtail);
+  float* qn2 = (float*)P(o_qn2);
+  int32_t* probes = (int32_t*)P(o_pr);
+  int32_t* npq = (int32_t*)P(o_npq);
+  int32_t* kq = (int32_t*)P(o_kq);
+  int* cnt = (int*)P(o_cnt);
+  int* fillc = (int*)P(o_fill);
+  int* boff = (int*)P(o_boff);
+  int* ioff = (int*)P(o_ioff);
+  int* tot = (int*)P(o_tot);
+  int32_t* bucket = (int32_t*)P(o_bucket);
+  int4* itA = (int4*)P(o_itA);
+  int4* itB = (int4*)P(o_itB);
+  unsigned long long* topk = (unsigned long long*)P(o_topk);
+  int* err = (int*)P(o_err);
+  unsigned long long* stats = (unsigned long long*)P(o_stats);
+  int rc = PANO_OK;
+  cudaEvent_t ev[7] = {};
+  if (timing)
+    for (auto& e : ev) PANO_CUDA(cudaEventCreate(&e));
+  auto mark = [&](int i) {
+    if (timing) cudaEventRecord(ev[i], st);
+  };
+  auto body = [&]() -> int {
+    PANO_CUDA(cudaMemsetAsync(cnt, 0, 2 * (size_t)nlist * 4, st));
+    PANO_CUDA(cudaMemsetAsync(fillc, 0, 2 * (size_t)nlist * 4, st));
+    PANO_CUDA(cudaMemsetAsync(tot, 0, 8 * 4, st));  // [4..5] verify counters
+    PANO_CUDA(cudaMemsetAsync(topk, 0xff, (size_t)nq * k_max * 8, st));
+    PANO_CUDA(cudaMemsetAsync(err, 0, 16, st));
+    PANO_CUDA(cudaMemsetAsync(stats, 0, 64, st));
+    prep_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(nq, nprobe, nprobe_scalar, np_cap, k,
+                                                              k_scalar, k_max, npq, kq, err);
+    PANO_CUDA(cudaGetLastError());
+    // a1
+    mark(0);
+    PANO_CUDA(gemm_nt(kStore, (int)nq, d, d, queries, d, I.mu32.as<float>(), I.T32.as<float>(), d,
+                      qt, d, nullptr, nullptr, st));
+    query_norms_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(
+        queries, qt, nq, d, L, I.level_off_d.as<int32_t>(), I.mu32.as<float>(), I.c_trans, qinfo,
+        qtail, qn2);
+    PANO_CUDA(cudaGetLastError());
+    // a2
+    mark(1);
+    if (nlist > 1) {
+      float* pd = (float*)P(o_pd);
+      PANO_CUDA(gemm_nt(kDist, (int)nq, nlist, d, queries, d, nullptr, I.cent.as<float>(), d, pd,
+                        nlist, qn2, I.cent_n2.as<float>(), st));
+      const float cmax = I.cmax;
+      size_t psm = (size_t)nlist * 4;
+      PANO_CUDA(allow_dynamic_smem((const void*)probe_select_kernel));
+      float gerr = (float)(2.0 * gamma_n(gemm_rounds(d) + 4));
+      probe_select_kernel<<<(unsigned)nq, NT, psm, st>>>(pd, nlist, queries, I.cent.as<float>(), d,
+                                                         qn2, cmax, gerr, npq, stride, probes, err);
+      PANO_CUDA(cudaGetLastError());
+    } else {
+      PANO_CUDA(cudaMemsetAsync(probes, 0, (size_t)nq * stride * 4, st));
+    }
+    // a3
+    mark(2);
+    const int64_t ne = nq * stride;
+    inv_count_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(nq, probes, stride, npq, cnt,
+                                                                   nlist);
+    inv_scan_kernel<<<1, 1024, 0, st>>>(cnt, nlist, I.chunk_off_d.as<int64_t>(), QBA, QBB, boff,
+                                        ioff, tot);
+    inv_scatter_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(nq, probes, stride, npq, boff,
+                                                                     tot, fillc, nlist, bucket);
+    PANO_CUDA(cudaGetLastError());
+    inv_emit_kernel<<<1024, 256, 0, st>>>(0, cnt, nlist, I.chunk_off_d.as<int64_t>(), QBA, boff,
+                                          ioff, tot, capA, itA, err);
+    inv_emit_kernel<<<1024, 256, 0, st>>>(1, cnt, nlist, I.chunk_off_d.as<int64_t>(), QBB, boff,
+                                          ioff, tot, capB, itB, err);
+    PANO_CUDA(cudaGetLastError());
+    // a4-a10
+    VerifyArgs va;
+    std::memset(&va, 0, sizeof(va));
+    va.slices = I.slices.as<float>();
+    va.tails = I.tails.as<float>();
+    va.xn2 = I.xn2.as<float>();
+    va.ex = I.ex.as<float>();
+    va.ids = I.ids.as<int32_t>();
+    va.rows = I.rows.as<float>();
+    va.chunk_off = I.chunk_off_d.as<int64_t>();
+    va.qt = qt;
+    va.qorig = queries;
+    va.qinfo = qinfo;
+    va.qtail = qtail;
+    va.kq = kq;
+    va.topk = topk;
+    va.err = err;
+    va.stats = stats;
+    va.d = d;
+    va.L = L;
+    va.max_w = I.max_w;
+    va.k_max = k_max;
+    va.gslack = (float)(2.0 * gamma_n(I.max_w + L + 8));
+    va.lb_scale = (float)((1.0 - 8.0 * kU32) / (1.0 + I.eta));
+    va.prune = mode == 0 ? 1 : 0;
+    va.collect = collect ? 1 : 0;
+    for (int l = 0; l <= L; ++l) va.level_off[l] = I.offs[l];
+    va.bucket = bucket;
+    // phase A
+    mark(3);
+    va.items = itA;
+    va.n_items = tot + 1;
+    va.counter = tot + 4;
+    va.items_cap = capA;
+    int r = launch_verify<QBA, CBA>(va, Smem::bytes(QBA, CBA, I.max_w, L), st);
+    if (r) return r;
+    // phase B
+    mark(4);
+    va.items = itB;
+    va.n_items = tot + 3;
+    va.counter = tot + 5;
+    va.items_cap = capB;
+    r = launch_verify<QBB, CBB>(va, Smem::bytes(QBB, CBB, I.max_w, L), st);
+    if (r) return r;
+    mark(5);
+    const int64_t no = nq * k_max;
+    decode_kernel<<<(unsigned)((no + 255) / 256), 256, 0, st>>>(nq, k_max, kq, topk, out_ids,
+                                                                out_dists);
+    PANO_CUDA(cudaGetLastError());
+    mark(6);
+    if (collect) {
+      pair_count_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+          nq, probes, stride, npq, I.list_size_d.as<int32_t>(), stats + 4);
+      PANO_CUDA(cudaGetLastError());
+    }
+    if (sync || collect) {
+      int herr[4];
+      unsigned long long hst[8];
+      int htot[8];
+      PANO_CUDA(cudaMemcpyAsync(herr, err, 16, cudaMemcpyDeviceToHost, st));
+      PANO_CUDA(cudaMemcpyAsync(hst, stats, 64, cudaMemcpyDeviceToHost, st));
+      PANO_CUDA(cudaMemcpyAsync(htot, tot, 32, cudaMemcpyDeviceToHost, st));
+      PANO_CUDA(cudaStreamSynchronize(st));
+      t_stats.pair_levels = (int64_t)hst[0];
+      t_stats.tile_levels = (int64_t)hst[1];
+      t_stats.slice_bytes = (int64_t)hst[2];
+      t_stats.reranked = (int64_t)hst[3];
+      t_stats.pairs = (int64_t)hst[4];
+      t_stats.work_items = (int64_t)htot[1] + htot[3];
+      t_stats.device_error = herr[0];
+      t_stats.dims_scanned = (int64_t)hst[5];
+      if (timing)
+        for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&t_stats.stage_ms[i], ev[i], ev[i + 1]);
+      if (herr[0] & kErrTimeout) return fail(PANO_ETIMEOUT, "a device-side wait timed out");
+    }
+    return PANO_OK;
+  };
+  rc = body();
+  if (timing)
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  cudaError_t fe = cudaFreeAsync(ws, st);
+  if (rc == PANO_OK && fe != cudaSuccess) return cuda_fail(fe, "cudaFreeAsync");
+  return rc;
+}
+
+int probe_only(const pano_index* ip, const float* queries, int64_t nq, int32_t nprobe,
+               int32_t* out, cudaStream_t st) {
+  PANO_CHECK(ip, PANO_EINVAL, "null index");
+  const pano_index& I = *ip;
+  PANO_CHECK(nprobe >= 1 && nprobe <= I.nlist, PANO_EINVAL, "nprobe must be in [1, nlist]");
+  PANO_CHECK(nq >= 0 && nq < (1LL << 31), PANO_EINVAL, "nq out of range");
+  PANO_CHECK(nq == 0 || (queries && out), PANO_EINVAL, "null argument");
+  if (nq == 0) return PANO_OK;
+  const int d = I.d, nlist = I.nlist;
+  if (nlist == 1) {
+    PANO_CUDA(cudaMemsetAsync(out, 0, nq * 4, st));
+    return PANO_OK;
+  }
+  Carver cv;
+  size_t o_pd = cv.take<float>((size_t)nq * nlist);
+  size_t o_qn = cv.take<float>(nq);
+  size_t o_np = cv.take<int32_t>(2 * nq);
+  size_t o_err = cv.take<int>(4);
+  void* ws = nullptr;
+  PANO_CUDA(cudaMallocAsync(&ws, cv.off, st));
+  char* W = (char*)ws;
+  float* pd = (float*)(W + o_pd);
+  float* qn2 = (float*)(W + o_qn);
+  int32_t* npq = (int32_t*)(W + o_np);
+  int* err = (int*)(W + o_err);
+  auto body = [&]() -> int {
+    PANO_CUDA(cudaMemsetAsync(err, 0, 16, st));
+    prep_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(nq, nullptr, nprobe, nlist, nullptr,
+                                                              0, 1, npq, npq + nq, err);
+    row_sqnorm_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(queries, nq, d, qn2);
+    PANO_CUDA(gemm_nt(kDist, (int)nq, nlist, d, queries, d, nullptr, I.cent.as<float>(), d, pd,
+                      nlist, qn2, I.cent_n2.as<float>(), st));
+    size_t psm = (size_t)nlist * 4;
+    PANO_CUDA(allow_dynamic_smem((const void*)probe_select_kernel));
+    float gerr = (float)(2.0 * gamma_n(gemm_rounds(d) + 4));
+    probe_select_kernel<<<(unsigned)nq, NT, psm, st>>>(pd, nlist, queries, I.cent.as<float>(), d,
+                                                       qn2, I.cmax, gerr, npq, nprobe, out, err);
+    PANO_CUDA(cudaGetLastError());
+    PANO_CUDA(cudaStreamSynchronize(st));
+    return PANO_OK;
+  };
+  int rc = body();
+  cudaFreeAsync(ws, st);
+  return rc;
+}
+
+const pano_search_stats& last_stats() { return t_stats; }
+
+}  // namespace pano

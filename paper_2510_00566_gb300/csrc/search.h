@@ -1,0 +1,19 @@
+// Host entry points of the search path (see search.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace pano {
+int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t* nprobe,
+           int32_t nprobe_scalar, const int32_t* k, int32_t k_scalar, int32_t k_max,
+           int64_t* out_ids, float* out_dists, cudaStream_t st, const pano_search_opts* opts);
+int probe_only(const pano_index* ip, const float* queries, int64_t nq, int32_t nprobe,
+               int32_t* out, cudaStream_t st);
+const pano_search_stats& last_stats();
+int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
+              const pano_build_opts* o, cudaStream_t st, pano_index** out);
+int make_levels(int d, const pano_build_opts* o, std::vector<int32_t>& widths,
+                std::vector<int32_t>& offs);
+int check_device(int* dev_out);
+}  // namespace pano

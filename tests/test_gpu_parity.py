@@ -1,0 +1,230 @@
+"""GPU parity: the library's search through the C-ABI against the CPU oracle
+on the same seeded inputs (sizes that span many chunks and end in ragged
+tails).  Tolerances: ids equal except at FP64 near-ties (< 1e-6 relative);
+distances within 1e-5 relative of FP64 (the stated bar)."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2510_00566_gb300 as pano
+import synth
+from parity import check_topk, gamma_of
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_00566_gb300 import _build
+    _build.build()
+    pano.lib()
+
+
+DEV = "cuda:0"
+
+
+def _flat_case(n, nq, d_cfg=1, n_levels=8, seed_cfg=None, **kw):
+    s = synth.scaled(d_cfg, n=n, n_queries=nq, nlist=1, n_clusters=0, **kw)
+    w = synth.generate(s)
+    return s, w.X.numpy(), w.Q.numpy()
+
+
+def _oracle_flat(X, Q, k):
+    return oracle.ivf_search(X, Q, np.zeros((1, X.shape[1])), 1, k,
+                             lists_of_vector=np.zeros(len(X), dtype=np.int64))
+
+
+# ------------------------------------------------------------- flat (cfg 1)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_flat_128d_workload_matches_oracle(mode):
+    """The 128-d workload at full size: N = 20,000, 100 queries, PCA, 8 x 16
+    levels, k = 10, exhaustive (one list)."""
+    s, X, Q = _flat_case(20_000, 100)
+    t = pano.panorama_fit_transform(X, n_levels=8)
+    idx = pano.panorama_build_ivf(t, torch.from_numpy(X).to(DEV), nlist=1)
+    ids, d = idx.search(torch.from_numpy(Q).to(DEV), 1, 10, mode=mode,
+                        collect_stats=True)
+    st = pano.last_stats()
+    ref = _oracle_flat(X, Q, 10)
+    worst, swaps = check_topk(X, Q, ids.cpu().numpy(), d.cpu().numpy(),
+                              ref["ids"], ref["dists"], 10)
+    assert st.pairs == 20_000 * 100
+    if mode == 0:
+        # pruning reads a fraction of the levels (Table 2: ~1/alpha)
+        assert st.pair_levels < 0.6 * st.pairs * 8
+    else:
+        assert st.pair_levels == st.pairs * 8
+
+
+def test_flat_ragged_tail_identity_transform_and_k_edges():
+    """n not a multiple of the 64-vector chunk, raw axes (T = I), k = 1, a
+    k larger than the candidate set, and k = 0 rows."""
+    s, X, Q = _flat_case(512 + 37, 20)
+    t = pano.panorama_fit_transform(X, identity=True)
+    idx = pano.panorama_build_ivf(t, torch.from_numpy(X).to(DEV), nlist=1,
+                                  n_levels=8)
+    q = torch.from_numpy(Q).to(DEV)
+    for k in (1, 10):
+        ids, d = idx.search(q, 1, k)
+        ref = _oracle_flat(X, Q, k)
+        check_topk(X, Q, ids.cpu().numpy(), d.cpu().numpy(), ref["ids"],
+                   ref["dists"], k)
+    kk = torch.tensor([0, 5, 600, 3] * 5, dtype=torch.int32, device=DEV)
+    ids, d = idx.search(q, 1, kk, k_max=600)
+    ref = _oracle_flat(X, Q, 600)
+    ids, d = ids.cpu().numpy(), d.cpu().numpy()
+    for i in range(len(Q)):
+        ki = int(kk[i])
+        if ki == 0:
+            assert np.all(ids[i] == -1) and np.all(np.isinf(d[i]))
+            continue
+        check_topk(X, Q[i:i + 1], ids[i:i + 1], d[i:i + 1],
+                   ref["ids"][i:i + 1], ref["dists"][i:i + 1], ki)
+    # k = 600 > n = 549: the last 51 columns are padding
+    assert np.all(ids[2, 549:] == -1) and np.all(ids[2, :549] >= 0)
+
+
+def test_single_level_and_uneven_widths():
+    """L = 1 (no early pruning: a brute-force scan) and uneven level widths
+    summing to d."""
+    s, X, Q = _flat_case(3_000, 16)
+    q = torch.from_numpy(Q).to(DEV)
+    ref = _oracle_flat(X, Q, 10)
+    t = pano.panorama_fit_transform(X)
+    for widths in ([128], [8, 24, 32, 64], [4] * 4 + [16] * 6 + [16]):
+        idx = pano.panorama_build_ivf(t, torch.from_numpy(X).to(DEV), nlist=1,
+                                      level_widths=widths)
+        ids, d = idx.search(q, 1, 10)
+        check_topk(X, Q, ids.cpu().numpy(), d.cpu().numpy(), ref["ids"],
+                   ref["dists"], 10)
+
+
+# --------------------------------------------------------------- IVF (cfg 2)
+def _ivf_case(n=40_000, nq=120, nlist=64, d_cfg=2, **kw):
+    s = synth.scaled(d_cfg, n=n, n_queries=nq, nlist=nlist,
+                     n_clusters=nlist, **kw)
+    w = synth.generate(s)
+    return s, w
+
+
+@pytest.fixture(scope="module")
+def ivf960():
+    """960-d mixture (the 1M-vector workload's recipe at 40k vectors), fixed
+    centroids handed to both sides, 16 x 60 levels."""
+    s, w = _ivf_case()
+    X, Q = w.X.numpy(), w.Q.numpy()
+    C = synth.initial_centroids(w.X, 64, seed=3002).numpy()
+    t = pano.panorama_fit_transform(X, n_levels=16)
+    idx = pano.panorama_build_ivf(t, w.X.to(DEV), nlist=64, n_levels=16,
+                                  centroids=C)
+    return s, X, Q, C, t, idx
+
+
+def test_ivf_assignment_matches_oracle(ivf960):
+    s, X, Q, C, t, idx = ivf960
+    lists, gap = oracle.assign(X, C)
+    got = idx.assignment()
+    diff = got != lists
+    assert np.all(gap[diff] < 1e-6), "assignment differs beyond a near-tie"
+    np.testing.assert_array_equal(idx.centroids(), C)
+
+
+def test_ivf_probe_matches_oracle(ivf960):
+    s, X, Q, C, t, idx = ivf960
+    got = pano.panorama_probe(idx, torch.from_numpy(Q).to(DEV), 8).cpu().numpy()
+    probes, gap = oracle.probe(Q, C, 8)
+    for i in range(len(Q)):
+        if gap[i] < 1e-6:  # a near-tie at the nprobe boundary
+            continue
+        assert got[i].tolist() == probes[i].tolist(), i
+
+
+@pytest.mark.parametrize("nprobe", [1, 8, 64])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_ivf_search_matches_oracle(ivf960, nprobe, mode):
+    s, X, Q, C, t, idx = ivf960
+    ids, d = idx.search(torch.from_numpy(Q).to(DEV), nprobe, 10, mode=mode)
+    lists, _ = oracle.assign(X, C)
+    ref = oracle.ivf_search(X, Q, C, nprobe, 10, lists_of_vector=lists)
+    keep = ref["probe_gap"] >= 1e-6
+    G = gamma_of(lists, ref["probes"])
+    check_topk(X, Q[keep], ids.cpu().numpy()[keep], d.cpu().numpy()[keep],
+               ref["ids"][keep], ref["dists"][keep], 10,
+               gamma_rows=[G[i] for i in np.nonzero(keep)[0]])
+
+
+def test_ivf_per_query_nprobe_and_k(ivf960):
+    s, X, Q, C, t, idx = ivf960
+    g = np.random.default_rng(5)
+    npq = g.integers(1, 17, size=len(Q)).astype(np.int32)
+    kq = g.choice([1, 10, 100], size=len(Q)).astype(np.int32)
+    ids, d = idx.search(torch.from_numpy(Q).to(DEV),
+                        torch.from_numpy(npq).to(DEV),
+                        torch.from_numpy(kq).to(DEV), k_max=100)
+    lists, _ = oracle.assign(X, C)
+    probes, pgap = oracle.probe(Q, C, npq)
+    ref_i, ref_d = oracle.ivf_topk(X, Q, *oracle.ivf_lists(lists, 64), probes, kq)
+    ids, d = ids.cpu().numpy(), d.cpu().numpy()
+    for i in range(len(Q)):
+        if pgap[i] < 1e-6:
+            continue
+        check_topk(X, Q[i:i + 1], ids[i:i + 1], d[i:i + 1], ref_i[i:i + 1],
+                   ref_d[i:i + 1], int(kq[i]))
+
+
+def test_ivf_with_library_kmeans_and_empty_lists():
+    """k-means inside the library (its centroids are read back and used by
+    the oracle), more lists than clusters so some lists are tiny or empty."""
+    s, w = _ivf_case(n=20_000, nq=60, nlist=48, d_cfg=2)
+    X, Q = w.X.numpy(), w.Q.numpy()
+    t = pano.panorama_fit_transform(X, n_levels=16)
+    idx = pano.panorama_build_ivf(t, w.X.to(DEV), nlist=200, n_levels=16,
+                                  kmeans_iters=5)
+    C = idx.centroids()
+    lists, gap = oracle.assign(X, C)
+    got = idx.assignment()
+    assert np.all(gap[got != lists] < 1e-6)
+    # the k-means objective does not beat the assignment's own optimum
+    ids, d = idx.search(torch.from_numpy(Q).to(DEV), 12, 10)
+    ref = oracle.ivf_search(X, Q, C, 12, 10, lists_of_vector=lists)
+    keep = ref["probe_gap"] >= 1e-6
+    check_topk(X, Q[keep], ids.cpu().numpy()[keep], d.cpu().numpy()[keep],
+               ref["ids"][keep], ref["dists"][keep], 10)
+
+
+def test_save_load_roundtrip_and_corruption(ivf960, tmp_path):
+    s, X, Q, C, t, idx = ivf960
+    q = torch.from_numpy(Q[:20]).to(DEV)
+    a_ids, a_d = idx.search(q, 8, 10)
+    path = str(tmp_path / "idx.pano")
+    pano.panorama_save(idx, path)
+    idx2 = pano.panorama_load(path)
+    b_ids, b_d = idx2.search(q, 8, 10)
+    assert torch.equal(a_ids, b_ids) and torch.equal(a_d, b_d)
+    raw = bytearray(open(path, "rb").read())
+    raw[len(raw) // 2] ^= 0x55
+    bad = str(tmp_path / "bad.pano")
+    open(bad, "wb").write(bytes(raw))
+    with pytest.raises(pano.LibraryError) as e:
+        pano.panorama_load(bad)
+    assert e.value.code == -5
+    open(bad, "wb").write(bytes(raw[:100]))
+    with pytest.raises(pano.LibraryError) as e:
+        pano.panorama_load(bad)
+    assert e.value.code == -5
+
+
+def test_empty_query_batch_and_bad_arguments(ivf960):
+    s, X, Q, C, t, idx = ivf960
+    q = torch.empty((0, X.shape[1]), device=DEV)
+    ids, d = idx.search(q, 4, 10)
+    assert ids.shape == (0, 10)
+    with pytest.raises(pano.LibraryError):
+        idx.search(torch.from_numpy(Q).to(DEV), 65, 10)  # nprobe > nlist
+    with pytest.raises(pano.LibraryError):
+        idx.search(torch.from_numpy(Q).to(DEV), 4, 10, k_max=5)
