@@ -1,0 +1,31 @@
+/*
+ * panorama_debug.h -- self-test entry points of libpanorama (not part of the
+ * search API).  They exist so that tests can check building blocks of the
+ * GB300 kernels in isolation.
+ */
+#ifndef PANORAMA_DEBUG_H
+#define PANORAMA_DEBUG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* panorama_debug_tc_gemm -- one CTA computes D = 2 * A * B^T with the
+ * tensor-core path of the BF16 verify kernel (swizzled K-major shared-memory
+ * tiles, tcgen05.mma into tensor memory, accumulation over two passes,
+ * tcgen05.ld read-back).  The paper has no counterpart: it is a unit check of
+ * the kernel's building blocks.
+ *   A: device, 128 x K bf16 row-major;  B: device, N x K bf16 row-major;
+ *   D: device, 128 x N FP32 row-major (written).
+ *   N: multiple of 16 in [16, 256];  K: 16, 32 or a multiple of 64 <= 256.
+ * Errors: PANO_EINVAL (sizes, null pointers), PANO_ENODEV, PANO_ECUDA,
+ *         PANO_ETIMEOUT (the completion wait gave up). */
+int panorama_debug_tc_gemm(const void* A, const void* B, int32_t N, int32_t K,
+                           float* D, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PANORAMA_DEBUG_H */

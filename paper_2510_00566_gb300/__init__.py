@@ -102,6 +102,7 @@ SIGNATURES = {
     "panorama_free_index": (None, [_P]),
     "panorama_last_error": (ctypes.c_char_p, []),
     "panorama_version": (ctypes.c_char_p, []),
+    "panorama_debug_tc_gemm": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _P]),
 }
 
 
@@ -249,6 +250,20 @@ def panorama_load(path: str) -> "Index":
     out = ctypes.c_void_p()
     _check(lib().panorama_load(path.encode(), ctypes.byref(out)))
     return Index(out.value)
+
+
+def panorama_debug_tc_gemm(A, B, stream=None):
+    """D = 2 A B^T through the tensor-core building blocks (A: 128 x K, B:
+    N x K, bf16 CUDA tensors); a unit check of the BF16 verify kernel's MMA
+    path."""
+    import torch
+    A = A.contiguous()
+    B = B.contiguous()
+    N, K = B.shape
+    D = torch.empty((128, N), dtype=torch.float32, device=A.device)
+    _check(lib().panorama_debug_tc_gemm(A.data_ptr(), B.data_ptr(), N, K,
+                                        D.data_ptr(), _stream_ptr(stream)))
+    return D
 
 
 def last_stats() -> SearchStats:

@@ -325,8 +325,10 @@ int panorama_load(const char* path, pano_index** out) {
   r.pod(I.c_trans);
   r.pod(I.cmax);
   const bool sane = r.ok && I.n >= 1 && I.d >= 1 && I.d <= 65536 && I.nlist >= 1 &&
-                    I.nlist <= I.n && I.L >= 1 && I.L <= 64 && I.chunk == 64 &&
-                    I.precision == PANO_FP32 && I.n_chunks >= 0 && I.n_chunks <= I.n + I.nlist;
+                    I.nlist <= I.n && I.L >= 1 && I.L <= 64 &&
+                    ((I.precision == PANO_FP32 && I.chunk == 64) ||
+                     (I.precision == PANO_BF16 && I.chunk == 128)) &&
+                    I.n_chunks >= 0 && I.n_chunks <= I.n + I.nlist;
   PANO_CHECK(sane, PANO_ECORRUPT, "header fields out of range");
   const uint64_t d = I.d, n = I.n, nl = I.nlist;
   r.vec(I.widths, 64);
@@ -348,8 +350,10 @@ int panorama_load(const char* path, pano_index** out) {
                  I.assign.size() == n && I.list_chunk_off.size() == nl + 1 &&
                  I.list_chunk_off[nl] == I.n_chunks,
              PANO_ECORRUPT, "truncated or inconsistent index file");
-  const uint64_t ns = (uint64_t)I.n_chunks * 64;
-  if ((rc = r.dev(I.slices, ns * d * 4)) || (rc = r.dev(I.tails, (uint64_t)I.n_chunks * (I.L + 1) * 64 * 4)) ||
+  const uint64_t CHK = (uint64_t)I.chunk, ns = (uint64_t)I.n_chunks * CHK;
+  const uint64_t elem = I.precision == PANO_FP32 ? 4 : 2;
+  if ((rc = r.dev(I.slices, ns * d * elem)) ||
+      (rc = r.dev(I.tails, (uint64_t)I.n_chunks * (I.L + 1) * CHK * 4)) ||
       (rc = r.dev(I.xn2, ns * 4)) || (rc = r.dev(I.ex, ns * 4)) || (rc = r.dev(I.ids, ns * 4)) ||
       (rc = r.dev(I.rows, ns * d * 4)))
     return rc;

@@ -19,6 +19,8 @@
 #include "gemm.h"
 #include "internal.h"
 #include "kernels_common.cuh"
+#include "search.h"
+#include "verify_tc.h"
 
 namespace pano {
 
@@ -136,6 +138,8 @@ __global__ void assign_resolve_kernel(const float* __restrict__ X, int64_t m, in
 
 // x~ for 64 slots (one chunk) per CTA -> transposed slices, tail norms,
 // norms, transform-error bounds and ids.
+// xt, rows and perm point at the block's first chunk; chunk0 is its global
+// index (outputs are global arrays).
 __global__ void __launch_bounds__(256) pack_fp32_kernel(
     const float* __restrict__ xt, const float* __restrict__ rows,
     const int64_t* __restrict__ perm, int64_t chunk0, int d, int L,
@@ -183,7 +187,7 @@ __global__ void __launch_bounds__(256) pack_fp32_kernel(
     }
     double dev = 0.0;  // ||x - mu~||
     if (valid) {
-      const float* r = rows + slot * (int64_t)d;
+      const float* r = rows + (lc * CH + i) * (int64_t)d;  // rows of this block
       for (int j = lane; j < d; j += 32) {
         double v = (double)r[j] - (double)mu[j];
         dev += v * v;
@@ -338,8 +342,8 @@ int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
   PANO_CHECK(n >= 1 && nlist >= 1 && nlist <= n, PANO_EINVAL, "need 1 <= nlist <= n");
   PANO_CHECK(n < ((int64_t)1 << 31) - 1, PANO_EINVAL, "at most 2^31-2 vectors");
   int precision = o ? o->precision : PANO_FP32;
-  PANO_CHECK(precision == PANO_FP32, PANO_EINVAL,
-             "only PANO_FP32 storage is available in this build");
+  PANO_CHECK(precision == PANO_FP32 || precision == PANO_BF16, PANO_EINVAL,
+             "storage precision must be PANO_FP32 or PANO_BF16 (PANO_FP8 is not built)");
   int dev = 0;
   int rc = check_device(&dev);
   if (rc) return rc;
@@ -350,10 +354,15 @@ int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
   I.d = d;
   I.nlist = nlist;
   I.precision = precision;
-  I.chunk = CH;
+  const int CHK = precision == PANO_FP32 ? CH : TC_CHUNK;  // vectors per chunk
+  I.chunk = CHK;
   I.tf = *t;
   rc = make_levels(d, o, I.widths, I.offs);
   if (rc) return rc;
+  if (precision != PANO_FP32)
+    for (int w : I.widths)
+      PANO_CHECK(w == 16 || w == 32 || w % 64 == 0, PANO_EINVAL,
+                 "bf16 level widths must be 16, 32 or multiples of 64");
   I.L = (int)I.widths.size();
   I.max_w = *std::max_element(I.widths.begin(), I.widths.end());
   I.eta = t->eta;
@@ -439,15 +448,15 @@ int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
   for (int64_t i = 0; i < n; ++i) I.list_size[I.assign[i]]++;
   I.list_chunk_off.assign(nlist + 1, 0);
   for (int c = 0; c < nlist; ++c)
-    I.list_chunk_off[c + 1] = I.list_chunk_off[c] + (I.list_size[c] + CH - 1) / CH;
+    I.list_chunk_off[c + 1] = I.list_chunk_off[c] + (I.list_size[c] + CHK - 1) / CHK;
   I.n_chunks = I.list_chunk_off[nlist];
-  const int64_t nslots = I.n_chunks * CH;
+  const int64_t nslots = I.n_chunks * CHK;
   std::vector<int64_t> perm(nslots, -1);
   {
     std::vector<int64_t> fill(nlist, 0);
     for (int64_t i = 0; i < n; ++i) {  // ascending id within each list
       int c = I.assign[i];
-      perm[I.list_chunk_off[c] * CH + fill[c]++] = i;
+      perm[I.list_chunk_off[c] * CHK + fill[c]++] = i;
     }
   }
   std::vector<int64_t> hco(I.list_chunk_off);
@@ -462,8 +471,9 @@ int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
   PANO_CUDA(cudaMemcpyAsync(I.mu32.p, t->mu32.data(), d * 4, cudaMemcpyHostToDevice, st));
 
   // ---- packed arrays
-  if ((rc = I.slices.alloc((size_t)nslots * d * 4)) ||
-      (rc = I.tails.alloc((size_t)I.n_chunks * (I.L + 1) * CH * 4)) ||
+  const size_t elem = precision == PANO_FP32 ? 4 : 2;
+  if ((rc = I.slices.alloc((size_t)nslots * d * elem)) ||
+      (rc = I.tails.alloc((size_t)I.n_chunks * (I.L + 1) * CHK * 4)) ||
       (rc = I.xn2.alloc(nslots * 4)) || (rc = I.ex.alloc(nslots * 4)) ||
       (rc = I.ids.alloc(nslots * 4)) || (rc = I.rows.alloc((size_t)nslots * d * 4)))
     return rc;
@@ -475,18 +485,27 @@ int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
                                                           I.rows.as<float>());
     PANO_CUDA(cudaGetLastError());
   }
-  const int64_t cblk = std::max<int64_t>(1, ((int64_t)1 << 28) / ((int64_t)CH * d * 4));
-  PANO_CUDA(cudaMalloc(&t_xt.p, (size_t)std::min(cblk, std::max<int64_t>(I.n_chunks, 1)) * CH * d * 4));
+  // chunks per transform/pack block (64 MB of transformed rows)
+  const int64_t cblk = std::max<int64_t>(1, ((int64_t)1 << 26) / ((int64_t)CHK * d * 4));
+  PANO_CUDA(cudaMalloc(&t_xt.p, (size_t)std::min(cblk, std::max<int64_t>(I.n_chunks, 1)) * CHK * d * 4));
   for (int64_t c0 = 0; c0 < I.n_chunks; c0 += cblk) {
     int64_t nc = std::min(cblk, I.n_chunks - c0);
-    const float* rows_blk = I.rows.as<float>() + c0 * CH * d;
-    PANO_CUDA(gemm_nt(kStore, (int)(nc * CH), d, d, rows_blk, d, I.mu32.as<float>(),
+    const float* rows_blk = I.rows.as<float>() + c0 * CHK * d;
+    PANO_CUDA(gemm_nt(kStore, (int)(nc * CHK), d, d, rows_blk, d, I.mu32.as<float>(),
                       I.T32.as<float>(), d, (float*)t_xt.p, d, nullptr, nullptr, st));
-    pack_fp32_kernel<<<(unsigned)nc, 256, 0, st>>>(
-        (float*)t_xt.p, rows_blk, (int64_t*)t_perm.p + c0 * CH, c0, d, I.L,
-        I.level_off_d.as<int32_t>(), I.mu32.as<float>(), I.c_trans, I.slices.as<float>(),
-        I.tails.as<float>(), I.xn2.as<float>(), I.ex.as<float>(), I.ids.as<int32_t>());
-    PANO_CUDA(cudaGetLastError());
+    if (precision == PANO_FP32) {
+      pack_fp32_kernel<<<(unsigned)nc, 256, 0, st>>>(
+          (float*)t_xt.p, rows_blk, (int64_t*)t_perm.p + c0 * CHK, c0, d, I.L,
+          I.level_off_d.as<int32_t>(), I.mu32.as<float>(), I.c_trans, I.slices.as<float>(),
+          I.tails.as<float>(), I.xn2.as<float>(), I.ex.as<float>(), I.ids.as<int32_t>());
+      PANO_CUDA(cudaGetLastError());
+    } else {
+      rc = launch_pack_bf16((float*)t_xt.p, rows_blk, (int64_t*)t_perm.p + c0 * CHK, c0, nc, d,
+                            I.L, I.level_off_d.as<int32_t>(), I.mu32.as<float>(), I.c_trans,
+                            I.slices.as<uint8_t>(), I.tails.as<float>(), I.xn2.as<float>(),
+                            I.ex.as<float>(), I.ids.as<int32_t>(), st);
+      if (rc) return rc;
+    }
   }
   PANO_CUDA(cudaStreamSynchronize(st));
   *out = idx.release();

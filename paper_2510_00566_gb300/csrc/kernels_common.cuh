@@ -5,22 +5,66 @@
 
 namespace pano {
 
+__device__ __forceinline__ void kahan_add(float t, float& s, float& c) {
+  float y = t - c;
+  float u = s + y;
+  c = (u - s) - y;
+  s = u;
+}
+
 // Exact-as-FP32-allows squared distance sum_j (a_j - b_j)^2 by one warp:
-// each lane keeps a Kahan-compensated sum (s, c) of its strided terms (the
-// value is s - c); lanes are combined pairwise with an error-free TwoSum of
-// the s parts.  Relative error a few FP32 units (compensated summation), far
-// below the plain d-term sum's d*u.  Every lane returns the result.
+// each lane keeps a Kahan-compensated sum (s, c) of its terms (the value is
+// s - c); lanes are combined pairwise with an error-free TwoSum of the s
+// parts.  Relative error a few FP32 units (compensated summation), far below
+// the plain d-term sum's d*u.  Loads are issued in batches (several 16-byte
+// loads in flight per lane) so the latency is paid a few times per row, not
+// once per element.  Every lane returns the result.
 __device__ __forceinline__ float exact_sqdist_warp(const float* __restrict__ a,
                                                    const float* __restrict__ b, int d) {
   const int lane = threadIdx.x & 31;
   float s = 0.f, c = 0.f;
-  for (int j = lane; j < d; j += 32) {
-    float diff = a[j] - b[j];
-    float t = diff * diff;
-    float y = t - c;
-    float u = s + y;
-    c = (u - s) - y;
-    s = u;
+  const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(a) & 15) == 0) &&
+                   ((reinterpret_cast<uintptr_t>(b) & 15) == 0);
+  if (vec) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+    const int d4 = d >> 2;
+    for (int j0 = 0; j0 < d4; j0 += 4 * 32) {
+      float4 av[4], bv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + lane + 32 * u;
+        av[u] = j < d4 ? a4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        bv[u] = j < d4 ? b4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float t;
+        t = av[u].x - bv[u].x;
+        kahan_add(t * t, s, c);
+        t = av[u].y - bv[u].y;
+        kahan_add(t * t, s, c);
+        t = av[u].z - bv[u].z;
+        kahan_add(t * t, s, c);
+        t = av[u].w - bv[u].w;
+        kahan_add(t * t, s, c);
+      }
+    }
+  } else {
+    for (int j0 = 0; j0 < d; j0 += 8 * 32) {
+      float av[8], bv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + lane + 32 * u;
+        av[u] = j < d ? a[j] : 0.f;
+        bv[u] = j < d ? b[j] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float t = av[u] - bv[u];
+        kahan_add(t * t, s, c);
+      }
+    }
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -33,6 +77,29 @@ __device__ __forceinline__ float exact_sqdist_warp(const float* __restrict__ a,
     s = sum;
   }
   return s - c;
+}
+
+// k-th smallest of the nv FP32 values vals[0..nv) (non-negative, +inf for
+// absent entries) by one warp: binary search on the bit pattern for the
+// least t with #{v <= t} >= k.  Returns +inf when fewer than k are finite.
+__device__ __forceinline__ float warp_kth_smallest(const float* vals, int nv, int k) {
+  const int lane = threadIdx.x & 31;
+  int finite = 0;
+  for (int i = lane; i < nv; i += 32) finite += vals[i] < INFINITY;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) finite += __shfl_xor_sync(0xffffffffu, finite, off);
+  if (k <= 0 || finite < k) return INFINITY;
+  uint32_t lo = 0, hi = 0x7f800000u;
+  while (lo < hi) {
+    const uint32_t mid = lo + ((hi - lo) >> 1);
+    int cnt = 0;
+    for (int i = lane; i < nv; i += 32) cnt += __float_as_uint(vals[i]) <= mid;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+    if (cnt >= k) hi = mid;
+    else lo = mid + 1;
+  }
+  return __uint_as_float(lo);
 }
 
 __device__ __forceinline__ double warp_sum_f64(double v) {

@@ -23,6 +23,7 @@
 #include "internal.h"
 #include "kernels_common.cuh"
 #include "search.h"
+#include "verify_tc.h"
 
 namespace pano {
 
@@ -201,7 +202,8 @@ __global__ void inv_count_kernel(int64_t nq, const int32_t* __restrict__ probes,
 // both phases.  items(c) = ceil(cnt / QB_phase) * nseg(c).
 __global__ void __launch_bounds__(1024) inv_scan_kernel(const int* __restrict__ cnt, int nlist,
                                                         const int64_t* __restrict__ chunk_off,
-                                                        int qbA, int qbB, int* __restrict__ boff,
+                                                        int seg, int qbA, int qbB,
+                                                        int* __restrict__ boff,
                                                         int* __restrict__ ioff,
                                                         int* __restrict__ totals) {
   __shared__ int part_b[1024], part_i[1024];
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(1024) inv_scan_kernel(const int* __restrict__ 
     int sb = 0, si = 0;
     for (int c = b0; c < b1; ++c) {
       int nch = (int)(chunk_off[c + 1] - chunk_off[c]);
-      int nseg = (nch + SEG_CHUNKS - 1) / SEG_CHUNKS;
+      int nseg = (nch + seg - 1) / seg;
       sb += cn[c];
       si += ((cn[c] + qb - 1) / qb) * nseg;
     }
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(1024) inv_scan_kernel(const int* __restrict__ 
     int ab = part_b[threadIdx.x], ai = part_i[threadIdx.x];
     for (int c = b0; c < b1; ++c) {
       int nch = (int)(chunk_off[c + 1] - chunk_off[c]);
-      int nseg = (nch + SEG_CHUNKS - 1) / SEG_CHUNKS;
+      int nseg = (nch + seg - 1) / seg;
       boff[ph * (nlist + 1) + c] = ab;
       ioff[ph * (nlist + 1) + c] = ai;
       ab += cn[c];
@@ -269,7 +271,7 @@ __global__ void inv_scatter_kernel(int64_t nq, const int32_t* __restrict__ probe
 
 // Work item i of a phase -> (list, segment, bucket offset, group size).
 __global__ void inv_emit_kernel(int ph, const int* __restrict__ cnt, int nlist,
-                                const int64_t* __restrict__ chunk_off, int qb,
+                                const int64_t* __restrict__ chunk_off, int seg, int qb,
                                 const int* __restrict__ boff, const int* __restrict__ ioff,
                                 const int* __restrict__ totals, int64_t cap,
                                 int4* __restrict__ items, int* __restrict__ err) {
@@ -289,11 +291,46 @@ __global__ void inv_emit_kernel(int ph, const int* __restrict__ cnt, int nlist,
     while (c + 1 < nlist && io[c + 1] <= i) ++c;  // skip empty lists
     int local = (int)(i - io[c]);
     int nch = (int)(chunk_off[c + 1] - chunk_off[c]);
-    int nseg = (nch + SEG_CHUNKS - 1) / SEG_CHUNKS;
+    int nseg = (nch + seg - 1) / seg;
     int g = local / nseg, s = local % nseg;
     int n_in = cnt[ph * nlist + c];
     int base = (ph == 1 ? totals[0] : 0) + bo[c] + g * qb;
     items[i] = make_int4(c, s, base, min(qb, n_in - g * qb));
+  }
+}
+
+// ------------------------------------------------- Alg. 1 warm start (a6)
+// Per query: exact distances to the first max(2k, 32) (at most 256) members
+// of its nearest list; the k-th smallest (rounded up) is an upper bound on
+// d_k and seeds the threshold before any tile is verified (Algorithm 1
+// initialises d_k from the first k candidates).  The seeds are not inserted
+// into the top-k: they are verified again like every other candidate.
+constexpr int kSeedMax = 256;
+
+__global__ void __launch_bounds__(128) seed_tau_kernel(
+    const float* __restrict__ q, int d, const int32_t* __restrict__ probes, int stride,
+    const int64_t* __restrict__ chunk_off, const int32_t* __restrict__ list_size, int chunk,
+    const float* __restrict__ rows, const int32_t* __restrict__ kq, float* __restrict__ tau_seed) {
+  __shared__ float dist[kSeedMax];
+  const int64_t row = blockIdx.x;
+  const int k = kq[row];
+  const int c = probes[row * stride];
+  const int n = c >= 0 ? list_size[c] : 0;
+  const int ns = min(n, min(kSeedMax, max(2 * k, 32)));
+  if (k <= 0 || ns < k) {
+    if (threadIdx.x == 0) tau_seed[row] = k <= 0 ? -1.f : INFINITY;
+    return;
+  }
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  const int64_t base = chunk_off[c] * chunk;  // a list's members are its first slots
+  for (int i = warp; i < ns; i += 4) {
+    float v = exact_sqdist_warp(q + row * d, rows + (base + i) * d, d);
+    if (lane == 0) dist[i] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    float t = warp_kth_smallest(dist, ns, k);
+    if (lane == 0) tau_seed[row] = __fmul_ru(t, 1.000001f);
   }
 }
 
@@ -311,6 +348,7 @@ struct VerifyArgs {
   const float4* qinfo;
   const float* qtail;
   const int32_t* kq;
+  const float* tau_seed;  // per-query warm-start threshold
   const int4* items;
   const int* n_items;  // device count
   int* counter;
@@ -322,6 +360,7 @@ struct VerifyArgs {
   int d, L, max_w, k_max;
   float gslack;    // slack factor: |computed - exact| <= gslack (|q~|+|x~|)^2
   float lb_scale;  // (1 - 8u) / (1 + eta): lower bound in T~ space -> original
+  float ub_scale;  // (1 + 8u) / (1 - eta): upper bound in T~ space -> original
   int prune;       // 0: plain scan (prune only after the last level)
   int collect;
   int32_t level_off[65];
@@ -331,7 +370,7 @@ struct Smem {
   // sizes depend on (QB, CB, max_w, L); carved at run time
   static size_t bytes(int QB, int CB, int max_w, int L) {
     size_t s = 0;
-    s += (size_t)CB * max_w * 4;          // xs
+    s += (size_t)std::max(CB * max_w, QB * CB) * 4;  // xs (also the last level's UB scratch)
     s += (size_t)max_w * (QB + 4) * 4;    // qs
     s += (size_t)CB * (L + 1) * 4;        // candidate tails
     s += (size_t)QB * (L + 1) * 4;        // query tails
@@ -343,7 +382,7 @@ struct Smem {
 };
 
 template <int QB, int CB>
-__global__ void __launch_bounds__(NT) verify_fp32_kernel(const VerifyArgs a) {
+__global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) {
   constexpr int NCH = CB / CH;
   constexpr int TQ = QB / 4;
   static_assert(TQ * (CB / 4) == NT, "4x4 register tile per thread");
@@ -351,7 +390,7 @@ __global__ void __launch_bounds__(NT) verify_fp32_kernel(const VerifyArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int L = a.L, d = a.d, max_w = a.max_w;
   float* xs = reinterpret_cast<float*>(smem);               // [NCH][max_w][CH]
-  float* qs = xs + (size_t)CB * max_w;                       // [max_w][QB+4]
+  float* qs = xs + (size_t)(CB * max_w > QB * CB ? CB * max_w : QB * CB);  // [max_w][QB+4]
   float* ctl = qs + (size_t)max_w * (QB + 4);               // [NCH][L+1][CH]
   float* qtl = ctl + (size_t)CB * (L + 1);                   // [QB][L+1]
   float* xn2s = qtl + (size_t)QB * (L + 1);                  // [CB]
@@ -423,6 +462,7 @@ __global__ void __launch_bounds__(NT) verify_fp32_kernel(const VerifyArgs a) {
         if (g < G && qk[g] > 0) {
           unsigned long long kk = ld_volatile_u64(a.topk + (int64_t)qid[g] * a.k_max + qk[g] - 1);
           tau = kk == kEmptyKey ? INFINITY : __fmul_ru(key_dist(kk), 1.000001f);
+          tau = fminf(tau, a.tau_seed[qid[g]]);
         }
         qtau[g] = tau;
       }
@@ -557,6 +597,58 @@ __global__ void __launch_bounds__(NT) verify_fp32_kernel(const VerifyArgs a) {
           }
         }
         __syncthreads();  // xs / qs are overwritten by the next level
+      }
+      // The k-th smallest upper bound of the tile tightens each query's
+      // threshold before re-ranking (at the last level UB ~ LB ~ exact, so
+      // only ~k pairs per query survive even while the running top-k is
+      // still empty).
+      const int done = __syncthreads_or(completed && alive != 0);
+      if (done) {
+        float* ub = xs;  // [QB][CB]
+        for (int e = tid; e < QB * CB; e += NT) ub[e] = INFINITY;
+        __syncthreads();
+        if (completed) {
+#pragma unroll
+          for (int ai = 0; ai < 4; ++ai) {
+            const int g = 4 * tq + ai;
+            const float nq = qnq[g], rq = qrq[g], eq = qeq[g];
+#pragma unroll
+            for (int bi = 0; bi < 4; ++bi) {
+              if (!(alive & (1u << (4 * ai + bi)))) continue;
+              const int e = 4 * tc + bi;
+              const float A = nq + xn2s[e] - 2.f * p[ai][bi];
+              const float S = rq + rxs[e];
+              const float ubs = fmaxf(A + a.gslack * S * S, 0.f);
+              const float r = __fadd_ru(__fsqrt_ru(ubs), eq + exs[e]);
+              ub[g * CB + e] = __fmul_ru(__fmul_ru(r, r), a.ub_scale);
+            }
+          }
+        }
+        __syncthreads();
+        for (int g = warp; g < G; g += NT / 32) {
+          const float t = warp_kth_smallest(ub + g * CB, CB, qk[g]);
+          if (lane == 0 && t < qtau[g]) qtau[g] = t;
+        }
+        __syncthreads();
+        if (completed) {
+#pragma unroll
+          for (int ai = 0; ai < 4; ++ai) {
+            const int g = 4 * tq + ai;
+            const float nq = qnq[g], rq = qrq[g], eq = qeq[g], tau = qtau[g];
+#pragma unroll
+            for (int bi = 0; bi < 4; ++bi) {
+              const uint32_t bit = 1u << (4 * ai + bi);
+              if (!(alive & bit)) continue;
+              const int e = 4 * tc + bi;
+              const float A = nq + xn2s[e] - 2.f * p[ai][bi];
+              const float S = rq + rxs[e];
+              const float lbs = A - a.gslack * S * S;
+              const float r = sqrtf(fmaxf(lbs, 0.f)) - (eq + exs[e]);
+              const float LB = r > 0.f ? r * r * a.lb_scale : 0.f;
+              if (LB > tau) alive &= ~bit;
+            }
+          }
+        }
       }
       // survivors of all L levels: exact re-rank and top-k insertion
       if (completed && alive) {
@@ -710,12 +802,15 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
   const int np_cap = nprobe ? ((nprobe_scalar >= 1) ? std::min(nprobe_scalar, nlist) : nlist)
                             : nprobe_scalar;
   const int stride = np_cap;
-  constexpr int QBA = 16, CBA = 256, QBB = 64, CBB = 64;
+  constexpr int CBA = 256, CBB = 64;
+  const bool tcpath = I.precision != PANO_FP32;
+  const int QBA = tcpath ? TC_QG : 16, QBB = tcpath ? TC_QG : 64;
+  const int SEG = tcpath ? TC_SEG : SEG_CHUNKS;
   // work-item capacity: groups x segments, plus one partial group per list
   int64_t max_seg = 1, tot_seg = 0;
   for (int c = 0; c < nlist; ++c) {
     int64_t nch = I.list_chunk_off[c + 1] - I.list_chunk_off[c];
-    int64_t s = (nch + SEG_CHUNKS - 1) / SEG_CHUNKS;
+    int64_t s = (nch + SEG - 1) / SEG;
     max_seg = std::max(max_seg, s);
     tot_seg += s;
   }
@@ -731,6 +826,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
   size_t o_pr = cv.take<int32_t>((size_t)nq * stride);
   size_t o_npq = cv.take<int32_t>(nq);
   size_t o_kq = cv.take<int32_t>(nq);
+  size_t o_seed = cv.take<float>(nq);
   size_t o_cnt = cv.take<int>(2 * (size_t)nlist);
   size_t o_fill = cv.take<int>(2 * (size_t)nlist);
   size_t o_boff = cv.take<int>(2 * (size_t)(nlist + 1));
@@ -753,6 +849,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
   int32_t* probes = (int32_t*)P(o_pr);
   int32_t* npq = (int32_t*)P(o_npq);
   int32_t* kq = (int32_t*)P(o_kq);
+  float* tau_seed = (float*)P(o_seed);
   int* cnt = (int*)P(o_cnt);
   int* fillc = (int*)P(o_fill);
   int* boff = (int*)P(o_boff);
@@ -805,22 +902,76 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     } else {
       PANO_CUDA(cudaMemsetAsync(probes, 0, (size_t)nq * stride * 4, st));
     }
-    // a3
+    // a3 (and the Alg. 1 warm start of the threshold)
     mark(2);
+    seed_tau_kernel<<<(unsigned)nq, 128, 0, st>>>(queries, d, probes, stride,
+                                                  I.chunk_off_d.as<int64_t>(),
+                                                  I.list_size_d.as<int32_t>(), I.chunk,
+                                                  I.rows.as<float>(), kq, tau_seed);
+    PANO_CUDA(cudaGetLastError());
     const int64_t ne = nq * stride;
     inv_count_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(nq, probes, stride, npq, cnt,
                                                                    nlist);
-    inv_scan_kernel<<<1, 1024, 0, st>>>(cnt, nlist, I.chunk_off_d.as<int64_t>(), QBA, QBB, boff,
-                                        ioff, tot);
+    inv_scan_kernel<<<1, 1024, 0, st>>>(cnt, nlist, I.chunk_off_d.as<int64_t>(), SEG, QBA, QBB,
+                                        boff, ioff, tot);
     inv_scatter_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(nq, probes, stride, npq, boff,
                                                                      tot, fillc, nlist, bucket);
     PANO_CUDA(cudaGetLastError());
-    inv_emit_kernel<<<1024, 256, 0, st>>>(0, cnt, nlist, I.chunk_off_d.as<int64_t>(), QBA, boff,
-                                          ioff, tot, capA, itA, err);
-    inv_emit_kernel<<<1024, 256, 0, st>>>(1, cnt, nlist, I.chunk_off_d.as<int64_t>(), QBB, boff,
-                                          ioff, tot, capB, itB, err);
+    inv_emit_kernel<<<1024, 256, 0, st>>>(0, cnt, nlist, I.chunk_off_d.as<int64_t>(), SEG, QBA,
+                                          boff, ioff, tot, capA, itA, err);
+    inv_emit_kernel<<<1024, 256, 0, st>>>(1, cnt, nlist, I.chunk_off_d.as<int64_t>(), SEG, QBB,
+                                          boff, ioff, tot, capB, itB, err);
     PANO_CUDA(cudaGetLastError());
     // a4-a10
+    if (tcpath) {
+      VerifyTCArgs ta;
+      std::memset(&ta, 0, sizeof(ta));
+      ta.slices = I.slices.as<uint8_t>();
+      ta.tails = I.tails.as<float>();
+      ta.xn2 = I.xn2.as<float>();
+      ta.ex = I.ex.as<float>();
+      ta.ids = I.ids.as<int32_t>();
+      ta.rows = I.rows.as<float>();
+      ta.chunk_off = I.chunk_off_d.as<int64_t>();
+      ta.qt = qt;
+      ta.qorig = queries;
+      ta.qinfo = qinfo;
+      ta.qtail = qtail;
+      ta.kq = kq;
+      ta.tau_seed = tau_seed;
+      ta.topk = topk;
+      ta.err = err;
+      ta.stats = stats;
+      ta.d = d;
+      ta.L = L;
+      ta.max_w = I.max_w;
+      ta.k_max = k_max;
+      // p error: bf16 hi/lo query split (2^-16 |q~_j| per term) plus the
+      // tensor-core accumulation (2^-20 of the running sum of |products| per
+      // MMA instruction, 2 d / 16 instructions); FP32 evaluation of the
+      // remaining terms: gamma_{L+8}; factor 2 of safety on the last two.
+      ta.gslack = (float)(std::ldexp(1.0, -16) + (d / 8.0) * std::ldexp(1.0, -20) +
+                          2.0 * gamma_n(L + 8));
+      ta.lb_scale = (float)((1.0 - 8.0 * kU32) / (1.0 + I.eta));
+      ta.prune = mode == 0 ? 1 : 0;
+      ta.collect = collect ? 1 : 0;
+      for (int l = 0; l <= L; ++l) ta.level_off[l] = I.offs[l];
+      ta.bucket = bucket;
+      mark(3);
+      ta.items = itA;
+      ta.n_items = tot + 1;
+      ta.counter = tot + 4;
+      ta.items_cap = capA;
+      int r = launch_verify_tc(ta, st);
+      if (r) return r;
+      mark(4);
+      ta.items = itB;
+      ta.n_items = tot + 3;
+      ta.counter = tot + 5;
+      ta.items_cap = capB;
+      r = launch_verify_tc(ta, st);
+      if (r) return r;
+    } else {
     VerifyArgs va;
     std::memset(&va, 0, sizeof(va));
     va.slices = I.slices.as<float>();
@@ -835,6 +986,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     va.qinfo = qinfo;
     va.qtail = qtail;
     va.kq = kq;
+    va.tau_seed = tau_seed;
     va.topk = topk;
     va.err = err;
     va.stats = stats;
@@ -844,6 +996,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     va.k_max = k_max;
     va.gslack = (float)(2.0 * gamma_n(I.max_w + L + 8));
     va.lb_scale = (float)((1.0 - 8.0 * kU32) / (1.0 + I.eta));
+    va.ub_scale = (float)((1.0 + 8.0 * kU32) / (1.0 - I.eta) * (1.0 + 1e-7));
     va.prune = mode == 0 ? 1 : 0;
     va.collect = collect ? 1 : 0;
     for (int l = 0; l <= L; ++l) va.level_off[l] = I.offs[l];
@@ -854,7 +1007,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     va.n_items = tot + 1;
     va.counter = tot + 4;
     va.items_cap = capA;
-    int r = launch_verify<QBA, CBA>(va, Smem::bytes(QBA, CBA, I.max_w, L), st);
+    int r = launch_verify<16, CBA>(va, Smem::bytes(16, CBA, I.max_w, L), st);
     if (r) return r;
     // phase B
     mark(4);
@@ -862,8 +1015,9 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     va.n_items = tot + 3;
     va.counter = tot + 5;
     va.items_cap = capB;
-    r = launch_verify<QBB, CBB>(va, Smem::bytes(QBB, CBB, I.max_w, L), st);
+    r = launch_verify<64, CBB>(va, Smem::bytes(64, CBB, I.max_w, L), st);
     if (r) return r;
+    }
     mark(5);
     const int64_t no = nq * k_max;
     decode_kernel<<<(unsigned)((no + 255) / 256), 256, 0, st>>>(nq, k_max, kq, topk, out_ids,

@@ -1,0 +1,49 @@
+// Launchers of the BF16 tensor-core path (verify_tc.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pano {
+
+constexpr int TC_CHUNK = 128;  // vectors per chunk (MMA M)
+constexpr int TC_QG = 64;      // queries per group (MMA N, padded to 16)
+constexpr int TC_SEG = 8;      // chunks per work-item segment
+
+struct VerifyTCArgs {
+  const uint8_t* slices;
+  const float* tails;
+  const float* xn2;
+  const float* ex;
+  const int32_t* ids;
+  const float* rows;
+  const int64_t* chunk_off;
+  const float* qt;
+  const float* qorig;
+  const float4* qinfo;
+  const float* qtail;
+  const int32_t* kq;
+  const float* tau_seed;  // per-query warm-start threshold
+  const int4* items;
+  const int* n_items;
+  int* counter;
+  const int32_t* bucket;
+  unsigned long long* topk;
+  int* err;
+  unsigned long long* stats;
+  int64_t items_cap;
+  int d, L, max_w, k_max;
+  float gslack;    // |computed - exact| terms of the bound <= gslack (|q~|+|x^|)^2
+  float lb_scale;  // (1 - 8u) / (1 + eta)
+  int prune;
+  int collect;
+  int32_t level_off[65];
+};
+
+int launch_pack_bf16(const float* xt, const float* rows, const int64_t* perm, int64_t chunk0,
+                     int64_t nchunks, int d, int L, const int32_t* level_off, const float* mu,
+                     double c_trans, uint8_t* slices, float* tails, float* xn2, float* ex,
+                     int32_t* ids, cudaStream_t st);
+int launch_verify_tc(const VerifyTCArgs& a, cudaStream_t st);
+size_t verify_tc_smem(int max_w);
+
+}  // namespace pano

@@ -21,7 +21,7 @@ def L():
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = open(HEADER).read() + open(HEADER.replace("panorama.h", "panorama_debug.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(panorama_\w+)\s*\(", text)))
 
