@@ -44,7 +44,27 @@ def parse():
     p.add_argument("--impl", default="panorama", choices=["panorama", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--scan-steps", type=int, default=3)
+    p.add_argument("--n", type=int, default=0, help="override N (profiling a smaller case)")
+    p.add_argument("--queries", type=int, default=0, help="override the query count")
+    p.add_argument("--nlist", type=int, default=0, help="override nlist (and clusters)")
+    p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
+
+
+def workload_spec(args):
+    import dataclasses
+    import synth
+    s = synth.spec(args.config)
+    upd = {}
+    if args.n:
+        upd["n"] = args.n
+    if args.queries:
+        upd["n_queries"] = args.queries
+    if args.nlist:
+        upd["nlist"] = args.nlist
+        if s.n_clusters:
+            upd["n_clusters"] = args.nlist
+    return dataclasses.replace(s, **upd) if upd else s
 
 
 def dist_env():
@@ -147,7 +167,7 @@ def run_reference(args):
     import numpy as np
     import torch
     import synth
-    s = synth.spec(args.config)
+    s = workload_spec(args)
     w = synth.generate(s, device="cpu")
     X, Q = w.X.numpy(), w.Q.numpy()
     import oracle
@@ -184,6 +204,44 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def e2e_time(idx, Q, s, k, args, stream, flush, world, dev):
+    """Per-step time of the public API call with HOST buffers: pinned H2D of
+    the queries, search, D2H of ids and distances, all inside the events."""
+    import torch
+    import torch.distributed as dist
+    nq = Q.shape[0]
+    qh = Q.cpu().pin_memory()
+    ids_h = torch.empty((nq, k), dtype=torch.int64).pin_memory()
+    d_h = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+    qd = torch.empty_like(Q)
+    for _ in range(2):
+        qd.copy_(qh, non_blocking=True)
+        a, b = idx.search(qd, s.nprobe, k)
+        ids_h.copy_(a, non_blocking=True)
+        d_h.copy_(b, non_blocking=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        qd.copy_(qh, non_blocking=True)
+        a, b = idx.search(qd, s.nprobe, k)
+        ids_h.copy_(a, non_blocking=True)
+        d_h.copy_(b, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    t = torch.tensor([total], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item() / args.steps
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -208,7 +266,7 @@ def main():
         dist.barrier()
     pano.lib()
 
-    s = synth.spec(args.config)
+    s = workload_spec(args)
     # every rank holds a replica of the index and verifies its own query batch
     w = synth.generate(s, device=dev)
     if rank > 0:
@@ -272,36 +330,9 @@ def main():
     scan_per = scan_ms / args.scan_steps
 
     # e2e: through the public API with host buffers (pinned H2D + D2H)
-    qh = Q.cpu().pin_memory()
-    ids_h = torch.empty((nq, k), dtype=torch.int64).pin_memory()
-    d_h = torch.empty((nq, k), dtype=torch.float32).pin_memory()
-    qd = torch.empty_like(Q)
-    for _ in range(2):
-        qd.copy_(qh, non_blocking=True)
-        a, b = idx.search(qd, s.nprobe, k)
-        ids_h.copy_(a, non_blocking=True)
-        d_h.copy_(b, non_blocking=True)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    e2e_total = 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        qd.copy_(qh, non_blocking=True)
-        a, b = idx.search(qd, s.nprobe, k)
-        ids_h.copy_(a, non_blocking=True)
-        d_h.copy_(b, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        e2e_total += e0.elapsed_time(e1)
-    t_e2e = torch.tensor([e2e_total], device=dev)
-    if world > 1:
-        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-    e2e_per = t_e2e.item() / args.steps
+    e2e_per = None
+    if not args.no_e2e:
+        e2e_per = e2e_time(idx, Q, s, k, args, stream, flush, world, dev)
 
     # roofline of the dominant kernel (verify phase B), measured live above
     pk, pk_kind = peaks()
@@ -339,9 +370,10 @@ def main():
             "qps": qps,
             "fp32_scan": {"value": pairs * world / (scan_per / 1e3), "qps": nq * world / (scan_per / 1e3),
                           "ms_per_step": scan_per, "speedup_of_pruned": scan_per / ms_per_step},
-            "e2e": {"value": pairs * world / (e2e_per / 1e3), "unit": "candidates/s",
-                    "qps": nq * world / (e2e_per / 1e3), "ms_per_step": e2e_per,
-                    "h2d_bytes_per_step": Q.numel() * 4, "d2h_bytes_per_step": nq * k * 12},
+            "e2e": None if e2e_per is None else {
+                "value": pairs * world / (e2e_per / 1e3), "unit": "candidates/s",
+                "qps": nq * world / (e2e_per / 1e3), "ms_per_step": e2e_per,
+                "h2d_bytes_per_step": Q.numel() * 4, "d2h_bytes_per_step": nq * k * 12},
             "gpu_launches": KERNELS_PER_SEARCH * args.steps,
             "roofline": roof,
             "stage_ms": stage,

@@ -372,7 +372,7 @@ struct Smem {
     size_t s = 0;
     s += (size_t)std::max(CB * max_w, QB * CB) * 4;  // xs (also the last level's UB scratch)
     s += (size_t)max_w * (QB + 4) * 4;    // qs
-    s += (size_t)CB * (L + 1) * 4;        // candidate tails
+    s += (size_t)CB * 4;                  // candidate tails of the current level
     s += (size_t)QB * (L + 1) * 4;        // query tails
     s += (size_t)CB * 4 * 4;              // xn2, rx, ex, ids
     s += (size_t)QB * 6 * 4;              // qid, nq, rq, eq, tau, k
@@ -391,8 +391,8 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
   const int L = a.L, d = a.d, max_w = a.max_w;
   float* xs = reinterpret_cast<float*>(smem);               // [NCH][max_w][CH]
   float* qs = xs + (size_t)(CB * max_w > QB * CB ? CB * max_w : QB * CB);  // [max_w][QB+4]
-  float* ctl = qs + (size_t)max_w * (QB + 4);               // [NCH][L+1][CH]
-  float* qtl = ctl + (size_t)CB * (L + 1);                   // [QB][L+1]
+  float* ctl = qs + (size_t)max_w * (QB + 4);               // [CB] tails, level l+1
+  float* qtl = ctl + CB;                                     // [QB][L+1]
   float* xn2s = qtl + (size_t)QB * (L + 1);                  // [CB]
   float* rxs = xn2s + CB;
   float* exs = rxs + CB;
@@ -480,11 +480,6 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
           ids_s[e] = -1;
         }
       }
-      for (int e = tid; e < nch * (L + 1) * CH; e += NT) {
-        int ch = e / ((L + 1) * CH);
-        int r = e % ((L + 1) * CH);
-        ctl[e] = a.tails[(tile + ch) * (L + 1) * CH + r];
-      }
       __syncthreads();
 
       uint32_t alive = 0;  // bit 4*ai + bi: pair (query 4tq+ai, cand 4tc+bi)
@@ -527,10 +522,26 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
           st_bytes += bytes;
           st_tile_levels += 1;
         }
-        for (int e = tid; e < QB * w; e += NT) {
-          int g = e / w, j = e % w;
-          qs[j * (QB + 4) + g] = g < G ? a.qt[(int64_t)qid[g] * d + m + j] : 0.f;
+        // the tile's tail column for level l+1 and the group's query slice:
+        // all loads are issued before any is used (one latency round)
+        float tail_v = 0.f;
+        if (tid < CB && tid / CH < nch)
+          tail_v = a.tails[((tile + tid / CH) * (L + 1) + l + 1) * CH + (tid % CH)];
+        for (int e0 = 0; e0 < QB * w; e0 += NT * 8) {
+          float v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int e = e0 + tid + u * NT;
+            const int g = e / w, j = e - (e / w) * w;
+            v[u] = (e < QB * w && g < G) ? a.qt[(int64_t)qid[g] * d + m + j] : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int e = e0 + tid + u * NT;
+            if (e < QB * w) qs[(e % w) * (QB + 4) + e / w] = v[u];
+          }
         }
+        if (tid < CB) ctl[tid] = tail_v;
         __syncthreads();
         if (tid < NCH) chunk_live[tid] = 0;  // read by thread 0 above
         if (!mbar_wait_bounded(&bar, phase)) {
@@ -584,7 +595,7 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
                 if (!(alive & bit)) continue;
                 const int e = 4 * tc + bi;
                 const float nx = xn2s[e], rx = rxs[e];
-                const float sx = ctl[((size_t)my_ch * (L + 1) + l + 1) * CH + my_i + bi];
+                const float sx = ctl[e];
                 const float A = nq + nx - 2.f * p[ai][bi];
                 const float C = sq * sx;
                 const float S = rq + rx;
@@ -953,6 +964,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
       ta.gslack = (float)(std::ldexp(1.0, -16) + (d / 8.0) * std::ldexp(1.0, -20) +
                           2.0 * gamma_n(L + 8));
       ta.lb_scale = (float)((1.0 - 8.0 * kU32) / (1.0 + I.eta));
+      ta.ub_scale = (float)((1.0 + 8.0 * kU32) / (1.0 - I.eta) * (1.0 + 1e-7));
       ta.prune = mode == 0 ? 1 : 0;
       ta.collect = collect ? 1 : 0;
       for (int l = 0; l <= L; ++l) ta.level_off[l] = I.offs[l];

@@ -9,14 +9,14 @@
 // norms, norms and error bounds are those of the dequantised vector
 // x^ = bf16(x~), with e_x bounding ||x^ - T~(x - mu~)||.
 //
-// Work item: (list, segment of <= 8 chunks, group of <= 64 queries).  The CTA
+// Work item: (list, segment of <= 4 chunks, group of <= 64 queries).  The CTA
 // walks the segment level by level (the paper's batch: every candidate moves
 // one level before the next level starts, the threshold is refreshed per
 // level).  Per (chunk, level) the partial products of all 128 candidates x
 // the group's queries are one MMA chain: A = level tile of the chunk, B = the
 // queries' level slices split into bf16 hi + lo parts (two MMAs into the same
-// accumulator), accumulated across levels in tensor memory (8 chunks x 64
-// columns = all 512 TMEM columns).  The epilogue thread of TMEM lane t owns
+// accumulator), accumulated across levels in tensor memory (4 chunks x 64
+// columns = 256 TMEM columns; two CTAs share an SM).  The epilogue thread of TMEM lane t owns
 // candidate row t: it reads its accumulators with tcgen05.ld and applies the
 // separable form of the margined Eq. 3 test, which costs three FMAs and a
 // compare per (candidate, query) pair.  Dead rows are not re-staged: at deep
@@ -39,7 +39,7 @@ namespace {
 
 constexpr int CH = TC_CHUNK;  // 128 rows (MMA M)
 constexpr int QG = TC_QG;     // 64 queries per group (MMA N, padded to 16)
-constexpr int S = TC_SEG;     // chunks per segment (8 x 64 = 512 TMEM columns)
+constexpr int S = TC_SEG;     // chunks per segment (4 x 64 = 256 TMEM columns)
 constexpr int NBUF = 3;       // staged A tiles in flight
 constexpr int NT = 128;       // thread t <-> TMEM lane t <-> chunk row t
 
@@ -114,18 +114,24 @@ __global__ void __launch_bounds__(256) pack_bf16_kernel(
 }
 
 // ------------------------------------------------------------------ search
+constexpr int TMEM_COLS = S * QG;  // 256: two CTAs can share an SM's tensor memory
+
 struct Smem {
   uint32_t abytes, bbytes;
   uint32_t off_b_hi, off_b_lo, off_alive, off_cand, off_q, off_surv, total;
   __host__ __device__ Smem(int max_w) {
-    abytes = (uint32_t)(CH * max_w * 2 + 1023) & ~1023u;
+    // A buffers double as the [QG][CH] upper-bound scratch of the last level
+    uint32_t a = (uint32_t)(CH * max_w * 2);
+    const uint32_t ub_need = (uint32_t)(QG * CH * 4 + NBUF - 1) / NBUF;
+    if (a < ub_need) a = ub_need;
+    abytes = (a + 1023) & ~1023u;
     bbytes = (uint32_t)(QG * max_w * 2 + 1023) & ~1023u;
     off_b_hi = NBUF * abytes;
     off_b_lo = off_b_hi + bbytes;
     off_alive = off_b_lo + bbytes;                   // [S][CH][2] u32
     off_cand = off_alive + S * CH * 2 * 4;           // 5 x [S][CH] (Hx, rx, ex, id, sx)
-    off_q = off_cand + 5 * S * CH * 4;               // 9 x [QG]
-    off_surv = off_q + 9 * QG * 4;                   // [CH * QG] u16
+    off_q = off_cand + 5 * S * CH * 4;               // 10 x [QG]
+    off_surv = off_q + 10 * QG * 4;                  // [CH * QG] u16
     total = off_surv + CH * QG * 2;
   }
 };
@@ -138,7 +144,7 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t& bits, int b,
   return false;
 }
 
-__global__ void __launch_bounds__(NT, 1) verify_tc_kernel(const VerifyTCArgs a) {
+__global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   const Smem lay(a.max_w);
@@ -160,6 +166,7 @@ __global__ void __launch_bounds__(NT, 1) verify_tc_kernel(const VerifyTCArgs a) 
   float* qsq = qH + QG;
   float* qgr = qsq + QG;
   float* qE = qgr + QG;
+  float* qtau = qE + QG;
   uint16_t* surv = reinterpret_cast<uint16_t*>(base + lay.off_surv);
   __shared__ __align__(8) uint64_t load_bar[NBUF], mma_bar[NBUF];
   __shared__ uint32_t tmem_base;
@@ -169,7 +176,7 @@ __global__ void __launch_bounds__(NT, 1) verify_tc_kernel(const VerifyTCArgs a) 
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
   if (warp == 0) {
-    tc::tmem_alloc(&tmem_base, 512);
+    tc::tmem_alloc(&tmem_base, TMEM_COLS);
     tc::tmem_relinquish();
   }
   if (tid == 0) {
@@ -184,11 +191,23 @@ __global__ void __launch_bounds__(NT, 1) verify_tc_kernel(const VerifyTCArgs a) 
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = tmem_base;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
   const int L = a.L, d = a.d;
   uint32_t load_bits = 0, mma_bits = 0;
   unsigned long long st_pairs = 0, st_dims = 0, st_tiles = 0, st_bytes = 0, st_rerank = 0;
   const float g_slack = a.gslack;
   constexpr float kEval = 32.f * 5.9604645e-08f;  // evaluation slack of the separable test
+
+  // per-query terms of the separable test for threshold tau (thread g < QG)
+  auto set_query_terms = [&](int g, float tau, float sq) {
+    const float st = tau == INFINITY ? 1e18f : fminf(__fsqrt_ru(__fdiv_ru(tau, a.lb_scale)), 1e18f);
+    const float E = __fadd_ru(qeq[g], st);
+    const float nq = qnq[g], rq = qrq[g];
+    qH[g] = 0.5f * (nq - g_slack * nq - E * E - kEval * (rq + E) * (rq + E));
+    qE[g] = E;
+    qsq[g] = sq;
+    qgr[g] = g_slack * rq;
+  };
 
   while (true) {
     if (tid == 0) s_item = atomicAdd(a.counter, 1);
@@ -252,58 +271,13 @@ __global__ void __launch_bounds__(NT, 1) verify_tc_kernel(const VerifyTCArgs a) 
     for (int l = 0; l < L; ++l) {
       const int m = a.level_off[l], w = a.level_off[l + 1] - m;
       const bool test = a.prune || l == L - 1;
-      // threshold refresh and per-query terms of the separable test
-      if (tid < QG) {
-        float H = -INFINITY, E = 0.f, sq = 0.f, gr = 0.f;
-        const int q = qid[tid];
-        if (q >= 0 && qk[tid] > 0) {
-          unsigned long long key =
-              ld_volatile_u64(a.topk + (int64_t)q * a.k_max + qk[tid] - 1);
-          float tau = key == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key), 1.000001f);
-          tau = fminf(tau, a.tau_seed[q]);
-          float st = tau == INFINITY ? 1e18f : fminf(__fsqrt_ru(__fdiv_ru(tau, a.lb_scale)), 1e18f);
-          E = __fadd_ru(qeq[tid], st);
-          const float nq = qnq[tid], rq = qrq[tid];
-          H = 0.5f * (nq - g_slack * nq - E * E - kEval * (rq + E) * (rq + E));
-          sq = a.qtail[(int64_t)q * (L + 1) + l + 1];
-          gr = g_slack * rq;
-        }
-        qH[tid] = H;
-        qE[tid] = E;
-        qsq[tid] = sq;
-        qgr[tid] = gr;
-      }
-      for (int e = tid; e < nch * CH; e += NT)
-        csx[e] = a.tails[((ch0 + e / CH) * (L + 1) + l + 1) * CH + (e % CH)];
-      // B tiles: the group's level-l query slices as bf16 hi / lo
-      for (int e = tid; e < Npad * (w / 8); e += NT) {
-        const int g = e / (w / 8), c8 = e % (w / 8);
-        __align__(16) __nv_bfloat16 hi[8], lo[8];
-        if (g < G) {
-          const float* src = a.qt + (int64_t)qid[g] * d + m + c8 * 8;
-          const float4 f0 = *reinterpret_cast<const float4*>(src);
-          const float4 f1 = *reinterpret_cast<const float4*>(src + 4);
-          const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
-#pragma unroll
-          for (int j = 0; j < 8; ++j) tc::split_bf16(f[j], hi[j], lo[j]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) hi[j] = lo[j] = __float2bfloat16_rn(0.f);
-        }
-        const uint32_t off = tc::swz_offset(g, c8 * 8, Npad, w);
-        *reinterpret_cast<uint4*>(bhi + off) = *reinterpret_cast<const uint4*>(hi);
-        *reinterpret_cast<uint4*>(blo + off) = *reinterpret_cast<const uint4*>(lo);
-      }
-      fence_proxy_async_smem();
       if (tid == 0) {
         int n = 0;
         for (int c = 0; c < nch; ++c)
           if (rowlive[c][0] | rowlive[c][1] | rowlive[c][2] | rowlive[c][3]) live_list[n++] = c;
         s_nlive = n;
       }
-      tc::fence_before_sync();
       __syncthreads();
-      tc::fence_after_sync();
       const int nlive = s_nlive;
       if (nlive == 0) {
         completed = false;
@@ -349,8 +323,58 @@ __global__ void __launch_bounds__(NT, 1) verify_tc_kernel(const VerifyTCArgs a) 
         }
         tc::mma_commit(&mma_bar[b]);
       };
+      // the first tiles are in flight while the query tiles are built
       if (warp == 0)
         for (int i = 0; i < nlive && i < NBUF; ++i) issue_load(i);
+      // candidates' tail norms after level l (all loads issued first)
+      {
+        float tv[S * CH / NT];
+#pragma unroll
+        for (int u = 0; u < S * CH / NT; ++u) {
+          const int e = tid + u * NT;
+          tv[u] = e < nch * CH ? a.tails[((ch0 + e / CH) * (L + 1) + l + 1) * CH + (e % CH)] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < S * CH / NT; ++u) csx[tid + u * NT] = tv[u];
+      }
+      // threshold refresh: running top-k and the warm-start seed
+      if (tid < QG) {
+        const int q = qid[tid];
+        if (q >= 0 && qk[tid] > 0) {
+          unsigned long long key = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + qk[tid] - 1);
+          float tau = key == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key), 1.000001f);
+          tau = fminf(tau, a.tau_seed[q]);
+          qtau[tid] = tau;
+          set_query_terms(tid, tau, a.qtail[(int64_t)q * (L + 1) + l + 1]);
+        } else {
+          qtau[tid] = -1.f;
+          qH[tid] = -INFINITY;
+          qE[tid] = qsq[tid] = qgr[tid] = 0.f;
+        }
+      }
+      // B tiles: the group's level-l query slices as bf16 hi / lo
+      for (int e = tid; e < Npad * (w / 8); e += NT) {
+        const int g = e / (w / 8), c8 = e % (w / 8);
+        __align__(16) __nv_bfloat16 hi[8], lo[8];
+        if (g < G) {
+          const float* src = a.qt + (int64_t)qid[g] * d + m + c8 * 8;
+          const float4 f0 = *reinterpret_cast<const float4*>(src);
+          const float4 f1 = *reinterpret_cast<const float4*>(src + 4);
+          const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+#pragma unroll
+          for (int j = 0; j < 8; ++j) tc::split_bf16(f[j], hi[j], lo[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) hi[j] = lo[j] = __float2bfloat16_rn(0.f);
+        }
+        const uint32_t off = tc::swz_offset(g, c8 * 8, Npad, w);
+        *reinterpret_cast<uint4*>(bhi + off) = *reinterpret_cast<const uint4*>(hi);
+        *reinterpret_cast<uint4*>(blo + off) = *reinterpret_cast<const uint4*>(lo);
+      }
+      fence_proxy_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
       if (tid == 0) {
         if (wait_phase(&load_bar[0], load_bits, 0, &s_fail)) issue_mma(0);
       }
@@ -368,7 +392,6 @@ __global__ void __launch_bounds__(NT, 1) verify_tc_kernel(const VerifyTCArgs a) 
         const bool any_warp =
             __any_sync(0xffffffffu, (w0 | w1) != 0) && __all_sync(0xffffffffu, ok);
         if (any_warp) {
-          const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
           const float sx = csx[c * CH + tid], rx = crx[c * CH + tid], exv = cex[c * CH + tid];
           const float Hx = cHx[c * CH + tid];
           if (a.collect) {
@@ -416,11 +439,74 @@ __global__ void __launch_bounds__(NT, 1) verify_tc_kernel(const VerifyTCArgs a) 
     }
     if (s_fail) break;
     if (!completed) continue;
-    // survivors of all levels: exact distances on the original rows
+
+    // Last level done: per chunk, the k-th smallest upper bound of each
+    // query tightens its threshold (at the last level UB ~ LB ~ exact), then
+    // the pairs are tested again, so only ~k per query reach re-ranking.
+    float* ub = reinterpret_cast<float*>(abuf);  // [QG][CH]
+    for (int c = 0; c < nch; ++c) {
+      if (!(rowlive[c][0] | rowlive[c][1] | rowlive[c][2] | rowlive[c][3])) continue;
+      const uint32_t w0 = alive[(c * CH + tid) * 2], w1 = alive[(c * CH + tid) * 2 + 1];
+      const bool any_warp = __any_sync(0xffffffffu, (w0 | w1) != 0);
+      if (any_warp) {
+        const float rx = crx[c * CH + tid], exv = cex[c * CH + tid];
+        const float nx2 = a.xn2[(ch0 + c) * CH + tid];
+        float v[32];
+        for (int half = 0; half < (Npad > 32 ? 2 : 1); ++half) {
+          tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
+          const uint32_t wm = half ? w1 : w0;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int g = 32 * half + j;
+            float u = INFINITY;
+            if ((wm >> j) & 1u) {
+              const float A = qnq[g] + nx2 - 2.f * v[j];
+              const float Ss = qrq[g] + rx;
+              const float r = __fadd_ru(__fsqrt_ru(fmaxf(A + g_slack * Ss * Ss, 0.f)),
+                                        qeq[g] + exv);
+              u = __fmul_ru(__fmul_ru(r, r), a.ub_scale);
+            }
+            ub[g * CH + tid] = u;
+          }
+        }
+        if (Npad <= 32)
+          for (int g = 32; g < 64; ++g) ub[g * CH + tid] = INFINITY;
+      } else {
+        for (int g = 0; g < 64; ++g) ub[g * CH + tid] = INFINITY;
+      }
+      __syncthreads();
+      for (int g = warp; g < G; g += NT / 32) {
+        const float t = warp_kth_smallest(ub + g * CH, CH, qk[g]);
+        if (lane == 0 && t < qtau[g]) qtau[g] = t;
+      }
+      __syncthreads();
+    }
+    if (tid < G && qk[tid] > 0) set_query_terms(tid, qtau[tid], 0.f);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    // survivors of the tightened test: exact distances on the original rows
     for (int c = 0; c < nch; ++c) {
       if (tid == 0) s_nsurv = 0;
+      uint32_t w0 = alive[(c * CH + tid) * 2], w1 = alive[(c * CH + tid) * 2 + 1];
+      const bool any_warp = __any_sync(0xffffffffu, (w0 | w1) != 0);
+      if (any_warp) {
+        const float rx = crx[c * CH + tid], exv = cex[c * CH + tid], Hx = cHx[c * CH + tid];
+        float v[32];
+        for (int half = 0; half < (Npad > 32 ? 2 : 1); ++half) {
+          tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
+          uint32_t& wm = half ? w1 : w0;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int g = 32 * half + j;
+            if ((wm >> j) & 1u) {
+              const float P = fmaf(qE[g], exv, fmaf(qgr[g], rx, v[j]));
+              if (P < qH[g] + Hx) wm &= ~(1u << j);
+            }
+          }
+        }
+      }
       __syncthreads();
-      const uint32_t w0 = alive[(c * CH + tid) * 2], w1 = alive[(c * CH + tid) * 2 + 1];
       for (int g = 0; g < 64; ++g) {
         const uint32_t bit = g < 32 ? (w0 >> g) & 1u : (w1 >> (g - 32)) & 1u;
         if (bit) surv[atomicAdd(&s_nsurv, 1)] = (uint16_t)((tid << 6) | g);
@@ -436,8 +522,13 @@ __global__ void __launch_bounds__(NT, 1) verify_tc_kernel(const VerifyTCArgs a) 
           topk_insert(a.topk + (int64_t)q * a.k_max, qk[g], make_key(dist, cid[c * CH + row]));
       }
       st_rerank += (tid == 0) ? ns : 0;
+      tc::fence_before_sync();
       __syncthreads();
+      tc::fence_after_sync();
     }
+    // the scratch written through the generic proxy is refilled by
+    // bulk-async copies in the next item
+    fence_proxy_async_smem();
   }
   if (s_fail && tid == 0) atomicOr(a.err, kErrTimeout);
   if (a.collect) {
@@ -459,7 +550,7 @@ __global__ void __launch_bounds__(NT, 1) verify_tc_kernel(const VerifyTCArgs a) 
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tbase, 512);
+  if (warp == 0) tc::tmem_dealloc(tbase, TMEM_COLS);
 }
 
 }  // namespace
@@ -476,8 +567,8 @@ int launch_pack_bf16(const float* xt, const float* rows, const int64_t* perm, in
 }
 
 size_t verify_tc_smem(int max_w) {
-  // keep one CTA per SM: the CTA owns all 512 TMEM columns
-  return std::max<size_t>(Smem(max_w).total + 1024, 120 * 1024);
+  // at most two CTAs per SM: each owns 256 of the 512 TMEM columns
+  return std::max<size_t>(Smem(max_w).total + 1024, 80 * 1024);
 }
 
 int launch_verify_tc(const VerifyTCArgs& a, cudaStream_t st) {
@@ -495,10 +586,13 @@ int launch_verify_tc(const VerifyTCArgs& a, cudaStream_t st) {
   });
   PANO_CUDA(attr_err);
   const size_t smem = verify_tc_smem(a.max_w);
-  int dev = 0, sms = 0;
+  int dev = 0, sms = 0, bps = 0;
   PANO_CUDA(cudaGetDevice(&dev));
   PANO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  verify_tc_kernel<<<sms, NT, smem, st>>>(a);
+  PANO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, verify_tc_kernel, NT, smem));
+  if (bps < 1) return fail(PANO_EINVAL, "tensor-core verify tile does not fit in shared memory");
+  bps = std::min(bps, 2);  // two CTAs x 256 TMEM columns fill the SM's tensor memory
+  verify_tc_kernel<<<sms * bps, NT, smem, st>>>(a);
   PANO_CUDA(cudaGetLastError());
   return PANO_OK;
 }

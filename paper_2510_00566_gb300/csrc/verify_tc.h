@@ -7,7 +7,7 @@ namespace pano {
 
 constexpr int TC_CHUNK = 128;  // vectors per chunk (MMA M)
 constexpr int TC_QG = 64;      // queries per group (MMA N, padded to 16)
-constexpr int TC_SEG = 8;      // chunks per work-item segment
+constexpr int TC_SEG = 4;      // chunks per work-item segment
 
 struct VerifyTCArgs {
   const uint8_t* slices;
@@ -34,6 +34,7 @@ struct VerifyTCArgs {
   int d, L, max_w, k_max;
   float gslack;    // |computed - exact| terms of the bound <= gslack (|q~|+|x^|)^2
   float lb_scale;  // (1 - 8u) / (1 + eta)
+  float ub_scale;  // (1 + 8u) / (1 - eta)
   int prune;
   int collect;
   int32_t level_off[65];

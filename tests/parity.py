@@ -53,3 +53,22 @@ def check_topk(X, Q, got_ids, got_d, ref_ids, ref_d, k, gamma_rows=None,
 
 def gamma_of(lists_of_vector, probes):
     return [np.nonzero(np.isin(lists_of_vector, p))[0] for p in probes]
+
+
+def oracle_dims_fraction(X, Q, C, lists, nprobe, widths, k, B=1024):
+    """Fraction of coordinates Algorithm 1 (the oracle) reads, averaged over
+    the queries Q, with each query's nearest list first (as the GPU's phase
+    A) and the PCA transform fitted on (up to) 65,536 rows of X."""
+    import oracle
+    d = X.shape[1]
+    probes, _ = oracle.probe(Q, C, nprobe)
+    mu, T, _ = oracle.pca_fit(X[:65536])
+    tX = oracle.transform(T, mu, X)
+    m = oracle.level_thresholds(d, widths)
+    fr = []
+    for i in range(len(Q)):
+        order = np.concatenate([np.nonzero(lists == p)[0] for p in probes[i]])
+        tq = oracle.transform(T, mu, Q[i:i + 1])[0]
+        _, _, rho = oracle.refine(tq, tX[order], order, m, k, B=B)
+        fr.append(rho.mean() / d)
+    return float(np.mean(fr))

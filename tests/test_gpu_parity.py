@@ -11,7 +11,7 @@ import torch
 import oracle
 import paper_2510_00566_gb300 as pano
 import synth
-from parity import check_topk, gamma_of
+from parity import check_topk, gamma_of, oracle_dims_fraction
 
 pytestmark = pytest.mark.gpu
 
@@ -55,8 +55,11 @@ def test_flat_128d_workload_matches_oracle(mode):
                               ref["ids"], ref["dists"], 10)
     assert st.pairs == 20_000 * 100
     if mode == 0:
-        # pruning reads a fraction of the levels (Table 2: ~1/alpha)
-        assert st.pair_levels < 0.6 * st.pairs * 8
+        # pruning at least about as effective as the oracle's Algorithm 1
+        frac = st.dims_scanned / (st.pairs * 128)
+        ref = oracle_dims_fraction(X, Q[:20], np.zeros((1, 128)),
+                                   np.zeros(len(X), dtype=np.int64), 1, [16] * 8, 10)
+        assert frac <= 1.2 * ref + 0.02, (frac, ref)
     else:
         assert st.pair_levels == st.pairs * 8
 

@@ -9,7 +9,7 @@ import torch
 import oracle
 import paper_2510_00566_gb300 as pano
 import synth
-from parity import check_topk, gamma_of
+from parity import check_topk, gamma_of, oracle_dims_fraction
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -50,13 +50,18 @@ def test_bf16_768d_single_gaussian(mode):
     s = synth.scaled(3, n=30_000, n_queries=120, nlist=32)
     w = synth.generate(s)
     C = synth.initial_centroids(w.X, 32, seed=3003).numpy()
-    st, *_ = _ivf(s, C, [64] * 12, nprobe=4, k=10, mode=mode)
+    st, idx, X, Q = _ivf(s, C, [64] * 12, nprobe=4, k=10, mode=mode)
     assert st.device_error == 0
+    if mode == 1:
+        assert st.dims_scanned == st.pairs * 768
+        return
+    # pruning at least about as effective as the oracle's Algorithm 1
+    idx.search(torch.from_numpy(Q[:20]).to(DEV), 4, 10, collect_stats=True)
+    st = pano.last_stats()
     frac = st.dims_scanned / (st.pairs * 768)
-    if mode == 0:
-        assert frac < 0.4, st.as_dict()
-    else:
-        assert frac == 1.0
+    lists, _ = oracle.assign(X, C)
+    ref = oracle_dims_fraction(X, Q[:20], C, lists, 4, [64] * 12, 10)
+    assert frac <= 1.2 * ref + 0.02, (frac, ref)
 
 
 def test_bf16_128d_narrow_levels_large_groups():
