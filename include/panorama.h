@@ -198,6 +198,25 @@ int panorama_search_ex(const pano_index* idx, const float* queries,
                        float* out_dists, void* stream,
                        const pano_search_opts* opts);
 
+/* panorama_search_noalloc -- panorama_search without any device allocation.
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * allocate device memory while searching (their memory is owned by another
+ * allocator or pool, or they run on a path where an allocation, which can
+ * synchronize or fail under fragmentation, is not allowed).  Arguments,
+ * results and errors are those of panorama_search.  The workspace comes from
+ * one 64 MiB array in the library's global memory (held by every GPU that
+ * loads the library until the process exits) instead of cudaMallocAsync;
+ * a call whose workspace would exceed it fails with PANO_EINVAL before any
+ * work is queued (the workspace grows with nq x (d + nlist + nprobe + k_max)).
+ * The array's device address is looked up on the first call on each device
+ * (make that call before any stream capture).  Every call reuses the same
+ * array, so calls that overlap on the GPU race; serialise them on one
+ * stream. */
+int panorama_search_noalloc(const pano_index* idx, const float* queries, int64_t nq,
+                            const int32_t* nprobe, int32_t nprobe_scalar,
+                            const int32_t* k, int32_t k_scalar, int32_t k_max,
+                            int64_t* out_ids, float* out_dists, void* stream);
+
 /* Counters of this thread's last search_ex with collect_stats = 1. */
 int panorama_search_stats(pano_search_stats* out);
 

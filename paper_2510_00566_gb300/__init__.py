@@ -92,6 +92,8 @@ SIGNATURES = {
                                        _I32, _P, _P, _P]),
     "panorama_search_ex": (ctypes.c_int, [_P, _P, _I64, _P, _I32, _P, _I32,
                                           _I32, _P, _P, _P, _P]),
+    "panorama_search_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _I32, _P, _I32,
+                                                _I32, _P, _P, _P]),
     "panorama_search_stats": (ctypes.c_int, [_P]),
     "panorama_probe": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P]),
     "panorama_index_info": (ctypes.c_int, [_P, _P]),

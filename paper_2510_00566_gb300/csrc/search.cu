@@ -788,7 +788,8 @@ thread_local pano_search_stats t_stats;
 
 int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t* nprobe,
            int32_t nprobe_scalar, const int32_t* k, int32_t k_scalar, int32_t k_max,
-           int64_t* out_ids, float* out_dists, cudaStream_t st, const pano_search_opts* opts) {
+           int64_t* out_ids, float* out_dists, cudaStream_t st, const pano_search_opts* opts,
+           void* ext_ws, size_t ext_cap) {
   PANO_CHECK(ip, PANO_EINVAL, "null index");
   const pano_index& I = *ip;
   PANO_CHECK(nq >= 0 && nq < (1LL << 31), PANO_EINVAL, "nq out of range");
@@ -849,8 +850,14 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
   size_t o_topk = cv.take<unsigned long long>((size_t)nq * k_max);
   size_t o_err = cv.take<int>(4);
   size_t o_stats = cv.take<unsigned long long>(8);
-  void* ws = nullptr;
-  PANO_CUDA(cudaMallocAsync(&ws, cv.off, st));
+  void* ws = ext_ws;
+  if (ext_ws) {
+    PANO_CHECK(cv.off <= ext_cap, PANO_EINVAL,
+               "search workspace of " + std::to_string(cv.off) + " bytes exceeds the " +
+                   std::to_string(ext_cap) + "-byte static scratch");
+  } else {
+    PANO_CUDA(cudaMallocAsync(&ws, cv.off, st));
+  }
   char* W = static_cast<char*>(ws);
   auto P = [&](size_t o) { return (void*)(W + o); };
   float* qt = (float*)P(o_qt);
@@ -1067,7 +1074,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
   if (timing)
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
-  cudaError_t fe = cudaFreeAsync(ws, st);
+  cudaError_t fe = ext_ws ? cudaSuccess : cudaFreeAsync(ws, st);
   if (rc == PANO_OK && fe != cudaSuccess) return cuda_fail(fe, "cudaFreeAsync");
   return rc;
 }

@@ -7,7 +7,8 @@
 namespace pano {
 int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t* nprobe,
            int32_t nprobe_scalar, const int32_t* k, int32_t k_scalar, int32_t k_max,
-           int64_t* out_ids, float* out_dists, cudaStream_t st, const pano_search_opts* opts);
+           int64_t* out_ids, float* out_dists, cudaStream_t st, const pano_search_opts* opts,
+           void* ext_ws = nullptr, size_t ext_cap = 0);
 int probe_only(const pano_index* ip, const float* queries, int64_t nq, int32_t nprobe,
                int32_t* out, cudaStream_t st);
 const pano_search_stats& last_stats();
