@@ -90,6 +90,8 @@ typedef struct {
   int32_t query_group; /* max queries sharing one tile (0 = automatic)      */
   int32_t collect_timing; /* 1 = record CUDA events around each stage on
                              `stream` (stage_ms in the stats; implies a wait) */
+  int32_t single_phase;   /* 1 = verify every probed list in one pass; 0 =
+                             each query's nearest list first (default)      */
 } pano_search_opts;
 
 /* Counters of the most recent search through this index from this thread
@@ -112,6 +114,12 @@ typedef struct {
    * [4] verify phase B (remaining lists), [5] result decode */
   float stage_ms[6];
   float pad2_[2];
+  /* device cycles (summed over the verify CTAs' first threads, collect_stats
+   * = 1) spent in: [0] work-item prologue, [1] MMA issue (tensor-core path)
+   * or slice staging, [2] epilogues (bound tests), [3] next-level staging,
+   * [4] last-level upper-bound filter, [5] exact re-ranking, [6] whole
+   * kernel, [7] number of CTAs that ran */
+  int64_t section_cycles[8];
 } pano_search_stats;
 
 /* Description of a built index. */
@@ -225,6 +233,93 @@ int panorama_search_stats(pano_search_stats* out);
  *   queries: device nq x d; out_lists: device nq x nprobe int32, ascending. */
 int panorama_probe(const pano_index* idx, const float* queries, int64_t nq,
                    int32_t nprobe, int32_t* out_lists, void* stream);
+
+/* ------------------------------------------------------------- batching
+ * A plan is one search of a fixed batch shape captured into a CUDA graph:
+ * workspace allocation, memsets, transform and probe GEMMs, work inversion,
+ * the two persistent verify kernels and the decode replay with a single
+ * cudaGraphLaunch (SURVEY "persistent graph-captured scheduler").
+ * panorama_plan_create runs the search once eagerly (so kernel attributes
+ * are settled), then captures it on a private stream.  The device pointers
+ * (queries, nprobe, k, out_ids, out_dists) are baked into the graph: every
+ * launch reads their current contents and overwrites the outputs.  mode as
+ * in pano_search_opts.  Device-side errors are not reported by launches;
+ * use panorama_search_ex to diagnose.  The index must outlive the plan.
+ * Errors: those of panorama_search, plus PANO_ECUDA for capture failures. */
+typedef struct pano_plan pano_plan;
+int panorama_plan_create(const pano_index* idx, const float* queries, int64_t nq,
+                         const int32_t* nprobe, int32_t nprobe_scalar,
+                         const int32_t* k, int32_t k_scalar, int32_t k_max,
+                         int64_t* out_ids, float* out_dists, int32_t mode,
+                         pano_plan** out);
+int panorama_plan_launch(pano_plan* plan, void* stream);
+void panorama_plan_free(pano_plan* plan);
+
+/* panorama_autotune_levels -- picks the level split (L and widths, the
+ * paper's L ablation of Section 7.5) that searches a sample fastest.
+ *   X: host or device n x d rows to index (a sample of the data set);
+ *   queries: device nq x d sample queries; nlist / nprobe / k / precision as
+ *   in the build and search calls;
+ *   widths: the candidates' widths concatenated, candidate c has
+ *   n_levels[c] widths summing to d; repeats: timed searches per candidate
+ *   (after one warm-up; the median counts).
+ *   Every candidate is built with the centroids of the first one (k-means
+ *   runs once) and timed with CUDA events on `stream`.  *best receives the
+ *   fastest candidate's index, ms_out[c] (optional) its median ms (+inf when
+ *   the split cannot be built, e.g. a bf16 width other than 16, 32 or a
+ *   multiple of 64). */
+int panorama_autotune_levels(const pano_transform* t, const float* X, int64_t n,
+                             const float* queries, int64_t nq, int32_t nlist,
+                             int32_t nprobe, int32_t k, int32_t precision,
+                             const int32_t* widths, const int32_t* n_levels,
+                             int32_t n_candidates, int32_t repeats, int32_t* best,
+                             float* ms_out, void* stream);
+
+/* -------------------------------------------------------------- serving
+ * A server batches single-query requests continuously over a device-resident
+ * index.  A worker thread owns max_inflight slots (stream, pinned staging,
+ * device buffers for max_batch queries); whenever a slot is free, requests
+ * are queued and the memory budget admits the batch (estimated search
+ * workspace + slot buffers, always admitted when nothing runs), up to
+ * max_batch queued requests are copied in and searched on the slot's
+ * stream.  Batches in different slots overlap on the device; requests that
+ * arrive meanwhile go to the next free slot.  Each result is the exact top-k
+ * of its own query (identical whatever it was batched with).  Latency is
+ * measured from submit to results on the host. */
+typedef struct pano_server pano_server;
+typedef struct {
+  int32_t max_batch;     /* queries per device batch (default 1024)           */
+  int32_t max_inflight;  /* concurrent device batches (default 2, <= 16)      */
+  int32_t k_max;         /* result row length (default 10)                    */
+  int32_t pad_;
+  int64_t memory_budget; /* device bytes for in-flight batches (default 1 GiB)*/
+} pano_server_opts;
+typedef struct {
+  int64_t submitted, completed, batches;
+  double mean_batch;     /* queries per launched batch                        */
+  double p50_us, p99_us, max_us; /* request latency (last 10^6 requests)      */
+  double qps;            /* completed / (last completion - first submit)      */
+} pano_server_stats;
+/* idx must outlive the server; opts may be NULL. */
+int panorama_server_create(const pano_index* idx, const pano_server_opts* opts,
+                           pano_server** out);
+/* query: host, d FP32 values (copied); 1 <= nprobe <= nlist, 0 <= k <= k_max. */
+int panorama_server_submit(pano_server* s, const float* query, int32_t nprobe,
+                           int32_t k, uint64_t* ticket);
+/* Blocks until the request is done (PANO_ETIMEOUT after timeout_ms; < 0 =
+ * no limit) and copies k_max ids / distances (host) and its latency. */
+int panorama_server_wait(pano_server* s, uint64_t ticket, int32_t timeout_ms,
+                         int64_t* ids, float* dists, double* latency_us);
+int panorama_server_stats(pano_server* s, pano_server_stats* out);
+/* Open-loop replay: submits query i (host nq x d) at arrival_us[i]
+ * microseconds after the call starts, then collects every result
+ * (out_ids / out_dists host nq x k_max) and its latency (optional). */
+int panorama_server_run_trace(pano_server* s, const float* queries, int64_t nq,
+                              const double* arrival_us, const int32_t* nprobe,
+                              const int32_t* k, int64_t* out_ids, float* out_dists,
+                              double* latency_us);
+/* Finishes queued work, then releases the server. */
+void panorama_server_free(pano_server* s);
 
 /* ------------------------------------------------------ index inspection */
 int panorama_index_info(const pano_index* idx, pano_index_info* out);

@@ -48,7 +48,8 @@ class SearchOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("synchronize", ctypes.c_int32),
                 ("collect_stats", ctypes.c_int32),
                 ("query_group", ctypes.c_int32),
-                ("collect_timing", ctypes.c_int32)]
+                ("collect_timing", ctypes.c_int32),
+                ("single_phase", ctypes.c_int32)]
 
 
 class SearchStats(ctypes.Structure):
@@ -59,15 +60,19 @@ class SearchStats(ctypes.Structure):
                 ("slice_bytes", ctypes.c_int64),
                 ("reranked", ctypes.c_int64), ("work_items", ctypes.c_int64),
                 ("device_error", ctypes.c_int32), ("pad_", ctypes.c_int32),
-                ("stage_ms", ctypes.c_float * 6), ("pad2_", ctypes.c_float * 2)]
+                ("stage_ms", ctypes.c_float * 6), ("pad2_", ctypes.c_float * 2),
+                ("section_cycles", ctypes.c_int64 * 8)]
 
     STAGES = ("transform", "probe", "inversion", "verify_a", "verify_b",
               "decode")
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_
-             if not f.startswith("pad") and f != "stage_ms"}
+             if not f.startswith("pad") and f not in ("stage_ms", "section_cycles")}
         d["stage_ms"] = dict(zip(self.STAGES, list(self.stage_ms)))
+        d["section_cycles"] = dict(zip(("prologue", "mma_issue", "epilogue", "next_level",
+                                        "ub_filter", "rerank", "kernel", "ctas"),
+                                       list(self.section_cycles)))
         return d
 
 
@@ -105,6 +110,19 @@ SIGNATURES = {
     "panorama_last_error": (ctypes.c_char_p, []),
     "panorama_version": (ctypes.c_char_p, []),
     "panorama_debug_tc_gemm": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _P]),
+    "panorama_plan_create": (ctypes.c_int, [_P, _P, _I64, _P, _I32, _P, _I32, _I32,
+                                            _P, _P, _I32, _P]),
+    "panorama_plan_launch": (ctypes.c_int, [_P, _P]),
+    "panorama_plan_free": (None, [_P]),
+    "panorama_server_create": (ctypes.c_int, [_P, _P, _P]),
+    "panorama_server_submit": (ctypes.c_int, [_P, _P, _I32, _I32, _P]),
+    "panorama_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, _I32, _P, _P, _P]),
+    "panorama_server_stats": (ctypes.c_int, [_P, _P]),
+    "panorama_server_run_trace": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P, _P, _P]),
+    "panorama_server_free": (None, [_P]),
+    "panorama_autotune_levels": (ctypes.c_int, [_P, _P, _I64, _P, _I64, _I32, _I32,
+                                                _I32, _I32, _P, _P, _I32, _I32, _P,
+                                                _P, _P]),
 }
 
 
@@ -191,7 +209,8 @@ def panorama_build_ivf(t: "Transform", X, nlist: int, n_levels=8,
 
 def panorama_search_ex(idx: "Index", queries, nprobe, k, k_max=None,
                        mode=0, collect_stats=False, synchronize=True,
-                       stream=None, out=None, collect_timing=False):
+                       stream=None, out=None, collect_timing=False,
+                       single_phase=False):
     """Returns (ids int64 [nq, k_max], dists float32 [nq, k_max]) on the GPU.
 
     nprobe / k: python ints, or CUDA int32 tensors with one value per query.
@@ -223,7 +242,8 @@ def panorama_search_ex(idx: "Index", queries, nprobe, k, k_max=None,
         ids, dists = out
     opts = SearchOpts(mode=mode, synchronize=1 if synchronize else 0,
                       collect_stats=1 if collect_stats else 0,
-                      collect_timing=1 if collect_timing else 0)
+                      collect_timing=1 if collect_timing else 0,
+                      single_phase=1 if single_phase else 0)
     _check(lib().panorama_search_ex(idx.handle, q.data_ptr(), nq, np_ptr,
                                     np_scalar, k_ptr, k_scalar, k_max,
                                     ids.data_ptr(), dists.data_ptr(),
@@ -266,6 +286,151 @@ def panorama_debug_tc_gemm(A, B, stream=None):
     _check(lib().panorama_debug_tc_gemm(A.data_ptr(), B.data_ptr(), N, K,
                                         D.data_ptr(), _stream_ptr(stream)))
     return D
+
+
+class Plan:
+    """One search of a fixed batch shape captured into a CUDA graph.
+
+    The tensors given here stay bound to the graph: refill ``queries`` (and
+    nprobe / k when they are tensors) in place, call ``launch()``, then read
+    ``ids`` / ``dists``."""
+
+    def __init__(self, idx: "Index", queries, nprobe, k, k_max=None, mode=0):
+        import torch
+        self.idx = idx
+        self.queries = queries
+        nq = queries.shape[0]
+        self._keep = []
+        np_ptr, np_scalar = None, 0
+        if isinstance(nprobe, torch.Tensor):
+            np_ptr, np_scalar = nprobe.data_ptr(), int(nprobe.max())
+            self._keep.append(nprobe)
+        else:
+            np_scalar = int(nprobe)
+        k_ptr, k_scalar = None, 0
+        if isinstance(k, torch.Tensor):
+            k_ptr = k.data_ptr()
+            self._keep.append(k)
+            k_max = k_max or int(k.max())
+        else:
+            k_scalar = int(k)
+            k_max = k_max or k_scalar
+        self.ids = torch.empty((nq, k_max), dtype=torch.int64, device=queries.device)
+        self.dists = torch.empty((nq, k_max), dtype=torch.float32, device=queries.device)
+        out = ctypes.c_void_p()
+        _check(lib().panorama_plan_create(idx.handle, queries.data_ptr(), nq, np_ptr,
+                                          np_scalar, k_ptr, k_scalar, k_max,
+                                          self.ids.data_ptr(), self.dists.data_ptr(),
+                                          mode, ctypes.byref(out)))
+        self.handle = out.value
+
+    def launch(self, stream=None):
+        _check(lib().panorama_plan_launch(self.handle, _stream_ptr(stream)))
+        return self.ids, self.dists
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.panorama_plan_free(self.handle)
+            self.handle = None
+
+
+def panorama_autotune_levels(t: "Transform", X, queries, nlist, nprobe, k,
+                             candidates, precision=PANO_FP32, repeats=3,
+                             stream=None):
+    """Index of the fastest candidate level split and every candidate's
+    median search time in ms (inf when it cannot be built)."""
+    import numpy as np
+    keep, ptr = _host_f32(X)
+    n = keep.shape[0]
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(c) for c in candidates]),
+                                dtype=np.int32)
+    lens = np.ascontiguousarray([len(c) for c in candidates], dtype=np.int32)
+    best = ctypes.c_int32(-1)
+    ms = np.zeros(len(candidates), dtype=np.float32)
+    q = queries.contiguous()
+    _check(lib().panorama_autotune_levels(t.handle, ptr, n, q.data_ptr(), q.shape[0],
+                                          nlist, nprobe, k, precision, flat.ctypes.data,
+                                          lens.ctypes.data, len(candidates), repeats,
+                                          ctypes.byref(best), ms.ctypes.data,
+                                          _stream_ptr(stream)))
+    return best.value, ms
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("k_max", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("memory_budget", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("mean_batch", ctypes.c_double),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+                ("max_us", ctypes.c_double), ("qps", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Server:
+    """Continuous-batching request server over an index (see panorama.h)."""
+
+    def __init__(self, idx: "Index", max_batch=1024, max_inflight=2, k_max=10,
+                 memory_budget=0):
+        self.idx = idx
+        self.k_max = k_max
+        self.d = idx.info().d
+        o = ServerOpts(max_batch=max_batch, max_inflight=max_inflight, k_max=k_max,
+                       memory_budget=memory_budget)
+        out = ctypes.c_void_p()
+        _check(lib().panorama_server_create(idx.handle, ctypes.byref(o), ctypes.byref(out)))
+        self.handle = out.value
+
+    def submit(self, query, nprobe, k):
+        import numpy as np
+        q = np.ascontiguousarray(query, dtype=np.float32)
+        t = ctypes.c_uint64()
+        _check(lib().panorama_server_submit(self.handle, q.ctypes.data, nprobe, k,
+                                            ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket, timeout_ms=60000):
+        import numpy as np
+        ids = np.empty(self.k_max, dtype=np.int64)
+        d = np.empty(self.k_max, dtype=np.float32)
+        lat = ctypes.c_double()
+        _check(lib().panorama_server_wait(self.handle, ticket, timeout_ms, ids.ctypes.data,
+                                          d.ctypes.data, ctypes.byref(lat)))
+        return ids, d, lat.value
+
+    def run_trace(self, queries, arrival_us, nprobe, k):
+        import numpy as np
+        Q = np.ascontiguousarray(queries, dtype=np.float32)
+        n = Q.shape[0]
+        arr = np.ascontiguousarray(arrival_us, dtype=np.float64)
+        npq = np.ascontiguousarray(np.broadcast_to(nprobe, (n,)), dtype=np.int32)
+        kq = np.ascontiguousarray(np.broadcast_to(k, (n,)), dtype=np.int32)
+        ids = np.empty((n, self.k_max), dtype=np.int64)
+        d = np.empty((n, self.k_max), dtype=np.float32)
+        lat = np.empty(n, dtype=np.float64)
+        _check(lib().panorama_server_run_trace(self.handle, Q.ctypes.data, n, arr.ctypes.data,
+                                               npq.ctypes.data, kq.ctypes.data,
+                                               ids.ctypes.data, d.ctypes.data,
+                                               lat.ctypes.data))
+        return ids, d, lat
+
+    def stats(self):
+        s = ServerStats()
+        _check(lib().panorama_server_stats(self.handle, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.panorama_server_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
 
 
 def last_stats() -> SearchStats:

@@ -112,6 +112,31 @@ __device__ __forceinline__ void topk_insert(unsigned long long* slots, int k,
   }
 }
 
+// topk_insert issued by a whole warp: the slots are read once in parallel
+// (one round instead of a chain of dependent reads) to find the first slot
+// not below the key; lane 0 then runs the compare-exchange chain from there.
+// All 32 lanes must call it with the same arguments.
+__device__ __forceinline__ void topk_insert_warp(unsigned long long* slots, int k,
+                                                 unsigned long long key) {
+  const int lane = threadIdx.x & 31;
+  int start = k;
+  for (int j0 = 0; j0 < k; j0 += 32) {
+    const int j = j0 + lane;
+    const bool ge = j < k && ld_volatile_u64(slots + j) >= key;
+    const unsigned m = __ballot_sync(0xffffffffu, ge);
+    if (m) {
+      start = j0 + __ffs(m) - 1;
+      break;
+    }
+  }
+  if (lane == 0)
+    for (int j = start; j < k; ++j) {
+      unsigned long long old = atomicMin(slots + j, key);
+      if (old == kEmptyKey) return;
+      key = old > key ? old : key;
+    }
+}
+
 // Order-preserving map of any FP32 value to uint32.
 __device__ __forceinline__ uint32_t float_ordered(float f) {
   uint32_t u = __float_as_uint(f);

@@ -102,6 +102,29 @@ __device__ __forceinline__ float warp_kth_smallest(const float* vals, int nv, in
   return __uint_as_float(lo);
 }
 
+// k-th smallest of nv non-negative bf16 bit patterns (+inf = 0x7f80 for
+// absent entries) by one warp; same search as warp_kth_smallest on 16 bits.
+// Returns the value as FP32 (+inf when fewer than k are finite).
+__device__ __forceinline__ float warp_kth_smallest_bf16(const uint16_t* vals, int nv, int k) {
+  const int lane = threadIdx.x & 31;
+  int finite = 0;
+  for (int i = lane; i < nv; i += 32) finite += vals[i] < 0x7f80u;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) finite += __shfl_xor_sync(0xffffffffu, finite, off);
+  if (k <= 0 || finite < k) return INFINITY;
+  uint32_t lo = 0, hi = 0x7f80u;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    int cnt = 0;
+    for (int i = lane; i < nv; i += 32) cnt += vals[i] <= mid;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+    if (cnt >= k) hi = mid;
+    else lo = mid + 1;
+  }
+  return __uint_as_float(lo << 16);
+}
+
 __device__ __forceinline__ double warp_sum_f64(double v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);

@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(NT) probe_select_kernel(
 // ------------------------------------------------------- a3: work inversion
 __global__ void inv_count_kernel(int64_t nq, const int32_t* __restrict__ probes, int stride,
                                  const int32_t* __restrict__ npq, int* __restrict__ cnt,
-                                 int nlist) {
+                                 int nlist, int first_rank_b) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nq * stride) return;
   int64_t qi = e / stride;
@@ -195,7 +195,7 @@ __global__ void inv_count_kernel(int64_t nq, const int32_t* __restrict__ probes,
   if (r >= npq[qi]) return;
   int c = probes[e];
   if (c < 0) return;
-  atomicAdd(&cnt[(r == 0 ? 0 : nlist) + c], 1);
+  atomicAdd(&cnt[(r < first_rank_b ? 0 : nlist) + c], 1);
 }
 
 // Single CTA: exclusive scans of bucket sizes and of work items per list for
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(1024) inv_scan_kernel(const int* __restrict__ 
 __global__ void inv_scatter_kernel(int64_t nq, const int32_t* __restrict__ probes, int stride,
                                    const int32_t* __restrict__ npq, const int* __restrict__ boff,
                                    const int* __restrict__ totals, int* __restrict__ fill,
-                                   int nlist, int32_t* __restrict__ bucket) {
+                                   int nlist, int first_rank_b, int32_t* __restrict__ bucket) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nq * stride) return;
   int64_t qi = e / stride;
@@ -263,7 +263,7 @@ __global__ void inv_scatter_kernel(int64_t nq, const int32_t* __restrict__ probe
   if (r >= npq[qi]) return;
   int c = probes[e];
   if (c < 0) return;
-  int ph = r == 0 ? 0 : 1;
+  int ph = r < first_rank_b ? 0 : 1;
   int base = ph == 1 ? totals[0] : 0;  // phase-B buckets follow the phase-A ones
   int pos = base + boff[ph * (nlist + 1) + c] + atomicAdd(&fill[ph * nlist + c], 1);
   bucket[pos] = (int32_t)qi;
@@ -300,7 +300,7 @@ __global__ void inv_emit_kernel(int ph, const int* __restrict__ cnt, int nlist,
 }
 
 // ------------------------------------------------- Alg. 1 warm start (a6)
-// Per query: exact distances to the first max(2k, 32) (at most 256) members
+// Per query: exact distances to the first max(4k, 64) (at most 256) members
 // of its nearest list; the k-th smallest (rounded up) is an upper bound on
 // d_k and seeds the threshold before any tile is verified (Algorithm 1
 // initialises d_k from the first k candidates).  The seeds are not inserted
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(128) seed_tau_kernel(
   const int k = kq[row];
   const int c = probes[row * stride];
   const int n = c >= 0 ? list_size[c] : 0;
-  const int ns = min(n, min(kSeedMax, max(2 * k, 32)));
+  const int ns = min(n, min(kSeedMax, max(4 * k, 64)));
   if (k <= 0 || ns < k) {
     if (threadIdx.x == 0) tau_seed[row] = k <= 0 ? -1.f : INFINITY;
     return;
@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
         const int q = qid[g];
         const int64_t slot = (tile + e / CH) * CH + (e % CH);
         float dist = exact_sqdist_warp(a.qorig + (int64_t)q * d, a.rows + slot * d, d);
-        if (lane == 0) topk_insert(a.topk + (int64_t)q * a.k_max, qk[g], make_key(dist, ids_s[e]));
+        topk_insert_warp(a.topk + (int64_t)q * a.k_max, qk[g], make_key(dist, ids_s[e]));
       }
       st_rerank += (tid == 0) ? ns : 0;
       __syncthreads();
@@ -757,15 +757,20 @@ int launch_verify(const VerifyArgs& a, size_t smem, cudaStream_t st) {
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   auto kern = verify_fp32_kernel<QB, CB>;
-  std::call_once(once, [&] { attr_err = allow_dynamic_smem((const void*)kern); });
+  std::call_once(once, [&] {
+    attr_err = allow_dynamic_smem((const void*)kern);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  });
   PANO_CUDA(attr_err);
-  int bps = 0;
-  PANO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, NT, smem));
-  if (bps < 1) return fail(PANO_EINVAL, "verify tile does not fit in shared memory");
-  int dev = 0, sms = 0;
+  int dev = 0, sms = 0, optin = 0;
   PANO_CUDA(cudaGetDevice(&dev));
   PANO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  kern<<<sms * bps, NT, smem, st>>>(a);
+  PANO_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (smem > (size_t)optin) return fail(PANO_EINVAL, "verify tile does not fit in shared memory");
+  // two CTAs per SM (the register budget); sized directly, not from the
+  // occupancy API, whose answer follows the SM's current carveout
+  kern<<<sms * 2, NT, smem, st>>>(a);
   PANO_CUDA(cudaGetLastError());
   return PANO_OK;
 }
@@ -827,7 +832,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     tot_seg += s;
   }
   const int64_t capA = ((nq + QBA - 1) / QBA) * max_seg + tot_seg;
-  const int64_t capB = ((nq * std::max(0, stride - 1) + QBB - 1) / QBB) * max_seg + tot_seg;
+  const int64_t capB = ((nq * stride + QBB - 1) / QBB) * max_seg + tot_seg;
 
   Carver cv;
   size_t o_qt = cv.take<float>((size_t)nq * d);
@@ -849,7 +854,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
   size_t o_itB = cv.take<int4>(std::max<int64_t>(capB, 1));
   size_t o_topk = cv.take<unsigned long long>((size_t)nq * k_max);
   size_t o_err = cv.take<int>(4);
-  size_t o_stats = cv.take<unsigned long long>(8);
+  size_t o_stats = cv.take<unsigned long long>(16);
   void* ws = ext_ws;
   if (ext_ws) {
     PANO_CHECK(cv.off <= ext_cap, PANO_EINVAL,
@@ -892,7 +897,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     PANO_CUDA(cudaMemsetAsync(tot, 0, 8 * 4, st));  // [4..5] verify counters
     PANO_CUDA(cudaMemsetAsync(topk, 0xff, (size_t)nq * k_max * 8, st));
     PANO_CUDA(cudaMemsetAsync(err, 0, 16, st));
-    PANO_CUDA(cudaMemsetAsync(stats, 0, 64, st));
+    PANO_CUDA(cudaMemsetAsync(stats, 0, 128, st));
     prep_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(nq, nprobe, nprobe_scalar, np_cap, k,
                                                               k_scalar, k_max, npq, kq, err);
     PANO_CUDA(cudaGetLastError());
@@ -928,12 +933,13 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
                                                   I.rows.as<float>(), kq, tau_seed);
     PANO_CUDA(cudaGetLastError());
     const int64_t ne = nq * stride;
+    const int first_rank_b = (opts && opts->single_phase) ? 0 : 1;
     inv_count_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(nq, probes, stride, npq, cnt,
-                                                                   nlist);
+                                                                   nlist, first_rank_b);
     inv_scan_kernel<<<1, 1024, 0, st>>>(cnt, nlist, I.chunk_off_d.as<int64_t>(), SEG, QBA, QBB,
                                         boff, ioff, tot);
-    inv_scatter_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(nq, probes, stride, npq, boff,
-                                                                     tot, fillc, nlist, bucket);
+    inv_scatter_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+        nq, probes, stride, npq, boff, tot, fillc, nlist, first_rank_b, bucket);
     PANO_CUDA(cudaGetLastError());
     inv_emit_kernel<<<1024, 256, 0, st>>>(0, cnt, nlist, I.chunk_off_d.as<int64_t>(), SEG, QBA,
                                           boff, ioff, tot, capA, itA, err);
@@ -1050,10 +1056,10 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     }
     if (sync || collect) {
       int herr[4];
-      unsigned long long hst[8];
+      unsigned long long hst[16];
       int htot[8];
       PANO_CUDA(cudaMemcpyAsync(herr, err, 16, cudaMemcpyDeviceToHost, st));
-      PANO_CUDA(cudaMemcpyAsync(hst, stats, 64, cudaMemcpyDeviceToHost, st));
+      PANO_CUDA(cudaMemcpyAsync(hst, stats, 128, cudaMemcpyDeviceToHost, st));
       PANO_CUDA(cudaMemcpyAsync(htot, tot, 32, cudaMemcpyDeviceToHost, st));
       PANO_CUDA(cudaStreamSynchronize(st));
       t_stats.pair_levels = (int64_t)hst[0];
@@ -1064,6 +1070,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
       t_stats.work_items = (int64_t)htot[1] + htot[3];
       t_stats.device_error = herr[0];
       t_stats.dims_scanned = (int64_t)hst[5];
+      for (int i = 0; i < 8; ++i) t_stats.section_cycles[i] = (int64_t)hst[8 + i];
       if (timing)
         for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&t_stats.stage_ms[i], ev[i], ev[i + 1]);
       if (herr[0] & kErrTimeout) return fail(PANO_ETIMEOUT, "a device-side wait timed out");

@@ -40,7 +40,6 @@ namespace {
 constexpr int CH = TC_CHUNK;  // 128 rows (MMA M)
 constexpr int QG = TC_QG;     // 64 queries per group (MMA N, padded to 16)
 constexpr int S = TC_SEG;     // chunks per segment (4 x 64 = 256 TMEM columns)
-constexpr int NBUF = 3;       // staged A tiles in flight
 constexpr int NT = 128;       // thread t <-> TMEM lane t <-> chunk row t
 
 // ------------------------------------------------------------------ build
@@ -114,25 +113,36 @@ __global__ void __launch_bounds__(256) pack_bf16_kernel(
 }
 
 // ------------------------------------------------------------------ search
-constexpr int TMEM_COLS = S * QG;  // 256: two CTAs can share an SM's tensor memory
+// One work item = (list, segment of S chunks, group of <= QG queries).  Each
+// chunk owns an A buffer; a chunk that stays live after level l has its
+// level-(l+1) tile staged right after its epilogue, while the other chunks
+// of level l are still being tested.  A level therefore starts with every
+// live chunk's tile resident: one thread issues all their MMAs back to back,
+// and the epilogues follow as the accumulators complete.  The next level's
+// query slices, tail norms and threshold terms are loaded into registers at
+// the start of a level and written to shared memory at its end.
+constexpr int TMEM_COLS = S * QG;  // 256: two CTAs share an SM's tensor memory
+constexpr int AW = (QG + 31) / 32;  // alive-mask words per candidate row
+constexpr int PF_CHUNKS = 4;        // 16-byte query chunks prefetched per thread
+static_assert(QG <= 64 && AW <= 2 && TMEM_COLS <= 256, "two CTAs per SM");
 
 struct Smem {
   uint32_t abytes, bbytes;
-  uint32_t off_b_hi, off_b_lo, off_alive, off_cand, off_q, off_surv, total;
+  uint32_t off_b_hi, off_b_lo, off_alive, off_cand, off_q, total;
   __host__ __device__ Smem(int max_w) {
-    // A buffers double as the [QG][CH] upper-bound scratch of the last level
+    // after the last level the A buffers hold the [QG][S*CH] bf16 upper
+    // bounds, then the [CH * QG] survivor list
     uint32_t a = (uint32_t)(CH * max_w * 2);
-    const uint32_t ub_need = (uint32_t)(QG * CH * 4 + NBUF - 1) / NBUF;
-    if (a < ub_need) a = ub_need;
+    const uint32_t per = (uint32_t)(QG * S * CH * 2 + S - 1) / S;
+    if (a < per) a = per;
     abytes = (a + 1023) & ~1023u;
     bbytes = (uint32_t)(QG * max_w * 2 + 1023) & ~1023u;
-    off_b_hi = NBUF * abytes;
+    off_b_hi = S * abytes;
     off_b_lo = off_b_hi + bbytes;
-    off_alive = off_b_lo + bbytes;                   // [S][CH][2] u32
-    off_cand = off_alive + S * CH * 2 * 4;           // 5 x [S][CH] (Hx, rx, ex, id, sx)
-    off_q = off_cand + 5 * S * CH * 4;               // 10 x [QG]
-    off_surv = off_q + 10 * QG * 4;                  // [CH * QG] u16
-    total = off_surv + CH * QG * 2;
+    off_alive = off_b_lo + bbytes;                   // [S][CH][AW] u32
+    off_cand = off_alive + S * CH * AW * 4;          // 5 x [S][CH] (Hx, rx, ex, id, sx)
+    off_q = off_cand + 5 * S * CH * 4;               // [QG] float4 + 6 x [QG]
+    total = off_q + 10 * QG * 4;
   }
 };
 
@@ -157,21 +167,19 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   float* cex = crx + S * CH;
   int32_t* cid = reinterpret_cast<int32_t*>(cex + S * CH);
   float* csx = reinterpret_cast<float*>(cid + S * CH);
-  int32_t* qid = reinterpret_cast<int32_t*>(base + lay.off_q);
+  // per-query terms of the separable test: (E, g*rq, sq, H)
+  float4* qterm = reinterpret_cast<float4*>(base + lay.off_q);  // [QG]
+  int32_t* qid = reinterpret_cast<int32_t*>(qterm + QG);
   int32_t* qk = qid + QG;
   float* qnq = reinterpret_cast<float*>(qk + QG);
   float* qrq = qnq + QG;
   float* qeq = qrq + QG;
-  float* qH = qeq + QG;
-  float* qsq = qH + QG;
-  float* qgr = qsq + QG;
-  float* qE = qgr + QG;
-  float* qtau = qE + QG;
-  uint16_t* surv = reinterpret_cast<uint16_t*>(base + lay.off_surv);
-  __shared__ __align__(8) uint64_t load_bar[NBUF], mma_bar[NBUF];
+  float* qtau = qeq + QG;
+  uint16_t* ub16 = reinterpret_cast<uint16_t*>(abuf);  // [QG][S*CH] bf16 bits
+  uint16_t* surv = reinterpret_cast<uint16_t*>(abuf);  // [CH * QG], after ub16 is read
+  __shared__ __align__(8) uint64_t load_bar[S], mma_bar[S];
   __shared__ uint32_t tmem_base;
-  __shared__ int s_item, s_nlive, s_nsurv, s_fail;
-  __shared__ int live_list[S];
+  __shared__ int s_item, s_nsurv, s_fail;
   __shared__ uint32_t rowlive[S][4];
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
@@ -180,9 +188,9 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    for (int b = 0; b < NBUF; ++b) {
-      mbar_init(&load_bar[b], 1);
-      mbar_init(&mma_bar[b], 1);
+    for (int c = 0; c < S; ++c) {
+      mbar_init(&load_bar[c], 1);
+      mbar_init(&mma_bar[c], 1);
     }
     fence_mbar_init();
     s_fail = 0;
@@ -195,18 +203,30 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   const int L = a.L, d = a.d;
   uint32_t load_bits = 0, mma_bits = 0;
   unsigned long long st_pairs = 0, st_dims = 0, st_tiles = 0, st_bytes = 0, st_rerank = 0;
+  unsigned long long sec[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // section cycles (thread 0)
+  const long long t_kernel = clock64();
+  long long t_mark = t_kernel;
+  auto section = [&](int i) {  // charge the time since the last mark to section i
+    if (a.collect && tid == 0) {
+      const long long now = clock64();
+      sec[i] += (unsigned long long)(now - t_mark);
+      t_mark = now;
+    }
+  };
   const float g_slack = a.gslack;
   constexpr float kEval = 32.f * 5.9604645e-08f;  // evaluation slack of the separable test
 
-  // per-query terms of the separable test for threshold tau (thread g < QG)
+  // threshold -> per-query terms of the separable test (thread g < QG)
   auto set_query_terms = [&](int g, float tau, float sq) {
     const float st = tau == INFINITY ? 1e18f : fminf(__fsqrt_ru(__fdiv_ru(tau, a.lb_scale)), 1e18f);
     const float E = __fadd_ru(qeq[g], st);
     const float nq = qnq[g], rq = qrq[g];
-    qH[g] = 0.5f * (nq - g_slack * nq - E * E - kEval * (rq + E) * (rq + E));
-    qE[g] = E;
-    qsq[g] = sq;
-    qgr[g] = g_slack * rq;
+    qterm[g] = make_float4(E, g_slack * rq, sq,
+                           0.5f * (nq - g_slack * nq - E * E - kEval * (rq + E) * (rq + E)));
+    qtau[g] = tau;
+  };
+  auto chunk_live = [&](int c) {
+    return (rowlive[c][0] | rowlive[c][1] | rowlive[c][2] | rowlive[c][3]) != 0u;
   };
 
   while (true) {
@@ -215,6 +235,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     const int item = s_item;
     const int64_t n_items = *a.n_items < a.items_cap ? *a.n_items : a.items_cap;
     if (item >= n_items || s_fail) break;
+    if (tid == 0) t_mark = clock64();
     const int4 it = a.items[item];
     const int64_t ch0 = a.chunk_off[it.x] + (int64_t)it.y * S;
     const int64_t chE = a.chunk_off[it.x + 1];
@@ -222,6 +243,63 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     const int G = it.w;
     const int Npad = G <= 16 ? 16 : ((G + 15) & ~15);
     const uint32_t idesc = tc::idesc_bf16(CH, Npad);
+    const uint8_t* item_src = a.slices + ch0 * (int64_t)CH * d * 2;
+
+    // stage chunk c's level-l tile (live rows only when few rows live)
+    auto issue_load = [&](int c, int l) {  // warp 0
+      const int m = a.level_off[l], w = a.level_off[l + 1] - m;
+      const uint32_t tbytes = (uint32_t)w * CH * 2;
+      const int rb = tc::row_bytes(w), npan = w >= 64 ? w / 64 : 1;
+      unsigned char* dst = abuf + (size_t)c * lay.abytes;
+      const uint8_t* src = item_src + (int64_t)c * CH * d * 2 + (size_t)m * CH * 2;
+      uint32_t atoms = 0;  // 8-row groups holding a live row
+      for (int t = 0; t < 16; ++t)
+        if ((rowlive[c][t >> 2] >> ((t & 3) * 8)) & 0xffu) atoms |= 1u << t;
+      const int na = __popc(atoms);
+      if (l == 0 || na * 4 >= 3 * 16) {
+        if (lane == 0) {
+          mbar_arrive_expect_tx(&load_bar[c], tbytes);
+          bulk_g2s(dst, src, tbytes, &load_bar[c]);
+        }
+        st_bytes += (lane == 0) ? tbytes : 0;
+      } else {
+        const uint32_t abytes_row = (uint32_t)(8 * rb);  // one 8-row atom of one panel
+        if (lane == 0) mbar_arrive_expect_tx(&load_bar[c], (uint32_t)na * npan * abytes_row);
+        __syncwarp();
+        for (int t = lane; t < 16 * npan; t += 32) {
+          const int at = t % 16, p = t / 16;
+          if ((atoms >> at) & 1u) {
+            const uint32_t o = (uint32_t)p * CH * 128 + (uint32_t)at * abytes_row;
+            bulk_g2s(dst + o, src + o, abytes_row, &load_bar[c]);
+          }
+        }
+        st_bytes += (lane == 0) ? (unsigned long long)na * npan * abytes_row : 0;
+      }
+    };
+    // B tiles for level l: query slices split into bf16 hi / lo
+    auto build_b = [&](int l, int first_chunk) {
+      const int m = a.level_off[l], w = a.level_off[l + 1] - m;
+      for (int e = tid + first_chunk * NT; e < Npad * (w / 8); e += NT) {
+        const int g = e / (w / 8), c8 = e % (w / 8);
+        __align__(16) __nv_bfloat16 hi[8], lo[8];
+        if (g < G) {
+          const float* src = a.qt + (int64_t)qid[g] * d + m + c8 * 8;
+          const float4 f0 = *reinterpret_cast<const float4*>(src);
+          const float4 f1 = *reinterpret_cast<const float4*>(src + 4);
+          const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+#pragma unroll
+          for (int j = 0; j < 8; ++j) tc::split_bf16(f[j], hi[j], lo[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) hi[j] = lo[j] = __float2bfloat16_rn(0.f);
+        }
+        const uint32_t off = tc::swz_offset(g, c8 * 8, Npad, w);
+        *reinterpret_cast<uint4*>(bhi + off) = *reinterpret_cast<const uint4*>(hi);
+        *reinterpret_cast<uint4*>(blo + off) = *reinterpret_cast<const uint4*>(lo);
+      }
+    };
+
+    // ---- item prologue: group, candidates, liveness, level-0 tiles
     if (tid < QG) {
       int q = tid < G ? a.bucket[it.z + tid] : -1;
       qid[tid] = q;
@@ -246,269 +324,287 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         crx[e] = rx;
         cex[e] = exv;
         cid[e] = a.ids[slot];
+        csx[e] = a.tails[((ch0 + c) * (L + 1) + 1) * CH + (e % CH)];
       } else {
-        cHx[e] = crx[e] = cex[e] = 0.f;
+        cHx[e] = crx[e] = cex[e] = csx[e] = 0.f;
         cid[e] = -1;
       }
     }
     __syncthreads();
-    // initial liveness: valid candidate x query with k > 0
-    uint32_t gm0 = 0, gm1 = 0;
-    for (int g = 0; g < G; ++g)
-      if (qk[g] > 0) {
-        if (g < 32) gm0 |= 1u << g;
-        else gm1 |= 1u << (g - 32);
+    {
+      uint32_t gm0 = 0, gm1 = 0;
+      for (int g = 0; g < G; ++g)
+        if (qk[g] > 0) {
+          if (g < 32) gm0 |= 1u << g;
+          else gm1 |= 1u << (g - 32);
+        }
+      for (int c = 0; c < S; ++c) {
+        const bool v = c < nch && cid[c * CH + tid] >= 0;
+        alive[(c * CH + tid) * AW] = v ? gm0 : 0u;
+        if (AW > 1) alive[(c * CH + tid) * AW + AW - 1] = v ? gm1 : 0u;
+        const unsigned bal = __ballot_sync(0xffffffffu, v && (gm0 | gm1));
+        if (lane == 0) rowlive[c][warp] = bal;
       }
-    for (int c = 0; c < S; ++c) {
-      const bool v = c < nch && cid[c * CH + tid] >= 0;
-      alive[(c * CH + tid) * 2] = v ? gm0 : 0u;
-      alive[(c * CH + tid) * 2 + 1] = v ? gm1 : 0u;
-      const unsigned bal = __ballot_sync(0xffffffffu, v && (gm0 | gm1));
-      if (lane == 0) rowlive[c][warp] = bal;
     }
-    bool completed = true;
-
-    for (int l = 0; l < L; ++l) {
-      const int m = a.level_off[l], w = a.level_off[l + 1] - m;
-      const bool test = a.prune || l == L - 1;
-      if (tid == 0) {
-        int n = 0;
-        for (int c = 0; c < nch; ++c)
-          if (rowlive[c][0] | rowlive[c][1] | rowlive[c][2] | rowlive[c][3]) live_list[n++] = c;
-        s_nlive = n;
+    __syncthreads();
+    if (warp == 0)
+      for (int c = 0; c < nch; ++c)
+        if (chunk_live(c)) issue_load(c, 0);
+    if (tid < QG) {
+      const int q = qid[tid];
+      if (q >= 0 && qk[tid] > 0) {
+        unsigned long long key = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + qk[tid] - 1);
+        float tau = key == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key), 1.000001f);
+        set_query_terms(tid, fminf(tau, a.tau_seed[q]), a.qtail[(int64_t)q * (L + 1) + 1]);
+      } else {
+        qterm[tid] = make_float4(0.f, 0.f, 0.f, -INFINITY);
+        qtau[tid] = -1.f;
       }
-      __syncthreads();
-      const int nlive = s_nlive;
-      if (nlive == 0) {
+    }
+    build_b(0, 0);
+    fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+
+    bool completed = true;
+    section(0);
+    for (int l = 0; l < L; ++l) {
+      const int w = a.level_off[l + 1] - a.level_off[l];
+      const bool test = a.prune || l == L - 1;
+      const bool has_next = l + 1 < L;
+      uint32_t live_mask = 0;
+      for (int c = 0; c < nch; ++c)
+        if (chunk_live(c)) live_mask |= 1u << c;
+      if (!live_mask) {
         completed = false;
         break;
       }
-      const uint8_t* lvl_src = a.slices + (size_t)m * CH * 2;
-      const uint32_t tbytes = (uint32_t)w * CH * 2;
-      const int rb = tc::row_bytes(w), npan = w >= 64 ? w / 64 : 1;
-      // warp 0 stages live chunk i of this level into buffer i % NBUF
-      auto issue_load = [&](int i) {
-        const int c = live_list[i], b = i % NBUF;
-        unsigned char* dst = abuf + (size_t)b * lay.abytes;
-        const uint8_t* src = lvl_src + (ch0 + c) * (int64_t)CH * d * 2;
-        const int nrows = __popc(rowlive[c][0]) + __popc(rowlive[c][1]) +
-                          __popc(rowlive[c][2]) + __popc(rowlive[c][3]);
-        if (nrows * 2 >= CH || l == 0) {
-          if (lane == 0) {
-            mbar_arrive_expect_tx(&load_bar[b], tbytes);
-            bulk_g2s(dst, src, tbytes, &load_bar[b]);
-          }
-          st_bytes += (lane == 0) ? tbytes : 0;
-        } else {
-          if (lane == 0) mbar_arrive_expect_tx(&load_bar[b], (uint32_t)nrows * w * 2);
-          __syncwarp();
-          for (int r = lane; r < CH; r += 32)
-            if ((rowlive[c][r >> 5] >> (r & 31)) & 1u)
-              for (int p = 0; p < npan; ++p) {
-                const uint32_t o = (uint32_t)p * CH * 128 + (uint32_t)r * rb;
-                bulk_g2s(dst + o, src + o, (uint32_t)rb, &load_bar[b]);
-              }
-          st_bytes += (lane == 0) ? (unsigned long long)nrows * w * 2 : 0;
-        }
-      };
-      auto issue_mma = [&](int i) {
-        const int c = live_list[i], b = i % NBUF;
-        const uint32_t a0 = smem_u32(abuf + (size_t)b * lay.abytes);
+      // every live chunk's tile is resident or in flight: issue all MMAs
+      if (tid == 0) {
         const uint32_t h0 = smem_u32(bhi), l0 = smem_u32(blo);
-        const uint32_t dt = tbase + (uint32_t)(c * QG);
-        for (int s = 0; s < w / 16; ++s) {
-          const uint64_t ad = tc::kstep_desc(a0, s, CH, w);
-          tc::mma_bf16(dt, ad, tc::kstep_desc(h0, s, Npad, w), idesc, (l > 0 || s > 0) ? 1u : 0u);
-          tc::mma_bf16(dt, ad, tc::kstep_desc(l0, s, Npad, w), idesc, 1u);
+        for (int c = 0; c < nch; ++c) {
+          if (!((live_mask >> c) & 1u)) continue;
+          if (!wait_phase(&load_bar[c], load_bits, c, &s_fail)) continue;
+          const uint32_t a0 = smem_u32(abuf + (size_t)c * lay.abytes);
+          const uint32_t dt = tbase + (uint32_t)(c * QG);
+          for (int s = 0; s < w / 16; ++s) {
+            const uint64_t ad = tc::kstep_desc(a0, s, CH, w);
+            tc::mma_bf16(dt, ad, tc::kstep_desc(h0, s, Npad, w), idesc,
+                         (l > 0 || s > 0) ? 1u : 0u);
+            tc::mma_bf16(dt, ad, tc::kstep_desc(l0, s, Npad, w), idesc, 1u);
+          }
+          tc::mma_commit(&mma_bar[c]);
         }
-        tc::mma_commit(&mma_bar[b]);
-      };
-      // the first tiles are in flight while the query tiles are built
-      if (warp == 0)
-        for (int i = 0; i < nlive && i < NBUF; ++i) issue_load(i);
-      // candidates' tail norms after level l (all loads issued first)
-      {
-        float tv[S * CH / NT];
+        st_tiles += __popc(live_mask);
+      }
+      section(1);
+      // prefetch the next level's query slices, tails and thresholds
+      float4 pf[2 * PF_CHUNKS];
+      float tail_pf[S * CH / NT];
+      unsigned long long key_pf = kEmptyKey;
+      float seed_pf = INFINITY, sq_pf = 0.f;
+      int m1 = 0, w1 = 16;
+      if (has_next) {
+        m1 = a.level_off[l + 1];
+        w1 = a.level_off[l + 2] - m1;
+#pragma unroll
+        for (int i = 0; i < PF_CHUNKS; ++i) {
+          const int e = tid + i * NT;
+          const int g = e / (w1 / 8), c8 = e % (w1 / 8);
+          if (e < Npad * (w1 / 8) && g < G) {
+            const float* src = a.qt + (int64_t)qid[g] * d + m1 + c8 * 8;
+            pf[2 * i] = *reinterpret_cast<const float4*>(src);
+            pf[2 * i + 1] = *reinterpret_cast<const float4*>(src + 4);
+          } else {
+            pf[2 * i] = pf[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
 #pragma unroll
         for (int u = 0; u < S * CH / NT; ++u) {
           const int e = tid + u * NT;
-          tv[u] = e < nch * CH ? a.tails[((ch0 + e / CH) * (L + 1) + l + 1) * CH + (e % CH)] : 0.f;
+          tail_pf[u] = e < nch * CH
+                           ? a.tails[((ch0 + e / CH) * (L + 1) + l + 2) * CH + (e % CH)]
+                           : 0.f;
         }
-#pragma unroll
-        for (int u = 0; u < S * CH / NT; ++u) csx[tid + u * NT] = tv[u];
-      }
-      // threshold refresh: running top-k and the warm-start seed
-      if (tid < QG) {
-        const int q = qid[tid];
-        if (q >= 0 && qk[tid] > 0) {
-          unsigned long long key = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + qk[tid] - 1);
-          float tau = key == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key), 1.000001f);
-          tau = fminf(tau, a.tau_seed[q]);
-          qtau[tid] = tau;
-          set_query_terms(tid, tau, a.qtail[(int64_t)q * (L + 1) + l + 1]);
-        } else {
-          qtau[tid] = -1.f;
-          qH[tid] = -INFINITY;
-          qE[tid] = qsq[tid] = qgr[tid] = 0.f;
+        if (tid < QG) {
+          const int q = qid[tid];
+          if (q >= 0 && qk[tid] > 0) {
+            key_pf = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + qk[tid] - 1);
+            seed_pf = a.tau_seed[q];
+            sq_pf = a.qtail[(int64_t)q * (L + 1) + l + 2];
+          }
         }
       }
-      // B tiles: the group's level-l query slices as bf16 hi / lo
-      for (int e = tid; e < Npad * (w / 8); e += NT) {
-        const int g = e / (w / 8), c8 = e % (w / 8);
-        __align__(16) __nv_bfloat16 hi[8], lo[8];
-        if (g < G) {
-          const float* src = a.qt + (int64_t)qid[g] * d + m + c8 * 8;
-          const float4 f0 = *reinterpret_cast<const float4*>(src);
-          const float4 f1 = *reinterpret_cast<const float4*>(src + 4);
-          const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
-#pragma unroll
-          for (int j = 0; j < 8; ++j) tc::split_bf16(f[j], hi[j], lo[j]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) hi[j] = lo[j] = __float2bfloat16_rn(0.f);
-        }
-        const uint32_t off = tc::swz_offset(g, c8 * 8, Npad, w);
-        *reinterpret_cast<uint4*>(bhi + off) = *reinterpret_cast<const uint4*>(hi);
-        *reinterpret_cast<uint4*>(blo + off) = *reinterpret_cast<const uint4*>(lo);
-      }
-      fence_proxy_async_smem();
-      tc::fence_before_sync();
-      __syncthreads();
-      tc::fence_after_sync();
-      if (tid == 0) {
-        if (wait_phase(&load_bar[0], load_bits, 0, &s_fail)) issue_mma(0);
-      }
-      st_tiles += (tid == 0) ? nlive : 0;
-      for (int i = 0; i < nlive; ++i) {
-        const int c = live_list[i], b = i % NBUF;
-        if (tid == 0 && i + 1 < nlive) {
-          const int b1 = (i + 1) % NBUF;
-          if (wait_phase(&load_bar[b1], load_bits, b1, &s_fail)) issue_mma(i + 1);
-        }
-        const bool ok = wait_phase(&mma_bar[b], mma_bits, b, &s_fail);
+      // epilogues in chunk order; a chunk that stays live restages at once
+      for (int c = 0; c < nch; ++c) {
+        if (!((live_mask >> c) & 1u)) continue;
+        const bool ok = wait_phase(&mma_bar[c], mma_bits, c, &s_fail);
         tc::fence_after_sync();
-        // epilogue: candidate row `tid` of chunk c against the group
-        uint32_t w0 = alive[(c * CH + tid) * 2], w1 = alive[(c * CH + tid) * 2 + 1];
+        uint32_t w0 = alive[(c * CH + tid) * AW];
+        uint32_t wv1 = AW > 1 ? alive[(c * CH + tid) * AW + AW - 1] : 0u;
         const bool any_warp =
-            __any_sync(0xffffffffu, (w0 | w1) != 0) && __all_sync(0xffffffffu, ok);
+            __any_sync(0xffffffffu, (w0 | wv1) != 0) && __all_sync(0xffffffffu, ok);
         if (any_warp) {
           const float sx = csx[c * CH + tid], rx = crx[c * CH + tid], exv = cex[c * CH + tid];
           const float Hx = cHx[c * CH + tid];
           if (a.collect) {
-            st_pairs += __popc(w0) + __popc(w1);
-            st_dims += (unsigned long long)(__popc(w0) + __popc(w1)) * w;
+            st_pairs += __popc(w0) + __popc(wv1);
+            st_dims += (unsigned long long)(__popc(w0) + __popc(wv1)) * w;
           }
           float v[32];
           tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG), v);
-          if (test) {
+          if (test && w0) {
 #pragma unroll
             for (int g = 0; g < 32; ++g)
               if ((w0 >> g) & 1u) {
-                const float P = fmaf(qE[g], exv, fmaf(qgr[g], rx, fmaf(qsq[g], sx, v[g])));
-                if (P < qH[g] + Hx) w0 &= ~(1u << g);
+                const float4 t = qterm[g];
+                const float P = fmaf(t.x, exv, fmaf(t.y, rx, fmaf(t.z, sx, v[g])));
+                if (P < t.w + Hx) w0 &= ~(1u << g);
               }
           }
-          if (Npad > 32) {
+          if (AW > 1 && Npad > 32) {
             tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32), v);
-            if (test) {
+            if (test && wv1) {
 #pragma unroll
               for (int g = 0; g < 32; ++g)
-                if ((w1 >> g) & 1u) {
-                  const float P =
-                      fmaf(qE[g + 32], exv, fmaf(qgr[g + 32], rx, fmaf(qsq[g + 32], sx, v[g])));
-                  if (P < qH[g + 32] + Hx) w1 &= ~(1u << g);
+                if ((wv1 >> g) & 1u) {
+                  const float4 t = qterm[g + 32];
+                  const float P = fmaf(t.x, exv, fmaf(t.y, rx, fmaf(t.z, sx, v[g])));
+                  if (P < t.w + Hx) wv1 &= ~(1u << g);
                 }
             }
           }
-          alive[(c * CH + tid) * 2] = w0;
-          alive[(c * CH + tid) * 2 + 1] = w1;
+          alive[(c * CH + tid) * AW] = w0;
+          if (AW > 1) alive[(c * CH + tid) * AW + AW - 1] = wv1;
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, (w0 | w1) != 0);
+        const unsigned bal = __ballot_sync(0xffffffffu, (w0 | wv1) != 0);
         if (lane == 0) rowlive[c][warp] = bal;
         tc::fence_before_sync();
         __syncthreads();
-        if (warp == 0) {
-          const int go = __shfl_sync(0xffffffffu, (i + NBUF < nlive && !s_fail) ? 1 : 0, 0);
-          if (go) issue_load(i + NBUF);
+        if (warp == 0 && has_next) {
+          const int go = __shfl_sync(0xffffffffu, (chunk_live(c) && !s_fail) ? 1 : 0, 0);
+          if (go) issue_load(c, l + 1);
         }
       }
+      section(2);
       if (s_fail) {
         completed = false;
         break;
       }
+      if (has_next) {
+        // next level's B tiles, tails and thresholds from the prefetch
+#pragma unroll
+        for (int i = 0; i < PF_CHUNKS; ++i) {
+          const int e = tid + i * NT;
+          if (e < Npad * (w1 / 8)) {
+            const int g = e / (w1 / 8), c8 = e % (w1 / 8);
+            const float f[8] = {pf[2 * i].x, pf[2 * i].y, pf[2 * i].z, pf[2 * i].w,
+                                pf[2 * i + 1].x, pf[2 * i + 1].y, pf[2 * i + 1].z,
+                                pf[2 * i + 1].w};
+            __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) tc::split_bf16(f[j], hi[j], lo[j]);
+            const uint32_t off = tc::swz_offset(g, c8 * 8, Npad, w1);
+            *reinterpret_cast<uint4*>(bhi + off) = *reinterpret_cast<const uint4*>(hi);
+            *reinterpret_cast<uint4*>(blo + off) = *reinterpret_cast<const uint4*>(lo);
+          }
+        }
+        if (Npad * (w1 / 8) > PF_CHUNKS * NT) build_b(l + 1, PF_CHUNKS);  // wide levels
+#pragma unroll
+        for (int u = 0; u < S * CH / NT; ++u) csx[tid + u * NT] = tail_pf[u];
+        if (tid < QG) {
+          if (qid[tid] >= 0 && qk[tid] > 0) {
+            float tau = key_pf == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key_pf), 1.000001f);
+            set_query_terms(tid, fminf(tau, seed_pf), sq_pf);
+          }
+        }
+        fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+      }
+      section(3);
     }
     if (s_fail) break;
     if (!completed) continue;
 
-    // Last level done: per chunk, the k-th smallest upper bound of each
-    // query tightens its threshold (at the last level UB ~ LB ~ exact), then
-    // the pairs are tested again, so only ~k per query reach re-ranking.
-    float* ub = reinterpret_cast<float*>(abuf);  // [QG][CH]
-    for (int c = 0; c < nch; ++c) {
-      if (!(rowlive[c][0] | rowlive[c][1] | rowlive[c][2] | rowlive[c][3])) continue;
-      const uint32_t w0 = alive[(c * CH + tid) * 2], w1 = alive[(c * CH + tid) * 2 + 1];
-      const bool any_warp = __any_sync(0xffffffffu, (w0 | w1) != 0);
+    // Last level done: the k-th smallest upper bound of each query over the
+    // whole segment tightens its threshold (at the last level UB ~ LB ~
+    // exact), then the pairs are tested again, so about k pairs per query
+    // reach re-ranking.  The bounds are kept as bf16 rounded up (still upper
+    // bounds) so that all S x CH of them fit next to each other.
+    for (int c = 0; c < S; ++c) {
+      uint32_t w0 = 0, wv1 = 0;
+      if (c < nch && chunk_live(c)) {
+        w0 = alive[(c * CH + tid) * AW];
+        wv1 = AW > 1 ? alive[(c * CH + tid) * AW + AW - 1] : 0u;
+      }
+      const bool any_warp = __any_sync(0xffffffffu, (w0 | wv1) != 0);
+      uint16_t* col = ub16 + c * CH + tid;  // stride S*CH between queries
       if (any_warp) {
         const float rx = crx[c * CH + tid], exv = cex[c * CH + tid];
         const float nx2 = a.xn2[(ch0 + c) * CH + tid];
         float v[32];
         for (int half = 0; half < (Npad > 32 ? 2 : 1); ++half) {
           tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
-          const uint32_t wm = half ? w1 : w0;
+          const uint32_t wm = half ? wv1 : w0;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int g = 32 * half + j;
-            float u = INFINITY;
+            uint16_t u = 0x7f80u;
             if ((wm >> j) & 1u) {
               const float A = qnq[g] + nx2 - 2.f * v[j];
               const float Ss = qrq[g] + rx;
               const float r = __fadd_ru(__fsqrt_ru(fmaxf(A + g_slack * Ss * Ss, 0.f)),
                                         qeq[g] + exv);
-              u = __fmul_ru(__fmul_ru(r, r), a.ub_scale);
+              u = __bfloat16_as_ushort(__float2bfloat16_ru(__fmul_ru(__fmul_ru(r, r), a.ub_scale)));
             }
-            ub[g * CH + tid] = u;
+            col[g * S * CH] = u;
           }
         }
-        if (Npad <= 32)
-          for (int g = 32; g < 64; ++g) ub[g * CH + tid] = INFINITY;
+        for (int g = (Npad > 32 ? 64 : 32); g < QG; ++g) col[g * S * CH] = 0x7f80u;
       } else {
-        for (int g = 0; g < 64; ++g) ub[g * CH + tid] = INFINITY;
+        for (int g = 0; g < QG; ++g) col[g * S * CH] = 0x7f80u;
       }
-      __syncthreads();
-      for (int g = warp; g < G; g += NT / 32) {
-        const float t = warp_kth_smallest(ub + g * CH, CH, qk[g]);
-        if (lane == 0 && t < qtau[g]) qtau[g] = t;
-      }
-      __syncthreads();
     }
+    __syncthreads();
+    for (int g = warp; g < G; g += NT / 32) {
+      const float t = warp_kth_smallest_bf16(ub16 + g * S * CH, S * CH, qk[g]);
+      if (lane == 0 && t < qtau[g]) qtau[g] = t;
+    }
+    __syncthreads();
     if (tid < G && qk[tid] > 0) set_query_terms(tid, qtau[tid], 0.f);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    section(4);
     // survivors of the tightened test: exact distances on the original rows
     for (int c = 0; c < nch; ++c) {
       if (tid == 0) s_nsurv = 0;
-      uint32_t w0 = alive[(c * CH + tid) * 2], w1 = alive[(c * CH + tid) * 2 + 1];
-      const bool any_warp = __any_sync(0xffffffffu, (w0 | w1) != 0);
+      uint32_t w0 = alive[(c * CH + tid) * AW];
+      uint32_t wv1 = AW > 1 ? alive[(c * CH + tid) * AW + AW - 1] : 0u;
+      const bool any_warp = __any_sync(0xffffffffu, (w0 | wv1) != 0);
       if (any_warp) {
         const float rx = crx[c * CH + tid], exv = cex[c * CH + tid], Hx = cHx[c * CH + tid];
         float v[32];
         for (int half = 0; half < (Npad > 32 ? 2 : 1); ++half) {
           tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
-          uint32_t& wm = half ? w1 : w0;
+          uint32_t& wm = half ? wv1 : w0;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int g = 32 * half + j;
             if ((wm >> j) & 1u) {
-              const float P = fmaf(qE[g], exv, fmaf(qgr[g], rx, v[j]));
-              if (P < qH[g] + Hx) wm &= ~(1u << j);
+              const float4 t = qterm[g];
+              const float P = fmaf(t.x, exv, fmaf(t.y, rx, v[j]));
+              if (P < t.w + Hx) wm &= ~(1u << j);
             }
           }
         }
       }
       __syncthreads();
-      for (int g = 0; g < 64; ++g) {
-        const uint32_t bit = g < 32 ? (w0 >> g) & 1u : (w1 >> (g - 32)) & 1u;
+      for (int g = 0; g < QG; ++g) {
+        const uint32_t bit = g < 32 ? (w0 >> g) & 1u : (wv1 >> (g - 32)) & 1u;
         if (bit) surv[atomicAdd(&s_nsurv, 1)] = (uint16_t)((tid << 6) | g);
       }
       __syncthreads();
@@ -518,8 +614,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         const int q = qid[g];
         const int64_t slot = (ch0 + c) * CH + row;
         const float dist = exact_sqdist_warp(a.qorig + (int64_t)q * d, a.rows + slot * d, d);
-        if (lane == 0)
-          topk_insert(a.topk + (int64_t)q * a.k_max, qk[g], make_key(dist, cid[c * CH + row]));
+        topk_insert_warp(a.topk + (int64_t)q * a.k_max, qk[g], make_key(dist, cid[c * CH + row]));
       }
       st_rerank += (tid == 0) ? ns : 0;
       tc::fence_before_sync();
@@ -529,8 +624,14 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     // the scratch written through the generic proxy is refilled by
     // bulk-async copies in the next item
     fence_proxy_async_smem();
+    section(5);
   }
   if (s_fail && tid == 0) atomicOr(a.err, kErrTimeout);
+  if (a.collect && tid == 0) {
+    sec[6] = (unsigned long long)(clock64() - t_kernel);
+    sec[7] = 1;  // CTAs that ran
+    for (int i = 0; i < 8; ++i) atomicAdd(&a.stats[8 + i], sec[i]);
+  }
   if (a.collect) {
     unsigned long long v = st_pairs, dv = st_dims;
 #pragma unroll
@@ -583,16 +684,24 @@ int launch_verify_tc(const VerifyTCArgs& a, cudaStream_t st) {
     if (attr_err == cudaSuccess)
       attr_err = cudaFuncSetAttribute(verify_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       optin - (int)fa.sharedSizeBytes);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute(verify_tc_kernel,
+                                      cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   });
   PANO_CUDA(attr_err);
   const size_t smem = verify_tc_smem(a.max_w);
-  int dev = 0, sms = 0, bps = 0;
+  int dev = 0, sms = 0, optin = 0;
   PANO_CUDA(cudaGetDevice(&dev));
   PANO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  PANO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, verify_tc_kernel, NT, smem));
-  if (bps < 1) return fail(PANO_EINVAL, "tensor-core verify tile does not fit in shared memory");
-  bps = std::min(bps, 2);  // two CTAs x 256 TMEM columns fill the SM's tensor memory
-  verify_tc_kernel<<<sms * bps, NT, smem, st>>>(a);
+  PANO_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (smem > (size_t)optin)
+    return fail(PANO_EINVAL, "tensor-core verify tile does not fit in shared memory");
+  // Two CTAs x 256 TMEM columns fill an SM's tensor memory.  The grid is
+  // not sized from the occupancy API: it reports the SM's current shared
+  // memory carveout, which switches only when a launch asks for more.  A
+  // persistent CTA that cannot be resident yet starts later and finds the
+  // queue drained, so over-provisioning is harmless.
+  verify_tc_kernel<<<sms * 2, NT, smem, st>>>(a);
   PANO_CUDA(cudaGetLastError());
   return PANO_OK;
 }
