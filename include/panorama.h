@@ -115,10 +115,11 @@ typedef struct {
   float stage_ms[6];
   float pad2_[2];
   /* device cycles (summed over the verify CTAs' first threads, collect_stats
-   * = 1) spent in: [0] work-item prologue, [1] MMA issue (tensor-core path)
-   * or slice staging, [2] epilogues (bound tests), [3] next-level staging,
-   * [4] last-level upper-bound filter, [5] exact re-ranking, [6] whole
-   * kernel, [7] number of CTAs that ran */
+   * = 1).  Tensor-core path: [0] work-item prologue, [1] MMA issue, [2]
+   * epilogues (bound tests), [3] next-level staging.  FP32 path: [0] item
+   * and tile setup, [1] slice staging, [2] level-0 partial products and
+   * tests, [3] the same for deeper levels.  Both: [4] last-level upper-bound
+   * filter, [5] exact re-ranking, [6] whole kernel, [7] CTAs that ran. */
   int64_t section_cycles[8];
 } pano_search_stats;
 

@@ -371,15 +371,22 @@ struct Smem {
   static size_t bytes(int QB, int CB, int max_w, int L) {
     size_t s = 0;
     s += (size_t)std::max(CB * max_w, QB * CB) * 4;  // xs (also the last level's UB scratch)
-    s += (size_t)max_w * (QB + 4) * 4;    // qs
-    s += (size_t)CB * 4;                  // candidate tails of the current level
+    s += (size_t)CB * 16;                 // candidate terms (ex, rx, Hx, |x|^2)
+    s += (size_t)QB * 16;                 // query terms (E, g rq, Hq, tau)
+    s += (size_t)max_w * (QB + 4) * 4;    // qs: query slice of the current level
+    s += (size_t)max_w * (QB + 4) * 4;    // qs0: the group's level-0 slice (per item)
+    s += (size_t)CB * 4;                  // candidate tails of the next level
     s += (size_t)QB * (L + 1) * 4;        // query tails
-    s += (size_t)CB * 4 * 4;              // xn2, rx, ex, ids
+    s += (size_t)CB * 4;                  // ids
     s += (size_t)QB * 6 * 4;              // qid, nq, rq, eq, tau, k
     s += (size_t)QB * CB * 2;             // survivors
     return s + 64;
   }
 };
+
+// Evaluation slack of the separable test below (FP32 rounding of its three
+// products and two sums, relative to (|q~| + E)(|x~| + e_x)).
+constexpr float kEvalSlack = 32.f * 5.9604645e-08f;
 
 template <int QB, int CB>
 __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) {
@@ -389,14 +396,15 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
   static_assert(TQ <= 32 && (32 % TQ) == 0, "query blocks of a candidate block share a warp");
   extern __shared__ __align__(16) unsigned char smem[];
   const int L = a.L, d = a.d, max_w = a.max_w;
+  const int w0 = a.level_off[1];
   float* xs = reinterpret_cast<float*>(smem);               // [NCH][max_w][CH]
-  float* qs = xs + (size_t)(CB * max_w > QB * CB ? CB * max_w : QB * CB);  // [max_w][QB+4]
-  float* ctl = qs + (size_t)max_w * (QB + 4);               // [CB] tails, level l+1
+  float4* cterm = reinterpret_cast<float4*>(xs + (size_t)(CB * max_w > QB * CB ? CB * max_w : QB * CB));
+  float4* qterm = cterm + CB;                                // [QB]
+  float* qs = reinterpret_cast<float*>(qterm + QB);          // [max_w][QB+4]
+  float* qs0 = qs + (size_t)max_w * (QB + 4);                // [w0][QB+4]
+  float* ctl = qs0 + (size_t)max_w * (QB + 4);               // [CB] tails, level l+1
   float* qtl = ctl + CB;                                     // [QB][L+1]
-  float* xn2s = qtl + (size_t)QB * (L + 1);                  // [CB]
-  float* rxs = xn2s + CB;
-  float* exs = rxs + CB;
-  int32_t* ids_s = reinterpret_cast<int32_t*>(exs + CB);
+  int32_t* ids_s = reinterpret_cast<int32_t*>(qtl + (size_t)QB * (L + 1));  // [CB]
   int32_t* qid = ids_s + CB;                                 // [QB]
   float* qnq = reinterpret_cast<float*>(qid + QB);
   float* qrq = qnq + QB;
@@ -421,6 +429,27 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
   uint32_t phase = 0;
   unsigned long long st_pair_levels = 0, st_dims = 0, st_tile_levels = 0, st_bytes = 0,
                      st_rerank = 0;
+  unsigned long long sec[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // section cycles (thread 0)
+  const long long t_kernel = clock64();
+  long long t_mark = t_kernel;
+  auto section = [&](int i) {  // charge the time since the last mark to section i
+    if (a.collect && tid == 0) {
+      const long long now = clock64();
+      sec[i] += (unsigned long long)(now - t_mark);
+      t_mark = now;
+    }
+  };
+  const float gs = a.gslack;
+  // per-query terms of the separable form of the margined Eq. 3 test:
+  // the pair is pruned when  p + sq sx + (g rq) rx + E ex  <  Hq + Hx, with
+  // E = e_q + sqrt(tau / lb_scale) rounded up (see the candidate terms)
+  auto set_query_terms = [&](int g, float tau) {
+    const float st = tau == INFINITY ? 1e18f : fminf(__fsqrt_ru(__fdiv_ru(tau, a.lb_scale)), 1e18f);
+    const float E = __fadd_ru(qeq[g], st);
+    const float nq = qnq[g], rq = qrq[g];
+    qterm[g] = make_float4(E, gs * rq, 0.5f * (nq - gs * nq - E * E - kEvalSlack * (rq + E) * (rq + E)),
+                           tau);
+  };
   bool failed = false;
 
   while (true) {
@@ -453,6 +482,22 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
       int g = e / (L + 1), l = e % (L + 1);
       qtl[e] = g < G ? a.qtail[(int64_t)qid[g] * (L + 1) + l] : 0.f;
     }
+    // the group's level-0 query slice serves every tile of the item
+    for (int e0 = 0; e0 < QB * w0; e0 += NT * 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + tid + u * NT;
+        const int g = e / w0, j = e - g * w0;
+        v[u] = (e < QB * w0 && g < G) ? a.qt[(int64_t)qid[g] * d + j] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + tid + u * NT;
+        if (e < QB * w0) qs0[(e % w0) * (QB + 4) + e / w0] = v[u];
+      }
+    }
+    section(0);
 
     for (int64_t tile = ch0; tile < ch1; tile += NCH) {
       const int nch = (int)imin64(NCH, ch1 - tile);
@@ -463,20 +508,23 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
           unsigned long long kk = ld_volatile_u64(a.topk + (int64_t)qid[g] * a.k_max + qk[g] - 1);
           tau = kk == kEmptyKey ? INFINITY : __fmul_ru(key_dist(kk), 1.000001f);
           tau = fminf(tau, a.tau_seed[qid[g]]);
+          qtau[g] = tau;
+          set_query_terms(g, tau);
+        } else {
+          qtau[g] = tau;
+          qterm[g] = make_float4(0.f, 0.f, -INFINITY, tau);
         }
-        qtau[g] = tau;
       }
       for (int e = tid; e < CB; e += NT) {
         int ch = e / CH, i = e % CH;
         if (ch < nch) {
           int64_t slot = (tile + ch) * CH + i;
-          float nx = a.xn2[slot];
-          xn2s[e] = nx;
-          rxs[e] = sqrtf(nx);
-          exs[e] = a.ex[slot];
+          const float nx = a.xn2[slot], rx = sqrtf(nx), exv = a.ex[slot];
+          cterm[e] = make_float4(
+              exv, rx, 0.5f * (nx - gs * nx - exv * exv - kEvalSlack * (rx + exv) * (rx + exv)), nx);
           ids_s[e] = a.ids[slot];
         } else {
-          xn2s[e] = rxs[e] = exs[e] = 0.f;
+          cterm[e] = make_float4(0.f, 0.f, 0.f, 0.f);
           ids_s[e] = -1;
         }
       }
@@ -497,6 +545,7 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
         for (int bi = 0; bi < 4; ++bi) p[ai][bi] = 0.f;
       const int my_ch = (4 * tc) / CH, my_i = (4 * tc) % CH;
       bool completed = true;
+      section(0);
 
       for (int l = 0; l < L; ++l) {
         // candidate-level liveness (any query of the group) -> live chunks
@@ -522,25 +571,26 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
           st_bytes += bytes;
           st_tile_levels += 1;
         }
-        // the tile's tail column for level l+1 and the group's query slice:
-        // all loads are issued before any is used (one latency round)
+        // the tile's tail column for level l+1 and (past level 0) the group's
+        // query slice: all loads are issued before any is used
         float tail_v = 0.f;
         if (tid < CB && tid / CH < nch)
           tail_v = a.tails[((tile + tid / CH) * (L + 1) + l + 1) * CH + (tid % CH)];
-        for (int e0 = 0; e0 < QB * w; e0 += NT * 8) {
-          float v[8];
+        if (l > 0)
+          for (int e0 = 0; e0 < QB * w; e0 += NT * 8) {
+            float v[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int e = e0 + tid + u * NT;
-            const int g = e / w, j = e - (e / w) * w;
-            v[u] = (e < QB * w && g < G) ? a.qt[(int64_t)qid[g] * d + m + j] : 0.f;
-          }
+            for (int u = 0; u < 8; ++u) {
+              const int e = e0 + tid + u * NT;
+              const int g = e / w, j = e - (e / w) * w;
+              v[u] = (e < QB * w && g < G) ? a.qt[(int64_t)qid[g] * d + m + j] : 0.f;
+            }
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int e = e0 + tid + u * NT;
-            if (e < QB * w) qs[(e % w) * (QB + 4) + e / w] = v[u];
+            for (int u = 0; u < 8; ++u) {
+              const int e = e0 + tid + u * NT;
+              if (e < QB * w) qs[(e % w) * (QB + 4) + e / w] = v[u];
+            }
           }
-        }
         if (tid < CB) ctl[tid] = tail_v;
         __syncthreads();
         if (tid < NCH) chunk_live[tid] = 0;  // read by thread 0 above
@@ -554,6 +604,7 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
           completed = false;
           break;
         }
+        section(1);
         if (cm != 0) {
           float acc[4][4];
 #pragma unroll
@@ -561,7 +612,7 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
 #pragma unroll
             for (int bi = 0; bi < 4; ++bi) acc[ai][bi] = 0.f;
           const float* xb = xs + (size_t)my_ch * max_w * CH + my_i;
-          const float* qb = qs + 4 * tq;
+          const float* qb = (l == 0 ? qs0 : qs) + 4 * tq;
 #pragma unroll 4
           for (int j = 0; j < w; ++j) {
             float4 qa = *reinterpret_cast<const float4*>(qb + j * (QB + 4));
@@ -582,32 +633,27 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
             st_dims += (unsigned long long)__popc(alive) * w;
           }
           // bound update and pruning (Eq. 3 with rounding margins)
-          const bool test = a.prune || (l == L - 1);
-          if (test) {
+          if (a.prune || l == L - 1) {
+            const float4 sx = *reinterpret_cast<const float4*>(ctl + 4 * tc);
+            const float sxv[4] = {sx.x, sx.y, sx.z, sx.w};
+            float4 ct[4];
+#pragma unroll
+            for (int bi = 0; bi < 4; ++bi) ct[bi] = cterm[4 * tc + bi];
 #pragma unroll
             for (int ai = 0; ai < 4; ++ai) {
               const int g = 4 * tq + ai;
-              const float nq = qnq[g], rq = qrq[g], eq = qeq[g], tau = qtau[g];
+              const float4 t = qterm[g];
               const float sq = qtl[g * (L + 1) + l + 1];
 #pragma unroll
               for (int bi = 0; bi < 4; ++bi) {
-                const uint32_t bit = 1u << (4 * ai + bi);
-                if (!(alive & bit)) continue;
-                const int e = 4 * tc + bi;
-                const float nx = xn2s[e], rx = rxs[e];
-                const float sx = ctl[e];
-                const float A = nq + nx - 2.f * p[ai][bi];
-                const float C = sq * sx;
-                const float S = rq + rx;
-                const float lbs = A - 2.f * C - a.gslack * S * S;
-                const float r = sqrtf(fmaxf(lbs, 0.f)) - (eq + exs[e]);
-                const float LB = r > 0.f ? r * r * a.lb_scale : 0.f;
-                if (LB > tau) alive &= ~bit;
+                const float P = fmaf(t.x, ct[bi].x, fmaf(t.y, ct[bi].y, fmaf(sq, sxv[bi], p[ai][bi])));
+                if (P < t.z + ct[bi].z) alive &= ~(1u << (4 * ai + bi));
               }
             }
           }
         }
         __syncthreads();  // xs / qs are overwritten by the next level
+        section(l == 0 ? 2 : 3);
       }
       // The k-th smallest upper bound of the tile tightens each query's
       // threshold before re-ranking (at the last level UB ~ LB ~ exact, so
@@ -627,10 +673,11 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
             for (int bi = 0; bi < 4; ++bi) {
               if (!(alive & (1u << (4 * ai + bi)))) continue;
               const int e = 4 * tc + bi;
-              const float A = nq + xn2s[e] - 2.f * p[ai][bi];
-              const float S = rq + rxs[e];
-              const float ubs = fmaxf(A + a.gslack * S * S, 0.f);
-              const float r = __fadd_ru(__fsqrt_ru(ubs), eq + exs[e]);
+              const float4 ct = cterm[e];
+              const float A = nq + ct.w - 2.f * p[ai][bi];
+              const float S = rq + ct.y;
+              const float ubs = fmaxf(A + gs * S * S, 0.f);
+              const float r = __fadd_ru(__fsqrt_ru(ubs), eq + ct.x);
               ub[g * CB + e] = __fmul_ru(__fmul_ru(r, r), a.ub_scale);
             }
           }
@@ -641,26 +688,25 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
           if (lane == 0 && t < qtau[g]) qtau[g] = t;
         }
         __syncthreads();
+        for (int g = tid; g < G; g += NT)
+          if (qk[g] > 0) set_query_terms(g, qtau[g]);
+        __syncthreads();
         if (completed) {
+          float4 ct[4];
+#pragma unroll
+          for (int bi = 0; bi < 4; ++bi) ct[bi] = cterm[4 * tc + bi];
 #pragma unroll
           for (int ai = 0; ai < 4; ++ai) {
-            const int g = 4 * tq + ai;
-            const float nq = qnq[g], rq = qrq[g], eq = qeq[g], tau = qtau[g];
+            const float4 t = qterm[4 * tq + ai];
 #pragma unroll
             for (int bi = 0; bi < 4; ++bi) {
-              const uint32_t bit = 1u << (4 * ai + bi);
-              if (!(alive & bit)) continue;
-              const int e = 4 * tc + bi;
-              const float A = nq + xn2s[e] - 2.f * p[ai][bi];
-              const float S = rq + rxs[e];
-              const float lbs = A - a.gslack * S * S;
-              const float r = sqrtf(fmaxf(lbs, 0.f)) - (eq + exs[e]);
-              const float LB = r > 0.f ? r * r * a.lb_scale : 0.f;
-              if (LB > tau) alive &= ~bit;
+              const float P = fmaf(t.x, ct[bi].x, fmaf(t.y, ct[bi].y, p[ai][bi]));
+              if (P < t.z + ct[bi].z) alive &= ~(1u << (4 * ai + bi));
             }
           }
         }
       }
+      section(4);
       // survivors of all L levels: exact re-rank and top-k insertion
       if (completed && alive) {
 #pragma unroll
@@ -684,8 +730,14 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
       st_rerank += (tid == 0) ? ns : 0;
       __syncthreads();
       if (tid == 0) s_nsurv = 0;
+      section(5);
     }
     __syncthreads();
+  }
+  if (a.collect && tid == 0) {
+    sec[6] = (unsigned long long)(clock64() - t_kernel);
+    sec[7] = 1;  // CTAs that ran
+    for (int i = 0; i < 8; ++i) atomicAdd(&a.stats[8 + i], sec[i]);
   }
   if (a.collect) {
     unsigned long long v = st_pair_levels;
