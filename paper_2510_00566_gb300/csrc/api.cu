@@ -351,8 +351,7 @@ int panorama_load(const char* path, pano_index** out) {
                  I.list_chunk_off[nl] == I.n_chunks,
              PANO_ECORRUPT, "truncated or inconsistent index file");
   const uint64_t CHK = (uint64_t)I.chunk, ns = (uint64_t)I.n_chunks * CHK;
-  const uint64_t elem = I.precision == PANO_FP32 ? 4 : 2;
-  if ((rc = r.dev(I.slices, ns * d * elem)) ||
+  if ((rc = r.dev(I.slices, I.slices_bytes())) ||
       (rc = r.dev(I.tails, (uint64_t)I.n_chunks * (I.L + 1) * CHK * 4)) ||
       (rc = r.dev(I.xn2, ns * 4)) || (rc = r.dev(I.ex, ns * 4)) || (rc = r.dev(I.ids, ns * 4)) ||
       (rc = r.dev(I.rows, ns * d * 4)))

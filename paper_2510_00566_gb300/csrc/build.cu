@@ -3,10 +3,13 @@
 //
 // Device layout of a built FP32 index (CH = 64 vectors per chunk, chunks of
 // one list are consecutive, lists in id order, a list's last chunk padded):
-//   slices [chunk][d][CH]   x~ transposed per chunk: the level-l slice of a
-//                           chunk is the contiguous [w_l][CH] block at dims
+//   slices [chunk][d+L+3][CH] x~ transposed per chunk, level by level: the
+//                           level-l block is the [w_l][CH] slice at dims
 //                           m_l..m_{l+1}-1 (the paper's level-major batch,
-//                           with B = CH), staged whole by one bulk copy;
+//                           with B = CH) followed by the tail row
+//                           sqrt(R_x^{(l+1,d)}); level 0's block also holds
+//                           ||x~||^2, e_x and the ids, so one bulk copy
+//                           stages everything a (chunk, level) step reads;
 //   tails  [chunk][L+1][CH] sqrt(R_x^{(l,d)}) rounded up (FP64 sums);
 //   xn2    [chunk][CH]      ||x~||^2;  ex [chunk][CH] bound on the transform
 //                           error ||x~ - T~(x - mu~)||;  ids [chunk][CH];
@@ -147,11 +150,21 @@ __global__ void __launch_bounds__(256) pack_fp32_kernel(
     float* __restrict__ slices, float* __restrict__ tails, float* __restrict__ xn2,
     float* __restrict__ ex, int32_t* __restrict__ ids) {
   __shared__ float tile[CH][33];
+  __shared__ int16_t lvl_of[8192];  // level of each dimension
   const int64_t lc = blockIdx.x;  // chunk within the block
   const int64_t g = chunk0 + lc;  // global chunk
   const float* xblk = xt + lc * CH * d;
   const int64_t* pb = perm + lc * CH;
-  float* sl = slices + g * (int64_t)d * CH;
+  float* sl = slices + g * (int64_t)(d + L + 3) * CH;
+  // row of dimension j in the chunk's block sequence
+  auto row_of = [&](int j) { const int l = lvl_of[j]; return j + (l == 0 ? 0 : l + 3); };
+  auto tail_row = [&](int l) { return level_off[l + 1] + (l == 0 ? 0 : l + 3); };
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    int l = 0;
+    while (level_off[l + 1] <= j) ++l;
+    lvl_of[j] = (int16_t)l;
+  }
+  __syncthreads();
   for (int j0 = 0; j0 < d; j0 += 32) {
     for (int e = threadIdx.x; e < CH * 32; e += blockDim.x) {
       int i = e / 32, jj = e % 32;
@@ -162,7 +175,7 @@ __global__ void __launch_bounds__(256) pack_fp32_kernel(
     __syncthreads();
     for (int e = threadIdx.x; e < CH * 32; e += blockDim.x) {
       int jj = e / CH, i = e % CH;
-      if (j0 + jj < d) sl[(int64_t)(j0 + jj) * CH + i] = tile[i][jj];
+      if (j0 + jj < d) sl[(int64_t)row_of(j0 + jj) * CH + i] = tile[i][jj];
     }
     __syncthreads();
   }
@@ -182,8 +195,11 @@ __global__ void __launch_bounds__(256) pack_fp32_kernel(
         }
       e = warp_sum_f64(e);
       suffix += e;
-      if (lane == 0)
-        tails[(g * (L + 1) + l) * CH + i] = __double2float_ru(sqrt(suffix * (1.0 + 1e-12)));
+      if (lane == 0) {
+        const float t = __double2float_ru(sqrt(suffix * (1.0 + 1e-12)));
+        tails[(g * (L + 1) + l) * CH + i] = t;
+        if (l > 0) sl[(int64_t)tail_row(l - 1) * CH + i] = t;
+      }
     }
     double dev = 0.0;  // ||x - mu~||
     if (valid) {
@@ -195,10 +211,17 @@ __global__ void __launch_bounds__(256) pack_fp32_kernel(
     }
     dev = warp_sum_f64(dev);
     if (lane == 0) {
+      const float exv = valid ? __double2float_ru(c_trans * sqrt(dev) * (1.0 + 1e-9)) : 0.f;
+      const int32_t id = valid ? (int32_t)pb[i] : -1;
       tails[(g * (L + 1) + L) * CH + i] = 0.f;
+      sl[(int64_t)tail_row(L - 1) * CH + i] = 0.f;
       xn2[slot] = (float)suffix;
-      ex[slot] = valid ? __double2float_ru(c_trans * sqrt(dev) * (1.0 + 1e-9)) : 0.f;
-      ids[slot] = valid ? (int32_t)pb[i] : -1;
+      ex[slot] = exv;
+      ids[slot] = id;
+      const int64_t r0 = tail_row(0);  // level 0's extra rows
+      sl[(r0 + 1) * CH + i] = (float)suffix;
+      sl[(r0 + 2) * CH + i] = exv;
+      sl[(r0 + 3) * CH + i] = __int_as_float(id);
     }
   }
 }
@@ -344,6 +367,7 @@ int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
   int precision = o ? o->precision : PANO_FP32;
   PANO_CHECK(precision == PANO_FP32 || precision == PANO_BF16, PANO_EINVAL,
              "storage precision must be PANO_FP32 or PANO_BF16 (PANO_FP8 is not built)");
+  PANO_CHECK(d <= 8192, PANO_EINVAL, "dimension must be at most 8192");
   int dev = 0;
   int rc = check_device(&dev);
   if (rc) return rc;
@@ -471,8 +495,7 @@ int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
   PANO_CUDA(cudaMemcpyAsync(I.mu32.p, t->mu32.data(), d * 4, cudaMemcpyHostToDevice, st));
 
   // ---- packed arrays
-  const size_t elem = precision == PANO_FP32 ? 4 : 2;
-  if ((rc = I.slices.alloc((size_t)nslots * d * elem)) ||
+  if ((rc = I.slices.alloc(I.slices_bytes())) ||
       (rc = I.tails.alloc((size_t)I.n_chunks * (I.L + 1) * CHK * 4)) ||
       (rc = I.xn2.alloc(nslots * 4)) || (rc = I.ex.alloc(nslots * 4)) ||
       (rc = I.ids.alloc(nslots * 4)) || (rc = I.rows.alloc((size_t)nslots * d * 4)))

@@ -337,10 +337,6 @@ __global__ void __launch_bounds__(128) seed_tau_kernel(
 // ------------------------------------------------------------ a4-a10 verify
 struct VerifyArgs {
   const float* slices;
-  const float* tails;
-  const float* xn2;
-  const float* ex;
-  const int32_t* ids;
   const float* rows;
   const int64_t* chunk_off;
   const float* qt;
@@ -348,7 +344,7 @@ struct VerifyArgs {
   const float4* qinfo;
   const float* qtail;
   const int32_t* kq;
-  const float* tau_seed;  // per-query warm-start threshold
+  float* tau_seed;  // per-query threshold: warm start, lowered by any tile
   const int4* items;
   const int* n_items;  // device count
   int* counter;
@@ -363,24 +359,43 @@ struct VerifyArgs {
   float ub_scale;  // (1 + 8u) / (1 - eta): upper bound in T~ space -> original
   int prune;       // 0: plain scan (prune only after the last level)
   int collect;
+  float inv_lb_up;  // 1 / lb_scale rounded up
   int32_t level_off[65];
+  int32_t row_off[65];  // first row (of 64 floats) of level l's block in a chunk
+  int64_t chunk_rows;   // rows per chunk in the slice array
 };
 
-struct Smem {
-  // sizes depend on (QB, CB, max_w, L); carved at run time
-  static size_t bytes(int QB, int CB, int max_w, int L) {
-    size_t s = 0;
-    s += (size_t)std::max(CB * max_w, QB * CB) * 4;  // xs (also the last level's UB scratch)
-    s += (size_t)CB * 16;                 // candidate terms (ex, rx, Hx, |x|^2)
-    s += (size_t)QB * 16;                 // query terms (E, g rq, Hq, tau)
-    s += (size_t)max_w * (QB + 4) * 4;    // qs: query slice of the current level
-    s += (size_t)max_w * (QB + 4) * 4;    // qs0: the group's level-0 slice (per item)
-    s += (size_t)CB * 4;                  // candidate tails of the next level
-    s += (size_t)QB * (L + 1) * 4;        // query tails
-    s += (size_t)CB * 4;                  // ids
-    s += (size_t)QB * 6 * 4;              // qid, nq, rq, eq, tau, k
-    s += (size_t)QB * CB * 2;             // survivors
-    return s + 64;
+// Shared-memory plan of the FP32 verify kernel, identical on host and device.
+// Three stage buffers rotate through (tile, level) steps; each holds, per
+// chunk of the tile, one level block of the slice array: the level slice,
+// the tail row of the next level and (level 0) the norms, error bounds and
+// ids, (max_w + 4) rows of 64 floats.  Query slices are kept
+// row-major per query with a row stride of 4 x (odd) floats, so the 128-bit
+// reads of four queries' rows by neighbouring threads hit distinct banks.
+struct FpSmem {
+  uint32_t stage_f;  // floats per stage (also the last level's UB scratch)
+  uint32_t qstride;  // floats between two queries' rows in a query slice
+  uint32_t qbuf_f;   // floats per query-slice buffer (also the survivor list)
+  uint32_t off_q0, off_qb, off_cterm, off_qterm, off_qtl, off_ids, off_q, off_pend, total;
+  static constexpr int kPend = 32;  // deferred re-rank entries
+  __host__ __device__ FpSmem(int QB, int CB, int max_w, int L) {
+    uint32_t sf = (uint32_t)(CB * (max_w + 4));
+    if (sf < (uint32_t)(QB * CB)) sf = (uint32_t)(QB * CB);
+    stage_f = (sf + 31u) & ~31u;
+    qstride = (uint32_t)((max_w + 3) & ~3);
+    if (((qstride / 4) & 1u) == 0) qstride += 4;
+    uint32_t qf = (uint32_t)QB * qstride;
+    if (qf < (uint32_t)(QB * CB / 2)) qf = (uint32_t)(QB * CB / 2);
+    qbuf_f = (qf + 31u) & ~31u;
+    off_q0 = 3u * stage_f * 4u;
+    off_qb = off_q0 + qbuf_f * 4u;  // two buffers: levels l >= 1 by parity
+    off_cterm = off_qb + 2u * qbuf_f * 4u;
+    off_qterm = off_cterm + CB * 16u;
+    off_qtl = off_qterm + QB * 16u;
+    off_ids = off_qtl + (((uint32_t)QB * (L + 1) * 4u + 15u) & ~15u);
+    off_q = off_ids + CB * 4u;
+    off_pend = off_q + QB * 6u * 4u;
+    total = off_pend + kPend * 16u;  // slot (8), query (4), id (4)
   }
 };
 
@@ -388,47 +403,133 @@ struct Smem {
 // products and two sums, relative to (|q~| + E)(|x~| + e_x)).
 constexpr float kEvalSlack = 32.f * 5.9604645e-08f;
 
-template <int QB, int CB>
-__global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) {
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// sqrt(tau / lb_scale) rounded up, from hardware-rounded operations: y is
+// rounded up, rsqrtf has at most 2 ulp error (CUDA's documented bound) and
+// the product one rounding; the factor 1 + 2^-19 covers both.
+__device__ __forceinline__ float sqrt_ratio_up(float tau, float inv_lb_up) {
+  const float y = __fmul_ru(tau, inv_lb_up);
+  if (!(y > 0.f)) return 0.f;
+  if (y > 1e36f) return 1e18f;
+  return __fmul_ru(y * rsqrtf(y), 1.0000019f);
+}
+
+// One CTA per work item at a time (persistent).  A tile is CB candidates
+// (CB / 64 chunks) x the item's query group (<= QB); thread (tq, tc) owns a
+// 4 x 4 register tile of partial products: queries tq + TQ*i, candidates
+// 4tc + j.  The tile walks the levels (Algorithm 1's batch step), and the
+// staging of the next step runs behind the arithmetic of the current one:
+// when level l of tile t starts, level l+1 of the chunks still live (and the
+// group's level-(l+1) query slice) is copied speculatively into a second
+// stage, and level 0 of tile t+1 (with its norms, bounds and ids) into the
+// third.  A tile that dies at level l leaves its speculative copy unused.
+// Survivors are re-ranked in batches, after their rows were prefetched into
+// L2; the delayed top-k insertions only leave the threshold larger for a
+// while, which is still a valid threshold.
+template <int QB, int CB, int NTH>
+__global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a) {
   constexpr int NCH = CB / CH;
   constexpr int TQ = QB / 4;
-  static_assert(TQ * (CB / 4) == NT, "4x4 register tile per thread");
+  constexpr int NW = NTH / 32;
+  static_assert(TQ * (CB / 4) == NTH, "4x4 register tile per thread");
   static_assert(TQ <= 32 && (32 % TQ) == 0, "query blocks of a candidate block share a warp");
-  extern __shared__ __align__(16) unsigned char smem[];
+  static_assert(NCH <= 32, "live-chunk mask");
+  // the thread that issues bulk copies: a warp with no per-query setup work
+  constexpr int ISSUER = 32 * ((QB + 31) / 32 < NW ? (QB + 31) / 32 : NW - 1);
+  extern __shared__ __align__(128) unsigned char smem[];
   const int L = a.L, d = a.d, max_w = a.max_w;
-  const int w0 = a.level_off[1];
-  float* xs = reinterpret_cast<float*>(smem);               // [NCH][max_w][CH]
-  float4* cterm = reinterpret_cast<float4*>(xs + (size_t)(CB * max_w > QB * CB ? CB * max_w : QB * CB));
-  float4* qterm = cterm + CB;                                // [QB]
-  float* qs = reinterpret_cast<float*>(qterm + QB);          // [max_w][QB+4]
-  float* qs0 = qs + (size_t)max_w * (QB + 4);                // [w0][QB+4]
-  float* ctl = qs0 + (size_t)max_w * (QB + 4);               // [CB] tails, level l+1
-  float* qtl = ctl + CB;                                     // [QB][L+1]
-  int32_t* ids_s = reinterpret_cast<int32_t*>(qtl + (size_t)QB * (L + 1));  // [CB]
-  int32_t* qid = ids_s + CB;                                 // [QB]
+  const FpSmem lay(QB, CB, max_w, L);
+  const int QS = (int)lay.qstride;
+  float* q0 = reinterpret_cast<float*>(smem + lay.off_q0);            // level-0 query slice
+  float4* cterm = reinterpret_cast<float4*>(smem + lay.off_cterm);    // (ex, rx, Hx, |x|^2)
+  float4* qterm = reinterpret_cast<float4*>(smem + lay.off_qterm);    // (E, g rq, Hq, tau)
+  float* qtl = reinterpret_cast<float*>(smem + lay.off_qtl);          // [QB][L+1]
+  int32_t* ids_s = reinterpret_cast<int32_t*>(smem + lay.off_ids);    // [CB]
+  int32_t* qid = reinterpret_cast<int32_t*>(smem + lay.off_q);        // [QB]
   float* qnq = reinterpret_cast<float*>(qid + QB);
   float* qrq = qnq + QB;
   float* qeq = qrq + QB;
   float* qtau = qeq + QB;
   int32_t* qk = reinterpret_cast<int32_t*>(qtau + QB);
-  uint16_t* surv = reinterpret_cast<uint16_t*>(qk + QB);    // [QB*CB]
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ int s_item, s_nsurv;
-  __shared__ int chunk_live[NCH];
+  int64_t* pslot = reinterpret_cast<int64_t*>(smem + lay.off_pend);   // deferred re-rank
+  int32_t* pq = reinterpret_cast<int32_t*>(pslot + FpSmem::kPend);
+  int32_t* pid = pq + FpSmem::kPend;
+  const int BR = (max_w + 4) * CH;  // floats per chunk block in a stage
+  auto stage_x = [&](int b) { return reinterpret_cast<float*>(smem + (uint32_t)b * lay.stage_f * 4u); };
+  auto qslice = [&](int l) {
+    return l == 0 ? q0 : reinterpret_cast<float*>(smem + lay.off_qb + (uint32_t)(l & 1) * lay.qbuf_f * 4u);
+  };
+  uint16_t* surv = reinterpret_cast<uint16_t*>(qslice(1));  // [QB*CB] after the levels
+  __shared__ __align__(8) uint64_t bar[3];
+  __shared__ int s_item, s_nsurv, s_npend;
+  __shared__ uint32_t s_live[2];
 
   const int tid = threadIdx.x;
   const int tq = tid % TQ, tc = tid / TQ;
   const int warp = tid / 32, lane = tid & 31;
   if (tid == 0) {
-    mbar_init(&bar, 1);
+    for (int b = 0; b < 3; ++b) mbar_init(&bar[b], 1);
     fence_mbar_init();
+    s_nsurv = 0;
+    s_npend = 0;
+    s_live[0] = s_live[1] = 0u;
   }
-  if (tid < NCH) chunk_live[tid] = 0;
-  if (tid == 0) s_nsurv = 0;
   __syncthreads();
-  uint32_t phase = 0;
+  // stage-buffer state, identical in every thread: phase and pending bits
+  uint32_t ph = 0, pend = 0;
+  bool failed = false;
+  auto wait_stage = [&](int b) {
+    if (!((pend >> b) & 1u)) return;
+    if (!mbar_wait_bounded(&bar[b], (ph >> b) & 1u)) failed = true;
+    ph ^= 1u << b;
+    pend &= ~(1u << b);
+  };
   unsigned long long st_pair_levels = 0, st_dims = 0, st_tile_levels = 0, st_bytes = 0,
                      st_rerank = 0;
+  // stage level l of tile `tile` (chunks in `live`) into buffer b; one
+  // thread issues, every thread records the pending copy
+  auto issue = [&](int b, int64_t tile, int nch, int l, uint32_t live) {
+    const int w = a.level_off[l + 1] - a.level_off[l];
+    if (tid == ISSUER) {
+      const uint32_t blk = (uint32_t)(w + (l == 0 ? 4 : 1)) * CH * 4;  // one level block
+      mbar_arrive_expect_tx(&bar[b], (uint32_t)__popc(live) * blk);
+      float* xs = stage_x(b);
+      for (int c = 0; c < nch; ++c)
+        if ((live >> c) & 1u)
+          bulk_g2s(xs + (size_t)c * BR, a.slices + ((tile + c) * a.chunk_rows + a.row_off[l]) * CH,
+                   blk, &bar[b]);
+      st_bytes += (unsigned long long)__popc(live) * w * CH * 4;
+    }
+    pend |= 1u << b;
+  };
+  // the group's query slice of level l -> [QB][QS], asynchronously when the
+  // rows are 16-byte aligned (completion: cp_async_wait_all + a barrier)
+  auto load_qslice = [&](int l, int G) {
+    const int m = a.level_off[l], w = a.level_off[l + 1] - m;
+    float* dst = qslice(l);
+    if (((d | m | w) & 3) == 0) {
+      const int nv = w / 4;
+      for (int e = tid; e < G * nv; e += NTH) {
+        const int g = e / nv, v = e - g * nv;
+        cp_async16(dst + g * QS + 4 * v, a.qt + (int64_t)qid[g] * d + m + 4 * v);
+      }
+      cp_async_commit();
+    } else {
+      for (int e = tid; e < G * w; e += NTH) {
+        const int g = e / w, j = e - g * w;
+        dst[g * QS + j] = a.qt[(int64_t)qid[g] * d + m + j];
+      }
+    }
+  };
   unsigned long long sec[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // section cycles (thread 0)
   const long long t_kernel = clock64();
   long long t_mark = t_kernel;
@@ -444,13 +545,44 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
   // the pair is pruned when  p + sq sx + (g rq) rx + E ex  <  Hq + Hx, with
   // E = e_q + sqrt(tau / lb_scale) rounded up (see the candidate terms)
   auto set_query_terms = [&](int g, float tau) {
-    const float st = tau == INFINITY ? 1e18f : fminf(__fsqrt_ru(__fdiv_ru(tau, a.lb_scale)), 1e18f);
+    const float st = tau == INFINITY ? 1e18f : sqrt_ratio_up(tau, a.inv_lb_up);
     const float E = __fadd_ru(qeq[g], st);
     const float nq = qnq[g], rq = qrq[g];
     qterm[g] = make_float4(E, gs * rq, 0.5f * (nq - gs * nq - E * E - kEvalSlack * (rq + E) * (rq + E)),
                            tau);
   };
-  bool failed = false;
+  // The running threshold of query slot g: k-th key of its top-k (rounded
+  // up) and its warm-start seed.  The loads are issued one tile ahead and
+  // combined when the tile that uses them starts; a value read early is an
+  // older, larger threshold: still a valid one.
+  struct TauRead {
+    unsigned long long key;
+    float seed;
+  };
+  auto read_tau = [&](int g, int G) {
+    TauRead r{kEmptyKey, -1.f};  // k == 0: nothing can enter
+    if (g < G && qk[g] > 0) {
+      r.key = ld_volatile_u64(a.topk + (int64_t)qid[g] * a.k_max + qk[g] - 1);
+      r.seed = __ldcg(a.tau_seed + qid[g]);
+    }
+    return r;
+  };
+  auto tau_of = [&](const TauRead& r) {
+    if (r.seed < 0.f) return -1.f;
+    const float t = r.key == kEmptyKey ? INFINITY : __fmul_ru(key_dist(r.key), 1.000001f);
+    return fminf(t, r.seed);
+  };
+  // exact distances of the deferred survivors (their rows were prefetched
+  // into L2 one tile earlier) and their top-k insertion
+  auto rerank_pending = [&]() {
+    const int np = s_npend;
+    for (int s = warp; s < np; s += NW) {
+      const int q = pq[s];
+      const float dist = exact_sqdist_warp(a.qorig + (int64_t)q * d, a.rows + pslot[s] * d, d);
+      topk_insert_warp(a.topk + (int64_t)q * a.k_max, a.kq[q], make_key(dist, pid[s]));
+    }
+    st_rerank += (tid == 0) ? np : 0;
+  };
 
   while (true) {
     if (tid == 0) s_item = atomicAdd(a.counter, 1);
@@ -462,7 +594,12 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
     const int64_t ch0 = a.chunk_off[it.x] + (int64_t)it.y * SEG_CHUNKS;
     const int64_t ch1 = imin64(a.chunk_off[it.x + 1], ch0 + SEG_CHUNKS);
     const int G = it.w;
-    for (int g = tid; g < QB; g += NT) {
+    int cur = 0;
+    {
+      const int nch0 = (int)imin64(NCH, ch1 - ch0);
+      issue(cur, ch0, nch0, 0, (1u << nch0) - 1u);
+    }
+    for (int g = tid; g < QB; g += NTH) {
       if (g < G) {
         int q = a.bucket[it.z + g];
         qid[g] = q;
@@ -478,51 +615,48 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
       }
     }
     __syncthreads();
-    for (int e = tid; e < QB * (L + 1); e += NT) {
+    for (int e = tid; e < QB * (L + 1); e += NTH) {
       int g = e / (L + 1), l = e % (L + 1);
       qtl[e] = g < G ? a.qtail[(int64_t)qid[g] * (L + 1) + l] : 0.f;
     }
-    // the group's level-0 query slice serves every tile of the item
-    for (int e0 = 0; e0 < QB * w0; e0 += NT * 8) {
-      float v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = e0 + tid + u * NT;
-        const int g = e / w0, j = e - g * w0;
-        v[u] = (e < QB * w0 && g < G) ? a.qt[(int64_t)qid[g] * d + j] : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = e0 + tid + u * NT;
-        if (e < QB * w0) qs0[(e % w0) * (QB + 4) + e / w0] = v[u];
-      }
-    }
+    load_qslice(0, G);
+    cp_async_wait_all();
+    TauRead tau_next = read_tau(tid, G);
     section(0);
 
     for (int64_t tile = ch0; tile < ch1; tile += NCH) {
       const int nch = (int)imin64(NCH, ch1 - tile);
-      // running threshold: k-th key of the query's top-k (rounded up)
-      for (int g = tid; g < QB; g += NT) {
-        float tau = -1.f;  // k == 0: nothing can enter
-        if (g < G && qk[g] > 0) {
-          unsigned long long kk = ld_volatile_u64(a.topk + (int64_t)qid[g] * a.k_max + qk[g] - 1);
-          tau = kk == kEmptyKey ? INFINITY : __fmul_ru(key_dist(kk), 1.000001f);
-          tau = fminf(tau, a.tau_seed[qid[g]]);
-          qtau[g] = tau;
-          set_query_terms(g, tau);
-        } else {
-          qtau[g] = tau;
-          qterm[g] = make_float4(0.f, 0.f, -INFINITY, tau);
-        }
+      const int nxt = (cur + 1) % 3;
+      int spec = (cur + 2) % 3;
+      wait_stage(cur);
+      if (__syncthreads_or(failed)) {
+        failed = true;
+        break;
       }
-      for (int e = tid; e < CB; e += NT) {
-        int ch = e / CH, i = e % CH;
-        if (ch < nch) {
-          int64_t slot = (tile + ch) * CH + i;
-          const float nx = a.xn2[slot], rx = sqrtf(nx), exv = a.ex[slot];
+      // the next tile's level 0 goes out before this tile's arithmetic
+      const int64_t tile_n = tile + NCH;
+      const bool has_next = tile_n < ch1;
+      if (has_next) {
+        const int nch_n = (int)imin64(NCH, ch1 - tile_n);
+        issue(nxt, tile_n, nch_n, 0, (1u << nch_n) - 1u);
+      }
+      if (tid < QB) {
+        // the global threshold, or the one this item's last tile reached
+        float tau = tau_of(tau_next);
+        if (tau >= 0.f && tile != ch0) tau = fminf(tau, qtau[tid]);
+        qtau[tid] = tau;
+        if (tau >= 0.f) set_query_terms(tid, tau);
+        else qterm[tid] = make_float4(0.f, 0.f, -INFINITY, tau);
+        if (has_next) tau_next = read_tau(tid, G);
+      }
+      // candidate terms by the highest threads (the lowest hold queries)
+      for (int e = NTH - 1 - tid; e < CB; e += NTH) {
+        if (e / CH < nch) {
+          const float* meta = stage_x(cur) + (e / CH) * BR + (a.level_off[1] + 1) * CH + (e % CH);
+          const float nx = meta[0], rx = sqrtf(nx), exv = meta[CH];
           cterm[e] = make_float4(
               exv, rx, 0.5f * (nx - gs * nx - exv * exv - kEvalSlack * (rx + exv) * (rx + exv)), nx);
-          ids_s[e] = a.ids[slot];
+          ids_s[e] = __float_as_int(meta[2 * CH]);
         } else {
           cterm[e] = make_float4(0.f, 0.f, 0.f, 0.f);
           ids_s[e] = -1;
@@ -530,12 +664,12 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
       }
       __syncthreads();
 
-      uint32_t alive = 0;  // bit 4*ai + bi: pair (query 4tq+ai, cand 4tc+bi)
+      uint32_t alive = 0;  // bit 4*ai + bi: pair (query tq + TQ ai, cand 4tc + bi)
 #pragma unroll
       for (int ai = 0; ai < 4; ++ai)
 #pragma unroll
         for (int bi = 0; bi < 4; ++bi) {
-          int g = 4 * tq + ai, e = 4 * tc + bi;
+          int g = tq + TQ * ai, e = 4 * tc + bi;
           if (g < G && qk[g] > 0 && ids_s[e] >= 0) alive |= 1u << (4 * ai + bi);
         }
       float p[4][4];
@@ -548,57 +682,28 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
       section(0);
 
       for (int l = 0; l < L; ++l) {
-        // candidate-level liveness (any query of the group) -> live chunks
+        // chunks with a live pair (any query of the group)
         uint32_t cm = alive;
 #pragma unroll
         for (int off = 1; off < TQ; off <<= 1) cm |= __shfl_xor_sync(0xffffffffu, cm, off);
-        if (tq == 0 && cm) chunk_live[my_ch] = 1;
+        if (tq == 0 && cm) atomicOr(&s_live[l & 1], 1u << my_ch);
         const int any = __syncthreads_or(alive != 0);
         if (!any) {
           completed = false;
           break;
         }
-        const int m = a.level_off[l], w = a.level_off[l + 1] - m;
-        if (tid == 0) {
-          uint32_t bytes = 0;
-          for (int c = 0; c < nch; ++c)
-            if (chunk_live[c]) bytes += (uint32_t)w * CH * 4;
-          mbar_arrive_expect_tx(&bar, bytes);
-          for (int c = 0; c < nch; ++c)
-            if (chunk_live[c])
-              bulk_g2s(xs + (size_t)c * max_w * CH, a.slices + ((tile + c) * d + m) * CH,
-                       (uint32_t)w * CH * 4, &bar);
-          st_bytes += bytes;
-          st_tile_levels += 1;
+        const uint32_t live = s_live[l & 1];
+        if (tid == 0) s_live[(l + 1) & 1] = 0u;  // last read at level l - 1
+        const int w = a.level_off[l + 1] - a.level_off[l];
+        // this level's query slice landed (issued one level ago) ...
+        cp_async_wait_all();
+        // ... and level l+1 goes out speculatively for the chunks live now
+        if (l + 1 < L) {
+          issue(spec, tile, nch, l + 1, live);
+          load_qslice(l + 1, G);
         }
-        // the tile's tail column for level l+1 and (past level 0) the group's
-        // query slice: all loads are issued before any is used
-        float tail_v = 0.f;
-        if (tid < CB && tid / CH < nch)
-          tail_v = a.tails[((tile + tid / CH) * (L + 1) + l + 1) * CH + (tid % CH)];
-        if (l > 0)
-          for (int e0 = 0; e0 < QB * w; e0 += NT * 8) {
-            float v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int e = e0 + tid + u * NT;
-              const int g = e / w, j = e - (e / w) * w;
-              v[u] = (e < QB * w && g < G) ? a.qt[(int64_t)qid[g] * d + m + j] : 0.f;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int e = e0 + tid + u * NT;
-              if (e < QB * w) qs[(e % w) * (QB + 4) + e / w] = v[u];
-            }
-          }
-        if (tid < CB) ctl[tid] = tail_v;
-        __syncthreads();
-        if (tid < NCH) chunk_live[tid] = 0;  // read by thread 0 above
-        if (!mbar_wait_bounded(&bar, phase)) {
-          if (tid == 0) atomicOr(a.err, kErrTimeout);
-          failed = true;
-        }
-        phase ^= 1;
+        if (tid == 0) st_tile_levels += 1;
+        if (l > 0) wait_stage(cur);
         if (__syncthreads_or(failed)) {
           failed = true;
           completed = false;
@@ -611,18 +716,44 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
           for (int ai = 0; ai < 4; ++ai)
 #pragma unroll
             for (int bi = 0; bi < 4; ++bi) acc[ai][bi] = 0.f;
-          const float* xb = xs + (size_t)my_ch * max_w * CH + my_i;
-          const float* qb = (l == 0 ? qs0 : qs) + 4 * tq;
-#pragma unroll 4
-          for (int j = 0; j < w; ++j) {
-            float4 qa = *reinterpret_cast<const float4*>(qb + j * (QB + 4));
-            float4 xv = *reinterpret_cast<const float4*>(xb + j * CH);
-            float qv[4] = {qa.x, qa.y, qa.z, qa.w};
-            float xx[4] = {xv.x, xv.y, xv.z, xv.w};
+          const float* xb = stage_x(cur) + (size_t)my_ch * BR + my_i;
+          const float* qb = qslice(l) + tq * QS;
+          const int w4 = w & ~3;
+#pragma unroll 2
+          for (int j = 0; j < w4; j += 4) {
+            float qv[4][4], xv[4][4];
 #pragma unroll
-            for (int ai = 0; ai < 4; ++ai)
+            for (int ai = 0; ai < 4; ++ai) {
+              const float4 t = *reinterpret_cast<const float4*>(qb + ai * TQ * QS + j);
+              qv[ai][0] = t.x;
+              qv[ai][1] = t.y;
+              qv[ai][2] = t.z;
+              qv[ai][3] = t.w;
+            }
 #pragma unroll
-              for (int bi = 0; bi < 4; ++bi) acc[ai][bi] = fmaf(qv[ai], xx[bi], acc[ai][bi]);
+            for (int u = 0; u < 4; ++u) {
+              const float4 t = *reinterpret_cast<const float4*>(xb + (j + u) * CH);
+              xv[u][0] = t.x;
+              xv[u][1] = t.y;
+              xv[u][2] = t.z;
+              xv[u][3] = t.w;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int ai = 0; ai < 4; ++ai)
+#pragma unroll
+                for (int bi = 0; bi < 4; ++bi) acc[ai][bi] = fmaf(qv[ai][u], xv[u][bi], acc[ai][bi]);
+          }
+          for (int j = w4; j < w; ++j) {
+            const float4 t = *reinterpret_cast<const float4*>(xb + j * CH);
+            const float xx[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int ai = 0; ai < 4; ++ai) {
+              const float qq = qb[ai * TQ * QS + j];
+#pragma unroll
+              for (int bi = 0; bi < 4; ++bi) acc[ai][bi] = fmaf(qq, xx[bi], acc[ai][bi]);
+            }
           }
 #pragma unroll
           for (int ai = 0; ai < 4; ++ai)
@@ -634,14 +765,14 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
           }
           // bound update and pruning (Eq. 3 with rounding margins)
           if (a.prune || l == L - 1) {
-            const float4 sx = *reinterpret_cast<const float4*>(ctl + 4 * tc);
+            const float4 sx = *reinterpret_cast<const float4*>(xb + w * CH);
             const float sxv[4] = {sx.x, sx.y, sx.z, sx.w};
             float4 ct[4];
 #pragma unroll
             for (int bi = 0; bi < 4; ++bi) ct[bi] = cterm[4 * tc + bi];
 #pragma unroll
             for (int ai = 0; ai < 4; ++ai) {
-              const int g = 4 * tq + ai;
+              const int g = tq + TQ * ai;
               const float4 t = qterm[g];
               const float sq = qtl[g * (L + 1) + l + 1];
 #pragma unroll
@@ -652,22 +783,29 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
             }
           }
         }
-        __syncthreads();  // xs / qs are overwritten by the next level
+        __syncthreads();  // the stage and the query slice are refilled next
         section(l == 0 ? 2 : 3);
+        if (l + 1 < L) {  // the speculative stage becomes current
+          const int t = cur;
+          cur = spec;
+          spec = t;
+        }
       }
+      if (failed) break;
+      cp_async_wait_all();  // an unused speculative query slice
       // The k-th smallest upper bound of the tile tightens each query's
       // threshold before re-ranking (at the last level UB ~ LB ~ exact, so
       // only ~k pairs per query survive even while the running top-k is
-      // still empty).
+      // still empty).  The last level's stage is free: it is the scratch.
       const int done = __syncthreads_or(completed && alive != 0);
       if (done) {
-        float* ub = xs;  // [QB][CB]
-        for (int e = tid; e < QB * CB; e += NT) ub[e] = INFINITY;
+        float* ub = stage_x(cur);  // [QB][CB]
+        for (int e = tid; e < QB * CB; e += NTH) ub[e] = INFINITY;
         __syncthreads();
         if (completed) {
 #pragma unroll
           for (int ai = 0; ai < 4; ++ai) {
-            const int g = 4 * tq + ai;
+            const int g = tq + TQ * ai;
             const float nq = qnq[g], rq = qrq[g], eq = qeq[g];
 #pragma unroll
             for (int bi = 0; bi < 4; ++bi) {
@@ -683,12 +821,17 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
           }
         }
         __syncthreads();
-        for (int g = warp; g < G; g += NT / 32) {
+        // k candidates with upper bounds <= t: t bounds the query's k-th
+        // distance, so it is published for every later tile of the query
+        for (int g = warp; g < G; g += NW) {
           const float t = warp_kth_smallest(ub + g * CB, CB, qk[g]);
-          if (lane == 0 && t < qtau[g]) qtau[g] = t;
+          if (lane == 0 && qk[g] > 0 && t < qtau[g]) {
+            qtau[g] = t;
+            atomicMin(reinterpret_cast<unsigned int*>(a.tau_seed) + qid[g], __float_as_uint(t));
+          }
         }
         __syncthreads();
-        for (int g = tid; g < G; g += NT)
+        for (int g = tid; g < G; g += NTH)
           if (qk[g] > 0) set_query_terms(g, qtau[g]);
         __syncthreads();
         if (completed) {
@@ -697,7 +840,7 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
           for (int bi = 0; bi < 4; ++bi) ct[bi] = cterm[4 * tc + bi];
 #pragma unroll
           for (int ai = 0; ai < 4; ++ai) {
-            const float4 t = qterm[4 * tq + ai];
+            const float4 t = qterm[tq + TQ * ai];
 #pragma unroll
             for (int bi = 0; bi < 4; ++bi) {
               const float P = fmaf(t.x, ct[bi].x, fmaf(t.y, ct[bi].y, p[ai][bi]));
@@ -707,7 +850,8 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
         }
       }
       section(4);
-      // survivors of all L levels: exact re-rank and top-k insertion
+      // survivors of all L levels join the deferred list (their rows are
+      // prefetched into L2); a full list is re-ranked by all warps at once
       if (completed && alive) {
 #pragma unroll
         for (int ai = 0; ai < 4; ++ai)
@@ -715,25 +859,63 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
           for (int bi = 0; bi < 4; ++bi)
             if (alive & (1u << (4 * ai + bi))) {
               int pos = atomicAdd(&s_nsurv, 1);
-              surv[pos] = (uint16_t)(((4 * tq + ai) << 8) | (4 * tc + bi));
+              surv[pos] = (uint16_t)(((tq + TQ * ai) << 8) | (4 * tc + bi));
             }
       }
       __syncthreads();
       const int ns = s_nsurv;
-      for (int s = warp; s < ns; s += NT / 32) {
-        const int g = surv[s] >> 8, e = surv[s] & 255;
-        const int q = qid[g];
-        const int64_t slot = (tile + e / CH) * CH + (e % CH);
-        float dist = exact_sqdist_warp(a.qorig + (int64_t)q * d, a.rows + slot * d, d);
-        topk_insert_warp(a.topk + (int64_t)q * a.k_max, qk[g], make_key(dist, ids_s[e]));
+      int np = s_npend;
+      if (np + ns > FpSmem::kPend) {  // the list is full: re-rank it (all warps)
+        rerank_pending();
+        np = 0;
+        __syncthreads();
       }
-      st_rerank += (tid == 0) ? ns : 0;
+      if (ns <= FpSmem::kPend) {
+        for (int s = tid; s < ns; s += NTH) {
+          const int g = surv[s] >> 8, e = surv[s] & 255;
+          const int64_t slot = (tile + e / CH) * CH + (e % CH);
+          pslot[np + s] = slot;
+          pq[np + s] = qid[g];
+          pid[np + s] = ids_s[e];
+          if ((d & 3) == 0) {
+            prefetch_l2(a.rows + slot * d, (uint32_t)d * 4);
+            prefetch_l2(a.qorig + (int64_t)qid[g] * d, (uint32_t)d * 4);
+          }
+        }
+      } else {  // too many to defer: re-rank them now
+        for (int s = warp; s < ns; s += NW) {
+          const int g = surv[s] >> 8, e = surv[s] & 255;
+          const int64_t slot = (tile + e / CH) * CH + (e % CH);
+          const float dist = exact_sqdist_warp(a.qorig + (int64_t)qid[g] * d, a.rows + slot * d, d);
+          topk_insert_warp(a.topk + (int64_t)qid[g] * a.k_max, qk[g], make_key(dist, ids_s[e]));
+        }
+        st_rerank += (tid == 0) ? ns : 0;
+      }
+      // an unused speculative copy must land before its buffer is reused
+      wait_stage(spec);
+      wait_stage(cur);
+      // generic-proxy writes (scratch) precede later bulk-async refills
+      fence_proxy_async_smem();
       __syncthreads();
-      if (tid == 0) s_nsurv = 0;
+      if (tid == 0) {
+        s_npend = ns <= FpSmem::kPend ? np + ns : np;
+        s_nsurv = 0;
+        s_live[0] = s_live[1] = 0u;
+      }
+      cur = nxt;
       section(5);
     }
-    __syncthreads();
+    // nothing may stay in flight past the item
+    for (int b = 0; b < 3; ++b) wait_stage(b);
+    failed = __syncthreads_or(failed) != 0;
   }
+  if (!failed) {  // the last deferred survivors
+    __syncthreads();
+    rerank_pending();
+  }
+  for (int b = 0; b < 3; ++b) wait_stage(b);  // bounded; after a failure too
+  cp_async_wait_all();
+  if (failed && tid == 0) atomicOr(a.err, kErrTimeout);
   if (a.collect && tid == 0) {
     sec[6] = (unsigned long long)(clock64() - t_kernel);
     sec[7] = 1;  // CTAs that ran
@@ -750,9 +932,9 @@ __global__ void __launch_bounds__(NT, 2) verify_fp32_kernel(const VerifyArgs a) 
     if (lane == 0) atomicAdd(&a.stats[5], dv);
     if (tid == 0) {
       atomicAdd(&a.stats[1], st_tile_levels);
-      atomicAdd(&a.stats[2], st_bytes);
       atomicAdd(&a.stats[3], st_rerank);
     }
+    if (tid == ISSUER) atomicAdd(&a.stats[2], st_bytes);
   }
 }
 
@@ -804,26 +986,78 @@ cudaError_t allow_dynamic_smem(const void* kern) {
                               optin - (int)fa.sharedSizeBytes);
 }
 
-template <int QB, int CB>
-int launch_verify(const VerifyArgs& a, size_t smem, cudaStream_t st) {
+// FP32 verify tiles (QB queries x CB candidates, NTH threads).  Phase A
+// (each query's nearest list: small groups) prefers wide candidate tiles,
+// phase B (many queries per list) 64-query groups; narrower tiles serve wide
+// levels whose stage buffers would not fit otherwise.
+struct TileCfg {
+  int QB, CB, NTH;
+};
+constexpr TileCfg kTilesA[] = {{16, 256, 256}, {16, 128, 128}, {16, 64, 64}};
+constexpr TileCfg kTilesB[] = {{64, 64, 256}, {32, 64, 128}, {16, 64, 64}};
+
+template <int QB, int CB, int NTH>
+cudaError_t tile_kernel_attrs(const void** kern, size_t* static_smem) {
   static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  auto kern = verify_fp32_kernel<QB, CB>;
+  static cudaError_t err = cudaSuccess;
+  static size_t st_smem = 0;
+  auto k = verify_fp32_kernel<QB, CB, NTH>;
   std::call_once(once, [&] {
-    attr_err = allow_dynamic_smem((const void*)kern);
-    if (attr_err == cudaSuccess)
-      attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    err = allow_dynamic_smem((const void*)k);
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncAttributes fa;
+    if (err == cudaSuccess) err = cudaFuncGetAttributes(&fa, k);
+    if (err == cudaSuccess) st_smem = fa.sharedSizeBytes;
   });
-  PANO_CUDA(attr_err);
-  int dev = 0, sms = 0, optin = 0;
+  *kern = (const void*)k;
+  *static_smem = st_smem;
+  return err;
+}
+
+cudaError_t tile_attrs(const TileCfg& c, const void** kern, size_t* static_smem) {
+  if (c.QB == 16 && c.CB == 256) return tile_kernel_attrs<16, 256, 256>(kern, static_smem);
+  if (c.QB == 16 && c.CB == 128) return tile_kernel_attrs<16, 128, 128>(kern, static_smem);
+  if (c.QB == 64) return tile_kernel_attrs<64, 64, 256>(kern, static_smem);
+  if (c.QB == 32) return tile_kernel_attrs<32, 64, 128>(kern, static_smem);
+  return tile_kernel_attrs<16, 64, 64>(kern, static_smem);
+}
+
+// First tile of `list` whose stage buffers fit (blocks per SM in *bps).
+int pick_tile(const TileCfg* list, int n, int max_w, int L, TileCfg* out, int* bps) {
+  int dev = 0, optin = 0, per_sm = 0;
+  PANO_CUDA(cudaGetDevice(&dev));
+  PANO_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  PANO_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  for (int i = 0; i < n; ++i) {
+    const void* k = nullptr;
+    size_t ss = 0;
+    PANO_CUDA(tile_attrs(list[i], &k, &ss));
+    const size_t smem = FpSmem(list[i].QB, list[i].CB, max_w, L).total;
+    const long two = (long)per_sm / 2 - 1024 - (long)ss, one = (long)optin - (long)ss;
+    const int b = (long)smem <= two ? 2 : ((long)smem <= one ? 1 : 0);
+    if (b) {
+      *out = list[i];
+      *bps = b;
+      return PANO_OK;
+    }
+  }
+  return fail(PANO_EINVAL, "verify tile does not fit in shared memory");
+}
+
+// Launches the picked tile.  The grid is sized from the shared-memory plan,
+// not from the occupancy API, whose answer follows the SM's current
+// shared-memory carveout.
+int launch_verify(const VerifyArgs& a, const TileCfg& c, int bps, cudaStream_t st) {
+  const void* k = nullptr;
+  size_t ss = 0;
+  PANO_CUDA(tile_attrs(c, &k, &ss));
+  int dev = 0, sms = 0;
   PANO_CUDA(cudaGetDevice(&dev));
   PANO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  PANO_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (smem > (size_t)optin) return fail(PANO_EINVAL, "verify tile does not fit in shared memory");
-  // two CTAs per SM (the register budget); sized directly, not from the
-  // occupancy API, whose answer follows the SM's current carveout
-  kern<<<sms * 2, NT, smem, st>>>(a);
-  PANO_CUDA(cudaGetLastError());
+  const size_t smem = FpSmem(c.QB, c.CB, a.max_w, a.L).total;
+  void* args[] = {const_cast<VerifyArgs*>(&a)};
+  PANO_CUDA(cudaLaunchKernel(k, dim3(sms * bps), dim3(c.NTH), args, smem, st));
   return PANO_OK;
 }
 
@@ -871,9 +1105,15 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
   const int np_cap = nprobe ? ((nprobe_scalar >= 1) ? std::min(nprobe_scalar, nlist) : nlist)
                             : nprobe_scalar;
   const int stride = np_cap;
-  constexpr int CBA = 256, CBB = 64;
   const bool tcpath = I.precision != PANO_FP32;
-  const int QBA = tcpath ? TC_QG : 16, QBB = tcpath ? TC_QG : 64;
+  TileCfg tileA{TC_QG, 0, 0}, tileB{TC_QG, 0, 0};
+  int bpsA = 0, bpsB = 0;
+  if (!tcpath) {
+    int r = pick_tile(kTilesA, 3, I.max_w, L, &tileA, &bpsA);
+    if (!r) r = pick_tile(kTilesB, 3, I.max_w, L, &tileB, &bpsB);
+    if (r) return r;
+  }
+  const int QBA = tileA.QB, QBB = tileB.QB;
   const int SEG = tcpath ? TC_SEG : SEG_CHUNKS;
   // work-item capacity: groups x segments, plus one partial group per list
   int64_t max_seg = 1, tot_seg = 0;
@@ -1052,10 +1292,6 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     VerifyArgs va;
     std::memset(&va, 0, sizeof(va));
     va.slices = I.slices.as<float>();
-    va.tails = I.tails.as<float>();
-    va.xn2 = I.xn2.as<float>();
-    va.ex = I.ex.as<float>();
-    va.ids = I.ids.as<int32_t>();
     va.rows = I.rows.as<float>();
     va.chunk_off = I.chunk_off_d.as<int64_t>();
     va.qt = qt;
@@ -1073,10 +1309,18 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     va.k_max = k_max;
     va.gslack = (float)(2.0 * gamma_n(I.max_w + L + 8));
     va.lb_scale = (float)((1.0 - 8.0 * kU32) / (1.0 + I.eta));
+    {
+      const double inv = 1.0 / (double)va.lb_scale;
+      float f = (float)inv;
+      if ((double)f < inv) f = std::nextafter(f, INFINITY);
+      va.inv_lb_up = f;
+    }
     va.ub_scale = (float)((1.0 + 8.0 * kU32) / (1.0 - I.eta) * (1.0 + 1e-7));
     va.prune = mode == 0 ? 1 : 0;
     va.collect = collect ? 1 : 0;
     for (int l = 0; l <= L; ++l) va.level_off[l] = I.offs[l];
+    for (int l = 0; l < L; ++l) va.row_off[l] = I.fp32_row_off(l);
+    va.chunk_rows = I.fp32_chunk_rows();
     va.bucket = bucket;
     // phase A
     mark(3);
@@ -1084,7 +1328,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     va.n_items = tot + 1;
     va.counter = tot + 4;
     va.items_cap = capA;
-    int r = launch_verify<16, CBA>(va, Smem::bytes(16, CBA, I.max_w, L), st);
+    int r = launch_verify(va, tileA, bpsA, st);
     if (r) return r;
     // phase B
     mark(4);
@@ -1092,7 +1336,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     va.n_items = tot + 3;
     va.counter = tot + 5;
     va.items_cap = capB;
-    r = launch_verify<64, CBB>(va, Smem::bytes(64, CBB, I.max_w, L), st);
+    r = launch_verify(va, tileB, bpsB, st);
     if (r) return r;
     }
     mark(5);

@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       if (q >= 0 && qk[tid] > 0) {
         unsigned long long key = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + qk[tid] - 1);
         float tau = key == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key), 1.000001f);
-        set_query_terms(tid, fminf(tau, a.tau_seed[q]), a.qtail[(int64_t)q * (L + 1) + 1]);
+        set_query_terms(tid, fminf(tau, __ldcg(a.tau_seed + q)), a.qtail[(int64_t)q * (L + 1) + 1]);
       } else {
         qterm[tid] = make_float4(0.f, 0.f, 0.f, -INFINITY);
         qtau[tid] = -1.f;
@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           const int q = qid[tid];
           if (q >= 0 && qk[tid] > 0) {
             key_pf = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + qk[tid] - 1);
-            seed_pf = a.tau_seed[q];
+            seed_pf = __ldcg(a.tau_seed + q);
             sq_pf = a.qtail[(int64_t)q * (L + 1) + l + 2];
           }
         }
@@ -571,7 +571,12 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     __syncthreads();
     for (int g = warp; g < G; g += NT / 32) {
       const float t = warp_kth_smallest_bf16(ub16 + g * S * CH, S * CH, qk[g]);
-      if (lane == 0 && t < qtau[g]) qtau[g] = t;
+      // k candidates with upper bounds <= t: a threshold for every later
+      // work item of the query too
+      if (lane == 0 && qk[g] > 0 && t < qtau[g]) {
+        qtau[g] = t;
+        atomicMin(reinterpret_cast<unsigned int*>(a.tau_seed) + qid[g], __float_as_uint(t));
+      }
     }
     __syncthreads();
     if (tid < G && qk[tid] > 0) set_query_terms(tid, qtau[tid], 0.f);

@@ -22,7 +22,7 @@ struct VerifyTCArgs {
   const float4* qinfo;
   const float* qtail;
   const int32_t* kq;
-  const float* tau_seed;  // per-query warm-start threshold
+  float* tau_seed;  // per-query threshold: warm start, lowered by any item
   const int4* items;
   const int* n_items;
   int* counter;

@@ -99,7 +99,7 @@ def test_single_level_and_uneven_widths():
     q = torch.from_numpy(Q).to(DEV)
     ref = _oracle_flat(X, Q, 10)
     t = pano.panorama_fit_transform(X)
-    for widths in ([128], [8, 24, 32, 64], [4] * 4 + [16] * 6 + [16]):
+    for widths in ([128], [8, 24, 32, 64], [4] * 4 + [16] * 6 + [16], [3, 5, 7, 113]):
         idx = pano.panorama_build_ivf(t, torch.from_numpy(X).to(DEV), nlist=1,
                                       level_widths=widths)
         ids, d = idx.search(q, 1, 10)
