@@ -366,7 +366,7 @@ struct VerifyArgs {
 };
 
 // Shared-memory plan of the FP32 verify kernel, identical on host and device.
-// Three stage buffers rotate through (tile, level) steps; each holds, per
+// NST stage buffers rotate through (tile, level) steps; each holds, per
 // chunk of the tile, one level block of the slice array: the level slice,
 // the tail row of the next level and (level 0) the norms, error bounds and
 // ids, (max_w + 4) rows of 64 floats.  Query slices are kept
@@ -375,27 +375,25 @@ struct VerifyArgs {
 struct FpSmem {
   uint32_t stage_f;  // floats per stage (also the last level's UB scratch)
   uint32_t qstride;  // floats between two queries' rows in a query slice
-  uint32_t qbuf_f;   // floats per query-slice buffer (also the survivor list)
-  uint32_t off_q0, off_qb, off_cterm, off_qterm, off_qtl, off_ids, off_q, off_pend, total;
-  static constexpr int kPend = 32;  // deferred re-rank entries
-  __host__ __device__ FpSmem(int QB, int CB, int max_w, int L) {
+  uint32_t qbuf_f;   // floats per query-slice buffer
+  uint32_t off_qb, off_cterm, off_qterm, off_qtl, off_ids, off_q, off_pend, total;
+  static constexpr int kPend = 256;  // deferred re-rank entries
+  __host__ __device__ FpSmem(int QB, int CB, int max_w, int L, int NST) {
     uint32_t sf = (uint32_t)(CB * (max_w + 4));
     if (sf < (uint32_t)(QB * CB)) sf = (uint32_t)(QB * CB);
     stage_f = (sf + 31u) & ~31u;
     qstride = (uint32_t)((max_w + 3) & ~3);
     if (((qstride / 4) & 1u) == 0) qstride += 4;
-    uint32_t qf = (uint32_t)QB * qstride;
-    if (qf < (uint32_t)(QB * CB / 2)) qf = (uint32_t)(QB * CB / 2);
-    qbuf_f = (qf + 31u) & ~31u;
-    off_q0 = 3u * stage_f * 4u;
-    off_qb = off_q0 + qbuf_f * 4u;  // two buffers: levels l >= 1 by parity
+    qbuf_f = ((uint32_t)QB * qstride + 31u) & ~31u;
+    off_qb = (uint32_t)NST * stage_f * 4u;  // two buffers: levels by parity
     off_cterm = off_qb + 2u * qbuf_f * 4u;
     off_qterm = off_cterm + CB * 16u;
     off_qtl = off_qterm + QB * 16u;
     off_ids = off_qtl + (((uint32_t)QB * (L + 1) * 4u + 15u) & ~15u);
     off_q = off_ids + CB * 4u;
     off_pend = off_q + QB * 6u * 4u;
-    total = off_pend + kPend * 16u;  // slot (8), query (4), id (4)
+    // slot (8); query, id, lower bound, this tile's bounds (4 each); kept (2)
+    total = off_pend + kPend * 26u;
   }
 };
 
@@ -432,10 +430,10 @@ __device__ __forceinline__ float sqrt_ratio_up(float tau, float inv_lb_up) {
 // group's level-(l+1) query slice) is copied speculatively into a second
 // stage, and level 0 of tile t+1 (with its norms, bounds and ids) into the
 // third.  A tile that dies at level l leaves its speculative copy unused.
-// Survivors are re-ranked in batches, after their rows were prefetched into
-// L2; the delayed top-k insertions only leave the threshold larger for a
-// while, which is still a valid threshold.
-template <int QB, int CB, int NTH>
+// Survivors are re-ranked in batches (those whose lower bound exceeds the
+// threshold by then are dropped); the delayed top-k insertions only leave
+// the threshold larger for a while, which is still a valid threshold.
+template <int QB, int CB, int NTH, int NST>
 __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a) {
   constexpr int NCH = CB / CH;
   constexpr int TQ = QB / 4;
@@ -447,9 +445,8 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
   constexpr int ISSUER = 32 * ((QB + 31) / 32 < NW ? (QB + 31) / 32 : NW - 1);
   extern __shared__ __align__(128) unsigned char smem[];
   const int L = a.L, d = a.d, max_w = a.max_w;
-  const FpSmem lay(QB, CB, max_w, L);
+  const FpSmem lay(QB, CB, max_w, L, NST);
   const int QS = (int)lay.qstride;
-  float* q0 = reinterpret_cast<float*>(smem + lay.off_q0);            // level-0 query slice
   float4* cterm = reinterpret_cast<float4*>(smem + lay.off_cterm);    // (ex, rx, Hx, |x|^2)
   float4* qterm = reinterpret_cast<float4*>(smem + lay.off_qterm);    // (E, g rq, Hq, tau)
   float* qtl = reinterpret_cast<float*>(smem + lay.off_qtl);          // [QB][L+1]
@@ -463,29 +460,35 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
   int64_t* pslot = reinterpret_cast<int64_t*>(smem + lay.off_pend);   // deferred re-rank
   int32_t* pq = reinterpret_cast<int32_t*>(pslot + FpSmem::kPend);
   int32_t* pid = pq + FpSmem::kPend;
+  float* plb = reinterpret_cast<float*>(pid + FpSmem::kPend);  // the pair's lower bound
+  float* lbt = plb + FpSmem::kPend;                             // this tile's, by survivor
+  uint16_t* keep = reinterpret_cast<uint16_t*>(lbt + FpSmem::kPend);  // entries to re-rank
   const int BR = (max_w + 4) * CH;  // floats per chunk block in a stage
   auto stage_x = [&](int b) { return reinterpret_cast<float*>(smem + (uint32_t)b * lay.stage_f * 4u); };
   auto qslice = [&](int l) {
-    return l == 0 ? q0 : reinterpret_cast<float*>(smem + lay.off_qb + (uint32_t)(l & 1) * lay.qbuf_f * 4u);
+    return reinterpret_cast<float*>(smem + lay.off_qb + (uint32_t)(l & 1) * lay.qbuf_f * 4u);
   };
-  uint16_t* surv = reinterpret_cast<uint16_t*>(qslice(1));  // [QB*CB] after the levels
-  __shared__ __align__(8) uint64_t bar[3];
-  __shared__ int s_item, s_nsurv, s_npend;
+  static_assert(NST == 3 || NST == 4, "stage count");
+  __shared__ __align__(8) uint64_t bar[NST];
+  __shared__ int s_item, s_nsurv, s_npend, s_nkeep;
   __shared__ uint32_t s_live[2];
 
   const int tid = threadIdx.x;
   const int tq = tid % TQ, tc = tid / TQ;
   const int warp = tid / 32, lane = tid & 31;
   if (tid == 0) {
-    for (int b = 0; b < 3; ++b) mbar_init(&bar[b], 1);
+    for (int b = 0; b < NST; ++b) mbar_init(&bar[b], 1);
     fence_mbar_init();
     s_nsurv = 0;
     s_npend = 0;
     s_live[0] = s_live[1] = 0u;
   }
   __syncthreads();
-  // stage-buffer state, identical in every thread: phase and pending bits
-  uint32_t ph = 0, pend = 0;
+  // stage-buffer state, identical in every thread: phase and pending bits,
+  // and a FIFO of free stages (2 bits each, front in the low bits) so that a
+  // stage released with an unused speculative copy in flight is reused last
+  uint32_t ph = 0, pend = 0, fq = 0;
+  int fn = 0;
   bool failed = false;
   auto wait_stage = [&](int b) {
     if (!((pend >> b) & 1u)) return;
@@ -493,12 +496,30 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
     ph ^= 1u << b;
     pend &= ~(1u << b);
   };
+  auto push_free = [&](int b) {
+    fq |= (uint32_t)b << (2 * fn);
+    ++fn;
+  };
+  auto pop_free = [&]() {
+    const int b = (int)(fq & 3u);
+    fq >>= 2;
+    --fn;
+    return b;
+  };
   unsigned long long st_pair_levels = 0, st_dims = 0, st_tile_levels = 0, st_bytes = 0,
                      st_rerank = 0;
   // stage level l of tile `tile` (chunks in `live`) into buffer b; one
   // thread issues, every thread records the pending copy
   auto issue = [&](int b, int64_t tile, int nch, int l, uint32_t live) {
     const int w = a.level_off[l + 1] - a.level_off[l];
+    if ((pend >> b) & 1u) {
+      // An earlier (unused) copy into b must have landed, and every thread
+      // must have seen that phase complete before the barrier is re-armed:
+      // a thread still waiting on the old parity after the next phase had
+      // completed too would wait for a phase that never comes.
+      wait_stage(b);
+      __syncthreads();
+    }
     if (tid == ISSUER) {
       const uint32_t blk = (uint32_t)(w + (l == 0 ? 4 : 1)) * CH * 4;  // one level block
       mbar_arrive_expect_tx(&bar[b], (uint32_t)__popc(live) * blk);
@@ -574,14 +595,33 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
   };
   // exact distances of the deferred survivors (their rows were prefetched
   // into L2 one tile earlier) and their top-k insertion
+  // (all threads call it)
   auto rerank_pending = [&]() {
     const int np = s_npend;
-    for (int s = warp; s < np; s += NW) {
+    if (tid == 0) s_nkeep = 0;
+    __syncthreads();
+    // the threshold may have dropped since a pair survived: a lower bound
+    // above it rules the pair out without its exact distance
+    for (int s = tid; s < np; s += NTH) {
       const int q = pq[s];
+      const unsigned long long key = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + a.kq[q] - 1);
+      const float tau = fminf(key == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key), 1.000001f),
+                              __ldcg(a.tau_seed + q));
+      if (!(plb[s] > tau)) keep[atomicAdd(&s_nkeep, 1)] = (uint16_t)s;
+    }
+    __syncthreads();
+    const int nk = s_nkeep;
+    if ((d & 3) == 0)  // all kept rows head for L2 at once
+      for (int i = tid; i < nk; i += NTH) {
+        prefetch_l2(a.rows + pslot[keep[i]] * d, (uint32_t)d * 4);
+        prefetch_l2(a.qorig + (int64_t)pq[keep[i]] * d, (uint32_t)d * 4);
+      }
+    for (int i = warp; i < nk; i += NW) {
+      const int s = keep[i], q = pq[s];
       const float dist = exact_sqdist_warp(a.qorig + (int64_t)q * d, a.rows + pslot[s] * d, d);
       topk_insert_warp(a.topk + (int64_t)q * a.k_max, a.kq[q], make_key(dist, pid[s]));
     }
-    st_rerank += (tid == 0) ? np : 0;
+    st_rerank += tid == 0 ? nk : 0;
   };
 
   while (true) {
@@ -594,11 +634,26 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
     const int64_t ch0 = a.chunk_off[it.x] + (int64_t)it.y * SEG_CHUNKS;
     const int64_t ch1 = imin64(a.chunk_off[it.x + 1], ch0 + SEG_CHUNKS);
     const int G = it.w;
-    int cur = 0;
+    fq = 0u;
+    fn = 0;
+    for (int b = 0; b < NST; ++b) push_free(b);
+    // Levels 0 .. PRE-1 of tile t+1 are staged while tile t runs (with four
+    // stages also level 1: nearly every tile reaches it); deeper levels are
+    // staged speculatively one level ahead.
+    constexpr int PRE = NST - 2;
+    const bool pre1 = PRE == 2 && L > 1;
+    int cur = pop_free(), c1 = -1;  // this tile's level-0 and level-1 stages
     {
       const int nch0 = (int)imin64(NCH, ch1 - ch0);
       issue(cur, ch0, nch0, 0, (1u << nch0) - 1u);
+      if (pre1) {
+        c1 = pop_free();
+        issue(c1, ch0, nch0, 1, (1u << nch0) - 1u);
+      }
     }
+    // levels 0 and 1's query slices stay in their buffers (by level parity)
+    // unless a deeper level reuses one
+    bool qok0 = true, qok1 = true;
     for (int g = tid; g < QB; g += NTH) {
       if (g < G) {
         int q = a.bucket[it.z + g];
@@ -620,25 +675,29 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
       qtl[e] = g < G ? a.qtail[(int64_t)qid[g] * (L + 1) + l] : 0.f;
     }
     load_qslice(0, G);
+    if (L > 1) load_qslice(1, G);
     cp_async_wait_all();
     TauRead tau_next = read_tau(tid, G);
     section(0);
 
     for (int64_t tile = ch0; tile < ch1; tile += NCH) {
       const int nch = (int)imin64(NCH, ch1 - tile);
-      const int nxt = (cur + 1) % 3;
-      int spec = (cur + 2) % 3;
       wait_stage(cur);
       if (__syncthreads_or(failed)) {
         failed = true;
         break;
       }
-      // the next tile's level 0 goes out before this tile's arithmetic
-      const int64_t tile_n = tile + NCH;
-      const bool has_next = tile_n < ch1;
+      // the next tile's first levels go out before this tile's arithmetic
+      const bool has_next = tile + NCH < ch1;
+      int n0 = -1, n1 = -1;
       if (has_next) {
-        const int nch_n = (int)imin64(NCH, ch1 - tile_n);
-        issue(nxt, tile_n, nch_n, 0, (1u << nch_n) - 1u);
+        const int nch_n = (int)imin64(NCH, ch1 - tile - NCH);
+        n0 = pop_free();
+        issue(n0, tile + NCH, nch_n, 0, (1u << nch_n) - 1u);
+        if (pre1) {
+          n1 = pop_free();
+          issue(n1, tile + NCH, nch_n, 1, (1u << nch_n) - 1u);
+        }
       }
       if (tid < QB) {
         // the global threshold, or the one this item's last tile reached
@@ -698,9 +757,21 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
         // this level's query slice landed (issued one level ago) ...
         cp_async_wait_all();
         // ... and level l+1 goes out speculatively for the chunks live now
+        // (unless it was staged with the tile)
+        int nb = -1;
         if (l + 1 < L) {
-          issue(spec, tile, nch, l + 1, live);
-          load_qslice(l + 1, G);
+          if (l == 0 && pre1) {
+            nb = c1;
+            c1 = -1;
+          } else {
+            nb = pop_free();
+            issue(nb, tile, nch, l + 1, live);
+          }
+          if (l + 1 >= 2) {
+            load_qslice(l + 1, G);
+            if ((l + 1) & 1) qok1 = false;
+            else qok0 = false;
+          }
         }
         if (tid == 0) st_tile_levels += 1;
         if (l > 0) wait_stage(cur);
@@ -785,10 +856,9 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
         }
         __syncthreads();  // the stage and the query slice are refilled next
         section(l == 0 ? 2 : 3);
-        if (l + 1 < L) {  // the speculative stage becomes current
-          const int t = cur;
-          cur = spec;
-          spec = t;
+        if (l + 1 < L) {  // the next level's stage becomes current
+          push_free(cur);
+          cur = nb;
         }
       }
       if (failed) break;
@@ -798,6 +868,16 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
       // only ~k pairs per query survive even while the running top-k is
       // still empty).  The last level's stage is free: it is the scratch.
       const int done = __syncthreads_or(completed && alive != 0);
+      // every thread's copies have landed: levels 0 and 1's query slices
+      // can be restaged for the next tile
+      if (has_next && !qok0) {
+        load_qslice(0, G);
+        qok0 = true;
+      }
+      if (has_next && !qok1) {
+        load_qslice(1, G);
+        qok1 = true;
+      }
       if (done) {
         float* ub = stage_x(cur);  // [QB][CB]
         for (int e = tid; e < QB * CB; e += NTH) ub[e] = INFINITY;
@@ -850,16 +930,28 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
         }
       }
       section(4);
-      // survivors of all L levels join the deferred list (their rows are
-      // prefetched into L2); a full list is re-ranked by all warps at once
+      // survivors of all L levels join the deferred list; a full list is
+      // checked against the thresholds of the moment and the rest re-ranked
+      // by all warps at once.
+      // The list [QB*CB] is kept in the tile's last stage, read by now (a
+      // tile with survivors completed every level: no copy is landing).
+      uint16_t* surv = reinterpret_cast<uint16_t*>(stage_x(cur));
       if (completed && alive) {
 #pragma unroll
         for (int ai = 0; ai < 4; ++ai)
 #pragma unroll
           for (int bi = 0; bi < 4; ++bi)
             if (alive & (1u << (4 * ai + bi))) {
-              int pos = atomicAdd(&s_nsurv, 1);
-              surv[pos] = (uint16_t)(((tq + TQ * ai) << 8) | (4 * tc + bi));
+              const int g = tq + TQ * ai, e = 4 * tc + bi;
+              const int pos = atomicAdd(&s_nsurv, 1);
+              surv[pos] = (uint16_t)((g << 8) | e);
+              if (pos < FpSmem::kPend) {  // its Eq. 3 lower bound (C = 0 at the end)
+                const float4 ct = cterm[e];
+                const float A = qnq[g] + ct.w - 2.f * p[ai][bi];
+                const float S = qrq[g] + ct.y;
+                const float r = sqrtf(fmaxf(A - gs * S * S, 0.f)) - (qeq[g] + ct.x);
+                lbt[pos] = r > 0.f ? r * r * a.lb_scale : 0.f;
+              }
             }
       }
       __syncthreads();
@@ -877,10 +969,7 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
           pslot[np + s] = slot;
           pq[np + s] = qid[g];
           pid[np + s] = ids_s[e];
-          if ((d & 3) == 0) {
-            prefetch_l2(a.rows + slot * d, (uint32_t)d * 4);
-            prefetch_l2(a.qorig + (int64_t)qid[g] * d, (uint32_t)d * 4);
-          }
+          plb[np + s] = lbt[s];
         }
       } else {  // too many to defer: re-rank them now
         for (int s = warp; s < ns; s += NW) {
@@ -891,9 +980,10 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
         }
         st_rerank += (tid == 0) ? ns : 0;
       }
-      // an unused speculative copy must land before its buffer is reused
-      wait_stage(spec);
-      wait_stage(cur);
+      // the stages go back to the free list (an unused speculative copy may
+      // still be landing: it is drained when the stage is reused)
+      push_free(cur);
+      if (c1 >= 0) push_free(c1);
       // generic-proxy writes (scratch) precede later bulk-async refills
       fence_proxy_async_smem();
       __syncthreads();
@@ -902,18 +992,20 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
         s_nsurv = 0;
         s_live[0] = s_live[1] = 0u;
       }
-      cur = nxt;
+      cur = n0;
+      c1 = n1;
       section(5);
     }
     // nothing may stay in flight past the item
-    for (int b = 0; b < 3; ++b) wait_stage(b);
+    for (int b = 0; b < NST; ++b) wait_stage(b);
+    cp_async_wait_all();
     failed = __syncthreads_or(failed) != 0;
   }
   if (!failed) {  // the last deferred survivors
     __syncthreads();
     rerank_pending();
   }
-  for (int b = 0; b < 3; ++b) wait_stage(b);  // bounded; after a failure too
+  for (int b = 0; b < NST; ++b) wait_stage(b);  // bounded; after a failure too
   cp_async_wait_all();
   if (failed && tid == 0) atomicOr(a.err, kErrTimeout);
   if (a.collect && tid == 0) {
@@ -930,10 +1022,8 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) dv += __shfl_xor_sync(0xffffffffu, dv, off);
     if (lane == 0) atomicAdd(&a.stats[5], dv);
-    if (tid == 0) {
-      atomicAdd(&a.stats[1], st_tile_levels);
-      atomicAdd(&a.stats[3], st_rerank);
-    }
+    if (tid == 0) atomicAdd(&a.stats[1], st_tile_levels);
+    if (lane == 0) atomicAdd(&a.stats[3], st_rerank);
     if (tid == ISSUER) atomicAdd(&a.stats[2], st_bytes);
   }
 }
@@ -990,18 +1080,20 @@ cudaError_t allow_dynamic_smem(const void* kern) {
 // (each query's nearest list: small groups) prefers wide candidate tiles,
 // phase B (many queries per list) 64-query groups; narrower tiles serve wide
 // levels whose stage buffers would not fit otherwise.
+// Phase B's tiles are short (most die after a level or two), so levels 0
+// and 1 of the next tile are staged ahead (four stages); phase A's run deep.
 struct TileCfg {
-  int QB, CB, NTH;
+  int QB, CB, NTH, NST;
 };
-constexpr TileCfg kTilesA[] = {{16, 256, 256}, {16, 128, 128}, {16, 64, 64}};
-constexpr TileCfg kTilesB[] = {{64, 64, 256}, {32, 64, 128}, {16, 64, 64}};
+constexpr TileCfg kTilesA[] = {{16, 256, 256, 3}, {16, 128, 128, 3}, {16, 64, 64, 3}};
+constexpr TileCfg kTilesB[] = {{64, 64, 256, 4}, {32, 64, 128, 4}, {16, 64, 64, 3}};
 
-template <int QB, int CB, int NTH>
+template <int QB, int CB, int NTH, int NST>
 cudaError_t tile_kernel_attrs(const void** kern, size_t* static_smem) {
   static std::once_flag once;
   static cudaError_t err = cudaSuccess;
   static size_t st_smem = 0;
-  auto k = verify_fp32_kernel<QB, CB, NTH>;
+  auto k = verify_fp32_kernel<QB, CB, NTH, NST>;
   std::call_once(once, [&] {
     err = allow_dynamic_smem((const void*)k);
     if (err == cudaSuccess)
@@ -1016,11 +1108,11 @@ cudaError_t tile_kernel_attrs(const void** kern, size_t* static_smem) {
 }
 
 cudaError_t tile_attrs(const TileCfg& c, const void** kern, size_t* static_smem) {
-  if (c.QB == 16 && c.CB == 256) return tile_kernel_attrs<16, 256, 256>(kern, static_smem);
-  if (c.QB == 16 && c.CB == 128) return tile_kernel_attrs<16, 128, 128>(kern, static_smem);
-  if (c.QB == 64) return tile_kernel_attrs<64, 64, 256>(kern, static_smem);
-  if (c.QB == 32) return tile_kernel_attrs<32, 64, 128>(kern, static_smem);
-  return tile_kernel_attrs<16, 64, 64>(kern, static_smem);
+  if (c.QB == 16 && c.CB == 256) return tile_kernel_attrs<16, 256, 256, 3>(kern, static_smem);
+  if (c.QB == 16 && c.CB == 128) return tile_kernel_attrs<16, 128, 128, 3>(kern, static_smem);
+  if (c.QB == 64) return tile_kernel_attrs<64, 64, 256, 4>(kern, static_smem);
+  if (c.QB == 32) return tile_kernel_attrs<32, 64, 128, 4>(kern, static_smem);
+  return tile_kernel_attrs<16, 64, 64, 3>(kern, static_smem);
 }
 
 // First tile of `list` whose stage buffers fit (blocks per SM in *bps).
@@ -1033,7 +1125,7 @@ int pick_tile(const TileCfg* list, int n, int max_w, int L, TileCfg* out, int* b
     const void* k = nullptr;
     size_t ss = 0;
     PANO_CUDA(tile_attrs(list[i], &k, &ss));
-    const size_t smem = FpSmem(list[i].QB, list[i].CB, max_w, L).total;
+    const size_t smem = FpSmem(list[i].QB, list[i].CB, max_w, L, list[i].NST).total;
     const long two = (long)per_sm / 2 - 1024 - (long)ss, one = (long)optin - (long)ss;
     const int b = (long)smem <= two ? 2 : ((long)smem <= one ? 1 : 0);
     if (b) {
@@ -1055,7 +1147,7 @@ int launch_verify(const VerifyArgs& a, const TileCfg& c, int bps, cudaStream_t s
   int dev = 0, sms = 0;
   PANO_CUDA(cudaGetDevice(&dev));
   PANO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const size_t smem = FpSmem(c.QB, c.CB, a.max_w, a.L).total;
+  const size_t smem = FpSmem(c.QB, c.CB, a.max_w, a.L, c.NST).total;
   void* args[] = {const_cast<VerifyArgs*>(&a)};
   PANO_CUDA(cudaLaunchKernel(k, dim3(sms * bps), dim3(c.NTH), args, smem, st));
   return PANO_OK;
@@ -1106,7 +1198,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
                             : nprobe_scalar;
   const int stride = np_cap;
   const bool tcpath = I.precision != PANO_FP32;
-  TileCfg tileA{TC_QG, 0, 0}, tileB{TC_QG, 0, 0};
+  TileCfg tileA{TC_QG, 0, 0, 0}, tileB{TC_QG, 0, 0, 0};
   int bpsA = 0, bpsB = 0;
   if (!tcpath) {
     int r = pick_tile(kTilesA, 3, I.max_w, L, &tileA, &bpsA);
