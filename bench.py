@@ -33,6 +33,10 @@ METRIC = ("candidates verified/sec and QPS at oracle-exact top-k: "
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS, FALLBACK_BF16_TFS = 6800.0, 1900.0
 KERNELS_PER_SEARCH = 14  # see the launch list in profiles/
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture of a smaller case of the same kernel scaled to the full launch
+# (profiles/ holds the capture summary); None once the kernel has changed.
+TRAFFIC = {}
 
 
 def parse():
@@ -139,18 +143,25 @@ def peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
-def cpu_baseline(X, Q, C, s, sample_queries):
+def cpu_baseline(X, Q, C, s, sample_queries, target_s=12.0):
     """The oracle (as it stands) on the host cores: FP64 brute force over each
-    sampled query's candidate set after its own FP64 list assignment."""
+    sampled query's candidate set after its own FP64 list assignment.  A
+    first batch of `sample_queries` sizes the timed sample to ~target_s."""
     import numpy as np
     import oracle
     lists, _ = oracle.assign(X, C)
     ptr, rows = oracle.ivf_lists(lists, C.shape[0])
-    qs = Q[:sample_queries]
-    t0 = time.perf_counter()
-    probes, _ = oracle.probe(qs, C, s.nprobe)
-    ids, _ = oracle.ivf_topk(X, qs, ptr, rows, probes, np.full(len(qs), s.k))
-    dt = time.perf_counter() - t0
+
+    def run(qs):
+        t0 = time.perf_counter()
+        probes, _ = oracle.probe(qs, C, s.nprobe)
+        oracle.ivf_topk(X, qs, ptr, rows, probes, np.full(len(qs), s.k))
+        return time.perf_counter() - t0, probes
+
+    dt0, _ = run(Q[:sample_queries])
+    n = int(min(len(Q), max(sample_queries, sample_queries * target_s / max(dt0, 1e-6))))
+    qs = Q[:n]
+    dt, probes = run(qs)
     pairs = sum(int(ptr[p + 1].sum() - ptr[p].sum()) for p in probes)
     return {"value": pairs / dt, "unit": "candidates/s", "cores": os.cpu_count(),
             "kind": "oracle", "qps": len(qs) / dt,
@@ -334,25 +345,34 @@ def main():
     if not args.no_e2e:
         e2e_per = e2e_time(idx, Q, s, k, args, stream, flush, world, dev)
 
-    # roofline of the dominant kernel (verify phase B), measured live above
+    # roofline of the dominant kernel (verify phase B: one launch per step),
+    # its duration measured live above with CUDA events on the search stream
     pk, pk_kind = peaks()
     va = float(np.median([v[0] for v in vms]))
     vb = float(np.median([v[1] for v in vms]))
     stage = {n: float(np.median([v[2][i] for v in vms])) for i, n in
              enumerate(("transform", "probe", "inversion", "verify_a", "verify_b", "decode"))}
-    verify_ms = va + vb
-    flops = 2.0 * st["dims_scanned"]
+    dims_b = st["dims_scanned"] - st["dims_scanned_a"]
+    flops_b = 2.0 * dims_b  # algorithmic: one FMA per coordinate an alive pair reads
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA pipes
-    achieved = flops / (verify_ms / 1e3) / 1e12
-    roof = {"bound": "alu", "kernel": f"verify ({s.precision}, phases A+B)",
-            "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "traffic": None,
-            "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
-                           f"(max clock from MEASURED_PEAKS.json, {pk_kind})",
+    if s.precision == "fp32":
+        peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA pipes
+        bound, kern = "alu", "verify_fp32_kernel<64,64,256,4> (phase B)"
+        src = (f"FP32 FMA: 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
+               f"(max clock of MEASURED_PEAKS.json, {pk_kind})")
+    else:
+        peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1900.0)))
+        bound, kern = "tensor", "verify_tc_kernel (phase B)"
+        src = f"dense bf16, sustained ({pk_kind})"
+    achieved = flops_b / (vb / 1e3) / 1e12
+    roof = {"bound": bound, "kernel": kern, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": TRAFFIC.get(s.name),
+            "peak_source": src, "flops_per_launch": flops_b, "ms_per_launch": vb,
+            "phase_a": {"ms": va, "flops": 2.0 * st["dims_scanned_a"],
+                        "achieved": 2.0 * st["dims_scanned_a"] / (va / 1e3) / 1e12},
             "slice_bytes_per_step": st["slice_bytes"],
-            "slice_GBps": st["slice_bytes"] / (verify_ms / 1e3) / 1e9,
-            "hbm_peak_GBps": pk.get("hbm_gbs"), "verify_ms": verify_ms}
+            "slice_GBps": st["slice_bytes"] / ((va + vb) / 1e3) / 1e9,
+            "hbm_peak_GBps": pk.get("hbm_gbs")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -374,12 +394,13 @@ def main():
                 "value": pairs * world / (e2e_per / 1e3), "unit": "candidates/s",
                 "qps": nq * world / (e2e_per / 1e3), "ms_per_step": e2e_per,
                 "h2d_bytes_per_step": Q.numel() * 4, "d2h_bytes_per_step": nq * k * 12},
-            "gpu_launches": KERNELS_PER_SEARCH * args.steps,
+            "gpu_launches": (KERNELS_PER_SEARCH if s.nlist > 1 else KERNELS_PER_SEARCH - 2)
+                            * args.steps,
             "roofline": roof,
             "stage_ms": stage,
             "search_stats": {kk: st[kk] for kk in ("pairs", "pair_levels", "dims_scanned",
-                                                     "tile_levels", "slice_bytes", "reranked",
-                                                     "work_items")},
+                                                     "dims_scanned_a", "tile_levels",
+                                                     "slice_bytes", "reranked", "work_items")},
             "dims_scanned_frac": st["dims_scanned"] / max(1, pairs * s.d),
             "cpu_baseline": cpu,
             "clocks": clocks,

@@ -121,6 +121,7 @@ typedef struct {
    * tests, [3] the same for deeper levels.  Both: [4] last-level upper-bound
    * filter, [5] exact re-ranking, [6] whole kernel, [7] CTAs that ran. */
   int64_t section_cycles[8];
+  int64_t dims_scanned_a; /* the part of dims_scanned read in phase A        */
 } pano_search_stats;
 
 /* Description of a built index. */

@@ -61,7 +61,8 @@ class SearchStats(ctypes.Structure):
                 ("reranked", ctypes.c_int64), ("work_items", ctypes.c_int64),
                 ("device_error", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("stage_ms", ctypes.c_float * 6), ("pad2_", ctypes.c_float * 2),
-                ("section_cycles", ctypes.c_int64 * 8)]
+                ("section_cycles", ctypes.c_int64 * 8),
+                ("dims_scanned_a", ctypes.c_int64)]
 
     STAGES = ("transform", "probe", "inversion", "verify_a", "verify_b",
               "decode")

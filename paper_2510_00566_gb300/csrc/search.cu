@@ -359,6 +359,7 @@ struct VerifyArgs {
   float ub_scale;  // (1 + 8u) / (1 - eta): upper bound in T~ space -> original
   int prune;       // 0: plain scan (prune only after the last level)
   int collect;
+  int phase;        // 0: phase A (its dims are also counted apart)
   float inv_lb_up;  // 1 / lb_scale rounded up
   int32_t level_off[65];
   int32_t row_off[65];  // first row (of 64 floats) of level l's block in a chunk
@@ -1021,7 +1022,7 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
     unsigned long long dv = st_dims;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) dv += __shfl_xor_sync(0xffffffffu, dv, off);
-    if (lane == 0) atomicAdd(&a.stats[5], dv);
+    if (lane == 0) atomicAdd(&a.stats[a.phase == 0 ? 6 : 7], dv);
     if (tid == 0) atomicAdd(&a.stats[1], st_tile_levels);
     if (lane == 0) atomicAdd(&a.stats[3], st_rerank);
     if (tid == ISSUER) atomicAdd(&a.stats[2], st_bytes);
@@ -1371,6 +1372,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
       ta.n_items = tot + 1;
       ta.counter = tot + 4;
       ta.items_cap = capA;
+      ta.phase = 0;
       int r = launch_verify_tc(ta, st);
       if (r) return r;
       mark(4);
@@ -1378,6 +1380,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
       ta.n_items = tot + 3;
       ta.counter = tot + 5;
       ta.items_cap = capB;
+      ta.phase = 1;
       r = launch_verify_tc(ta, st);
       if (r) return r;
     } else {
@@ -1420,6 +1423,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     va.n_items = tot + 1;
     va.counter = tot + 4;
     va.items_cap = capA;
+    va.phase = 0;
     int r = launch_verify(va, tileA, bpsA, st);
     if (r) return r;
     // phase B
@@ -1428,6 +1432,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     va.n_items = tot + 3;
     va.counter = tot + 5;
     va.items_cap = capB;
+    va.phase = 1;
     r = launch_verify(va, tileB, bpsB, st);
     if (r) return r;
     }
@@ -1457,7 +1462,8 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
       t_stats.pairs = (int64_t)hst[4];
       t_stats.work_items = (int64_t)htot[1] + htot[3];
       t_stats.device_error = herr[0];
-      t_stats.dims_scanned = (int64_t)hst[5];
+      t_stats.dims_scanned = (int64_t)(hst[5] + hst[6] + hst[7]);
+      t_stats.dims_scanned_a = (int64_t)hst[6];
       for (int i = 0; i < 8; ++i) t_stats.section_cycles[i] = (int64_t)hst[8 + i];
       if (timing)
         for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&t_stats.stage_ms[i], ev[i], ev[i + 1]);

@@ -646,7 +646,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     }
     if (lane == 0) {
       atomicAdd(&a.stats[0], v);
-      atomicAdd(&a.stats[5], dv);
+      atomicAdd(&a.stats[a.phase == 0 ? 6 : 7], dv);
     }
     if (tid == 0) {
       atomicAdd(&a.stats[1], st_tiles);

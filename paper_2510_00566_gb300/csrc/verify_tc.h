@@ -37,6 +37,7 @@ struct VerifyTCArgs {
   float ub_scale;  // (1 + 8u) / (1 - eta)
   int prune;
   int collect;
+  int phase;  // 0: phase A (its dims are also counted apart)
   int32_t level_off[65];
 };
 
