@@ -16,10 +16,11 @@
 // the group's queries are one MMA chain: A = level tile of the chunk, B = the
 // queries' level slices split into bf16 hi + lo parts (two MMAs into the same
 // accumulator), accumulated across levels in tensor memory (4 chunks x 64
-// columns = 256 TMEM columns; two CTAs share an SM).  The epilogue thread of TMEM lane t owns
-// candidate row t: it reads its accumulators with tcgen05.ld and applies the
-// separable form of the margined Eq. 3 test, which costs three FMAs and a
-// compare per (candidate, query) pair.  Dead rows are not re-staged: at deep
+// columns = 256 TMEM columns; two CTAs share an SM).  Candidate row t is
+// owned by two epilogue threads (warps w and w + 4 read the same TMEM lane
+// quarter), one per half of the query group: each reads its 32 accumulators
+// with tcgen05.ld and applies the separable form of the margined Eq. 3 test,
+// which costs three FMAs and a compare per (candidate, query) pair.  Dead rows are not re-staged: at deep
 // levels only live rows are copied (a row-granular gather), or the whole
 // slice when most rows live.
 #include <cuda_bf16.h>
@@ -40,7 +41,10 @@ namespace {
 constexpr int CH = TC_CHUNK;  // 128 rows (MMA M)
 constexpr int QG = TC_QG;     // 64 queries per group (MMA N, padded to 16)
 constexpr int S = TC_SEG;     // chunks per segment (4 x 64 = 256 TMEM columns)
-constexpr int NT = 128;       // thread t <-> TMEM lane t <-> chunk row t
+// thread t: TMEM lane / chunk row t % 128 and query half t / 128 (queries
+// 32h .. 32h+31 are TMEM columns 32h.. of each chunk's accumulator); warps
+// w and w + 4 share a lane quarter
+constexpr int NT = 256;
 
 // ------------------------------------------------------------------ build
 // One CTA per chunk: bf16 tiles, tail norms / norms of the dequantised
@@ -123,8 +127,8 @@ __global__ void __launch_bounds__(256) pack_bf16_kernel(
 // the start of a level and written to shared memory at its end.
 constexpr int TMEM_COLS = S * QG;  // 256: two CTAs share an SM's tensor memory
 constexpr int AW = (QG + 31) / 32;  // alive-mask words per candidate row
-constexpr int PF_CHUNKS = 4;        // 16-byte query chunks prefetched per thread
-static_assert(QG <= 64 && AW <= 2 && TMEM_COLS <= 256, "two CTAs per SM");
+constexpr int PF_CHUNKS = 2;        // 16-byte query chunks prefetched per thread
+static_assert(QG == 64 && AW == 2 && TMEM_COLS <= 256, "two query halves; two CTAs per SM");
 
 struct Smem {
   uint32_t abytes, bbytes;
@@ -180,9 +184,10 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   __shared__ __align__(8) uint64_t load_bar[S], mma_bar[S];
   __shared__ uint32_t tmem_base;
   __shared__ int s_item, s_nsurv, s_fail;
-  __shared__ uint32_t rowlive[S][4];
+  __shared__ uint32_t rowlive[S][NT / 32];  // per warp: its rows live in its half
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
+  const int row = tid & (CH - 1), half = tid / CH;
   if (warp == 0) {
     tc::tmem_alloc(&tmem_base, TMEM_COLS);
     tc::tmem_relinquish();
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = tmem_base;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   const int L = a.L, d = a.d;
   uint32_t load_bits = 0, mma_bits = 0;
   unsigned long long st_pairs = 0, st_dims = 0, st_tiles = 0, st_bytes = 0, st_rerank = 0;
@@ -226,7 +231,10 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     qtau[g] = tau;
   };
   auto chunk_live = [&](int c) {
-    return (rowlive[c][0] | rowlive[c][1] | rowlive[c][2] | rowlive[c][3]) != 0u;
+    uint32_t m = 0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) m |= rowlive[c][i];
+    return m != 0u;
   };
 
   while (true) {
@@ -254,7 +262,8 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       const uint8_t* src = item_src + (int64_t)c * CH * d * 2 + (size_t)m * CH * 2;
       uint32_t atoms = 0;  // 8-row groups holding a live row
       for (int t = 0; t < 16; ++t)
-        if ((rowlive[c][t >> 2] >> ((t & 3) * 8)) & 0xffu) atoms |= 1u << t;
+        if (((rowlive[c][t >> 2] | rowlive[c][4 + (t >> 2)]) >> ((t & 3) * 8)) & 0xffu)
+          atoms |= 1u << t;
       const int na = __popc(atoms);
       if (l == 0 || na * 4 >= 3 * 16) {
         if (lane == 0) {
@@ -338,11 +347,11 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           if (g < 32) gm0 |= 1u << g;
           else gm1 |= 1u << (g - 32);
         }
+      const uint32_t gm = half ? gm1 : gm0;
       for (int c = 0; c < S; ++c) {
-        const bool v = c < nch && cid[c * CH + tid] >= 0;
-        alive[(c * CH + tid) * AW] = v ? gm0 : 0u;
-        if (AW > 1) alive[(c * CH + tid) * AW + AW - 1] = v ? gm1 : 0u;
-        const unsigned bal = __ballot_sync(0xffffffffu, v && (gm0 | gm1));
+        const bool v = c < nch && cid[c * CH + row] >= 0;
+        alive[(c * CH + row) * AW + half] = v ? gm : 0u;
+        const unsigned bal = __ballot_sync(0xffffffffu, v && gm);
         if (lane == 0) rowlive[c][warp] = bal;
       }
     }
@@ -441,44 +450,30 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         if (!((live_mask >> c) & 1u)) continue;
         const bool ok = wait_phase(&mma_bar[c], mma_bits, c, &s_fail);
         tc::fence_after_sync();
-        uint32_t w0 = alive[(c * CH + tid) * AW];
-        uint32_t wv1 = AW > 1 ? alive[(c * CH + tid) * AW + AW - 1] : 0u;
-        const bool any_warp =
-            __any_sync(0xffffffffu, (w0 | wv1) != 0) && __all_sync(0xffffffffu, ok);
+        uint32_t wm = alive[(c * CH + row) * AW + half];
+        const bool any_warp = __any_sync(0xffffffffu, wm != 0) && __all_sync(0xffffffffu, ok);
         if (any_warp) {
-          const float sx = csx[c * CH + tid], rx = crx[c * CH + tid], exv = cex[c * CH + tid];
-          const float Hx = cHx[c * CH + tid];
+          const float sx = csx[c * CH + row], rx = crx[c * CH + row], exv = cex[c * CH + row];
+          const float Hx = cHx[c * CH + row];
           if (a.collect) {
-            st_pairs += __popc(w0) + __popc(wv1);
-            st_dims += (unsigned long long)(__popc(w0) + __popc(wv1)) * w;
+            st_pairs += __popc(wm);
+            st_dims += (unsigned long long)__popc(wm) * w;
           }
           float v[32];
-          tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG), v);
-          if (test && w0) {
+          tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
+          if (test && wm) {
+            const float4* qt = qterm + 32 * half;
 #pragma unroll
             for (int g = 0; g < 32; ++g)
-              if ((w0 >> g) & 1u) {
-                const float4 t = qterm[g];
+              if ((wm >> g) & 1u) {
+                const float4 t = qt[g];
                 const float P = fmaf(t.x, exv, fmaf(t.y, rx, fmaf(t.z, sx, v[g])));
-                if (P < t.w + Hx) w0 &= ~(1u << g);
+                if (P < t.w + Hx) wm &= ~(1u << g);
               }
           }
-          if (AW > 1 && Npad > 32) {
-            tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32), v);
-            if (test && wv1) {
-#pragma unroll
-              for (int g = 0; g < 32; ++g)
-                if ((wv1 >> g) & 1u) {
-                  const float4 t = qterm[g + 32];
-                  const float P = fmaf(t.x, exv, fmaf(t.y, rx, fmaf(t.z, sx, v[g])));
-                  if (P < t.w + Hx) wv1 &= ~(1u << g);
-                }
-            }
-          }
-          alive[(c * CH + tid) * AW] = w0;
-          if (AW > 1) alive[(c * CH + tid) * AW + AW - 1] = wv1;
+          alive[(c * CH + row) * AW + half] = wm;
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, (w0 | wv1) != 0);
+        const unsigned bal = __ballot_sync(0xffffffffu, wm != 0);
         if (lane == 0) rowlive[c][warp] = bal;
         tc::fence_before_sync();
         __syncthreads();
@@ -535,37 +530,30 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     // reach re-ranking.  The bounds are kept as bf16 rounded up (still upper
     // bounds) so that all S x CH of them fit next to each other.
     for (int c = 0; c < S; ++c) {
-      uint32_t w0 = 0, wv1 = 0;
-      if (c < nch && chunk_live(c)) {
-        w0 = alive[(c * CH + tid) * AW];
-        wv1 = AW > 1 ? alive[(c * CH + tid) * AW + AW - 1] : 0u;
-      }
-      const bool any_warp = __any_sync(0xffffffffu, (w0 | wv1) != 0);
-      uint16_t* col = ub16 + c * CH + tid;  // stride S*CH between queries
+      uint32_t wm = 0;
+      if (c < nch && chunk_live(c)) wm = alive[(c * CH + row) * AW + half];
+      const bool any_warp = __any_sync(0xffffffffu, wm != 0);
+      uint16_t* col = ub16 + (32 * half) * S * CH + c * CH + row;  // stride S*CH per query
       if (any_warp) {
-        const float rx = crx[c * CH + tid], exv = cex[c * CH + tid];
-        const float nx2 = a.xn2[(ch0 + c) * CH + tid];
+        const float rx = crx[c * CH + row], exv = cex[c * CH + row];
+        const float nx2 = a.xn2[(ch0 + c) * CH + row];
         float v[32];
-        for (int half = 0; half < (Npad > 32 ? 2 : 1); ++half) {
-          tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
-          const uint32_t wm = half ? wv1 : w0;
+        tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int g = 32 * half + j;
-            uint16_t u = 0x7f80u;
-            if ((wm >> j) & 1u) {
-              const float A = qnq[g] + nx2 - 2.f * v[j];
-              const float Ss = qrq[g] + rx;
-              const float r = __fadd_ru(__fsqrt_ru(fmaxf(A + g_slack * Ss * Ss, 0.f)),
-                                        qeq[g] + exv);
-              u = __bfloat16_as_ushort(__float2bfloat16_ru(__fmul_ru(__fmul_ru(r, r), a.ub_scale)));
-            }
-            col[g * S * CH] = u;
+        for (int j = 0; j < 32; ++j) {
+          const int g = 32 * half + j;
+          uint16_t u = 0x7f80u;
+          if ((wm >> j) & 1u) {
+            const float A = qnq[g] + nx2 - 2.f * v[j];
+            const float Ss = qrq[g] + rx;
+            const float r = __fadd_ru(__fsqrt_ru(fmaxf(A + g_slack * Ss * Ss, 0.f)),
+                                      qeq[g] + exv);
+            u = __bfloat16_as_ushort(__float2bfloat16_ru(__fmul_ru(__fmul_ru(r, r), a.ub_scale)));
           }
+          col[j * S * CH] = u;
         }
-        for (int g = (Npad > 32 ? 64 : 32); g < QG; ++g) col[g * S * CH] = 0x7f80u;
       } else {
-        for (int g = 0; g < QG; ++g) col[g * S * CH] = 0x7f80u;
+        for (int j = 0; j < 32; ++j) col[j * S * CH] = 0x7f80u;
       }
     }
     __syncthreads();
@@ -587,39 +575,32 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     // survivors of the tightened test: exact distances on the original rows
     for (int c = 0; c < nch; ++c) {
       if (tid == 0) s_nsurv = 0;
-      uint32_t w0 = alive[(c * CH + tid) * AW];
-      uint32_t wv1 = AW > 1 ? alive[(c * CH + tid) * AW + AW - 1] : 0u;
-      const bool any_warp = __any_sync(0xffffffffu, (w0 | wv1) != 0);
+      uint32_t wm = alive[(c * CH + row) * AW + half];
+      const bool any_warp = __any_sync(0xffffffffu, wm != 0);
       if (any_warp) {
-        const float rx = crx[c * CH + tid], exv = cex[c * CH + tid], Hx = cHx[c * CH + tid];
+        const float rx = crx[c * CH + row], exv = cex[c * CH + row], Hx = cHx[c * CH + row];
         float v[32];
-        for (int half = 0; half < (Npad > 32 ? 2 : 1); ++half) {
-          tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
-          uint32_t& wm = half ? wv1 : w0;
+        tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
+        const float4* qt = qterm + 32 * half;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int g = 32 * half + j;
-            if ((wm >> j) & 1u) {
-              const float4 t = qterm[g];
-              const float P = fmaf(t.x, exv, fmaf(t.y, rx, v[j]));
-              if (P < t.w + Hx) wm &= ~(1u << j);
-            }
+        for (int j = 0; j < 32; ++j)
+          if ((wm >> j) & 1u) {
+            const float4 t = qt[j];
+            const float P = fmaf(t.x, exv, fmaf(t.y, rx, v[j]));
+            if (P < t.w + Hx) wm &= ~(1u << j);
           }
-        }
       }
       __syncthreads();
-      for (int g = 0; g < QG; ++g) {
-        const uint32_t bit = g < 32 ? (w0 >> g) & 1u : (wv1 >> (g - 32)) & 1u;
-        if (bit) surv[atomicAdd(&s_nsurv, 1)] = (uint16_t)((tid << 6) | g);
-      }
+      for (int j = 0; j < 32; ++j)
+        if ((wm >> j) & 1u) surv[atomicAdd(&s_nsurv, 1)] = (uint16_t)((row << 6) | (32 * half + j));
       __syncthreads();
       const int ns = s_nsurv;
       for (int s = warp; s < ns; s += NT / 32) {
-        const int row = surv[s] >> 6, g = surv[s] & 63;
+        const int r = surv[s] >> 6, g = surv[s] & 63;
         const int q = qid[g];
-        const int64_t slot = (ch0 + c) * CH + row;
+        const int64_t slot = (ch0 + c) * CH + r;
         const float dist = exact_sqdist_warp(a.qorig + (int64_t)q * d, a.rows + slot * d, d);
-        topk_insert_warp(a.topk + (int64_t)q * a.k_max, qk[g], make_key(dist, cid[c * CH + row]));
+        topk_insert_warp(a.topk + (int64_t)q * a.k_max, qk[g], make_key(dist, cid[c * CH + r]));
       }
       st_rerank += (tid == 0) ? ns : 0;
       tc::fence_before_sync();
