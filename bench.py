@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--queries", type=int, default=0, help="override the query count")
     p.add_argument("--nlist", type=int, default=0, help="override nlist (and clusters)")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-bf16", action="store_true",
+                   help="skip the BF16-storage run on FP32 workloads")
     return p.parse_args()
 
 
@@ -374,6 +376,40 @@ def main():
             "slice_GBps": st["slice_bytes"] / ((va + vb) / 1e3) / 1e9,
             "hbm_peak_GBps": pk.get("hbm_gbs")}
 
+    # pruned BF16 storage on the same data and queries (the metric's pruned
+    # BF16 vs plain FP32): level widths must be 16, 32 or multiples of 64,
+    # so d / 64 levels of 64; same transform and centroids
+    bf16 = None
+    if s.precision == "fp32" and not args.no_bf16 and s.d % 64 == 0:
+        idx16 = pano.panorama_build_ivf(t, X, nlist=s.nlist, level_widths=[64] * (s.d // 64),
+                                        precision=pano.PANO_BF16,
+                                        centroids=idx.centroids() if s.nlist > 1 else None)
+        for _ in range(args.warmup):
+            idx16.search(Q, s.nprobe, k)
+        torch.cuda.synchronize()
+        tot16 = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            idx16.search(Q, s.nprobe, k)
+            e1.record(stream)
+            e1.synchronize()
+            tot16 += e0.elapsed_time(e1)
+        t16 = torch.tensor([tot16], device=dev)
+        if world > 1:
+            dist.all_reduce(t16, op=dist.ReduceOp.MAX)
+        ms16 = t16.item() / args.steps
+        idx16.search(Q, s.nprobe, k, collect_stats=True)
+        st16 = pano.last_stats().as_dict()
+        bf16 = {"levels": f"{s.d // 64}x64", "ms_per_step": ms16,
+                "value": pairs * world / (ms16 / 1e3), "qps": nq * world / (ms16 / 1e3),
+                "speedup_vs_fp32_scan": scan_per / ms16,
+                "dims_scanned_frac": st16["dims_scanned"] / max(1, pairs * s.d),
+                "reranked": st16["reranked"]}
+        del idx16
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         Xh, Qh = X.cpu().numpy(), Q.cpu().numpy()
@@ -394,6 +430,7 @@ def main():
                 "value": pairs * world / (e2e_per / 1e3), "unit": "candidates/s",
                 "qps": nq * world / (e2e_per / 1e3), "ms_per_step": e2e_per,
                 "h2d_bytes_per_step": Q.numel() * 4, "d2h_bytes_per_step": nq * k * 12},
+            "bf16_pruned": bf16,
             "gpu_launches": (KERNELS_PER_SEARCH if s.nlist > 1 else KERNELS_PER_SEARCH - 2)
                             * args.steps,
             "roofline": roof,

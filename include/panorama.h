@@ -90,8 +90,13 @@ typedef struct {
   int32_t query_group; /* max queries sharing one tile (0 = automatic)      */
   int32_t collect_timing; /* 1 = record CUDA events around each stage on
                              `stream` (stage_ms in the stats; implies a wait) */
-  int32_t single_phase;   /* 1 = verify every probed list in one pass; 0 =
-                             each query's nearest list first (default)      */
+  int32_t single_phase;   /* 0 (default) = automatic: each query's nearest
+                             list first (phase A, which sets a tight
+                             threshold) unless the index is BF16 and there
+                             are fewer than 8 queries per list on average
+                             (phase A's groups would fill few MMA columns);
+                             1 = every probed list in one pass; 2 = two
+                             phases always                                  */
 } pano_search_opts;
 
 /* Counters of the most recent search through this index from this thread

@@ -211,10 +211,12 @@ def panorama_build_ivf(t: "Transform", X, nlist: int, n_levels=8,
 def panorama_search_ex(idx: "Index", queries, nprobe, k, k_max=None,
                        mode=0, collect_stats=False, synchronize=True,
                        stream=None, out=None, collect_timing=False,
-                       single_phase=False):
+                       single_phase=None):
     """Returns (ids int64 [nq, k_max], dists float32 [nq, k_max]) on the GPU.
 
     nprobe / k: python ints, or CUDA int32 tensors with one value per query.
+    single_phase: None = the library chooses, True = one pass, False = each
+    query's nearest list first.
     """
     import torch
     q = queries.contiguous()
@@ -244,7 +246,7 @@ def panorama_search_ex(idx: "Index", queries, nprobe, k, k_max=None,
     opts = SearchOpts(mode=mode, synchronize=1 if synchronize else 0,
                       collect_stats=1 if collect_stats else 0,
                       collect_timing=1 if collect_timing else 0,
-                      single_phase=1 if single_phase else 0)
+                      single_phase=0 if single_phase is None else (1 if single_phase else 2))
     _check(lib().panorama_search_ex(idx.handle, q.data_ptr(), nq, np_ptr,
                                     np_scalar, k_ptr, k_scalar, k_max,
                                     ids.data_ptr(), dists.data_ptr(),

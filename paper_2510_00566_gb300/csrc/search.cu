@@ -1318,7 +1318,13 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
                                                   I.rows.as<float>(), kq, tau_seed);
     PANO_CUDA(cudaGetLastError());
     const int64_t ne = nq * stride;
-    const int first_rank_b = (opts && opts->single_phase) ? 0 : 1;
+    // Phase A (each query's nearest list, verified first for a tight
+    // threshold) pays off unless its query groups are nearly empty: on the
+    // tensor-core path a group fills MMA columns, so fewer than 8 queries per
+    // list on average make one pass the better choice.
+    const int sp = opts ? opts->single_phase : 0;
+    const bool one_pass = sp == 1 || (sp == 0 && tcpath && nq < 8 * (int64_t)nlist);
+    const int first_rank_b = one_pass ? 0 : 1;
     inv_count_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(nq, probes, stride, npq, cnt,
                                                                    nlist, first_rank_b);
     inv_scan_kernel<<<1, 1024, 0, st>>>(cnt, nlist, I.chunk_off_d.as<int64_t>(), SEG, QBA, QBB,

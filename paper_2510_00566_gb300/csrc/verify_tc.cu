@@ -389,25 +389,6 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         completed = false;
         break;
       }
-      // every live chunk's tile is resident or in flight: issue all MMAs
-      if (tid == 0) {
-        const uint32_t h0 = smem_u32(bhi), l0 = smem_u32(blo);
-        for (int c = 0; c < nch; ++c) {
-          if (!((live_mask >> c) & 1u)) continue;
-          if (!wait_phase(&load_bar[c], load_bits, c, &s_fail)) continue;
-          const uint32_t a0 = smem_u32(abuf + (size_t)c * lay.abytes);
-          const uint32_t dt = tbase + (uint32_t)(c * QG);
-          for (int s = 0; s < w / 16; ++s) {
-            const uint64_t ad = tc::kstep_desc(a0, s, CH, w);
-            tc::mma_bf16(dt, ad, tc::kstep_desc(h0, s, Npad, w), idesc,
-                         (l > 0 || s > 0) ? 1u : 0u);
-            tc::mma_bf16(dt, ad, tc::kstep_desc(l0, s, Npad, w), idesc, 1u);
-          }
-          tc::mma_commit(&mma_bar[c]);
-        }
-        st_tiles += __popc(live_mask);
-      }
-      section(1);
       // prefetch the next level's query slices, tails and thresholds
       float4 pf[2 * PF_CHUNKS];
       float tail_pf[S * CH / NT];
@@ -445,9 +426,10 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           }
         }
       }
-      // epilogues in chunk order; a chunk that stays live restages at once
-      for (int c = 0; c < nch; ++c) {
-        if (!((live_mask >> c) & 1u)) continue;
+      // chunk c's MMAs go out before chunk c-1's epilogue, so the tensor
+      // core works while the previous accumulator is tested, and the first
+      // epilogue never waits for the last chunk's tile to land
+      auto epilogue = [&](int c) {
         const bool ok = wait_phase(&mma_bar[c], mma_bits, c, &s_fail);
         tc::fence_after_sync();
         uint32_t wm = alive[(c * CH + row) * AW + half];
@@ -477,11 +459,36 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         if (lane == 0) rowlive[c][warp] = bal;
         tc::fence_before_sync();
         __syncthreads();
+        // the tile stays live: its next level is staged into its (now
+        // free) buffer at once
         if (warp == 0 && has_next) {
           const int go = __shfl_sync(0xffffffffu, (chunk_live(c) && !s_fail) ? 1 : 0, 0);
           if (go) issue_load(c, l + 1);
         }
+      };
+      int prev = -1;
+      for (int c = 0; c < nch; ++c) {
+        if (!((live_mask >> c) & 1u)) continue;
+        if (tid == 0) {
+          const uint32_t h0 = smem_u32(bhi), l0 = smem_u32(blo);
+          if (wait_phase(&load_bar[c], load_bits, c, &s_fail)) {
+            const uint32_t a0 = smem_u32(abuf + (size_t)c * lay.abytes);
+            const uint32_t dt = tbase + (uint32_t)(c * QG);
+            for (int s = 0; s < w / 16; ++s) {
+              const uint64_t ad = tc::kstep_desc(a0, s, CH, w);
+              tc::mma_bf16(dt, ad, tc::kstep_desc(h0, s, Npad, w), idesc,
+                           (l > 0 || s > 0) ? 1u : 0u);
+              tc::mma_bf16(dt, ad, tc::kstep_desc(l0, s, Npad, w), idesc, 1u);
+            }
+          }
+          // committed even after a failed wait, so the epilogue's wait ends
+          tc::mma_commit(&mma_bar[c]);
+        }
+        if (prev >= 0) epilogue(prev);
+        prev = c;
       }
+      if (prev >= 0) epilogue(prev);
+      if (tid == 0) st_tiles += __popc(live_mask);
       section(2);
       if (s_fail) {
         completed = false;
