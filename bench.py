@@ -424,8 +424,10 @@ def main():
                        "l2": "256 MB buffer written between timed steps (L2 flushed)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "qps": qps,
-            "fp32_scan": {"value": pairs * world / (scan_per / 1e3), "qps": nq * world / (scan_per / 1e3),
-                          "ms_per_step": scan_per, "speedup_of_pruned": scan_per / ms_per_step},
+            # the comparator: a plain full-distance scan of the same index
+            "plain_scan": {"storage": s.precision, "value": pairs * world / (scan_per / 1e3),
+                           "qps": nq * world / (scan_per / 1e3), "ms_per_step": scan_per,
+                           "speedup_of_pruned": scan_per / ms_per_step},
             "e2e": None if e2e_per is None else {
                 "value": pairs * world / (e2e_per / 1e3), "unit": "candidates/s",
                 "qps": nq * world / (e2e_per / 1e3), "ms_per_step": e2e_per,

@@ -1,11 +1,13 @@
 // FP32 SIMT "NT" GEMM used by the query/database transform (q~ = T~(q-mu~)),
 // the coarse IVF probe and k-means:  C[m][n] = sum_k (A[m][k] - mu[k]) B[n][k].
 //
-// 128x128 CTA tile, 16-deep K tile double-buffered through shared memory,
-// 256 threads with an 8x8 register tile each.  Every K tile is accumulated in
-// a fresh register before being added to the running total, which bounds the
-// roundings a product sees by GEMM_KT + ceil(K/GEMM_KT) + 1 (used by the
-// rigorous error terms of the bounds).
+// kStore / kDist: 128x64 CTA tile (8x4 register tile per thread, so two
+// CTAs fit an SM's registers), float4 global loads when rows are 16-byte
+// aligned.  kArgmin2: 128x128 tile (8x8 per thread).  Both use a 16-deep K
+// tile double-buffered through shared memory, and every K tile is
+// accumulated in a fresh register before being added to the running total,
+// which bounds the roundings a product sees by GEMM_KT + ceil(K/GEMM_KT) + 1
+// (used by the rigorous error terms of the bounds).
 //
 // Epilogues: kStore (C = acc), kDist (C = an[m] + bn[n] - 2 acc, the squared
 // distance expansion) and kArgmin2 (no C: each row's two smallest expansion
@@ -113,27 +115,149 @@ __device__ __forceinline__ int col_of(int j) {
   return (j < 4) ? ((threadIdx.x & 15) * 4 + j) : (64 + (threadIdx.x & 15) * 4 + j - 4);
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(NT) gemm_nt_kernel(int M, int N, int K,
-                                                     const float* __restrict__ A, int lda,
-                                                     const float* __restrict__ mu,
-                                                     const float* __restrict__ B, int ldb,
-                                                     float* __restrict__ C, int64_t ldc,
-                                                     const float* __restrict__ an,
-                                                     const float* __restrict__ bn) {
+// ---- 128 x 64 tile (kStore, kDist)
+constexpr int BN2 = 64;
+
+struct Tile2 {
+  float a[2][BK][BM + PAD];
+  float b[2][BK][BN2 + PAD];
+};
+
+// thread's share of one K tile: rows r_a(i) of A (2 x float4 or 8 scalars)
+// and rows of B (1 x float4 or 4 scalars)
+template <bool VEC>
+__device__ __forceinline__ void load_tile2(const float* __restrict__ A, int lda,
+                                           const float* __restrict__ mu,
+                                           const float* __restrict__ B, int ldb, int M, int N,
+                                           int K, int m0, int n0, int k0, float (&ra)[8],
+                                           float (&rb)[4]) {
+  const int tid = threadIdx.x;
+  if (VEC) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int e = tid + NT * i, r = e >> 2, k4 = (e & 3) * 4, gm = m0 + r, gk = k0 + k4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gm < M && gk < K) {
+        v = *reinterpret_cast<const float4*>(A + (int64_t)gm * lda + gk);
+        if (mu) {
+          const float4 u = *reinterpret_cast<const float4*>(mu + gk);
+          v.x -= u.x;
+          v.y -= u.y;
+          v.z -= u.z;
+          v.w -= u.w;
+        }
+      }
+      ra[4 * i] = v.x;
+      ra[4 * i + 1] = v.y;
+      ra[4 * i + 2] = v.z;
+      ra[4 * i + 3] = v.w;
+    }
+    const int r = tid >> 2, k4 = (tid & 3) * 4, gn = n0 + r, gk = k0 + k4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (gn < N && gk < K) v = *reinterpret_cast<const float4*>(B + (int64_t)gn * ldb + gk);
+    rb[0] = v.x;
+    rb[1] = v.y;
+    rb[2] = v.z;
+    rb[3] = v.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int e = tid + NT * i, r = e >> 4, kk = e & 15, gm = m0 + r, gk = k0 + kk;
+      ra[i] = (gm < M && gk < K) ? A[(int64_t)gm * lda + gk] - (mu ? mu[gk] : 0.f) : 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + NT * i, r = e >> 4, kk = e & 15, gn = n0 + r, gk = k0 + kk;
+      rb[i] = (gn < N && gk < K) ? B[(int64_t)gn * ldb + gk] : 0.f;
+    }
+  }
+}
+
+template <bool VEC>
+__device__ __forceinline__ void store_tile2(Tile2& s, int buf, const float (&ra)[8],
+                                            const float (&rb)[4]) {
+  const int tid = threadIdx.x;
+  if (VEC) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int e = tid + NT * i, r = e >> 2, k4 = (e & 3) * 4;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s.a[buf][k4 + j][r] = ra[4 * i + j];
+    }
+    const int r = tid >> 2, k4 = (tid & 3) * 4;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s.b[buf][k4 + j][r] = rb[j];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int e = tid + NT * i;
+      s.a[buf][e & 15][e >> 4] = ra[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + NT * i;
+      s.b[buf][e & 15][e >> 4] = rb[i];
+    }
+  }
+}
+
+// rows ty*4 + {0..3} and 64 + ty*4 + {0..3}; columns tx*4 + {0..3}
+template <int MODE, bool VEC>
+__global__ void __launch_bounds__(NT, 2) gemm_nt64_kernel(int M, int N, int K,
+                                                          const float* __restrict__ A, int lda,
+                                                          const float* __restrict__ mu,
+                                                          const float* __restrict__ B, int ldb,
+                                                          float* __restrict__ C, int64_t ldc,
+                                                          const float* __restrict__ an,
+                                                          const float* __restrict__ bn) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Tile& s = *reinterpret_cast<Tile*>(smem_raw);
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  float tot[8][8];
-  mainloop(s, A, lda, mu, B, ldb, M, N, K, m0, n0, tot);
+  Tile2& s = *reinterpret_cast<Tile2*>(smem_raw);
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN2;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float tot[8][4], ra[8], rb[4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tot[i][j] = 0.f;
+  const int nk = (K + BK - 1) / BK;
+  load_tile2<VEC>(A, lda, mu, B, ldb, M, N, K, m0, n0, 0, ra, rb);
+  store_tile2<VEC>(s, 0, ra, rb);
+  __syncthreads();
+  for (int t = 0; t < nk; ++t) {
+    const int buf = t & 1;
+    if (t + 1 < nk) load_tile2<VEC>(A, lda, mu, B, ldb, M, N, K, m0, n0, (t + 1) * BK, ra, rb);
+    float acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&s.a[buf][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&s.a[buf][kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&s.b[buf][kk][tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[4] = {b0.x, b0.y, b0.z, b0.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) tot[i][j] += acc[i][j];
+    if (t + 1 < nk) store_tile2<VEC>(s, buf ^ 1, ra, rb);
+    __syncthreads();
+  }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    int gm = m0 + row_of(i);
+    const int gm = m0 + ((i < 4) ? ty * 4 + i : 64 + ty * 4 + i - 4);
     if (gm >= M) continue;
-    float am = (MODE == kDist) ? an[gm] : 0.f;
+    const float am = (MODE == kDist) ? an[gm] : 0.f;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      int gn = n0 + col_of(j);
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx * 4 + j;
       if (gn >= N) continue;
       float v = tot[i][j];
       if (MODE == kDist) v = am + bn[gn] - 2.0f * v;
@@ -208,14 +332,23 @@ cudaError_t gemm_nt(int mode, int M, int N, int K, const float* A, int lda, cons
                     const float* B, int ldb, float* C, int64_t ldc, const float* an,
                     const float* bn, cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+  dim3 grid((M + BM - 1) / BM, (N + BN2 - 1) / BN2);
   if (grid.y > 65535) return cudaErrorInvalidValue;
-  if (mode == kStore)
-    gemm_nt_kernel<kStore><<<grid, NT, tile_smem(), st>>>(M, N, K, A, lda, mu, B, ldb, C, ldc,
-                                                          an, bn);
-  else
-    gemm_nt_kernel<kDist><<<grid, NT, tile_smem(), st>>>(M, N, K, A, lda, mu, B, ldb, C, ldc,
-                                                         an, bn);
+  // float4 loads need 16-byte aligned rows (and mu)
+  const bool vec = ((K | lda | ldb) & 3) == 0 && ((uintptr_t)A & 15) == 0 &&
+                   ((uintptr_t)B & 15) == 0 && ((uintptr_t)mu & 15) == 0;
+  const size_t sm = sizeof(Tile2);  // 25.3 KB
+  if (mode == kStore) {
+    if (vec)
+      gemm_nt64_kernel<kStore, true><<<grid, NT, sm, st>>>(M, N, K, A, lda, mu, B, ldb, C, ldc, an, bn);
+    else
+      gemm_nt64_kernel<kStore, false><<<grid, NT, sm, st>>>(M, N, K, A, lda, mu, B, ldb, C, ldc, an, bn);
+  } else {
+    if (vec)
+      gemm_nt64_kernel<kDist, true><<<grid, NT, sm, st>>>(M, N, K, A, lda, mu, B, ldb, C, ldc, an, bn);
+    else
+      gemm_nt64_kernel<kDist, false><<<grid, NT, sm, st>>>(M, N, K, A, lda, mu, B, ldb, C, ldc, an, bn);
+  }
   return cudaGetLastError();
 }
 

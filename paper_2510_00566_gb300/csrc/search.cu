@@ -1379,7 +1379,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
       ta.counter = tot + 4;
       ta.items_cap = capA;
       ta.phase = 0;
-      int r = launch_verify_tc(ta, st);
+      int r = one_pass ? PANO_OK : launch_verify_tc(ta, st);  // one pass: phase A is empty
       if (r) return r;
       mark(4);
       ta.items = itB;
@@ -1430,7 +1430,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     va.counter = tot + 4;
     va.items_cap = capA;
     va.phase = 0;
-    int r = launch_verify(va, tileA, bpsA, st);
+    int r = one_pass ? PANO_OK : launch_verify(va, tileA, bpsA, st);  // one pass: phase A is empty
     if (r) return r;
     // phase B
     mark(4);

@@ -443,15 +443,16 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           }
           float v[32];
           tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
-          if (test && wm) {
+          if (test && wm) {  // every slot is tested (no branches); dead ones stay dead
             const float4* qt = qterm + 32 * half;
+            uint32_t pruned = 0;
 #pragma unroll
-            for (int g = 0; g < 32; ++g)
-              if ((wm >> g) & 1u) {
-                const float4 t = qt[g];
-                const float P = fmaf(t.x, exv, fmaf(t.y, rx, fmaf(t.z, sx, v[g])));
-                if (P < t.w + Hx) wm &= ~(1u << g);
-              }
+            for (int g = 0; g < 32; ++g) {
+              const float4 t = qt[g];
+              const float P = fmaf(t.x, exv, fmaf(t.y, rx, fmaf(t.z, sx, v[g])));
+              pruned |= (P < t.w + Hx ? 1u : 0u) << g;
+            }
+            wm &= ~pruned;
           }
           alive[(c * CH + row) * AW + half] = wm;
         }
@@ -589,13 +590,14 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         float v[32];
         tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
         const float4* qt = qterm + 32 * half;
+        uint32_t pruned = 0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if ((wm >> j) & 1u) {
-            const float4 t = qt[j];
-            const float P = fmaf(t.x, exv, fmaf(t.y, rx, v[j]));
-            if (P < t.w + Hx) wm &= ~(1u << j);
-          }
+        for (int j = 0; j < 32; ++j) {
+          const float4 t = qt[j];
+          const float P = fmaf(t.x, exv, fmaf(t.y, rx, v[j]));
+          pruned |= (P < t.w + Hx ? 1u : 0u) << j;
+        }
+        wm &= ~pruned;
       }
       __syncthreads();
       for (int j = 0; j < 32; ++j)
