@@ -477,12 +477,19 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
   const int tid = threadIdx.x;
   const int tq = tid % TQ, tc = tid / TQ;
   const int warp = tid / 32, lane = tid & 31;
+  // counters (collect_stats) live in shared memory, off the registers:
+  // [0] pair-levels, [1] dims, [2] tile-levels, [3] bytes, [4] reranked
+  __shared__ unsigned long long s_stat[5], s_sec[8];
+  __shared__ long long s_tmark, s_tkernel;
   if (tid == 0) {
     for (int b = 0; b < NST; ++b) mbar_init(&bar[b], 1);
     fence_mbar_init();
     s_nsurv = 0;
     s_npend = 0;
     s_live[0] = s_live[1] = 0u;
+    for (int i = 0; i < 5; ++i) s_stat[i] = 0;
+    for (int i = 0; i < 8; ++i) s_sec[i] = 0;
+    s_tkernel = s_tmark = clock64();
   }
   __syncthreads();
   // stage-buffer state, identical in every thread: phase and pending bits,
@@ -507,8 +514,6 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
     --fn;
     return b;
   };
-  unsigned long long st_pair_levels = 0, st_dims = 0, st_tile_levels = 0, st_bytes = 0,
-                     st_rerank = 0;
   // stage level l of tile `tile` (chunks in `live`) into buffer b; one
   // thread issues, every thread records the pending copy
   auto issue = [&](int b, int64_t tile, int nch, int l, uint32_t live) {
@@ -529,7 +534,7 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
         if ((live >> c) & 1u)
           bulk_g2s(xs + (size_t)c * BR, a.slices + ((tile + c) * a.chunk_rows + a.row_off[l]) * CH,
                    blk, &bar[b]);
-      st_bytes += (unsigned long long)__popc(live) * w * CH * 4;
+      if (a.collect) s_stat[3] += (unsigned long long)__popc(live) * w * CH * 4;
     }
     pend |= 1u << b;
   };
@@ -552,14 +557,11 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
       }
     }
   };
-  unsigned long long sec[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // section cycles (thread 0)
-  const long long t_kernel = clock64();
-  long long t_mark = t_kernel;
   auto section = [&](int i) {  // charge the time since the last mark to section i
     if (a.collect && tid == 0) {
       const long long now = clock64();
-      sec[i] += (unsigned long long)(now - t_mark);
-      t_mark = now;
+      s_sec[i] += (unsigned long long)(now - s_tmark);
+      s_tmark = now;
     }
   };
   const float gs = a.gslack;
@@ -622,7 +624,7 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
       const float dist = exact_sqdist_warp(a.qorig + (int64_t)q * d, a.rows + pslot[s] * d, d);
       topk_insert_warp(a.topk + (int64_t)q * a.k_max, a.kq[q], make_key(dist, pid[s]));
     }
-    st_rerank += tid == 0 ? nk : 0;
+    if (a.collect && tid == 0) s_stat[4] += nk;
   };
 
   while (true) {
@@ -774,7 +776,7 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
             else qok0 = false;
           }
         }
-        if (tid == 0) st_tile_levels += 1;
+        if (a.collect && tid == 0) s_stat[2] += 1;
         if (l > 0) wait_stage(cur);
         if (__syncthreads_or(failed)) {
           failed = true;
@@ -832,8 +834,11 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
 #pragma unroll
             for (int bi = 0; bi < 4; ++bi) p[ai][bi] += acc[ai][bi];
           if (a.collect) {
-            st_pair_levels += __popc(alive);
-            st_dims += (unsigned long long)__popc(alive) * w;
+            const unsigned np = __reduce_add_sync(__activemask(), (unsigned)__popc(alive));
+            if ((threadIdx.x & 31) == __ffs(__activemask()) - 1) {
+              atomicAdd(&s_stat[0], (unsigned long long)np);
+              atomicAdd(&s_stat[1], (unsigned long long)np * w);
+            }
           }
           // bound update and pruning (Eq. 3 with rounding margins)
           if (a.prune || l == L - 1) {
@@ -979,7 +984,7 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
           const float dist = exact_sqdist_warp(a.qorig + (int64_t)qid[g] * d, a.rows + slot * d, d);
           topk_insert_warp(a.topk + (int64_t)qid[g] * a.k_max, qk[g], make_key(dist, ids_s[e]));
         }
-        st_rerank += (tid == 0) ? ns : 0;
+        if (a.collect && tid == 0) s_stat[4] += ns;
       }
       // the stages go back to the free list (an unused speculative copy may
       // still be landing: it is drained when the stage is reused)
@@ -1009,23 +1014,16 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
   for (int b = 0; b < NST; ++b) wait_stage(b);  // bounded; after a failure too
   cp_async_wait_all();
   if (failed && tid == 0) atomicOr(a.err, kErrTimeout);
+  __syncthreads();
   if (a.collect && tid == 0) {
-    sec[6] = (unsigned long long)(clock64() - t_kernel);
-    sec[7] = 1;  // CTAs that ran
-    for (int i = 0; i < 8; ++i) atomicAdd(&a.stats[8 + i], sec[i]);
-  }
-  if (a.collect) {
-    unsigned long long v = st_pair_levels;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) atomicAdd(&a.stats[0], v);
-    unsigned long long dv = st_dims;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) dv += __shfl_xor_sync(0xffffffffu, dv, off);
-    if (lane == 0) atomicAdd(&a.stats[a.phase == 0 ? 6 : 7], dv);
-    if (tid == 0) atomicAdd(&a.stats[1], st_tile_levels);
-    if (lane == 0) atomicAdd(&a.stats[3], st_rerank);
-    if (tid == ISSUER) atomicAdd(&a.stats[2], st_bytes);
+    s_sec[6] = (unsigned long long)(clock64() - s_tkernel);
+    s_sec[7] = 1;  // CTAs that ran
+    for (int i = 0; i < 8; ++i) atomicAdd(&a.stats[8 + i], s_sec[i]);
+    atomicAdd(&a.stats[0], s_stat[0]);
+    atomicAdd(&a.stats[a.phase == 0 ? 6 : 7], s_stat[1]);
+    atomicAdd(&a.stats[1], s_stat[2]);
+    atomicAdd(&a.stats[2], s_stat[3]);
+    atomicAdd(&a.stats[3], s_stat[4]);
   }
 }
 

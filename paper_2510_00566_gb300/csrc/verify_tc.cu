@@ -133,9 +133,10 @@ static_assert(QG == 64 && AW == 2 && TMEM_COLS <= 256, "two query halves; two CT
 struct Smem {
   uint32_t abytes, bbytes;
   uint32_t off_b_hi, off_b_lo, off_alive, off_cand, off_q, total;
+  static constexpr int kPend = 256;  // deferred re-rank entries (static shared memory)
   __host__ __device__ Smem(int max_w) {
     // after the last level the A buffers hold the [QG][S*CH] bf16 upper
-    // bounds, then the [CH * QG] survivor list
+    // bounds, then the [CH * QG] survivor list and their lower bounds
     uint32_t a = (uint32_t)(CH * max_w * 2);
     const uint32_t per = (uint32_t)(QG * S * CH * 2 + S - 1) / S;
     if (a < per) a = per;
@@ -149,6 +150,38 @@ struct Smem {
     total = off_q + 10 * QG * 4;
   }
 };
+
+// The deferred pairs are checked against their queries' thresholds of the
+// moment (a lower bound above one rules the pair out); the rest get their
+// exact distance and top-k insertion.  All threads of the CTA call it; kept
+// out of line so that it does not add to the level loop's registers.
+// Returns the number re-ranked (thread 0; 0 elsewhere).
+__device__ __noinline__ int flush_pending(const VerifyTCArgs& a, int np,
+                                          const int64_t* __restrict__ pslot,
+                                          const int32_t* __restrict__ pq,
+                                          const int32_t* __restrict__ pid,
+                                          const float* __restrict__ plb, uint16_t* keep,
+                                          int* s_nkeep) {
+  const int tid = threadIdx.x, warp = tid / 32;
+  if (tid == 0) *s_nkeep = 0;
+  __syncthreads();
+  for (int s = tid; s < np; s += blockDim.x) {
+    const int q = pq[s];
+    const unsigned long long key = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + a.kq[q] - 1);
+    const float tau = fminf(key == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key), 1.000001f),
+                            __ldcg(a.tau_seed + q));
+    if (!(plb[s] > tau)) keep[atomicAdd(s_nkeep, 1)] = (uint16_t)s;
+  }
+  __syncthreads();
+  const int nk = *s_nkeep;
+  for (int i = warp; i < nk; i += blockDim.x / 32) {
+    const int s = keep[i], q = pq[s];
+    const float dist = exact_sqdist_warp(a.qorig + (int64_t)q * a.d, a.rows + pslot[s] * a.d, a.d);
+    topk_insert_warp(a.topk + (int64_t)q * a.k_max, a.kq[q], make_key(dist, pid[s]));
+  }
+  __syncthreads();
+  return tid == 0 ? nk : 0;
+}
 
 __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t& bits, int b, int* fail) {
   const uint32_t par = (bits >> b) & 1u;
@@ -181,9 +214,16 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   float* qtau = qeq + QG;
   uint16_t* ub16 = reinterpret_cast<uint16_t*>(abuf);  // [QG][S*CH] bf16 bits
   uint16_t* surv = reinterpret_cast<uint16_t*>(abuf);  // [CH * QG], after ub16 is read
+  // [32][NT] each thread's last accumulators (slot j of thread t at j*NT + t)
+  float* vdump = reinterpret_cast<float*>(abuf + CH * QG * 2);
+  // deferred re-rank list: (slot, query, id, lower bound) per pair
+  __shared__ int64_t pslot[Smem::kPend];
+  __shared__ int32_t pq[Smem::kPend], pid[Smem::kPend];
+  __shared__ float plb[Smem::kPend];
+  __shared__ uint16_t keep[Smem::kPend];
   __shared__ __align__(8) uint64_t load_bar[S], mma_bar[S];
   __shared__ uint32_t tmem_base;
-  __shared__ int s_item, s_nsurv, s_fail;
+  __shared__ int s_item, s_nsurv, s_fail, s_npend, s_nkeep;
   __shared__ uint32_t rowlive[S][NT / 32];  // per warp: its rows live in its half
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
@@ -199,6 +239,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     }
     fence_mbar_init();
     s_fail = 0;
+    s_npend = 0;
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -207,15 +248,20 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   const int L = a.L, d = a.d;
   uint32_t load_bits = 0, mma_bits = 0;
-  unsigned long long st_pairs = 0, st_dims = 0, st_tiles = 0, st_bytes = 0, st_rerank = 0;
-  unsigned long long sec[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // section cycles (thread 0)
-  const long long t_kernel = clock64();
-  long long t_mark = t_kernel;
+  // counters (collect_stats) live in shared memory, off the registers:
+  // [0] pairs, [1] dims, [2] tiles, [3] bytes, [4] reranked; section cycles
+  __shared__ unsigned long long s_stat[5], s_sec[8];
+  __shared__ long long s_tmark, s_tkernel;
+  if (tid == 0) {
+    for (int i = 0; i < 5; ++i) s_stat[i] = 0;
+    for (int i = 0; i < 8; ++i) s_sec[i] = 0;
+    s_tkernel = s_tmark = clock64();
+  }
   auto section = [&](int i) {  // charge the time since the last mark to section i
     if (a.collect && tid == 0) {
       const long long now = clock64();
-      sec[i] += (unsigned long long)(now - t_mark);
-      t_mark = now;
+      s_sec[i] += (unsigned long long)(now - s_tmark);
+      s_tmark = now;
     }
   };
   const float g_slack = a.gslack;
@@ -230,6 +276,10 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
                            0.5f * (nq - g_slack * nq - E * E - kEval * (rq + E) * (rq + E)));
     qtau[g] = tau;
   };
+  auto rerank_pending = [&]() {
+    const int nk = flush_pending(a, s_npend, pslot, pq, pid, plb, keep, &s_nkeep);
+    if (a.collect && tid == 0) s_stat[4] += nk;
+  };
   auto chunk_live = [&](int c) {
     uint32_t m = 0;
 #pragma unroll
@@ -243,7 +293,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     const int item = s_item;
     const int64_t n_items = *a.n_items < a.items_cap ? *a.n_items : a.items_cap;
     if (item >= n_items || s_fail) break;
-    if (tid == 0) t_mark = clock64();
+    if (a.collect && tid == 0) s_tmark = clock64();
     const int4 it = a.items[item];
     const int64_t ch0 = a.chunk_off[it.x] + (int64_t)it.y * S;
     const int64_t chE = a.chunk_off[it.x + 1];
@@ -270,7 +320,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           mbar_arrive_expect_tx(&load_bar[c], tbytes);
           bulk_g2s(dst, src, tbytes, &load_bar[c]);
         }
-        st_bytes += (lane == 0) ? tbytes : 0;
+        if (a.collect && lane == 0) s_stat[3] += tbytes;
       } else {
         const uint32_t abytes_row = (uint32_t)(8 * rb);  // one 8-row atom of one panel
         if (lane == 0) mbar_arrive_expect_tx(&load_bar[c], (uint32_t)na * npan * abytes_row);
@@ -282,7 +332,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
             bulk_g2s(dst + o, src + o, abytes_row, &load_bar[c]);
           }
         }
-        st_bytes += (lane == 0) ? (unsigned long long)na * npan * abytes_row : 0;
+        if (a.collect && lane == 0) s_stat[3] += (unsigned long long)na * npan * abytes_row;
       }
     };
     // B tiles for level l: query slices split into bf16 hi / lo
@@ -438,8 +488,11 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           const float sx = csx[c * CH + row], rx = crx[c * CH + row], exv = cex[c * CH + row];
           const float Hx = cHx[c * CH + row];
           if (a.collect) {
-            st_pairs += __popc(wm);
-            st_dims += (unsigned long long)__popc(wm) * w;
+            const unsigned np = __reduce_add_sync(0xffffffffu, (unsigned)__popc(wm));
+            if (lane == 0) {
+              atomicAdd(&s_stat[0], (unsigned long long)np);
+              atomicAdd(&s_stat[1], (unsigned long long)np * w);
+            }
           }
           float v[32];
           tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
@@ -489,7 +542,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         prev = c;
       }
       if (prev >= 0) epilogue(prev);
-      if (tid == 0) st_tiles += __popc(live_mask);
+      if (a.collect && tid == 0) s_stat[2] += __popc(live_mask);
       section(2);
       if (s_fail) {
         completed = false;
@@ -580,9 +633,12 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     __syncthreads();
     tc::fence_after_sync();
     section(4);
-    // survivors of the tightened test: exact distances on the original rows
+    // survivors of the tightened test join the deferred re-rank list with
+    // their Eq. 3 lower bound (C = 0 after the last level); a full list is
+    // checked and re-ranked by all warps at once
     for (int c = 0; c < nch; ++c) {
       if (tid == 0) s_nsurv = 0;
+      __syncthreads();
       uint32_t wm = alive[(c * CH + row) * AW + half];
       const bool any_warp = __any_sync(0xffffffffu, wm != 0);
       if (any_warp) {
@@ -598,51 +654,71 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           pruned |= (P < t.w + Hx ? 1u : 0u) << j;
         }
         wm &= ~pruned;
+        if (wm) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) vdump[j * NT + tid] = v[j];
+        }
       }
-      __syncthreads();
-      for (int j = 0; j < 32; ++j)
-        if ((wm >> j) & 1u) surv[atomicAdd(&s_nsurv, 1)] = (uint16_t)((row << 6) | (32 * half + j));
+      for (uint32_t m = wm; m; m &= m - 1) {
+        const int j = __ffs(m) - 1;
+        surv[atomicAdd(&s_nsurv, 1)] = (uint16_t)((row << 6) | (32 * half + j));
+      }
       __syncthreads();
       const int ns = s_nsurv;
-      for (int s = warp; s < ns; s += NT / 32) {
-        const int r = surv[s] >> 6, g = surv[s] & 63;
-        const int q = qid[g];
-        const int64_t slot = (ch0 + c) * CH + r;
-        const float dist = exact_sqdist_warp(a.qorig + (int64_t)q * d, a.rows + slot * d, d);
-        topk_insert_warp(a.topk + (int64_t)q * a.k_max, qk[g], make_key(dist, cid[c * CH + r]));
+      int np = s_npend;
+      if (np + ns > Smem::kPend) {
+        rerank_pending();
+        np = 0;
       }
-      st_rerank += (tid == 0) ? ns : 0;
+      if (ns <= Smem::kPend) {
+        for (int s = tid; s < ns; s += NT) {
+          const int r = surv[s] >> 6, g = surv[s] & 63;
+          const int64_t slot = (ch0 + c) * CH + r;
+          const float rx = crx[c * CH + r], exv = cex[c * CH + r];
+          const float p = vdump[(g & 31) * NT + r + CH * (g >> 5)];  // all levels
+          const float A = qnq[g] + a.xn2[slot] - 2.f * p;
+          const float Ss = qrq[g] + rx;
+          const float lr = sqrtf(fmaxf(A - g_slack * Ss * Ss, 0.f)) - (qeq[g] + exv);
+          pslot[np + s] = slot;
+          pq[np + s] = qid[g];
+          pid[np + s] = cid[c * CH + r];
+          plb[np + s] = lr > 0.f ? lr * lr * a.lb_scale : 0.f;
+        }
+      } else {  // too many to defer: re-rank them now
+        for (int s = warp; s < ns; s += NT / 32) {
+          const int r = surv[s] >> 6, g = surv[s] & 63;
+          const int q = qid[g];
+          const int64_t slot = (ch0 + c) * CH + r;
+          const float dist = exact_sqdist_warp(a.qorig + (int64_t)q * d, a.rows + slot * d, d);
+          topk_insert_warp(a.topk + (int64_t)q * a.k_max, qk[g], make_key(dist, cid[c * CH + r]));
+        }
+        if (a.collect && tid == 0) s_stat[4] += ns;
+      }
       tc::fence_before_sync();
       __syncthreads();
       tc::fence_after_sync();
+      if (tid == 0) s_npend = ns <= Smem::kPend ? np + ns : np;
     }
     // the scratch written through the generic proxy is refilled by
     // bulk-async copies in the next item
     fence_proxy_async_smem();
     section(5);
   }
-  if (s_fail && tid == 0) atomicOr(a.err, kErrTimeout);
-  if (a.collect && tid == 0) {
-    sec[6] = (unsigned long long)(clock64() - t_kernel);
-    sec[7] = 1;  // CTAs that ran
-    for (int i = 0; i < 8; ++i) atomicAdd(&a.stats[8 + i], sec[i]);
+  if (!s_fail) {  // the last deferred survivors
+    __syncthreads();
+    rerank_pending();
   }
-  if (a.collect) {
-    unsigned long long v = st_pairs, dv = st_dims;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      v += __shfl_xor_sync(0xffffffffu, v, off);
-      dv += __shfl_xor_sync(0xffffffffu, dv, off);
-    }
-    if (lane == 0) {
-      atomicAdd(&a.stats[0], v);
-      atomicAdd(&a.stats[a.phase == 0 ? 6 : 7], dv);
-    }
-    if (tid == 0) {
-      atomicAdd(&a.stats[1], st_tiles);
-      atomicAdd(&a.stats[3], st_rerank);
-    }
-    if (lane == 0) atomicAdd(&a.stats[2], st_bytes);
+  if (s_fail && tid == 0) atomicOr(a.err, kErrTimeout);
+  __syncthreads();
+  if (a.collect && tid == 0) {
+    s_sec[6] = (unsigned long long)(clock64() - s_tkernel);
+    s_sec[7] = 1;  // CTAs that ran
+    for (int i = 0; i < 8; ++i) atomicAdd(&a.stats[8 + i], s_sec[i]);
+    atomicAdd(&a.stats[0], s_stat[0]);
+    atomicAdd(&a.stats[a.phase == 0 ? 6 : 7], s_stat[1]);
+    atomicAdd(&a.stats[1], s_stat[2]);
+    atomicAdd(&a.stats[2], s_stat[3]);
+    atomicAdd(&a.stats[3], s_stat[4]);
   }
   tc::fence_before_sync();
   __syncthreads();
