@@ -97,6 +97,10 @@ typedef struct {
                              (phase A's groups would fill few MMA columns);
                              1 = every probed list in one pass; 2 = two
                              phases always                                  */
+  float epsilon;          /* 0 or 1 (default) = exact pruning with Eq. 3's
+                             LB; in (0, 1): Eq. 4's relaxed LB_eps = A -
+                             2 eps C prunes more and may lose true
+                             neighbours (returned distances stay exact)    */
 } pano_search_opts;
 
 /* Counters of the most recent search through this index from this thread
@@ -343,6 +347,34 @@ int panorama_index_assignment(const pano_index* idx, int32_t* out);
 int panorama_save(const pano_index* idx, const char* path);
 int panorama_load(const char* path, pano_index** out);
 void panorama_free_index(pano_index* idx);
+
+/* ------------------------------------------------------ list sharding
+ * Host-side helpers of a search sharded by IVF lists over several GPUs
+ * (each GPU holds the index of the vectors of its lists, with all
+ * centroids, so its probes are the global ones; every candidate lives on
+ * exactly one shard).  The paper's search is single-machine and has no
+ * counterpart; the merge is the k-smallest selection of Problem 1 (§3) over
+ * the union of the shards' candidate sets, which the shards' own top-k
+ * lists contain.  Neither call touches the GPU.
+ *
+ * panorama_partition_lists: owner[c] in [0, n_shards) for every list, by
+ * greedy bin packing (lists by decreasing size, ties by id, each to the
+ * least-loaded shard, ties by shard id), so Σ sizes per shard is balanced.
+ * list_size: host int32[nlist].  Errors: PANO_EINVAL (null pointer, nlist
+ * < 1, n_shards < 1, negative size).
+ *
+ * panorama_merge_topk: n_parts partial results, part p at ids[p][nq][k] /
+ * dists[p][nq][k] (host, contiguous: ids + (p * nq + i) * k), each row
+ * sorted by (dist, id) and padded with (-1, +inf), as panorama_search
+ * writes them.  Writes out_ids/out_dists [nq][k] (host): per query the k
+ * smallest (dist, id) pairs over all parts, ascending, padded the same
+ * way; an id in more than one part counts once, at its smallest distance.
+ * Errors:
+ * PANO_EINVAL (null pointer, n_parts < 1, nq < 0, k < 1). */
+int panorama_partition_lists(const int32_t* list_size, int32_t nlist, int32_t n_shards,
+                             int32_t* owner);
+int panorama_merge_topk(const int64_t* ids, const float* dists, int32_t n_parts, int64_t nq,
+                        int32_t k, int64_t* out_ids, float* out_dists);
 
 /* Message of the calling thread's last failed call ("" if none). */
 const char* panorama_last_error(void);

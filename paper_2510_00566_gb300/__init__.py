@@ -49,7 +49,8 @@ class SearchOpts(ctypes.Structure):
                 ("collect_stats", ctypes.c_int32),
                 ("query_group", ctypes.c_int32),
                 ("collect_timing", ctypes.c_int32),
-                ("single_phase", ctypes.c_int32)]
+                ("single_phase", ctypes.c_int32),
+                ("epsilon", ctypes.c_float)]
 
 
 class SearchStats(ctypes.Structure):
@@ -89,6 +90,8 @@ class IndexInfo(ctypes.Structure):
 # name -> (restype, argtypes); the exported C-ABI (include/panorama.h)
 _P, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
 SIGNATURES = {
+    "panorama_partition_lists": (ctypes.c_int, [_P, _I32, _I32, _P]),
+    "panorama_merge_topk": (ctypes.c_int, [_P, _P, _I32, _I64, _I32, _P, _P]),
     "panorama_fit_transform": (ctypes.c_int, [_P, _I64, _I32, _P, _P]),
     "panorama_transform_export": (ctypes.c_int, [_P, _P, _P, _P]),
     "panorama_transform_dim": (ctypes.c_int, [_P]),
@@ -211,12 +214,13 @@ def panorama_build_ivf(t: "Transform", X, nlist: int, n_levels=8,
 def panorama_search_ex(idx: "Index", queries, nprobe, k, k_max=None,
                        mode=0, collect_stats=False, synchronize=True,
                        stream=None, out=None, collect_timing=False,
-                       single_phase=None):
+                       single_phase=None, epsilon=1.0):
     """Returns (ids int64 [nq, k_max], dists float32 [nq, k_max]) on the GPU.
 
     nprobe / k: python ints, or CUDA int32 tensors with one value per query.
     single_phase: None = the library chooses, True = one pass, False = each
-    query's nearest list first.
+    query's nearest list first.  epsilon < 1: Eq. 4's relaxed pruning
+    (approximate; exact distances for what is returned).
     """
     import torch
     q = queries.contiguous()
@@ -246,7 +250,8 @@ def panorama_search_ex(idx: "Index", queries, nprobe, k, k_max=None,
     opts = SearchOpts(mode=mode, synchronize=1 if synchronize else 0,
                       collect_stats=1 if collect_stats else 0,
                       collect_timing=1 if collect_timing else 0,
-                      single_phase=0 if single_phase is None else (1 if single_phase else 2))
+                      single_phase=0 if single_phase is None else (1 if single_phase else 2),
+                      epsilon=float(epsilon))
     _check(lib().panorama_search_ex(idx.handle, q.data_ptr(), nq, np_ptr,
                                     np_scalar, k_ptr, k_scalar, k_max,
                                     ids.data_ptr(), dists.data_ptr(),
@@ -495,3 +500,49 @@ class Index:
 
     def __del__(self):
         self.free()
+
+
+# ------------------------------------------------------------ list sharding
+def panorama_partition_lists(list_size, n_shards: int):
+    """Owner shard of every IVF list (greedy balance of list sizes); host."""
+    import numpy as np
+    ls = np.ascontiguousarray(list_size, dtype=np.int32)
+    owner = np.empty(ls.shape[0], dtype=np.int32)
+    _check(lib().panorama_partition_lists(ls.ctypes.data, ls.shape[0], int(n_shards),
+                                          owner.ctypes.data))
+    return owner
+
+
+def panorama_merge_topk(ids_parts, dists_parts):
+    """Exact merge of per-shard top-k results (host arrays [n_parts, nq, k]
+    or lists of [nq, k]); returns (ids int64 [nq, k], dists float32 [nq, k])."""
+    import numpy as np
+    ids = np.ascontiguousarray(np.stack([np.asarray(x) for x in ids_parts]), dtype=np.int64)
+    dists = np.ascontiguousarray(np.stack([np.asarray(x) for x in dists_parts]),
+                                 dtype=np.float32)
+    n_parts, nq, k = ids.shape
+    out_i = np.empty((nq, k), dtype=np.int64)
+    out_d = np.empty((nq, k), dtype=np.float32)
+    _check(lib().panorama_merge_topk(ids.ctypes.data, dists.ctypes.data, n_parts, nq, k,
+                                     out_i.ctypes.data, out_d.ctypes.data))
+    return out_i, out_d
+
+
+def gather_merge_topk(ids, dists, group=None, dst: int = 0):
+    """Every rank's partial top-k (torch tensors [nq, k], any device) are
+    gathered on rank `dst` (torch.distributed, e.g. gloo or nccl) and merged
+    there; returns (ids, dists) numpy arrays on `dst`, None elsewhere."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    ids_c = ids.detach().to("cpu", torch.int64).contiguous()
+    dists_c = dists.detach().to("cpu", torch.float32).contiguous()
+    gi = [torch.empty_like(ids_c) for _ in range(world)] if rank == dst else None
+    gd = [torch.empty_like(dists_c) for _ in range(world)] if rank == dst else None
+    dist.gather(ids_c, gi, dst=dst, group=group)
+    dist.gather(dists_c, gd, dst=dst, group=group)
+    if rank != dst:
+        return None
+    return panorama_merge_topk([t.numpy() for t in gi], [t.numpy() for t in gd])
+

@@ -360,6 +360,7 @@ struct VerifyArgs {
   int prune;       // 0: plain scan (prune only after the last level)
   int collect;
   int phase;        // 0: phase A (its dims are also counted apart)
+  float eps;        // Eq. 4: the query tail term of the pruning test is scaled by eps
   float inv_lb_up;  // 1 / lb_scale rounded up
   int32_t level_off[65];
   int32_t row_off[65];  // first row (of 64 floats) of level l's block in a chunk
@@ -675,7 +676,7 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
     __syncthreads();
     for (int e = tid; e < QB * (L + 1); e += NTH) {
       int g = e / (L + 1), l = e % (L + 1);
-      qtl[e] = g < G ? a.qtail[(int64_t)qid[g] * (L + 1) + l] : 0.f;
+      qtl[e] = g < G ? a.eps * a.qtail[(int64_t)qid[g] * (L + 1) + l] : 0.f;
     }
     load_qslice(0, G);
     if (L > 1) load_qslice(1, G);
@@ -1182,6 +1183,8 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
                "nprobe must be in [1, nlist]");
   if (!k) PANO_CHECK(k_scalar >= 0 && k_scalar <= k_max, PANO_EINVAL, "k must be in [0, k_max]");
   const int mode = opts ? opts->mode : 0;
+  // Eq. 4: LB_eps = A - 2 eps C (0 and 1 mean the exact Eq. 3)
+  const float eps = (opts && opts->epsilon > 0.f && opts->epsilon < 1.f) ? opts->epsilon : 1.f;
   const bool timing = opts ? opts->collect_timing != 0 : false;
   const bool sync = (opts ? opts->synchronize != 0 : true) || timing;
   const bool collect = opts ? opts->collect_stats != 0 : false;
@@ -1368,6 +1371,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
       ta.lb_scale = (float)((1.0 - 8.0 * kU32) / (1.0 + I.eta));
       ta.ub_scale = (float)((1.0 + 8.0 * kU32) / (1.0 - I.eta) * (1.0 + 1e-7));
       ta.prune = mode == 0 ? 1 : 0;
+      ta.eps = eps;
       ta.collect = collect ? 1 : 0;
       for (int l = 0; l <= L; ++l) ta.level_off[l] = I.offs[l];
       ta.bucket = bucket;
@@ -1416,6 +1420,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     }
     va.ub_scale = (float)((1.0 + 8.0 * kU32) / (1.0 - I.eta) * (1.0 + 1e-7));
     va.prune = mode == 0 ? 1 : 0;
+    va.eps = eps;
     va.collect = collect ? 1 : 0;
     for (int l = 0; l <= L; ++l) va.level_off[l] = I.offs[l];
     for (int l = 0; l < L; ++l) va.row_off[l] = I.fp32_row_off(l);

@@ -414,7 +414,8 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       if (q >= 0 && qk[tid] > 0) {
         unsigned long long key = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + qk[tid] - 1);
         float tau = key == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key), 1.000001f);
-        set_query_terms(tid, fminf(tau, __ldcg(a.tau_seed + q)), a.qtail[(int64_t)q * (L + 1) + 1]);
+        set_query_terms(tid, fminf(tau, __ldcg(a.tau_seed + q)),
+                        a.eps * a.qtail[(int64_t)q * (L + 1) + 1]);
       } else {
         qterm[tid] = make_float4(0.f, 0.f, 0.f, -INFINITY);
         qtau[tid] = -1.f;
@@ -472,7 +473,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           if (q >= 0 && qk[tid] > 0) {
             key_pf = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + qk[tid] - 1);
             seed_pf = __ldcg(a.tau_seed + q);
-            sq_pf = a.qtail[(int64_t)q * (L + 1) + l + 2];
+            sq_pf = a.eps * a.qtail[(int64_t)q * (L + 1) + l + 2];
           }
         }
       }
@@ -494,9 +495,9 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
               atomicAdd(&s_stat[1], (unsigned long long)np * w);
             }
           }
-          float v[32];
-          tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
-          if (test && wm) {  // every slot is tested (no branches); dead ones stay dead
+          if (test) {  // every slot is tested (no branches); dead ones stay dead
+            float v[32];
+            tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
             const float4* qt = qterm + 32 * half;
             uint32_t pruned = 0;
 #pragma unroll

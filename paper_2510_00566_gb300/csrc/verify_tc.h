@@ -38,6 +38,7 @@ struct VerifyTCArgs {
   int prune;
   int collect;
   int phase;  // 0: phase A (its dims are also counted apart)
+  float eps;  // Eq. 4: the query tail term of the pruning test is scaled by eps
   int32_t level_off[65];
 };
 

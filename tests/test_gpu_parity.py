@@ -161,6 +161,38 @@ def test_ivf_search_matches_oracle(ivf960, nprobe, mode):
                gamma_rows=[G[i] for i in np.nonzero(keep)[0]])
 
 
+@pytest.mark.gpu
+def test_epsilon_relaxed_pruning(ivf960):
+    """Eq. 4: eps < 1 prunes with LB_eps = A - 2 eps C.  What is returned is
+    still exact (true candidates, exact distances, sorted, distinct); recall
+    against the exact top-k is measured, and the coordinates read shrink.
+    eps = 1 is the exact search."""
+    s, X, Q, C, t, idx = ivf960
+    q = torch.from_numpy(Q).to(DEV)
+    ids1, d1 = idx.search(q, 8, 10, collect_stats=True)
+    dims1 = pano.last_stats().dims_scanned
+    ids_one, _ = idx.search(q, 8, 10, epsilon=1.0)
+    assert torch.equal(ids1, ids_one)
+    ids_e, d_e = idx.search(q, 8, 10, epsilon=0.5, collect_stats=True)
+    dims_e = pano.last_stats().dims_scanned
+    ids_e, d_e, ids1 = ids_e.cpu().numpy(), d_e.cpu().numpy(), ids1.cpu().numpy()
+    lists = idx.assignment()
+    probes, gap = oracle.probe(Q, C, 8)
+    hits = 0
+    for i in range(len(Q)):
+        g = ids_e[i][ids_e[i] >= 0]
+        assert len(set(g.tolist())) == len(g)
+        if gap[i] >= 1e-6:  # (a probe near-tie may be ordered either way)
+            assert np.all(np.isin(lists[g], probes[i]))
+        true_d = ((X[g].astype(np.float64) - Q[i]) ** 2).sum(1)
+        assert np.all(np.abs(d_e[i][:len(g)] - true_d) <= 1e-5 * np.maximum(true_d, 1e-30))
+        assert np.all(np.diff(d_e[i][:len(g)]) >= 0)
+        hits += len(set(g.tolist()) & set(ids1[i].tolist()))
+    recall = hits / ids1.size
+    assert recall >= 0.5, recall
+    assert dims_e <= dims1, (dims_e, dims1)
+
+
 def test_ivf_per_query_nprobe_and_k(ivf960):
     s, X, Q, C, t, idx = ivf960
     g = np.random.default_rng(5)
