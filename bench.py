@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-bf16", action="store_true",
                    help="skip the BF16-storage run on FP32 workloads")
+    p.add_argument("--no-serve", action="store_true",
+                   help="skip the arrival traces of the serving workload")
+    p.add_argument("--serve-requests", type=int, default=20000)
     return p.parse_args()
 
 
@@ -145,7 +148,7 @@ def peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
-def cpu_baseline(X, Q, C, s, sample_queries, target_s=12.0):
+def cpu_baseline(X, Q, C, s, sample_queries, npq, kq, target_s=12.0):
     """The oracle (as it stands) on the host cores: FP64 brute force over each
     sampled query's candidate set after its own FP64 list assignment.  A
     first batch of `sample_queries` sizes the timed sample to ~target_s."""
@@ -156,8 +159,8 @@ def cpu_baseline(X, Q, C, s, sample_queries, target_s=12.0):
 
     def run(qs):
         t0 = time.perf_counter()
-        probes, _ = oracle.probe(qs, C, s.nprobe)
-        oracle.ivf_topk(X, qs, ptr, rows, probes, np.full(len(qs), s.k))
+        probes, _ = oracle.probe(qs, C, npq[:len(qs)])
+        oracle.ivf_topk(X, qs, ptr, rows, probes, kq[:len(qs)])
         return time.perf_counter() - t0, probes
 
     dt0, _ = run(Q[:sample_queries])
@@ -183,6 +186,7 @@ def run_reference(args):
     s = workload_spec(args)
     w = synth.generate(s, device="cpu")
     X, Q = w.X.numpy(), w.Q.numpy()
+    npq, kq = w.nprobe.numpy(), w.k.numpy()
     import oracle
     g = np.random.default_rng(3000 + s.cfg)
     C = X[np.sort(g.choice(len(X), s.nlist, replace=False))].astype(np.float32)
@@ -190,9 +194,10 @@ def run_reference(args):
     ptr, rows = oracle.ivf_lists(lists, s.nlist)
     per_step = 24
     def step(i):
-        qs = Q[(i * per_step) % len(Q):][:per_step]
-        probes, _ = oracle.probe(qs, C, s.nprobe)
-        oracle.ivf_topk(X, qs, ptr, rows, probes, np.full(len(qs), s.k))
+        o = (i * per_step) % len(Q)
+        qs = Q[o:][:per_step]
+        probes, _ = oracle.probe(qs, C, npq[o:][:len(qs)])
+        oracle.ivf_topk(X, qs, ptr, rows, probes, kq[o:][:len(qs)])
         return sum(int(ptr[p + 1].sum() - ptr[p].sum()) for p in probes)
     for i in range(args.warmup):
         step(i)
@@ -217,19 +222,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def e2e_time(idx, Q, s, k, args, stream, flush, world, dev):
+def e2e_time(idx, Q, npa, ka, k, args, stream, flush, world, dev):
     """Per-step time of the public API call with HOST buffers: pinned H2D of
     the queries, search, D2H of ids and distances, all inside the events."""
     import torch
     import torch.distributed as dist
     nq = Q.shape[0]
     qh = Q.cpu().pin_memory()
+    # per-query nprobe / k are inputs of the step too
+    par = [(x.cpu().pin_memory(), torch.empty_like(x)) for x in (npa, ka)
+           if isinstance(x, torch.Tensor)]
+    if par:
+        npa = par[0][1] if isinstance(npa, torch.Tensor) else npa
+        ka = par[-1][1] if isinstance(ka, torch.Tensor) else ka
     ids_h = torch.empty((nq, k), dtype=torch.int64).pin_memory()
     d_h = torch.empty((nq, k), dtype=torch.float32).pin_memory()
     qd = torch.empty_like(Q)
     for _ in range(2):
         qd.copy_(qh, non_blocking=True)
-        a, b = idx.search(qd, s.nprobe, k)
+        for h, dv in par:
+            dv.copy_(h, non_blocking=True)
+        a, b = idx.search(qd, npa, ka, k_max=k)
         ids_h.copy_(a, non_blocking=True)
         d_h.copy_(b, non_blocking=True)
     torch.cuda.synchronize()
@@ -243,7 +256,9 @@ def e2e_time(idx, Q, s, k, args, stream, flush, world, dev):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         qd.copy_(qh, non_blocking=True)
-        a, b = idx.search(qd, s.nprobe, k)
+        for h, dv in par:
+            dv.copy_(h, non_blocking=True)
+        a, b = idx.search(qd, npa, ka, k_max=k)
         ids_h.copy_(a, non_blocking=True)
         d_h.copy_(b, non_blocking=True)
         e1.record(stream)
@@ -252,7 +267,7 @@ def e2e_time(idx, Q, s, k, args, stream, flush, world, dev):
     t = torch.tensor([total], device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return t.item() / args.steps
+    return t.item() / args.steps, Q.numel() * 4 + sum(h.numel() * 4 for h, _ in par)
 
 
 def main():
@@ -289,19 +304,39 @@ def main():
     X, Q = w.X, w.Q
     t = pano.panorama_fit_transform(X[:65536], n_levels=s.n_levels)
     prec = {"fp32": pano.PANO_FP32, "bf16": pano.PANO_BF16}[s.precision]
+    # per-query nprobe / k (the batching workload) or scalars
+    per_query = not isinstance(s.nprobe, int) or not isinstance(s.k, int)
+    npa = w.nprobe.to(dev) if not isinstance(s.nprobe, int) else s.nprobe
+    ka = w.k.to(dev) if not isinstance(s.k, int) else s.k
+    k = int(w.k.max()) if not isinstance(s.k, int) else s.k  # k_max
+    widths, tune = None, None
+    if per_query:
+        # level widths chosen by the autotuner (median search time of each
+        # candidate split on a query sample, k-means run once)
+        cands = [[w_] * (s.d // w_) for w_ in (16, 32, 64, 128) if s.d % w_ == 0]
+        qs = Q[:min(len(Q), 8192)]
+        best, ms = pano.panorama_autotune_levels(t, X, qs, s.nlist, 64, 10, cands,
+                                                 precision=prec, repeats=2)
+        widths = cands[best]
+        tune = {"candidates": [f"{len(c)}x{c[0]}" for c in cands],
+                "ms": [float(x) for x in ms], "chosen": f"{len(widths)}x{widths[0]}",
+                "sample": f"{len(qs)} queries, nprobe 64, k 10"}
     idx = pano.panorama_build_ivf(t, X, nlist=s.nlist, n_levels=s.n_levels, seed=3000 + s.cfg,
-                                  precision=prec)
+                                  precision=prec, level_widths=widths)
     nq = Q.shape[0]
-    k = s.k if isinstance(s.k, int) else max(s.k)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > L2
+    # the batching workload runs as one graph-captured launch per step
+    plan = pano.Plan(idx, Q, npa, ka, k_max=k) if per_query else None
 
     def step(mode=0, timing=False):
-        return idx.search(Q, s.nprobe, k, mode=mode, collect_timing=timing)
+        if plan is not None and mode == 0 and not timing:
+            return plan.launch(stream)
+        return idx.search(Q, npa, ka, k_max=k, mode=mode, collect_timing=timing)
 
     # counters (one instrumented search, outside the timed region)
     step(0)
-    idx.search(Q, s.nprobe, k, collect_stats=True)
+    idx.search(Q, npa, ka, k_max=k, collect_stats=True)
     st = pano.last_stats().as_dict()
 
     def timed(mode, steps, warmup, timing=True):
@@ -332,7 +367,9 @@ def main():
             dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
         return t_all.item(), verify_ms, clocks
 
-    total_ms, vms, clocks = timed(0, args.steps, args.warmup)
+    total_ms, vms, clocks = timed(0, args.steps, args.warmup, timing=plan is None)
+    if plan is not None:  # stage times from separate, instrumented searches
+        _, vms, _ = timed(0, 3, 1, timing=True)
     ms_per_step = total_ms / args.steps
     pairs = st["pairs"]
     value = pairs * world / (ms_per_step / 1e3)
@@ -343,9 +380,9 @@ def main():
     scan_per = scan_ms / args.scan_steps
 
     # e2e: through the public API with host buffers (pinned H2D + D2H)
-    e2e_per = None
+    e2e_per, h2d = None, 0
     if not args.no_e2e:
-        e2e_per = e2e_time(idx, Q, s, k, args, stream, flush, world, dev)
+        e2e_per, h2d = e2e_time(idx, Q, npa, ka, k, args, stream, flush, world, dev)
 
     # roofline of the dominant kernel (verify phase B: one launch per step),
     # its duration measured live above with CUDA events on the search stream
@@ -385,7 +422,7 @@ def main():
                                         precision=pano.PANO_BF16,
                                         centroids=idx.centroids() if s.nlist > 1 else None)
         for _ in range(args.warmup):
-            idx16.search(Q, s.nprobe, k)
+            idx16.search(Q, npa, ka, k_max=k)
         torch.cuda.synchronize()
         tot16 = 0.0
         for _ in range(args.steps):
@@ -393,7 +430,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            idx16.search(Q, s.nprobe, k)
+            idx16.search(Q, npa, ka, k_max=k)
             e1.record(stream)
             e1.synchronize()
             tot16 += e0.elapsed_time(e1)
@@ -401,7 +438,7 @@ def main():
         if world > 1:
             dist.all_reduce(t16, op=dist.ReduceOp.MAX)
         ms16 = t16.item() / args.steps
-        idx16.search(Q, s.nprobe, k, collect_stats=True)
+        idx16.search(Q, npa, ka, k_max=k, collect_stats=True)
         st16 = pano.last_stats().as_dict()
         bf16 = {"levels": f"{s.d // 64}x64", "ms_per_step": ms16,
                 "value": pairs * world / (ms16 / 1e3), "qps": nq * world / (ms16 / 1e3),
@@ -410,10 +447,42 @@ def main():
                 "reranked": st16["reranked"]}
         del idx16
 
+    # the serving workload: Poisson arrivals through the continuous-batching
+    # server (batches of up to 1024 formed from what has arrived, several in
+    # flight, admission by memory); QPS and latency percentiles per rate
+    serving = None
+    if "serving" in s.name and not args.no_serve:
+        import dataclasses
+        import numpy as np
+        n_req = args.serve_requests
+        sq = dataclasses.replace(s, n_queries=n_req, cfg=s.cfg + 50)
+        wq = synth.generate(sq, device="cpu", queries_only=True)
+        srv = pano.Server(idx, max_batch=1024, max_inflight=4, k_max=10)
+        rng = np.random.default_rng(6000 + s.cfg)
+        serving = []
+        for rate in (20_000, 50_000, 100_000, 200_000):
+            arr = np.cumsum(rng.exponential(1e6 / rate, size=n_req))
+            b0 = srv.stats()
+            _, _, lat = srv.run_trace(wq.Q.numpy(), arr, wq.nprobe.numpy(), wq.k.numpy())
+            b1 = srv.stats()
+            nb = b1["batches"] - b0["batches"]
+            nbq = b1["mean_batch"] * b1["batches"] - b0["mean_batch"] * b0["batches"]
+            span_us = float(np.max(arr + lat) - arr[0])
+            serving.append({"offered_qps": rate, "qps": n_req / (span_us / 1e6),
+                            "p50_us": float(np.percentile(lat, 50)),
+                            "p99_us": float(np.percentile(lat, 99)),
+                            "max_us": float(lat.max()),
+                            "mean_batch": nbq / max(nb, 1), "requests": n_req})
+        srv.close()
+
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if s.n * s.nlist * s.d > 1e13:  # the oracle's FP64 list assignment alone
+        cpu = {"kind": "oracle", "value": None,
+               "skipped": "the oracle's FP64 assignment of N vectors to nlist lists would take "
+                          "hours on the host cores"}
+    elif rank == 0 and world == 1 and not args.no_cpu_baseline:
         Xh, Qh = X.cpu().numpy(), Q.cpu().numpy()
-        cpu = cpu_baseline(Xh, Qh, idx.centroids(), s, sample_queries=48)
+        cpu = cpu_baseline(Xh, Qh, idx.centroids(), s, 48, w.nprobe.numpy(), w.k.numpy())
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world,
@@ -431,8 +500,10 @@ def main():
             "e2e": None if e2e_per is None else {
                 "value": pairs * world / (e2e_per / 1e3), "unit": "candidates/s",
                 "qps": nq * world / (e2e_per / 1e3), "ms_per_step": e2e_per,
-                "h2d_bytes_per_step": Q.numel() * 4, "d2h_bytes_per_step": nq * k * 12},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": nq * k * 12},
             "bf16_pruned": bf16,
+            "autotune": tune,
+            "serving": serving,
             "gpu_launches": (KERNELS_PER_SEARCH if s.nlist > 1 else KERNELS_PER_SEARCH - 2)
                             * args.steps,
             "roofline": roof,

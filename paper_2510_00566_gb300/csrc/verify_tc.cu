@@ -495,9 +495,9 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
               atomicAdd(&s_stat[1], (unsigned long long)np * w);
             }
           }
-          if (test) {  // every slot is tested (no branches); dead ones stay dead
-            float v[32];
-            tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
+          float v[32];
+          tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
+          if (test && wm) {  // every slot is tested (no branches); dead ones stay dead
             const float4* qt = qterm + 32 * half;
             uint32_t pruned = 0;
 #pragma unroll
