@@ -489,7 +489,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if s.precision == "fp32" else s.precision, "data": "synthetic",
-            "config": {"workload": workload_name(s),
+            "config": {"workload": workload_name(s) + (
+                           f" (levels autotuned: {tune['chosen']})" if tune else ""),
                        "l2": "256 MB buffer written between timed steps (L2 flushed)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "qps": qps,
