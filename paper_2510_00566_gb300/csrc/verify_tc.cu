@@ -495,18 +495,34 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
               atomicAdd(&s_stat[1], (unsigned long long)np * w);
             }
           }
-          float v[32];
-          tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
-          if (test && wm) {  // every slot is tested (no branches); dead ones stay dead
-            const float4* qt = qterm + 32 * half;
-            uint32_t pruned = 0;
+          if (Npad <= 16) {  // a group of <= 16 queries: 16 columns (half 0 only)
+            float v[16];
+            tc::tmem_ld16(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
+            if (test && wm) {
+              const float4* qt = qterm + 32 * half;
+              uint32_t pruned = 0;
 #pragma unroll
-            for (int g = 0; g < 32; ++g) {
-              const float4 t = qt[g];
-              const float P = fmaf(t.x, exv, fmaf(t.y, rx, fmaf(t.z, sx, v[g])));
-              pruned |= (P < t.w + Hx ? 1u : 0u) << g;
+              for (int g = 0; g < 16; ++g) {
+                const float4 t = qt[g];
+                const float P = fmaf(t.x, exv, fmaf(t.y, rx, fmaf(t.z, sx, v[g])));
+                pruned |= (P < t.w + Hx ? 1u : 0u) << g;
+              }
+              wm &= ~pruned;
             }
-            wm &= ~pruned;
+          } else {
+            float v[32];
+            tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
+            if (test && wm) {  // every slot is tested (no branches); dead ones stay dead
+              const float4* qt = qterm + 32 * half;
+              uint32_t pruned = 0;
+#pragma unroll
+              for (int g = 0; g < 32; ++g) {
+                const float4 t = qt[g];
+                const float P = fmaf(t.x, exv, fmaf(t.y, rx, fmaf(t.z, sx, v[g])));
+                pruned |= (P < t.w + Hx ? 1u : 0u) << g;
+              }
+              wm &= ~pruned;
+            }
           }
           alive[(c * CH + row) * AW + half] = wm;
         }
