@@ -125,6 +125,58 @@ __device__ __forceinline__ float warp_kth_smallest_bf16(const uint16_t* vals, in
   return __uint_as_float(lo << 16);
 }
 
+// Compensated FP32 sum of squares after Ogita, Rump & Oishi ("Accurate sum
+// and dot product", SIAM J. Sci. Comput. 26(6), 2005): each term v*v is split
+// exactly into p + e by an FMA (TwoProduct) and each addition s + p into
+// t + err by TwoSum, so s + (exact sum of the error terms) is the exact sum;
+// c accumulates those error terms in plain FP32.  The intrinsics keep the
+// compiler from fusing the product into the addition, which would break the
+// TwoSum identity.  For n terms spread over lanes, a 5-step lane tree and L
+// level additions, the error of c is below (2n/32 + 2L + 12)(n/32 + L + 6) u^2
+// of the sum, under 2^-30 of it for n <= 8192, L <= 64 (non-negative terms).
+struct Acc2 {
+  float s, c;
+};
+
+// TwoSum: t + err == x + y exactly.
+__device__ __forceinline__ float two_sum(float x, float y, float& err) {
+  const float t = __fadd_rn(x, y);
+  const float bb = __fsub_rn(t, x);
+  err = __fadd_rn(__fsub_rn(x, __fsub_rn(t, bb)), __fsub_rn(y, bb));
+  return t;
+}
+
+__device__ __forceinline__ void acc2_sq(Acc2& a, float v) {
+  const float p = __fmul_rn(v, v);
+  const float e = __fmaf_rn(v, v, -p);
+  float err;
+  a.s = two_sum(a.s, p, err);
+  a.c = __fadd_rn(a.c, __fadd_rn(err, e));
+}
+
+// Adds b into a.  Symmetric in a and b (TwoSum's t and err are, and so is
+// a.c + b.c), so both lanes of a shuffle pair hold the same result.
+__device__ __forceinline__ void acc2_add(Acc2& a, Acc2 b) {
+  float err;
+  a.s = two_sum(a.s, b.s, err);
+  a.c = __fadd_rn(__fadd_rn(a.c, b.c), err);
+}
+
+__device__ __forceinline__ Acc2 warp_sum_acc2(Acc2 a) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    Acc2 b{__shfl_xor_sync(0xffffffffu, a.s, off), __shfl_xor_sync(0xffffffffu, a.c, off)};
+    acc2_add(a, b);
+  }
+  return a;
+}
+
+// Upper bound of the exact sum held by a (relative slack 2^-23 over the
+// 2^-30 error bound; FLT_MIN covers terms lost to underflow).
+__device__ __forceinline__ float acc2_upper(Acc2 a, float rel) {
+  return __fadd_ru(__fmul_ru(__fadd_ru(a.s, a.c), 1.0f + rel), 0x1p-126f);
+}
+
 __device__ __forceinline__ double warp_sum_f64(double v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);

@@ -36,55 +36,65 @@ constexpr int NT = 256;
 __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 
 // --------------------------------------------------------------- a1: norms
-__global__ void query_norms_kernel(const float* __restrict__ q, const float* __restrict__ qt,
-                                   int64_t nq, int d, int L, const int32_t* __restrict__ level_off,
-                                   const float* __restrict__ mu, double c_trans,
-                                   float4* __restrict__ qinfo, float* __restrict__ qtail,
-                                   float* __restrict__ qn2) {
-  int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+// One warp per query.  The transformed row is first staged in shared memory
+// with one batch of coalesced loads (so the level loop below does not wait
+// on global memory L times).  Level energies are summed from the last level
+// backwards in compensated FP32 (Acc2: the FP64 pipe is a small fraction of
+// the FP32 one), giving the rounded-up tail norms directly; the rounded
+// norms keep the accuracy of one rounding of the exact value.
+constexpr int kNormRows = 8;      // queries (warps) per CTA
+constexpr int kNormMaxD = 1536;   // staged row length (48 KB per CTA); longer rows read global memory
+
+__global__ void __launch_bounds__(kNormRows * 32) query_norms_kernel(
+    const float* __restrict__ q, const float* __restrict__ qt, int64_t nq, int d, int L,
+    const int32_t* __restrict__ level_off, const float* __restrict__ mu, float c_trans_up,
+    float4* __restrict__ qinfo, float* __restrict__ qtail, float* __restrict__ qn2) {
+  extern __shared__ float qrow_s[];  // [kNormRows][d] when d <= kNormMaxD
+  const int w = threadIdx.x / 32, lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * kNormRows + w;
   if (row >= nq) return;
-  const int lane = threadIdx.x & 31;
   const float* x = qt + row * d;
-  double suffix = 0.0;
+  if (d <= kNormMaxD) {
+    float* xs = qrow_s + (size_t)w * d;
+    for (int j = lane; j < d; j += 32) xs[j] = x[j];
+    __syncwarp();
+    x = xs;
+  }
+  Acc2 suffix{0.f, 0.f};
   for (int l = L - 1; l >= 0; --l) {
-    double e = 0.0;
-    for (int j = level_off[l] + lane; j < level_off[l + 1]; j += 32) {
-      double v = x[j];
-      e += v * v;
-    }
-    suffix += warp_sum_f64(e);
-    if (lane == 0)
-      qtail[row * (L + 1) + l] = __double2float_ru(sqrt(suffix * (1.0 + 1e-12)));
+    Acc2 e{0.f, 0.f};
+    for (int j = level_off[l] + lane; j < level_off[l + 1]; j += 32) acc2_sq(e, x[j]);
+    acc2_add(suffix, warp_sum_acc2(e));
+    if (lane == 0) qtail[row * (L + 1) + l] = __fsqrt_ru(acc2_upper(suffix, 0x1p-23f));
   }
-  double dev = 0.0, on = 0.0;
+  // deviation from the mean: each fl(q_j - mu_j) is within u of the exact
+  // difference, so the slack 4u covers the squares' 2u and Acc2's 2^-30
+  Acc2 dev{0.f, 0.f}, on{0.f, 0.f};
   for (int j = lane; j < d; j += 32) {
-    double v = q[row * d + j];
-    double w = v - (double)mu[j];
-    dev += w * w;
-    on += v * v;
+    const float v = q[row * d + j];
+    acc2_sq(dev, __fsub_rn(v, mu[j]));
+    acc2_sq(on, v);
   }
-  dev = warp_sum_f64(dev);
-  on = warp_sum_f64(on);
+  dev = warp_sum_acc2(dev);
+  on = warp_sum_acc2(on);
   if (lane == 0) {
     qtail[row * (L + 1) + L] = 0.f;
-    float nqf = (float)suffix;
-    qinfo[row] = make_float4(nqf, sqrtf(nqf), __double2float_ru(c_trans * sqrt(dev) * (1.0 + 1e-9)), 0.f);
-    qn2[row] = (float)on;
+    const float nqf = __fadd_rn(suffix.s, suffix.c);
+    qinfo[row] = make_float4(nqf, sqrtf(nqf),
+                             __fmul_ru(c_trans_up, __fsqrt_ru(acc2_upper(dev, 0x1p-21f))), 0.f);
+    qn2[row] = __fadd_rn(on.s, on.c);
   }
 }
 
-// FP32 squared norms of rows (accumulated in FP64, rounded once).
+// FP32 squared norms of rows (compensated FP32 sums, rounded once).
 __global__ void row_sqnorm_kernel(const float* __restrict__ X, int64_t m, int d,
                                   float* __restrict__ out) {
   int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (row >= m) return;
-  double s = 0.0;
-  for (int j = threadIdx.x & 31; j < d; j += 32) {
-    double v = X[row * d + j];
-    s += v * v;
-  }
-  s = warp_sum_f64(s);
-  if ((threadIdx.x & 31) == 0) out[row] = (float)s;
+  Acc2 s{0.f, 0.f};
+  for (int j = threadIdx.x & 31; j < d; j += 32) acc2_sq(s, X[row * d + j]);
+  s = warp_sum_acc2(s);
+  if ((threadIdx.x & 31) == 0) out[row] = __fadd_rn(s.s, s.c);
 }
 
 // nprobe / k per query, clamped to [1, nlist] and [0, k_max].
@@ -135,14 +145,41 @@ __global__ void __launch_bounds__(NT) probe_select_kernel(
       if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255], 1);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      int acc = 0, b = 0;
-      for (; b < 256; ++b) {
-        if (acc + hist[b] >= remaining) break;
-        acc += hist[b];
+    if (threadIdx.x < 32) {
+      // first bin b with (count below b) + hist[b] >= remaining: lane l
+      // holds bins 8l..8l+7; a warp scan of the lane totals and a ballot
+      // find the lane, which walks its eight bins (b = 256 if none)
+      const int lane = threadIdx.x;
+      int h[8], tot = 0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        h[u] = hist[lane * 8 + u];
+        tot += h[u];
       }
-      s_bin = b;
-      s_below = acc;
+      int inc = tot;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+      }
+      const unsigned hit = __ballot_sync(0xffffffffu, inc >= remaining);
+      if (lane == (hit ? __ffs(hit) - 1 : 31)) {
+        int acc = inc - tot, b = lane * 8 + 8;
+        bool found = false;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (!found) {
+            if (acc + h[u] >= remaining) {
+              found = true;
+              b = lane * 8 + u;
+            } else {
+              acc += h[u];
+            }
+          }
+        }
+        s_bin = b;
+        s_below = acc;
+      }
     }
     __syncthreads();
     prefix |= (uint32_t)s_bin << shift;
@@ -300,17 +337,28 @@ __global__ void inv_emit_kernel(int ph, const int* __restrict__ cnt, int nlist,
 }
 
 // ------------------------------------------------- Alg. 1 warm start (a6)
-// Per query: exact distances to the first max(4k, 64) (at most 256) members
-// of its nearest list; the k-th smallest (rounded up) is an upper bound on
-// d_k and seeds the threshold before any tile is verified (Algorithm 1
-// initialises d_k from the first k candidates).  The seeds are not inserted
-// into the top-k: they are verified again like every other candidate.
+// Per query: distances to the first max(4k, 64) (at most 256) members of its
+// nearest list; the k-th smallest is an upper bound on d_k and seeds the
+// threshold before any tile is verified (Algorithm 1 initialises d_k from
+// the first k candidates).  The seeds are not inserted into the top-k: they
+// are verified again like every other candidate.
+//
+// The query row sits in shared memory; a warp loads a whole row (up to 1024
+// dims) in one batch and sums fl(q_j - x_j)^2 by FMA into four interleaved
+// sums per lane.  Each term meets at most m = ceil(d/128) + 8 roundings, so
+// with the differences' relative error u the exact distance is at most the
+// computed one times 1 / ((1 - gamma_m)(1 - u)^2) <= slack = 1 + 2(m + 3)u
+// (host-computed, rounded up); multiplying by it (rounding up) keeps every
+// seed distance an upper bound on the exact one.
 constexpr int kSeedMax = 256;
+constexpr int kSeedWarps = 8;
 
-__global__ void __launch_bounds__(128) seed_tau_kernel(
+__global__ void __launch_bounds__(kSeedWarps * 32) seed_tau_kernel(
     const float* __restrict__ q, int d, const int32_t* __restrict__ probes, int stride,
     const int64_t* __restrict__ chunk_off, const int32_t* __restrict__ list_size, int chunk,
-    const float* __restrict__ rows, const int32_t* __restrict__ kq, float* __restrict__ tau_seed) {
+    const float* __restrict__ rows, const int32_t* __restrict__ kq, float slack,
+    float* __restrict__ tau_seed) {
+  extern __shared__ float4 qs4[];  // the query row (d floats)
   __shared__ float dist[kSeedMax];
   const int64_t row = blockIdx.x;
   const int k = kq[row];
@@ -321,16 +369,69 @@ __global__ void __launch_bounds__(128) seed_tau_kernel(
     if (threadIdx.x == 0) tau_seed[row] = k <= 0 ? -1.f : INFINITY;
     return;
   }
+  float* qs = reinterpret_cast<float*>(qs4);
+  for (int j = threadIdx.x; j < d; j += kSeedWarps * 32) qs[j] = q[row * d + j];
+  __syncthreads();
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   const int64_t base = chunk_off[c] * chunk;  // a list's members are its first slots
-  for (int i = warp; i < ns; i += 4) {
-    float v = exact_sqdist_warp(q + row * d, rows + (base + i) * d, d);
-    if (lane == 0) dist[i] = v;
+  const bool vec = (d & 3) == 0 && (reinterpret_cast<uintptr_t>(rows) & 15) == 0;
+  for (int i = warp; i < ns; i += kSeedWarps) {
+    const float* x = rows + (base + i) * d;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    if (vec) {
+      const float4* x4 = reinterpret_cast<const float4*>(x);
+      const int d4 = d >> 2;
+      for (int j0 = 0; j0 < d4; j0 += 8 * 32) {
+        float4 xv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int j = j0 + lane + 32 * u;
+          xv[u] = j < d4 ? x4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int j = j0 + lane + 32 * u;
+          if (j < d4) {
+            const float4 qv = qs4[j];
+            float t;
+            t = qv.x - xv[u].x;
+            acc[0] = fmaf(t, t, acc[0]);
+            t = qv.y - xv[u].y;
+            acc[1] = fmaf(t, t, acc[1]);
+            t = qv.z - xv[u].z;
+            acc[2] = fmaf(t, t, acc[2]);
+            t = qv.w - xv[u].w;
+            acc[3] = fmaf(t, t, acc[3]);
+          }
+        }
+      }
+    } else {
+      for (int j0 = 0; j0 < d; j0 += 8 * 32) {
+        float xv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int j = j0 + lane + 32 * u;
+          xv[u] = j < d ? x[j] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int j = j0 + lane + 32 * u;
+          if (j < d) {
+            const float t = qs[j] - xv[u];
+            acc[u & 3] = fmaf(t, t, acc[u & 3]);
+          }
+        }
+      }
+    }
+    float s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) dist[i] = __fadd_ru(__fmul_ru(s, slack), 0x1p-126f);
   }
   __syncthreads();
   if (warp == 0) {
-    float t = warp_kth_smallest(dist, ns, k);
-    if (lane == 0) tau_seed[row] = __fmul_ru(t, 1.000001f);
+    const float t = warp_kth_smallest(dist, ns, k);
+    if (lane == 0) tau_seed[row] = t;
   }
 }
 
@@ -1291,8 +1392,11 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     mark(0);
     PANO_CUDA(gemm_nt(kStore, (int)nq, d, d, queries, d, I.mu32.as<float>(), I.T32.as<float>(), d,
                       qt, d, nullptr, nullptr, st));
-    query_norms_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(
-        queries, qt, nq, d, L, I.level_off_d.as<int32_t>(), I.mu32.as<float>(), I.c_trans, qinfo,
+    float c_trans_up = (float)I.c_trans;  // rounded up: the e_q bound stays an upper bound
+    if ((double)c_trans_up < I.c_trans) c_trans_up = std::nextafter(c_trans_up, INFINITY);
+    query_norms_kernel<<<(unsigned)((nq + kNormRows - 1) / kNormRows), kNormRows * 32,
+                         d <= kNormMaxD ? (size_t)kNormRows * d * 4 : 0, st>>>(
+        queries, qt, nq, d, L, I.level_off_d.as<int32_t>(), I.mu32.as<float>(), c_trans_up, qinfo,
         qtail, qn2);
     PANO_CUDA(cudaGetLastError());
     // a2
@@ -1313,10 +1417,13 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     }
     // a3 (and the Alg. 1 warm start of the threshold)
     mark(2);
-    seed_tau_kernel<<<(unsigned)nq, 128, 0, st>>>(queries, d, probes, stride,
-                                                  I.chunk_off_d.as<int64_t>(),
-                                                  I.list_size_d.as<int32_t>(), I.chunk,
-                                                  I.rows.as<float>(), kq, tau_seed);
+    const double seed_m = (d + 127) / 128 + 8;
+    const double seed_sl = 1.0 + 2.0 * (seed_m + 3.0) * kU32;
+    float seed_slack = (float)seed_sl;
+    if ((double)seed_slack < seed_sl) seed_slack = std::nextafter(seed_slack, INFINITY);
+    seed_tau_kernel<<<(unsigned)nq, kSeedWarps * 32, (size_t)d * 4, st>>>(
+        queries, d, probes, stride, I.chunk_off_d.as<int64_t>(), I.list_size_d.as<int32_t>(),
+        I.chunk, I.rows.as<float>(), kq, seed_slack, tau_seed);
     PANO_CUDA(cudaGetLastError());
     const int64_t ne = nq * stride;
     // Phase A (each query's nearest list, verified first for a tight
