@@ -131,6 +131,8 @@ typedef struct {
    * filter, [5] exact re-ranking, [6] whole kernel, [7] CTAs that ran. */
   int64_t section_cycles[8];
   int64_t dims_scanned_a; /* the part of dims_scanned read in phase A        */
+  int64_t pairs_a;        /* the part of pairs in phase A (0 in one pass)    */
+  int64_t section_cycles_a[8]; /* the part of section_cycles from phase A    */
 } pano_search_stats;
 
 /* Description of a built index. */

@@ -63,18 +63,21 @@ class SearchStats(ctypes.Structure):
                 ("device_error", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("stage_ms", ctypes.c_float * 6), ("pad2_", ctypes.c_float * 2),
                 ("section_cycles", ctypes.c_int64 * 8),
-                ("dims_scanned_a", ctypes.c_int64)]
+                ("dims_scanned_a", ctypes.c_int64), ("pairs_a", ctypes.c_int64),
+                ("section_cycles_a", ctypes.c_int64 * 8)]
 
     STAGES = ("transform", "probe", "inversion", "verify_a", "verify_b",
               "decode")
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_
-             if not f.startswith("pad") and f not in ("stage_ms", "section_cycles")}
+             if not f.startswith("pad")
+             and f not in ("stage_ms", "section_cycles", "section_cycles_a")}
         d["stage_ms"] = dict(zip(self.STAGES, list(self.stage_ms)))
-        d["section_cycles"] = dict(zip(("prologue", "mma_issue", "epilogue", "next_level",
-                                        "ub_filter", "rerank", "kernel", "ctas"),
-                                       list(self.section_cycles)))
+        names = ("prologue", "mma_issue", "epilogue", "next_level", "ub_filter", "rerank",
+                 "kernel", "ctas")
+        d["section_cycles"] = dict(zip(names, list(self.section_cycles)))
+        d["section_cycles_a"] = dict(zip(names, list(self.section_cycles_a)))
         return d
 
 

@@ -112,6 +112,30 @@ __device__ __forceinline__ void topk_insert(unsigned long long* slots, int k,
   }
 }
 
+// topk_insert by one thread whose slot reads go out in batches of eight
+// independent loads (one round per eight slots, not one per slot), so that
+// many threads can each insert a key at once and their compare-exchange
+// chains overlap.  A read may be stale: slots only ever decrease, so the
+// first slot found not below the key is never past the key's place, and
+// starting early only adds steps that leave a slot unchanged.
+__device__ __forceinline__ void topk_insert_thread(unsigned long long* slots, int k,
+                                                   unsigned long long key) {
+  int start = k;
+  for (int j0 = 0; j0 < k && start == k; j0 += 8) {
+    unsigned long long v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = j0 + u < k ? ld_volatile_u64(slots + j0 + u) : kEmptyKey;
+#pragma unroll
+    for (int u = 7; u >= 0; --u)
+      if (v[u] >= key) start = j0 + u;
+  }
+  for (int j = start; j < k; ++j) {
+    unsigned long long old = atomicMin(slots + j, key);
+    if (old == kEmptyKey) return;
+    key = old > key ? old : key;
+  }
+}
+
 // topk_insert issued by a whole warp: the slots are read once in parallel
 // (one round instead of a chain of dependent reads) to find the first slot
 // not below the key; lane 0 then runs the compare-exchange chain from there.

@@ -30,6 +30,10 @@ namespace pano {
 namespace {
 
 constexpr int CH = 64;
+// Device statistics words: [0] pair-levels, [1] tile-levels, [2] slice bytes,
+// [3] reranked, [4] pairs, [5] unused, [6] / [7] dims of phase A / B,
+// [8..15] section cycles, [16..23] their phase-A part, [24] phase-A pairs.
+constexpr int kStatWords = 25;
 constexpr int SEG_CHUNKS = 32;  // chunks per work-item segment
 constexpr int NT = 256;
 
@@ -452,7 +456,7 @@ struct VerifyArgs {
   const int32_t* bucket;
   unsigned long long* topk;
   int* err;
-  unsigned long long* stats;  // 8 counters (see pano_search_stats order)
+  unsigned long long* stats;  // kStatWords counters (layout at kStatWords)
   int64_t items_cap;
   int d, L, max_w, k_max;
   float gslack;    // slack factor: |computed - exact| <= gslack (|q~|+|x~|)^2
@@ -495,8 +499,9 @@ struct FpSmem {
     off_ids = off_qtl + (((uint32_t)QB * (L + 1) * 4u + 15u) & ~15u);
     off_q = off_ids + CB * 4u;
     off_pend = off_q + QB * 6u * 4u;
-    // slot (8); query, id, lower bound, this tile's bounds (4 each); kept (2)
-    total = off_pend + kPend * 26u;
+    // slot (8); query, id, lower and upper bound, this tile's bounds (4 each);
+    // kept (2)
+    total = off_pend + kPend * 34u;
   }
 };
 
@@ -564,8 +569,10 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
   int32_t* pq = reinterpret_cast<int32_t*>(pslot + FpSmem::kPend);
   int32_t* pid = pq + FpSmem::kPend;
   float* plb = reinterpret_cast<float*>(pid + FpSmem::kPend);  // the pair's lower bound
-  float* lbt = plb + FpSmem::kPend;                             // this tile's, by survivor
-  uint16_t* keep = reinterpret_cast<uint16_t*>(lbt + FpSmem::kPend);  // entries to re-rank
+  float* pub = plb + FpSmem::kPend;                             // the pair's upper bound
+  float* lbt = pub + FpSmem::kPend;                             // this tile's, by survivor
+  float* ubt = lbt + FpSmem::kPend;
+  uint16_t* keep = reinterpret_cast<uint16_t*>(ubt + FpSmem::kPend);  // entries to re-rank
   const int BR = (max_w + 4) * CH;  // floats per chunk block in a stage
   auto stage_x = [&](int b) { return reinterpret_cast<float*>(smem + (uint32_t)b * lay.stage_f * 4u); };
   auto qslice = [&](int l) {
@@ -706,13 +713,23 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
     if (tid == 0) s_nkeep = 0;
     __syncthreads();
     // the threshold may have dropped since a pair survived: a lower bound
-    // above it rules the pair out without its exact distance
+    // above it rules the pair out without its exact distance; so do k
+    // pending pairs of the same query whose upper bounds lie below it (all
+    // k are closer; the pair's own upper bound is never below its lower one)
     for (int s = tid; s < np; s += NTH) {
-      const int q = pq[s];
-      const unsigned long long key = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + a.kq[q] - 1);
+      const int q = pq[s], kk = a.kq[q];
+      const unsigned long long key = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + kk - 1);
       const float tau = fminf(key == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key), 1.000001f),
                               __ldcg(a.tau_seed + q));
-      if (!(plb[s] > tau)) keep[atomicAdd(&s_nkeep, 1)] = (uint16_t)s;
+      const float lb = plb[s];
+      bool keep_s = !(lb > tau);
+      if (keep_s) {
+        int below = 0;
+        for (int o = 0; o < np && below < kk; ++o)
+          below += (pq[o] == q) & (__fmul_ru(pub[o], 1.000001f) < lb);
+        keep_s = below < kk;
+      }
+      if (keep_s) keep[atomicAdd(&s_nkeep, 1)] = (uint16_t)s;
     }
     __syncthreads();
     const int nk = s_nkeep;
@@ -721,10 +738,17 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
         prefetch_l2(a.rows + pslot[keep[i]] * d, (uint32_t)d * 4);
         prefetch_l2(a.qorig + (int64_t)pq[keep[i]] * d, (uint32_t)d * 4);
       }
+    // exact distances (a warp each; they replace the lower bounds), then
+    // the top-k insertions (a thread each, so their chains overlap)
     for (int i = warp; i < nk; i += NW) {
+      const int s = keep[i];
+      const float dist = exact_sqdist_warp(a.qorig + (int64_t)pq[s] * d, a.rows + pslot[s] * d, d);
+      if (lane == 0) plb[s] = dist;
+    }
+    __syncthreads();
+    for (int i = tid; i < nk; i += NTH) {
       const int s = keep[i], q = pq[s];
-      const float dist = exact_sqdist_warp(a.qorig + (int64_t)q * d, a.rows + pslot[s] * d, d);
-      topk_insert_warp(a.topk + (int64_t)q * a.k_max, a.kq[q], make_key(dist, pid[s]));
+      topk_insert_thread(a.topk + (int64_t)q * a.k_max, a.kq[q], make_key(plb[s], pid[s]));
     }
     if (a.collect && tid == 0) s_stat[4] += nk;
   };
@@ -1053,12 +1077,14 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
               const int g = tq + TQ * ai, e = 4 * tc + bi;
               const int pos = atomicAdd(&s_nsurv, 1);
               surv[pos] = (uint16_t)((g << 8) | e);
-              if (pos < FpSmem::kPend) {  // its Eq. 3 lower bound (C = 0 at the end)
+              if (pos < FpSmem::kPend) {  // its Eq. 3 bounds (C = 0 at the end)
                 const float4 ct = cterm[e];
                 const float A = qnq[g] + ct.w - 2.f * p[ai][bi];
                 const float S = qrq[g] + ct.y;
                 const float r = sqrtf(fmaxf(A - gs * S * S, 0.f)) - (qeq[g] + ct.x);
                 lbt[pos] = r > 0.f ? r * r * a.lb_scale : 0.f;
+                const float ru = __fadd_ru(__fsqrt_ru(fmaxf(A + gs * S * S, 0.f)), qeq[g] + ct.x);
+                ubt[pos] = __fmul_ru(__fmul_ru(ru, ru), a.ub_scale);
               }
             }
       }
@@ -1078,6 +1104,7 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
           pq[np + s] = qid[g];
           pid[np + s] = ids_s[e];
           plb[np + s] = lbt[s];
+          pub[np + s] = ubt[s];
         }
       } else {  // too many to defer: re-rank them now
         for (int s = warp; s < ns; s += NW) {
@@ -1121,6 +1148,8 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
     s_sec[6] = (unsigned long long)(clock64() - s_tkernel);
     s_sec[7] = 1;  // CTAs that ran
     for (int i = 0; i < 8; ++i) atomicAdd(&a.stats[8 + i], s_sec[i]);
+    if (a.phase == 0)
+      for (int i = 0; i < 8; ++i) atomicAdd(&a.stats[16 + i], s_sec[i]);
     atomicAdd(&a.stats[0], s_stat[0]);
     atomicAdd(&a.stats[a.phase == 0 ? 6 : 7], s_stat[1]);
     atomicAdd(&a.stats[1], s_stat[2]);
@@ -1147,19 +1176,27 @@ __global__ void decode_kernel(int64_t nq, int k_max, const int32_t* __restrict__
 }
 
 // Pairs in all candidate sets (stats): sum over (q, r < nprobe_q) of list sizes.
+// Pairs of all probes into out[0]; those of phase A (rank 0, when the search
+// runs two phases) into out_a[0].
 __global__ void pair_count_kernel(int64_t nq, const int32_t* __restrict__ probes, int stride,
                                   const int32_t* __restrict__ npq, const int32_t* __restrict__ lsz,
-                                  unsigned long long* __restrict__ out) {
+                                  int two_phase, unsigned long long* __restrict__ out,
+                                  unsigned long long* __restrict__ out_a) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned long long v = 0;
+  unsigned long long v = 0, va = 0;
   if (e < nq * stride) {
     int64_t qi = e / stride;
     int r = (int)(e % stride);
     if (r < npq[qi] && probes[e] >= 0) v = lsz[probes[e]];
+    if (r == 0 && two_phase) va = v;
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  for (int off = 16; off > 0; off >>= 1) {
+    v += __shfl_xor_sync(0xffffffffu, v, off);
+    va += __shfl_xor_sync(0xffffffffu, va, off);
+  }
   if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+  if ((threadIdx.x & 31) == 0 && va) atomicAdd(out_a, va);
 }
 
 // Lets `kern` use all the dynamic shared memory the device allows next to its
@@ -1341,7 +1378,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
   size_t o_itB = cv.take<int4>(std::max<int64_t>(capB, 1));
   size_t o_topk = cv.take<unsigned long long>((size_t)nq * k_max);
   size_t o_err = cv.take<int>(4);
-  size_t o_stats = cv.take<unsigned long long>(16);
+  size_t o_stats = cv.take<unsigned long long>(kStatWords);
   void* ws = ext_ws;
   if (ext_ws) {
     PANO_CHECK(cv.off <= ext_cap, PANO_EINVAL,
@@ -1384,7 +1421,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     PANO_CUDA(cudaMemsetAsync(tot, 0, 8 * 4, st));  // [4..5] verify counters
     PANO_CUDA(cudaMemsetAsync(topk, 0xff, (size_t)nq * k_max * 8, st));
     PANO_CUDA(cudaMemsetAsync(err, 0, 16, st));
-    PANO_CUDA(cudaMemsetAsync(stats, 0, 128, st));
+    PANO_CUDA(cudaMemsetAsync(stats, 0, kStatWords * 8, st));
     prep_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(nq, nprobe, nprobe_scalar, np_cap, k,
                                                               k_scalar, k_max, npq, kq, err);
     PANO_CUDA(cudaGetLastError());
@@ -1560,15 +1597,16 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     mark(6);
     if (collect) {
       pair_count_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
-          nq, probes, stride, npq, I.list_size_d.as<int32_t>(), stats + 4);
+          nq, probes, stride, npq, I.list_size_d.as<int32_t>(), one_pass ? 0 : 1, stats + 4,
+          stats + 24);
       PANO_CUDA(cudaGetLastError());
     }
     if (sync || collect) {
       int herr[4];
-      unsigned long long hst[16];
+      unsigned long long hst[kStatWords];
       int htot[8];
       PANO_CUDA(cudaMemcpyAsync(herr, err, 16, cudaMemcpyDeviceToHost, st));
-      PANO_CUDA(cudaMemcpyAsync(hst, stats, 128, cudaMemcpyDeviceToHost, st));
+      PANO_CUDA(cudaMemcpyAsync(hst, stats, kStatWords * 8, cudaMemcpyDeviceToHost, st));
       PANO_CUDA(cudaMemcpyAsync(htot, tot, 32, cudaMemcpyDeviceToHost, st));
       PANO_CUDA(cudaStreamSynchronize(st));
       t_stats.pair_levels = (int64_t)hst[0];
@@ -1581,6 +1619,8 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
       t_stats.dims_scanned = (int64_t)(hst[5] + hst[6] + hst[7]);
       t_stats.dims_scanned_a = (int64_t)hst[6];
       for (int i = 0; i < 8; ++i) t_stats.section_cycles[i] = (int64_t)hst[8 + i];
+      for (int i = 0; i < 8; ++i) t_stats.section_cycles_a[i] = (int64_t)hst[16 + i];
+      t_stats.pairs_a = (int64_t)hst[24];
       if (timing)
         for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&t_stats.stage_ms[i], ev[i], ev[i + 1]);
       if (herr[0] & kErrTimeout) return fail(PANO_ETIMEOUT, "a device-side wait timed out");

@@ -160,24 +160,43 @@ __device__ __noinline__ int flush_pending(const VerifyTCArgs& a, int np,
                                           const int64_t* __restrict__ pslot,
                                           const int32_t* __restrict__ pq,
                                           const int32_t* __restrict__ pid,
-                                          const float* __restrict__ plb, uint16_t* keep,
+                                          float* __restrict__ plb,
+                                          const float* __restrict__ pub, uint16_t* keep,
                                           int* s_nkeep) {
   const int tid = threadIdx.x, warp = tid / 32;
   if (tid == 0) *s_nkeep = 0;
   __syncthreads();
+  // a pair is re-ranked unless its lower bound exceeds the threshold or the
+  // upper bounds of k pending pairs of the same query (all k are closer)
   for (int s = tid; s < np; s += blockDim.x) {
-    const int q = pq[s];
-    const unsigned long long key = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + a.kq[q] - 1);
+    const int q = pq[s], kk = a.kq[q];
+    const unsigned long long key = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + kk - 1);
     const float tau = fminf(key == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key), 1.000001f),
                             __ldcg(a.tau_seed + q));
-    if (!(plb[s] > tau)) keep[atomicAdd(s_nkeep, 1)] = (uint16_t)s;
+    const float lb = plb[s];
+    bool keep_s = !(lb > tau);
+    if (keep_s) {
+      int below = 0;
+      for (int o = 0; o < np && below < kk; ++o)
+        below += (pq[o] == q) & (__fmul_ru(pub[o], 1.000001f) < lb);
+      keep_s = below < kk;
+    }
+    if (keep_s) keep[atomicAdd(s_nkeep, 1)] = (uint16_t)s;
   }
   __syncthreads();
   const int nk = *s_nkeep;
+  // exact distances (a warp each; they replace the lower bounds), then the
+  // top-k insertions (a thread each, so their chains overlap)
   for (int i = warp; i < nk; i += blockDim.x / 32) {
+    const int s = keep[i];
+    const float dist =
+        exact_sqdist_warp(a.qorig + (int64_t)pq[s] * a.d, a.rows + pslot[s] * a.d, a.d);
+    if ((tid & 31) == 0) plb[s] = dist;
+  }
+  __syncthreads();
+  for (int i = tid; i < nk; i += blockDim.x) {
     const int s = keep[i], q = pq[s];
-    const float dist = exact_sqdist_warp(a.qorig + (int64_t)q * a.d, a.rows + pslot[s] * a.d, a.d);
-    topk_insert_warp(a.topk + (int64_t)q * a.k_max, a.kq[q], make_key(dist, pid[s]));
+    topk_insert_thread(a.topk + (int64_t)q * a.k_max, a.kq[q], make_key(plb[s], pid[s]));
   }
   __syncthreads();
   return tid == 0 ? nk : 0;
@@ -219,7 +238,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   // deferred re-rank list: (slot, query, id, lower bound) per pair
   __shared__ int64_t pslot[Smem::kPend];
   __shared__ int32_t pq[Smem::kPend], pid[Smem::kPend];
-  __shared__ float plb[Smem::kPend];
+  __shared__ float plb[Smem::kPend], pub[Smem::kPend];
   __shared__ uint16_t keep[Smem::kPend];
   __shared__ __align__(8) uint64_t load_bar[S], mma_bar[S];
   __shared__ uint32_t tmem_base;
@@ -277,7 +296,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     qtau[g] = tau;
   };
   auto rerank_pending = [&]() {
-    const int nk = flush_pending(a, s_npend, pslot, pq, pid, plb, keep, &s_nkeep);
+    const int nk = flush_pending(a, s_npend, pslot, pq, pid, plb, pub, keep, &s_nkeep);
     if (a.collect && tid == 0) s_stat[4] += nk;
   };
   auto chunk_live = [&](int c) {
@@ -700,6 +719,8 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           pq[np + s] = qid[g];
           pid[np + s] = cid[c * CH + r];
           plb[np + s] = lr > 0.f ? lr * lr * a.lb_scale : 0.f;
+          const float ru = __fadd_ru(__fsqrt_ru(fmaxf(A + g_slack * Ss * Ss, 0.f)), qeq[g] + exv);
+          pub[np + s] = __fmul_ru(__fmul_ru(ru, ru), a.ub_scale);
         }
       } else {  // too many to defer: re-rank them now
         for (int s = warp; s < ns; s += NT / 32) {
@@ -731,6 +752,8 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     s_sec[6] = (unsigned long long)(clock64() - s_tkernel);
     s_sec[7] = 1;  // CTAs that ran
     for (int i = 0; i < 8; ++i) atomicAdd(&a.stats[8 + i], s_sec[i]);
+    if (a.phase == 0)
+      for (int i = 0; i < 8; ++i) atomicAdd(&a.stats[16 + i], s_sec[i]);
     atomicAdd(&a.stats[0], s_stat[0]);
     atomicAdd(&a.stats[a.phase == 0 ? 6 : 7], s_stat[1]);
     atomicAdd(&a.stats[1], s_stat[2]);
