@@ -79,6 +79,62 @@ __device__ __forceinline__ float exact_sqdist_warp(const float* __restrict__ a,
   return s - c;
 }
 
+// exact_sqdist_warp with the row fetched in batches of 8 float4 per lane per
+// operand (one round of loads for d <= 1024) and two interleaved compensated
+// sums per lane (half the dependent chain), combined by TwoSum at the end.
+// For the re-ranking flushes, where a warp's distances are latency-bound.
+__device__ __forceinline__ float exact_sqdist_warp_wide(const float* __restrict__ a,
+                                                        const float* __restrict__ b, int d) {
+  const int lane = threadIdx.x & 31;
+  if ((d & 3) != 0 || ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15))
+    return exact_sqdist_warp(a, b, d);
+  float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+  const float4* a4 = reinterpret_cast<const float4*>(a);
+  const float4* b4 = reinterpret_cast<const float4*>(b);
+  const int d4 = d >> 2;
+  for (int j0 = 0; j0 < d4; j0 += 8 * 32) {
+    float4 av[8], bv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + lane + 32 * u;
+      av[u] = j < d4 ? a4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+      bv[u] = j < d4 ? b4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      float t;
+      t = av[u].x - bv[u].x;
+      kahan_add(t * t, s0, c0);
+      t = av[u].y - bv[u].y;
+      kahan_add(t * t, s1, c1);
+      t = av[u].z - bv[u].z;
+      kahan_add(t * t, s0, c0);
+      t = av[u].w - bv[u].w;
+      kahan_add(t * t, s1, c1);
+    }
+  }
+  // (s0 - c0) + (s1 - c1): TwoSum of the s parts, the c parts and the error
+  // term summed plainly (the same pattern as the lane tree below)
+  float s = s0 + s1;
+  {
+    const float bb = s - s0;
+    const float err = (s0 - (s - bb)) + (s1 - bb);
+    c0 = (c0 + c1) - err;
+  }
+  float c = c0;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    float s2 = __shfl_xor_sync(0xffffffffu, s, off);
+    float c2 = __shfl_xor_sync(0xffffffffu, c, off);
+    float sum = s + s2;
+    float bb = sum - s;
+    float err = (s - (sum - bb)) + (s2 - bb);
+    c = (c + c2) - err;
+    s = sum;
+  }
+  return s - c;
+}
+
 // k-th smallest of the nv FP32 values vals[0..nv) (non-negative, +inf for
 // absent entries) by one warp: binary search on the bit pattern for the
 // least t with #{v <= t} >= k.  Returns +inf when fewer than k are finite.

@@ -742,7 +742,8 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
     // the top-k insertions (a thread each, so their chains overlap)
     for (int i = warp; i < nk; i += NW) {
       const int s = keep[i];
-      const float dist = exact_sqdist_warp(a.qorig + (int64_t)pq[s] * d, a.rows + pslot[s] * d, d);
+      const float dist =
+          exact_sqdist_warp_wide(a.qorig + (int64_t)pq[s] * d, a.rows + pslot[s] * d, d);
       if (lane == 0) plb[s] = dist;
     }
     __syncthreads();
@@ -1110,7 +1111,8 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
         for (int s = warp; s < ns; s += NW) {
           const int g = surv[s] >> 8, e = surv[s] & 255;
           const int64_t slot = (tile + e / CH) * CH + (e % CH);
-          const float dist = exact_sqdist_warp(a.qorig + (int64_t)qid[g] * d, a.rows + slot * d, d);
+          const float dist =
+              exact_sqdist_warp_wide(a.qorig + (int64_t)qid[g] * d, a.rows + slot * d, d);
           topk_insert_warp(a.topk + (int64_t)qid[g] * a.k_max, qk[g], make_key(dist, ids_s[e]));
         }
         if (a.collect && tid == 0) s_stat[4] += ns;

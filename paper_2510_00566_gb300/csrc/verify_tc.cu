@@ -190,7 +190,7 @@ __device__ __noinline__ int flush_pending(const VerifyTCArgs& a, int np,
   for (int i = warp; i < nk; i += blockDim.x / 32) {
     const int s = keep[i];
     const float dist =
-        exact_sqdist_warp(a.qorig + (int64_t)pq[s] * a.d, a.rows + pslot[s] * a.d, a.d);
+        exact_sqdist_warp_wide(a.qorig + (int64_t)pq[s] * a.d, a.rows + pslot[s] * a.d, a.d);
     if ((tid & 31) == 0) plb[s] = dist;
   }
   __syncthreads();
@@ -727,7 +727,8 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           const int r = surv[s] >> 6, g = surv[s] & 63;
           const int q = qid[g];
           const int64_t slot = (ch0 + c) * CH + r;
-          const float dist = exact_sqdist_warp(a.qorig + (int64_t)q * d, a.rows + slot * d, d);
+          const float dist =
+              exact_sqdist_warp_wide(a.qorig + (int64_t)q * d, a.rows + slot * d, d);
           topk_insert_warp(a.topk + (int64_t)q * a.k_max, qk[g], make_key(dist, cid[c * CH + r]));
         }
         if (a.collect && tid == 0) s_stat[4] += ns;
