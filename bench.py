@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-bf16", action="store_true",
                    help="skip the BF16-storage run on FP32 workloads")
+    p.add_argument("--no-fp8", action="store_true",
+                   help="skip the FP8-storage run on FP32 and BF16 workloads")
     p.add_argument("--no-serve", action="store_true",
                    help="skip the arrival traces of the serving workload")
     p.add_argument("--serve-requests", type=int, default=20000)
@@ -303,7 +305,7 @@ def main():
         w.Q = synth.generate(sq, device=dev, queries_only=True).Q
     X, Q = w.X, w.Q
     t = pano.panorama_fit_transform(X[:65536], n_levels=s.n_levels)
-    prec = {"fp32": pano.PANO_FP32, "bf16": pano.PANO_BF16}[s.precision]
+    prec = {"fp32": pano.PANO_FP32, "bf16": pano.PANO_BF16, "fp8": pano.PANO_FP8}[s.precision]
     # per-query nprobe / k (the batching workload) or scalars
     per_query = not isinstance(s.nprobe, int) or not isinstance(s.k, int)
     npa = w.nprobe.to(dev) if not isinstance(s.nprobe, int) else s.nprobe
@@ -413,39 +415,45 @@ def main():
             "slice_GBps": st["slice_bytes"] / ((va + vb) / 1e3) / 1e9,
             "hbm_peak_GBps": pk.get("hbm_gbs")}
 
-    # pruned BF16 storage on the same data and queries (the metric's pruned
-    # BF16 vs plain FP32): level widths must be 16, 32 or multiples of 64,
-    # so d / 64 levels of 64; same transform and centroids
-    bf16 = None
-    if s.precision == "fp32" and not args.no_bf16 and s.d % 64 == 0:
-        idx16 = pano.panorama_build_ivf(t, X, nlist=s.nlist, level_widths=[64] * (s.d // 64),
-                                        precision=pano.PANO_BF16,
-                                        centroids=idx.centroids() if s.nlist > 1 else None)
+    # pruned BF16 and FP8 storage on the same data and queries (the metric's
+    # pruned BF16/FP8 vs plain FP32): d / 64 levels of 64 (valid widths for
+    # both), same transform and centroids
+    def quantised_run(precision):
+        idxq = pano.panorama_build_ivf(t, X, nlist=s.nlist, level_widths=[64] * (s.d // 64),
+                                       precision=precision,
+                                       centroids=idx.centroids() if s.nlist > 1 else None)
         for _ in range(args.warmup):
-            idx16.search(Q, npa, ka, k_max=k)
+            idxq.search(Q, npa, ka, k_max=k)
         torch.cuda.synchronize()
-        tot16 = 0.0
+        totq = 0.0
         for _ in range(args.steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            idx16.search(Q, npa, ka, k_max=k)
+            idxq.search(Q, npa, ka, k_max=k)
             e1.record(stream)
             e1.synchronize()
-            tot16 += e0.elapsed_time(e1)
-        t16 = torch.tensor([tot16], device=dev)
+            totq += e0.elapsed_time(e1)
+        tq = torch.tensor([totq], device=dev)
         if world > 1:
-            dist.all_reduce(t16, op=dist.ReduceOp.MAX)
-        ms16 = t16.item() / args.steps
-        idx16.search(Q, npa, ka, k_max=k, collect_stats=True)
-        st16 = pano.last_stats().as_dict()
-        bf16 = {"levels": f"{s.d // 64}x64", "ms_per_step": ms16,
-                "value": pairs * world / (ms16 / 1e3), "qps": nq * world / (ms16 / 1e3),
-                "speedup_vs_fp32_scan": scan_per / ms16,
-                "dims_scanned_frac": st16["dims_scanned"] / max(1, pairs * s.d),
-                "reranked": st16["reranked"]}
-        del idx16
+            dist.all_reduce(tq, op=dist.ReduceOp.MAX)
+        msq = tq.item() / args.steps
+        idxq.search(Q, npa, ka, k_max=k, collect_stats=True)
+        stq = pano.last_stats().as_dict()
+        out = {"levels": f"{s.d // 64}x64", "ms_per_step": msq,
+               "value": pairs * world / (msq / 1e3), "qps": nq * world / (msq / 1e3),
+               "speedup_vs_fp32_scan": scan_per / msq if s.precision == "fp32" else None,
+               "dims_scanned_frac": stq["dims_scanned"] / max(1, pairs * s.d),
+               "reranked": stq["reranked"], "index_gb": idxq.info().device_bytes / 1e9}
+        del idxq
+        return out
+
+    bf16 = fp8 = None
+    if s.precision == "fp32" and not args.no_bf16 and s.d % 64 == 0:
+        bf16 = quantised_run(pano.PANO_BF16)
+    if s.precision in ("fp32", "bf16") and not args.no_fp8 and s.d % 64 == 0:
+        fp8 = quantised_run(pano.PANO_FP8)
 
     # the serving workload: Poisson arrivals through the continuous-batching
     # server (batches of up to 1024 formed from what has arrived, several in
@@ -503,6 +511,7 @@ def main():
                 "qps": nq * world / (e2e_per / 1e3), "ms_per_step": e2e_per,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": nq * k * 12},
             "bf16_pruned": bf16,
+            "fp8_pruned": fp8,
             "autotune": tune,
             "serving": serving,
             "gpu_launches": (KERNELS_PER_SEARCH if s.nlist > 1 else KERNELS_PER_SEARCH - 2)

@@ -56,7 +56,8 @@ extern "C" {
 /* ------------------------------------------------------ storage precision */
 #define PANO_FP32 0 /* level slices in FP32, SIMT partial products          */
 #define PANO_BF16 1 /* level slices in BF16, tensor-core partial products   */
-#define PANO_FP8 2  /* level slices in FP8 E4M3 with a per-vector scale     */
+#define PANO_FP8 2  /* level slices in FP8 E4M3 with a per-vector power-of-
+                       two scale, tensor-core partial products               */
 
 typedef struct pano_transform pano_transform; /* opaque, library-owned */
 typedef struct pano_index pano_index;         /* opaque, library-owned */
@@ -180,6 +181,9 @@ void panorama_free_transform(pano_transform* t);
  *   vector, per-vector tail norms and rounding-error bounds, level-major
  *   packing in chunks, and an FP32 copy of the original rows for the exact
  *   re-ranking step.  Blocks until the index is complete.
+ *   Level widths: PANO_BF16 needs 16, 32 or multiples of 64; PANO_FP8 32,
+ *   64 or multiples of 128 (its tiles have the byte layout of bf16 tiles of
+ *   half the width); both need d <= 8192.
  * Errors: PANO_EINVAL (d mismatch, nlist < 1 or > n, bad level split,
  *         unknown precision), PANO_ENOMEM, PANO_ECUDA, PANO_ENODEV. */
 int panorama_build_ivf(const pano_transform* t, const float* X, int64_t n,

@@ -25,6 +25,16 @@ extern "C" {
 int panorama_debug_tc_gemm(const void* A, const void* B, int32_t N, int32_t K,
                            float* D, void* stream);
 
+/* panorama_debug_tc_gemm_fp8 -- the same with E4M3 tiles and the FP8 verify
+ * kernel's MMA (tcgen05.mma kind::f8f6f4, 32 K elements per instruction; the
+ * tile of K E4M3 bytes per row has the byte layout of a K/2-wide bf16 tile).
+ *   A: device, 128 x K E4M3 bytes row-major;  B: device, N x K E4M3 bytes;
+ *   D: device, 128 x N FP32 row-major (written).
+ *   N: multiple of 16 in [16, 256];  K: 32, 64 or a multiple of 128 <= 512.
+ * Errors: as panorama_debug_tc_gemm. */
+int panorama_debug_tc_gemm_fp8(const void* A, const void* B, int32_t N, int32_t K,
+                               float* D, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -117,6 +117,7 @@ SIGNATURES = {
     "panorama_last_error": (ctypes.c_char_p, []),
     "panorama_version": (ctypes.c_char_p, []),
     "panorama_debug_tc_gemm": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _P]),
+    "panorama_debug_tc_gemm_fp8": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _P]),
     "panorama_plan_create": (ctypes.c_int, [_P, _P, _I64, _P, _I32, _P, _I32, _I32,
                                             _P, _P, _I32, _P]),
     "panorama_plan_launch": (ctypes.c_int, [_P, _P]),
@@ -296,6 +297,19 @@ def panorama_debug_tc_gemm(A, B, stream=None):
     D = torch.empty((128, N), dtype=torch.float32, device=A.device)
     _check(lib().panorama_debug_tc_gemm(A.data_ptr(), B.data_ptr(), N, K,
                                         D.data_ptr(), _stream_ptr(stream)))
+    return D
+
+
+def panorama_debug_tc_gemm_fp8(A, B, stream=None):
+    """D = 2 A B^T with E4M3 tiles (A: 128 x K, B: N x K uint8 CUDA tensors of
+    E4M3 bytes); a unit check of the FP8 verify kernel's MMA path."""
+    import torch
+    A = A.contiguous()
+    B = B.contiguous()
+    N, K = B.shape
+    D = torch.empty((128, N), dtype=torch.float32, device=A.device)
+    _check(lib().panorama_debug_tc_gemm_fp8(A.data_ptr(), B.data_ptr(), N, K,
+                                            D.data_ptr(), _stream_ptr(stream)))
     return D
 
 

@@ -283,7 +283,8 @@ int panorama_save(const pano_index* idx, const char* path) {
   w.vec(I.list_size);
   int rc;
   if ((rc = w.dev(I.slices)) || (rc = w.dev(I.tails)) || (rc = w.dev(I.xn2)) ||
-      (rc = w.dev(I.ex)) || (rc = w.dev(I.ids)) || (rc = w.dev(I.rows)))
+      (rc = w.dev(I.ex)) || (rc = w.dev(I.ids)) || (rc = w.dev(I.rows)) ||
+      (I.precision == PANO_FP8 && (rc = w.dev(I.xscale))))
     return rc;
   uint64_t h = w.fnv.h;
   w.f.write(reinterpret_cast<const char*>(&h), 8);
@@ -327,7 +328,8 @@ int panorama_load(const char* path, pano_index** out) {
   const bool sane = r.ok && I.n >= 1 && I.d >= 1 && I.d <= 65536 && I.nlist >= 1 &&
                     I.nlist <= I.n && I.L >= 1 && I.L <= 64 &&
                     ((I.precision == PANO_FP32 && I.chunk == 64) ||
-                     (I.precision == PANO_BF16 && I.chunk == 128)) &&
+                     ((I.precision == PANO_BF16 || I.precision == PANO_FP8) &&
+                      I.chunk == 128)) &&
                     I.n_chunks >= 0 && I.n_chunks <= I.n + I.nlist;
   PANO_CHECK(sane, PANO_ECORRUPT, "header fields out of range");
   const uint64_t d = I.d, n = I.n, nl = I.nlist;
@@ -354,7 +356,8 @@ int panorama_load(const char* path, pano_index** out) {
   if ((rc = r.dev(I.slices, I.slices_bytes())) ||
       (rc = r.dev(I.tails, (uint64_t)I.n_chunks * (I.L + 1) * CHK * 4)) ||
       (rc = r.dev(I.xn2, ns * 4)) || (rc = r.dev(I.ex, ns * 4)) || (rc = r.dev(I.ids, ns * 4)) ||
-      (rc = r.dev(I.rows, ns * d * 4)))
+      (rc = r.dev(I.rows, ns * d * 4)) ||
+      (I.precision == PANO_FP8 && (rc = r.dev(I.xscale, ns * 4))))
     return rc;
   PANO_CHECK(r.ok && r.remaining == 0, PANO_ECORRUPT, "truncated index file");
   uint64_t h = 0;

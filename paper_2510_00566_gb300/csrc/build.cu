@@ -365,8 +365,8 @@ int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
   PANO_CHECK(n >= 1 && nlist >= 1 && nlist <= n, PANO_EINVAL, "need 1 <= nlist <= n");
   PANO_CHECK(n < ((int64_t)1 << 31) - 1, PANO_EINVAL, "at most 2^31-2 vectors");
   int precision = o ? o->precision : PANO_FP32;
-  PANO_CHECK(precision == PANO_FP32 || precision == PANO_BF16, PANO_EINVAL,
-             "storage precision must be PANO_FP32 or PANO_BF16 (PANO_FP8 is not built)");
+  PANO_CHECK(precision == PANO_FP32 || precision == PANO_BF16 || precision == PANO_FP8,
+             PANO_EINVAL, "storage precision must be PANO_FP32, PANO_BF16 or PANO_FP8");
   PANO_CHECK(d <= 8192, PANO_EINVAL, "dimension must be at most 8192");
   int dev = 0;
   int rc = check_device(&dev);
@@ -383,10 +383,14 @@ int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
   I.tf = *t;
   rc = make_levels(d, o, I.widths, I.offs);
   if (rc) return rc;
-  if (precision != PANO_FP32)
+  if (precision == PANO_BF16)
     for (int w : I.widths)
       PANO_CHECK(w == 16 || w == 32 || w % 64 == 0, PANO_EINVAL,
                  "bf16 level widths must be 16, 32 or multiples of 64");
+  if (precision == PANO_FP8)  // the byte layout of bf16 tiles of half the width
+    for (int w : I.widths)
+      PANO_CHECK(w == 32 || w == 64 || w % 128 == 0, PANO_EINVAL,
+                 "fp8 level widths must be 32, 64 or multiples of 128");
   I.L = (int)I.widths.size();
   I.max_w = *std::max_element(I.widths.begin(), I.widths.end());
   I.eta = t->eta;
@@ -498,7 +502,8 @@ int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
   if ((rc = I.slices.alloc(I.slices_bytes())) ||
       (rc = I.tails.alloc((size_t)I.n_chunks * (I.L + 1) * CHK * 4)) ||
       (rc = I.xn2.alloc(nslots * 4)) || (rc = I.ex.alloc(nslots * 4)) ||
-      (rc = I.ids.alloc(nslots * 4)) || (rc = I.rows.alloc((size_t)nslots * d * 4)))
+      (rc = I.ids.alloc(nslots * 4)) || (rc = I.rows.alloc((size_t)nslots * d * 4)) ||
+      (precision == PANO_FP8 && (rc = I.xscale.alloc(nslots * 4))))
     return rc;
   Tmp t_perm, t_xt;
   PANO_CUDA(cudaMalloc(&t_perm.p, nslots * sizeof(int64_t)));
@@ -522,11 +527,17 @@ int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
           I.level_off_d.as<int32_t>(), I.mu32.as<float>(), I.c_trans, I.slices.as<float>(),
           I.tails.as<float>(), I.xn2.as<float>(), I.ex.as<float>(), I.ids.as<int32_t>());
       PANO_CUDA(cudaGetLastError());
-    } else {
+    } else if (precision == PANO_BF16) {
       rc = launch_pack_bf16((float*)t_xt.p, rows_blk, (int64_t*)t_perm.p + c0 * CHK, c0, nc, d,
                             I.L, I.level_off_d.as<int32_t>(), I.mu32.as<float>(), I.c_trans,
                             I.slices.as<uint8_t>(), I.tails.as<float>(), I.xn2.as<float>(),
                             I.ex.as<float>(), I.ids.as<int32_t>(), st);
+      if (rc) return rc;
+    } else {
+      rc = launch_pack_fp8((float*)t_xt.p, rows_blk, (int64_t*)t_perm.p + c0 * CHK, c0, nc, d,
+                           I.L, I.level_off_d.as<int32_t>(), I.mu32.as<float>(), I.c_trans,
+                           I.slices.as<uint8_t>(), I.tails.as<float>(), I.xn2.as<float>(),
+                           I.ex.as<float>(), I.xscale.as<float>(), I.ids.as<int32_t>(), st);
       if (rc) return rc;
     }
   }
@@ -540,5 +551,5 @@ int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
 size_t pano_index::device_bytes() const {
   return T32.bytes + mu32.bytes + cent.bytes + cent_n2.bytes + chunk_off_d.bytes +
          list_size_d.bytes + level_off_d.bytes + slices.bytes + tails.bytes + xn2.bytes +
-         ex.bytes + ids.bytes + rows.bytes;
+         ex.bytes + ids.bytes + rows.bytes + xscale.bytes;
 }

@@ -161,6 +161,12 @@ __device__ __forceinline__ void topk_insert_warp(unsigned long long* slots, int 
     }
 }
 
+// Hint that `bytes` (a multiple of 16, 16-byte aligned) at p will be read
+// soon: a bulk prefetch into L2 (no completion to wait for).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Order-preserving map of any FP32 value to uint32.
 __device__ __forceinline__ uint32_t float_ordered(float f) {
   uint32_t u = __float_as_uint(f);

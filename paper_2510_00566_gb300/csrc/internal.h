@@ -97,12 +97,14 @@ struct pano_index {
   pano::DevBuf level_off_d;      // L + 1 int32 (m_l)
   // FP32: per chunk, per level l a block of [w_l + 1][64] floats (the level
   // slice, dims-major, then the tail column sqrt(R^{(l+1,d)})); level 0's
-  // block has three more rows (||x~||^2, e_x, id bits).  BF16: see verify_tc.
+  // block has three more rows (||x~||^2, e_x, id bits).  BF16 / FP8: see
+  // verify_tc.
   pano::DevBuf slices;
   pano::DevBuf tails;    // [chunk][L+1][CH] sqrt tail energy, rounded up
   pano::DevBuf xn2;      // [chunk][CH] ||x~||^2
   pano::DevBuf ex;       // [chunk][CH] bound on ||x~ - T~(x - mu~)||
   pano::DevBuf ids;      // [chunk][CH] int32 original id, -1 = padding
+  pano::DevBuf xscale;   // FP8: [chunk][CH] power-of-two scale s_x of each vector
   pano::DevBuf rows;     // [chunk * CH][d] original FP32 rows (re-ranking)
   size_t device_bytes() const;
   // FP32 slice layout: rows (of 64 floats) per chunk, and the first row of
@@ -110,7 +112,8 @@ struct pano_index {
   int64_t fp32_chunk_rows() const { return (int64_t)d + L + 3; }
   int32_t fp32_row_off(int l) const { return l == 0 ? 0 : offs[l] + l + 3; }
   size_t slices_bytes() const {
-    return precision == PANO_FP32 ? (size_t)n_chunks * chunk * fp32_chunk_rows() * 4
-                          : (size_t)n_chunks * chunk * d * 2;
+    return precision == PANO_FP32  ? (size_t)n_chunks * chunk * fp32_chunk_rows() * 4
+           : precision == PANO_BF16 ? (size_t)n_chunks * chunk * d * 2
+                                    : (size_t)n_chunks * chunk * d;
   }
 };

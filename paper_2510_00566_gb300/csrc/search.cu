@@ -65,9 +65,13 @@ __global__ void __launch_bounds__(kNormRows * 32) query_norms_kernel(
     x = xs;
   }
   Acc2 suffix{0.f, 0.f};
+  float xmax = 0.f;  // largest |q~_j| (the FP8 path's query scale)
   for (int l = L - 1; l >= 0; --l) {
     Acc2 e{0.f, 0.f};
-    for (int j = level_off[l] + lane; j < level_off[l + 1]; j += 32) acc2_sq(e, x[j]);
+    for (int j = level_off[l] + lane; j < level_off[l + 1]; j += 32) {
+      acc2_sq(e, x[j]);
+      xmax = fmaxf(xmax, fabsf(x[j]));
+    }
     acc2_add(suffix, warp_sum_acc2(e));
     if (lane == 0) qtail[row * (L + 1) + l] = __fsqrt_ru(acc2_upper(suffix, 0x1p-23f));
   }
@@ -81,11 +85,14 @@ __global__ void __launch_bounds__(kNormRows * 32) query_norms_kernel(
   }
   dev = warp_sum_acc2(dev);
   on = warp_sum_acc2(on);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+    xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, off));
   if (lane == 0) {
     qtail[row * (L + 1) + L] = 0.f;
     const float nqf = __fadd_rn(suffix.s, suffix.c);
     qinfo[row] = make_float4(nqf, sqrtf(nqf),
-                             __fmul_ru(c_trans_up, __fsqrt_ru(acc2_upper(dev, 0x1p-21f))), 0.f);
+                             __fmul_ru(c_trans_up, __fsqrt_ru(acc2_upper(dev, 0x1p-21f))), xmax);
     qn2[row] = __fadd_rn(on.s, on.c);
   }
 }
@@ -515,9 +522,6 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
 
 // sqrt(tau / lb_scale) rounded up, from hardware-rounded operations: y is
 // rounded up, rsqrtf has at most 2 ulp error (CUDA's documented bound) and
@@ -1493,6 +1497,8 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
       ta.xn2 = I.xn2.as<float>();
       ta.ex = I.ex.as<float>();
       ta.ids = I.ids.as<int32_t>();
+      ta.fp8 = I.precision == PANO_FP8 ? 1 : 0;
+      ta.xscale = ta.fp8 ? I.xscale.as<float>() : nullptr;
       ta.rows = I.rows.as<float>();
       ta.chunk_off = I.chunk_off_d.as<int64_t>();
       ta.qt = qt;
@@ -1512,8 +1518,16 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
       // tensor-core accumulation (2^-20 of the running sum of |products| per
       // MMA instruction, 2 d / 16 instructions); FP32 evaluation of the
       // remaining terms: gamma_{L+8}; factor 2 of safety on the last two.
-      ta.gslack = (float)(std::ldexp(1.0, -16) + (d / 8.0) * std::ldexp(1.0, -20) +
-                          2.0 * gamma_n(L + 8));
+      // BF16: the query's hi/lo split (2^-16 of |q|), d/8 MMAs at 2^-20 of
+      // the running sum of |products| each, the FP32 epilogue.  FP8: the
+      // three-term E4M3 split (2^-12 of |q| doubled; its underflow is a
+      // separate per-group term), 3d/32 MMAs on products of at most
+      // (1 + 2^-4 + 2^-8) |x^| |q|, one more rounding for the row factor.
+      ta.gslack = ta.fp8 ? (float)(std::ldexp(1.0, -11) +
+                                   (3.0 * d / 32.0 + 1.0) * 1.1 * std::ldexp(1.0, -20) +
+                                   2.0 * gamma_n(L + 9))
+                         : (float)(std::ldexp(1.0, -16) + (d / 8.0) * std::ldexp(1.0, -20) +
+                                   2.0 * gamma_n(L + 8));
       ta.lb_scale = (float)((1.0 - 8.0 * kU32) / (1.0 + I.eta));
       ta.ub_scale = (float)((1.0 + 8.0 * kU32) / (1.0 - I.eta) * (1.0 + 1e-7));
       ta.prune = mode == 0 ? 1 : 0;

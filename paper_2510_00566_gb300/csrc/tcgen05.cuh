@@ -4,7 +4,10 @@
 // warp-wide TMEM loads for the epilogue.
 //
 // Shared-memory operand layout used throughout (K-major, "swizzled"): a tile
-// of R rows x K bf16 elements is stored as row-major rows of RB bytes
+// of R rows x K bf16 elements (or 2K FP8 elements: the layout is one of bytes,
+// so an FP8 tile of width w is addressed as a bf16 tile of width w / 2, and
+// one 32-byte K-step holds 16 bf16 or 32 FP8 elements) is stored as row-major
+// rows of RB bytes
 // (RB = 32, 64 or 128); wider K is split into panels of 64 elements
 // (128-byte rows) stored one after another (panel stride R * 128 bytes).
 // Within each 8-row atom the 16-byte chunk c of row r sits at chunk position
@@ -14,6 +17,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
 
 #include "device_common.cuh"
@@ -78,6 +82,12 @@ __host__ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
          ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor of kind::f8f6f4 with E4M3 A and B (format code 0 in
+// [7,10) and [10,13)), f32 D, both K-major; one MMA covers 32 K elements.
+__host__ __device__ __forceinline__ uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 // ------------------------------------------------------------------ TMEM
 // Allocate `ncols` (power of two >= 32) columns; the address is written to
 // *dst_smem.  Executed by one full warp.
@@ -107,6 +117,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// The same for E4M3 operands (kind::f8f6f4).
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
@@ -157,6 +176,32 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
   hi = __float2bfloat16_rn(x);
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// E4M3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits; no
+// infinities) of an FP32 value, rounded to nearest even and saturated to
+// +-448; and the exact FP32 value of an E4M3 byte.
+__device__ __forceinline__ uint8_t f32_to_e4m3(float x) {
+  return (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+}
+__device__ __forceinline__ float e4m3_to_f32(uint8_t b) {
+  // normal: exponent rebiased (7 -> 127), mantissa to FP32's top bits;
+  // subnormal (exponent field 0): mantissa * 2^-9
+  const uint32_t e = (b >> 3) & 0xfu, mm = b & 7u;
+  const float m = e ? __uint_as_float(((e + 120u) << 23) | (mm << 20)) : (float)mm * 0x1p-9f;
+  return (b & 0x80u) ? -m : m;
+}
+
+// Three-term E4M3 split of an FP32 value y with |y| <= 448: y ~= t0 + t1 + t2,
+// each term the E4M3 rounding of the remainder (the remainders are exact in
+// FP32).  |y - t0 - t1 - t2| <= max(2^-12 |y|, 2^-10): each rounding loses at
+// most 2^-4 of a normal value or 2^-10 below E4M3's normal range.
+__device__ __forceinline__ void split3_e4m3(float y, uint8_t& t0, uint8_t& t1, uint8_t& t2) {
+  t0 = f32_to_e4m3(y);
+  const float r1 = y - e4m3_to_f32(t0);
+  t1 = f32_to_e4m3(r1);
+  const float r2 = r1 - e4m3_to_f32(t1);
+  t2 = f32_to_e4m3(r2);
 }
 
 }  // namespace tc

@@ -116,6 +116,98 @@ __global__ void __launch_bounds__(256) pack_bf16_kernel(
   }
 }
 
+// FP8 storage: each vector gets a power-of-two scale s_x = 2^e (the least with
+// max |x~_j| / s_x <= 448, E4M3's largest finite value; e clamped to [-60,
+// 60]) and its elements are stored as E4M3 of x~ / s_x, rounded to nearest.
+// Level tiles have the byte layout of bf16 tiles of half the width; tail
+// norms, norms and e_x are those of x^ = s_x e4m3(x~ / s_x).  Widths are 32,
+// 64 or multiples of 128, so 16-element groups never straddle a level.
+__global__ void __launch_bounds__(256) pack_fp8_kernel(
+    const float* __restrict__ xt, const float* __restrict__ rows,
+    const int64_t* __restrict__ perm, int64_t chunk0, int d, int L,
+    const int32_t* __restrict__ level_off, const float* __restrict__ mu, double c_trans,
+    uint8_t* __restrict__ slices, float* __restrict__ tails, float* __restrict__ xn2,
+    float* __restrict__ ex, float* __restrict__ xscale, int32_t* __restrict__ ids) {
+  __shared__ int16_t lvl_of[8192 / 16];  // level of each 16-element group of a row
+  __shared__ float s_scale[CH], s_inv[CH];
+  const int64_t lc = blockIdx.x, g = chunk0 + lc;
+  const float* xblk = xt + lc * CH * d;
+  const int64_t* pb = perm + lc * CH;
+  uint8_t* cbase = slices + g * (int64_t)CH * d;
+  for (int c16 = threadIdx.x; c16 < d / 16; c16 += blockDim.x) {
+    int l = 0;
+    while (level_off[l + 1] <= c16 * 16) ++l;
+    lvl_of[c16] = (int16_t)l;
+  }
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  for (int i = warp; i < CH; i += blockDim.x / 32) {
+    float m = 0.f;
+    if (pb[i] >= 0)
+      for (int j = lane; j < d; j += 32) m = fmaxf(m, fabsf(xblk[(int64_t)i * d + j]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    int e = 0;
+    if (m > 0.f) frexpf(m / 448.f, &e);  // m / 448 < 2^e, so m / 2^e < 448
+    e = max(-60, min(60, e));
+    if (lane == 0) {
+      s_scale[i] = ldexpf(1.f, e);
+      s_inv[i] = ldexpf(1.f, -e);
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < CH * (d / 16); e += blockDim.x) {
+    const int r = e / (d / 16), c16 = e % (d / 16);
+    const int l = lvl_of[c16];
+    const int m = level_off[l], w = level_off[l + 1] - m;
+    const bool valid = pb[r] >= 0;
+    const float inv = s_inv[r];
+    __align__(16) uint8_t v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      v[j] = tc::f32_to_e4m3(valid ? xblk[(int64_t)r * d + c16 * 16 + j] * inv : 0.f);
+    *reinterpret_cast<uint4*>(cbase + (size_t)m * CH +
+                              tc::swz_offset(r, (c16 * 16 - m) / 2, CH, w / 2)) =
+        *reinterpret_cast<const uint4*>(v);
+  }
+  for (int i = warp; i < CH; i += blockDim.x / 32) {
+    const int64_t slot = g * CH + i;
+    const bool valid = pb[i] >= 0;
+    const float* x = xblk + (int64_t)i * d;
+    const float sc = s_scale[i], inv = s_inv[i];
+    double suffix = 0.0, qerr = 0.0;
+    for (int l = L - 1; l >= 0; --l) {
+      double e = 0.0;
+      if (valid)
+        for (int j = level_off[l] + lane; j < level_off[l + 1]; j += 32) {
+          const double xf = x[j];
+          const double xh = (double)(tc::e4m3_to_f32(tc::f32_to_e4m3(x[j] * inv)) * sc);
+          e += xh * xh;
+          qerr += (xh - xf) * (xh - xf);
+        }
+      suffix += warp_sum_f64(e);
+      if (lane == 0)
+        tails[(g * (L + 1) + l) * CH + i] = __double2float_ru(sqrt(suffix * (1.0 + 1e-12)));
+    }
+    qerr = warp_sum_f64(qerr);
+    double dev = 0.0;
+    if (valid) {
+      const float* r = rows + (lc * CH + i) * (int64_t)d;
+      for (int j = lane; j < d; j += 32) {
+        double v = (double)r[j] - (double)mu[j];
+        dev += v * v;
+      }
+    }
+    dev = warp_sum_f64(dev);
+    if (lane == 0) {
+      tails[(g * (L + 1) + L) * CH + i] = 0.f;
+      xn2[slot] = (float)suffix;
+      ex[slot] = valid ? __double2float_ru((sqrt(qerr) + c_trans * sqrt(dev)) * (1.0 + 1e-9)) : 0.f;
+      xscale[slot] = sc;
+      ids[slot] = valid ? (int32_t)pb[i] : -1;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ search
 // One work item = (list, segment of S chunks, group of <= QG queries).  Each
 // chunk owns an A buffer; a chunk that stays live after level l has its
@@ -134,10 +226,12 @@ struct Smem {
   uint32_t abytes, bbytes;
   uint32_t off_b_hi, off_b_lo, off_alive, off_cand, off_q, total;
   static constexpr int kPend = 256;  // deferred re-rank entries (static shared memory)
-  __host__ __device__ Smem(int max_w) {
+  // eb: bytes per stored element (2 BF16, 1 FP8).  The B buffers hold the
+  // bf16 hi and lo tiles, or the three E4M3 term tiles (two in the first).
+  __host__ __device__ Smem(int max_w, int eb) {
     // after the last level the A buffers hold the [QG][S*CH] bf16 upper
     // bounds, then the [CH * QG] survivor list and their lower bounds
-    uint32_t a = (uint32_t)(CH * max_w * 2);
+    uint32_t a = (uint32_t)(CH * max_w * eb);
     const uint32_t per = (uint32_t)(QG * S * CH * 2 + S - 1) / S;
     if (a < per) a = per;
     abytes = (a + 1023) & ~1023u;
@@ -145,61 +239,93 @@ struct Smem {
     off_b_hi = S * abytes;
     off_b_lo = off_b_hi + bbytes;
     off_alive = off_b_lo + bbytes;                   // [S][CH][AW] u32
-    off_cand = off_alive + S * CH * AW * 4;          // 5 x [S][CH] (Hx, rx, ex, id, sx)
-    off_q = off_cand + 5 * S * CH * 4;               // [QG] float4 + 6 x [QG]
+    off_cand = off_alive + S * CH * AW * 4;  // 6 x [S][CH] (Hx, rx, ex, id, sx, FP8 factor)
+    off_q = off_cand + 6 * S * CH * 4;       // [QG] float4 + 6 x [QG]
     total = off_q + 10 * QG * 4;
   }
 };
 
 // The deferred pairs are checked against their queries' thresholds of the
-// moment (a lower bound above one rules the pair out); the rest get their
-// exact distance and top-k insertion.  All threads of the CTA call it; kept
-// out of line so that it does not add to the level loop's registers.
-// Returns the number re-ranked (thread 0; 0 elsewhere).
+// moment and against each other (below); the rest get their exact distance
+// and top-k insertion, in two passes: first each query's k kept pairs of
+// smallest lower bound (ties by entry), whose exact distances usually set
+// its threshold, then the others that still pass the threshold.  All threads
+// of the CTA call it (one thread per entry at most: kPend <= NT); kept out of
+// line so that it does not add to the level loop's registers.  Returns the
+// number re-ranked (thread 0; 0 elsewhere).
 __device__ __noinline__ int flush_pending(const VerifyTCArgs& a, int np,
                                           const int64_t* __restrict__ pslot,
                                           const int32_t* __restrict__ pq,
                                           const int32_t* __restrict__ pid,
                                           float* __restrict__ plb,
                                           const float* __restrict__ pub, uint16_t* keep,
-                                          int* s_nkeep) {
-  const int tid = threadIdx.x, warp = tid / 32;
-  if (tid == 0) *s_nkeep = 0;
+                                          uint16_t* rank, int* s_cnt) {
+  const int tid = threadIdx.x, warp = tid / 32, nw = blockDim.x / 32;
+  if (tid == 0) s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
   __syncthreads();
+  auto tau_of = [&](int q, int kk) {
+    const unsigned long long key = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + kk - 1);
+    return fminf(key == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key), 1.000001f),
+                 __ldcg(a.tau_seed + q));
+  };
   // a pair is re-ranked unless its lower bound exceeds the threshold or the
   // upper bounds of k pending pairs of the same query (all k are closer)
-  for (int s = tid; s < np; s += blockDim.x) {
-    const int q = pq[s], kk = a.kq[q];
-    const unsigned long long key = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + kk - 1);
-    const float tau = fminf(key == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key), 1.000001f),
-                            __ldcg(a.tau_seed + q));
+  if (tid < np) {
+    const int s = tid, q = pq[s], kk = a.kq[q];
     const float lb = plb[s];
-    bool keep_s = !(lb > tau);
+    bool keep_s = !(lb > tau_of(q, kk));
     if (keep_s) {
       int below = 0;
       for (int o = 0; o < np && below < kk; ++o)
         below += (pq[o] == q) & (__fmul_ru(pub[o], 1.000001f) < lb);
       keep_s = below < kk;
     }
-    if (keep_s) keep[atomicAdd(s_nkeep, 1)] = (uint16_t)s;
+    if (keep_s) keep[atomicAdd(&s_cnt[0], 1)] = (uint16_t)s;
   }
   __syncthreads();
-  const int nk = *s_nkeep;
+  const int nk = s_cnt[0];
+  if (tid < nk && (a.d & 3) == 0)  // all kept rows head for L2 at once
+    prefetch_l2(a.rows + pslot[keep[tid]] * a.d, (uint32_t)a.d * 4);
+  bool first = false;
+  if (tid < nk) {  // rank among the kept pairs of its query
+    const int s = keep[tid], q = pq[s];
+    const float lb = plb[s];
+    int r = 0;
+    for (int j = 0; j < nk; ++j) {
+      const int o = keep[j];
+      r += (pq[o] == q) & ((plb[o] < lb) | ((plb[o] == lb) & (o < s)));
+    }
+    first = r < a.kq[q];
+    rank[tid] = first ? 1 : 0;
+    if (first) atomicAdd(&s_cnt[1], 1);
+  }
+  __syncthreads();
   // exact distances (a warp each; they replace the lower bounds), then the
   // top-k insertions (a thread each, so their chains overlap)
-  for (int i = warp; i < nk; i += blockDim.x / 32) {
-    const int s = keep[i];
-    const float dist =
-        exact_sqdist_warp_wide(a.qorig + (int64_t)pq[s] * a.d, a.rows + pslot[s] * a.d, a.d);
-    if ((tid & 31) == 0) plb[s] = dist;
+  auto rerank = [&](const uint16_t* list, int n, const uint16_t* sel) {
+    for (int i = warp; i < n; i += nw) {
+      if (sel && !sel[i]) continue;
+      const int s = list[i];
+      const float dist =
+          exact_sqdist_warp_wide(a.qorig + (int64_t)pq[s] * a.d, a.rows + pslot[s] * a.d, a.d);
+      if ((tid & 31) == 0) plb[s] = dist;
+    }
+    __syncthreads();
+    if (tid < n && (!sel || sel[tid])) {
+      const int s = list[tid], q = pq[s];
+      topk_insert_thread(a.topk + (int64_t)q * a.k_max, a.kq[q], make_key(plb[s], pid[s]));
+    }
+    __syncthreads();
+  };
+  rerank(keep, nk, rank);
+  // the others, against the thresholds of the moment (rank now lists them)
+  if (tid < nk && !first) {
+    const int s = keep[tid], q = pq[s];
+    if (!(plb[s] > tau_of(q, a.kq[q]))) rank[atomicAdd(&s_cnt[2], 1)] = (uint16_t)s;
   }
   __syncthreads();
-  for (int i = tid; i < nk; i += blockDim.x) {
-    const int s = keep[i], q = pq[s];
-    topk_insert_thread(a.topk + (int64_t)q * a.k_max, a.kq[q], make_key(plb[s], pid[s]));
-  }
-  __syncthreads();
-  return tid == 0 ? nk : 0;
+  rerank(rank, s_cnt[2], nullptr);
+  return tid == 0 ? s_cnt[1] + s_cnt[2] : 0;
 }
 
 __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t& bits, int b, int* fail) {
@@ -210,10 +336,17 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t& bits, int b,
   return false;
 }
 
+// FP8 = false: BF16 tiles, kind::f16 MMAs with the query split into bf16 hi +
+// lo.  FP8 = true: E4M3 tiles (the byte layout of bf16 tiles of half the
+// width), kind::f8f6f4 MMAs with the query split into three E4M3 terms at one
+// power-of-two scale per group; the accumulator times the row's factor
+// s_x / (group scale) is the partial product.
+template <bool FP8>
 __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) {
+  constexpr int EB = FP8 ? 1 : 2;  // bytes per stored element
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-  const Smem lay(a.max_w);
+  const Smem lay(a.max_w, EB);
   unsigned char* abuf = base;
   unsigned char* bhi = base + lay.off_b_hi;
   unsigned char* blo = base + lay.off_b_lo;
@@ -223,6 +356,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   float* cex = crx + S * CH;
   int32_t* cid = reinterpret_cast<int32_t*>(cex + S * CH);
   float* csx = reinterpret_cast<float*>(cid + S * CH);
+  float* cfr = csx + S * CH;  // FP8: s_x / group scale, the accumulator's factor
   // per-query terms of the separable test: (E, g*rq, sq, H)
   float4* qterm = reinterpret_cast<float4*>(base + lay.off_q);  // [QG]
   int32_t* qid = reinterpret_cast<int32_t*>(qterm + QG);
@@ -239,10 +373,16 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   __shared__ int64_t pslot[Smem::kPend];
   __shared__ int32_t pq[Smem::kPend], pid[Smem::kPend];
   __shared__ float plb[Smem::kPend], pub[Smem::kPend];
-  __shared__ uint16_t keep[Smem::kPend];
+  __shared__ uint16_t keep[Smem::kPend], rnk[Smem::kPend];
+  __shared__ int s_flush[3];
+  static_assert(Smem::kPend <= NT, "the flush gives each pending pair one thread");
   __shared__ __align__(8) uint64_t load_bar[S], mma_bar[S];
   __shared__ uint32_t tmem_base;
-  __shared__ int s_item, s_nsurv, s_fail, s_npend, s_nkeep;
+  __shared__ int s_item, s_nsurv, s_fail, s_npend;
+  // FP8: the group's largest |q~_j| (as bits), query scale and the absolute
+  // bound of the query split's underflow per unit of |x|_2
+  __shared__ unsigned int s_qmax;
+  __shared__ float s_qs, s_cunder;
   __shared__ uint32_t rowlive[S][NT / 32];  // per warp: its rows live in its half
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
@@ -291,12 +431,14 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     const float st = tau == INFINITY ? 1e18f : fminf(__fsqrt_ru(__fdiv_ru(tau, a.lb_scale)), 1e18f);
     const float E = __fadd_ru(qeq[g], st);
     const float nq = qnq[g], rq = qrq[g];
-    qterm[g] = make_float4(E, g_slack * rq, sq,
+    // FP8: the query split's underflow error (at most s_cunder |x|_2 on the
+    // partial product) joins the g rq coefficient of rx
+    qterm[g] = make_float4(E, FP8 ? fmaf(g_slack, rq, s_cunder) : g_slack * rq, sq,
                            0.5f * (nq - g_slack * nq - E * E - kEval * (rq + E) * (rq + E)));
     qtau[g] = tau;
   };
-  auto rerank_pending = [&]() {
-    const int nk = flush_pending(a, s_npend, pslot, pq, pid, plb, pub, keep, &s_nkeep);
+  auto rerank_pending = [&](int np) {
+    const int nk = flush_pending(a, np, pslot, pq, pid, plb, pub, keep, rnk, s_flush);
     if (a.collect && tid == 0) s_stat[4] += nk;
   };
   auto chunk_live = [&](int c) {
@@ -307,7 +449,10 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   };
 
   while (true) {
-    if (tid == 0) s_item = atomicAdd(a.counter, 1);
+    if (tid == 0) {
+      s_item = atomicAdd(a.counter, 1);
+      s_qmax = 0u;
+    }
     __syncthreads();
     const int item = s_item;
     const int64_t n_items = *a.n_items < a.items_cap ? *a.n_items : a.items_cap;
@@ -319,16 +464,17 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     const int nch = (int)((chE - ch0) < S ? (chE - ch0) : S);
     const int G = it.w;
     const int Npad = G <= 16 ? 16 : ((G + 15) & ~15);
-    const uint32_t idesc = tc::idesc_bf16(CH, Npad);
-    const uint8_t* item_src = a.slices + ch0 * (int64_t)CH * d * 2;
+    const uint32_t idesc = FP8 ? tc::idesc_e4m3(CH, Npad) : tc::idesc_bf16(CH, Npad);
+    const uint8_t* item_src = a.slices + ch0 * (int64_t)CH * d * EB;
 
     // stage chunk c's level-l tile (live rows only when few rows live)
     auto issue_load = [&](int c, int l) {  // warp 0
       const int m = a.level_off[l], w = a.level_off[l + 1] - m;
-      const uint32_t tbytes = (uint32_t)w * CH * 2;
-      const int rb = tc::row_bytes(w), npan = w >= 64 ? w / 64 : 1;
+      const int wl = FP8 ? w / 2 : w;  // width of the bf16 tile with the same bytes
+      const uint32_t tbytes = (uint32_t)w * CH * EB;
+      const int rb = tc::row_bytes(wl), npan = wl >= 64 ? wl / 64 : 1;
       unsigned char* dst = abuf + (size_t)c * lay.abytes;
-      const uint8_t* src = item_src + (int64_t)c * CH * d * 2 + (size_t)m * CH * 2;
+      const uint8_t* src = item_src + (int64_t)c * CH * d * EB + (size_t)m * CH * EB;
       uint32_t atoms = 0;  // 8-row groups holding a live row
       for (int t = 0; t < 16; ++t)
         if (((rowlive[c][t >> 2] | rowlive[c][4 + (t >> 2)]) >> ((t & 3) * 8)) & 0xffu)
@@ -354,26 +500,40 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         if (a.collect && lane == 0) s_stat[3] += (unsigned long long)na * npan * abytes_row;
       }
     };
-    // B tiles for level l: query slices split into bf16 hi / lo
+    // B tiles for level l, 8 query elements at a time: bf16 hi / lo parts,
+    // or (FP8) three E4M3 terms of the scaled query in three tiles
+    auto store_b = [&](int g, int c8, int w, const float (&f)[8]) {
+      if (FP8) {
+        const float qs = s_qs;
+        __align__(8) uint8_t t0[8], t1[8], t2[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) tc::split3_e4m3(f[j] * qs, t0[j], t1[j], t2[j]);
+        const uint32_t off = tc::swz_offset(g, c8 * 4, Npad, w / 2);
+        *reinterpret_cast<uint2*>(bhi + off) = *reinterpret_cast<const uint2*>(t0);
+        *reinterpret_cast<uint2*>(bhi + QG * a.max_w + off) = *reinterpret_cast<const uint2*>(t1);
+        *reinterpret_cast<uint2*>(blo + off) = *reinterpret_cast<const uint2*>(t2);
+      } else {
+        __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) tc::split_bf16(f[j], hi[j], lo[j]);
+        const uint32_t off = tc::swz_offset(g, c8 * 8, Npad, w);
+        *reinterpret_cast<uint4*>(bhi + off) = *reinterpret_cast<const uint4*>(hi);
+        *reinterpret_cast<uint4*>(blo + off) = *reinterpret_cast<const uint4*>(lo);
+      }
+    };
     auto build_b = [&](int l, int first_chunk) {
       const int m = a.level_off[l], w = a.level_off[l + 1] - m;
       for (int e = tid + first_chunk * NT; e < Npad * (w / 8); e += NT) {
         const int g = e / (w / 8), c8 = e % (w / 8);
-        __align__(16) __nv_bfloat16 hi[8], lo[8];
+        float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (g < G) {
           const float* src = a.qt + (int64_t)qid[g] * d + m + c8 * 8;
           const float4 f0 = *reinterpret_cast<const float4*>(src);
           const float4 f1 = *reinterpret_cast<const float4*>(src + 4);
-          const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
-#pragma unroll
-          for (int j = 0; j < 8; ++j) tc::split_bf16(f[j], hi[j], lo[j]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) hi[j] = lo[j] = __float2bfloat16_rn(0.f);
+          f[0] = f0.x, f[1] = f0.y, f[2] = f0.z, f[3] = f0.w;
+          f[4] = f1.x, f[5] = f1.y, f[6] = f1.z, f[7] = f1.w;
         }
-        const uint32_t off = tc::swz_offset(g, c8 * 8, Npad, w);
-        *reinterpret_cast<uint4*>(bhi + off) = *reinterpret_cast<const uint4*>(hi);
-        *reinterpret_cast<uint4*>(blo + off) = *reinterpret_cast<const uint4*>(lo);
+        store_b(g, c8, w, f);
       }
     };
 
@@ -387,6 +547,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         qrq[tid] = inf.y;
         qeq[tid] = inf.z;
         qk[tid] = a.kq[q];
+        if (FP8) atomicMax(&s_qmax, __float_as_uint(inf.w));  // inf.w = max_j |q~_j| >= 0
       } else {
         qnq[tid] = qrq[tid] = qeq[tid] = 0.f;
         qk[tid] = 0;
@@ -409,6 +570,20 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       }
     }
     __syncthreads();
+    if (FP8 && tid == 0) {
+      // query scale 2^-e: the group's largest |q~_j| times it is at most 448
+      // (no E4M3 term saturates); a smaller e (at most -60) only adds
+      // underflow, which s_cunder bounds: each element loses at most 2^-10
+      // of the scaled unit, so the partial product at most
+      // 2^-10 2^e sqrt(d) |x|_2
+      const float qm = __uint_as_float(s_qmax);
+      int e = 0;
+      if (qm > 0.f) frexpf(qm / 448.f, &e);
+      if (e > 60) atomicOr(a.err, kErrBadInput);
+      e = max(-60, min(60, e));
+      s_qs = ldexpf(1.f, -e);
+      s_cunder = __fmul_ru(ldexpf(1.f, e - 10), __fsqrt_ru((float)d));
+    }
     {
       uint32_t gm0 = 0, gm1 = 0;
       for (int g = 0; g < G; ++g)
@@ -439,6 +614,11 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         qterm[tid] = make_float4(0.f, 0.f, 0.f, -INFINITY);
         qtau[tid] = -1.f;
       }
+    }
+    if (FP8) {
+      const float qinv = 1.f / s_qs;  // a power of two: exact
+      for (int e = tid; e < S * CH; e += NT)
+        cfr[e] = e / CH < nch ? a.xscale[(ch0 + e / CH) * CH + (e % CH)] * qinv : 0.f;
     }
     build_b(0, 0);
     fence_proxy_async_smem();
@@ -507,6 +687,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         if (any_warp) {
           const float sx = csx[c * CH + row], rx = crx[c * CH + row], exv = cex[c * CH + row];
           const float Hx = cHx[c * CH + row];
+          const float fr = FP8 ? cfr[c * CH + row] : 1.f;
           if (a.collect) {
             const unsigned np = __reduce_add_sync(0xffffffffu, (unsigned)__popc(wm));
             if (lane == 0) {
@@ -523,7 +704,8 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
 #pragma unroll
               for (int g = 0; g < 16; ++g) {
                 const float4 t = qt[g];
-                const float P = fmaf(t.x, exv, fmaf(t.y, rx, fmaf(t.z, sx, v[g])));
+                const float p = FP8 ? v[g] * fr : v[g];
+                const float P = fmaf(t.x, exv, fmaf(t.y, rx, fmaf(t.z, sx, p)));
                 pruned |= (P < t.w + Hx ? 1u : 0u) << g;
               }
               wm &= ~pruned;
@@ -537,7 +719,8 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
 #pragma unroll
               for (int g = 0; g < 32; ++g) {
                 const float4 t = qt[g];
-                const float P = fmaf(t.x, exv, fmaf(t.y, rx, fmaf(t.z, sx, v[g])));
+                const float p = FP8 ? v[g] * fr : v[g];
+                const float P = fmaf(t.x, exv, fmaf(t.y, rx, fmaf(t.z, sx, p)));
                 pruned |= (P < t.w + Hx ? 1u : 0u) << g;
               }
               wm &= ~pruned;
@@ -564,11 +747,22 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           if (wait_phase(&load_bar[c], load_bits, c, &s_fail)) {
             const uint32_t a0 = smem_u32(abuf + (size_t)c * lay.abytes);
             const uint32_t dt = tbase + (uint32_t)(c * QG);
-            for (int s = 0; s < w / 16; ++s) {
-              const uint64_t ad = tc::kstep_desc(a0, s, CH, w);
-              tc::mma_bf16(dt, ad, tc::kstep_desc(h0, s, Npad, w), idesc,
-                           (l > 0 || s > 0) ? 1u : 0u);
-              tc::mma_bf16(dt, ad, tc::kstep_desc(l0, s, Npad, w), idesc, 1u);
+            if (FP8) {  // 32 elements per K-step; tiles addressed at half width
+              const uint32_t m0 = h0 + (uint32_t)(QG * a.max_w);
+              for (int s = 0; s < w / 32; ++s) {
+                const uint64_t ad = tc::kstep_desc(a0, s, CH, w / 2);
+                tc::mma_e4m3(dt, ad, tc::kstep_desc(h0, s, Npad, w / 2), idesc,
+                             (l > 0 || s > 0) ? 1u : 0u);
+                tc::mma_e4m3(dt, ad, tc::kstep_desc(m0, s, Npad, w / 2), idesc, 1u);
+                tc::mma_e4m3(dt, ad, tc::kstep_desc(l0, s, Npad, w / 2), idesc, 1u);
+              }
+            } else {
+              for (int s = 0; s < w / 16; ++s) {
+                const uint64_t ad = tc::kstep_desc(a0, s, CH, w);
+                tc::mma_bf16(dt, ad, tc::kstep_desc(h0, s, Npad, w), idesc,
+                             (l > 0 || s > 0) ? 1u : 0u);
+                tc::mma_bf16(dt, ad, tc::kstep_desc(l0, s, Npad, w), idesc, 1u);
+              }
             }
           }
           // committed even after a failed wait, so the epilogue's wait ends
@@ -594,12 +788,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
             const float f[8] = {pf[2 * i].x, pf[2 * i].y, pf[2 * i].z, pf[2 * i].w,
                                 pf[2 * i + 1].x, pf[2 * i + 1].y, pf[2 * i + 1].z,
                                 pf[2 * i + 1].w};
-            __align__(16) __nv_bfloat16 hi[8], lo[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) tc::split_bf16(f[j], hi[j], lo[j]);
-            const uint32_t off = tc::swz_offset(g, c8 * 8, Npad, w1);
-            *reinterpret_cast<uint4*>(bhi + off) = *reinterpret_cast<const uint4*>(hi);
-            *reinterpret_cast<uint4*>(blo + off) = *reinterpret_cast<const uint4*>(lo);
+            store_b(g, c8, w1, f);
           }
         }
         if (Npad * (w1 / 8) > PF_CHUNKS * NT) build_b(l + 1, PF_CHUNKS);  // wide levels
@@ -634,6 +823,8 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       if (any_warp) {
         const float rx = crx[c * CH + row], exv = cex[c * CH + row];
         const float nx2 = a.xn2[(ch0 + c) * CH + row];
+        const float fr = FP8 ? cfr[c * CH + row] : 1.f;
+        const float under = FP8 ? 2.f * s_cunder * rx : 0.f;  // FP8 query split
         float v[32];
         tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
 #pragma unroll
@@ -641,9 +832,9 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           const int g = 32 * half + j;
           uint16_t u = 0x7f80u;
           if ((wm >> j) & 1u) {
-            const float A = qnq[g] + nx2 - 2.f * v[j];
+            const float A = qnq[g] + nx2 - 2.f * (FP8 ? v[j] * fr : v[j]);
             const float Ss = qrq[g] + rx;
-            const float r = __fadd_ru(__fsqrt_ru(fmaxf(A + g_slack * Ss * Ss, 0.f)),
+            const float r = __fadd_ru(__fsqrt_ru(fmaxf(A + fmaf(g_slack * Ss, Ss, under), 0.f)),
                                       qeq[g] + exv);
             u = __bfloat16_as_ushort(__float2bfloat16_ru(__fmul_ru(__fmul_ru(r, r), a.ub_scale)));
           }
@@ -679,6 +870,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       const bool any_warp = __any_sync(0xffffffffu, wm != 0);
       if (any_warp) {
         const float rx = crx[c * CH + row], exv = cex[c * CH + row], Hx = cHx[c * CH + row];
+        const float fr = FP8 ? cfr[c * CH + row] : 1.f;
         float v[32];
         tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
         const float4* qt = qterm + 32 * half;
@@ -686,7 +878,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const float4 t = qt[j];
-          const float P = fmaf(t.x, exv, fmaf(t.y, rx, v[j]));
+          const float P = fmaf(t.x, exv, fmaf(t.y, rx, FP8 ? v[j] * fr : v[j]));
           pruned |= (P < t.w + Hx ? 1u : 0u) << j;
         }
         wm &= ~pruned;
@@ -702,41 +894,41 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       __syncthreads();
       const int ns = s_nsurv;
       int np = s_npend;
-      if (np + ns > Smem::kPend) {
-        rerank_pending();
-        np = 0;
-      }
-      if (ns <= Smem::kPend) {
-        for (int s = tid; s < ns; s += NT) {
-          const int r = surv[s] >> 6, g = surv[s] & 63;
+      // all survivors go through the deferred list, a full list being
+      // checked and re-ranked before more join (the survivor list and the
+      // accumulators dumped above stay untouched by a flush)
+      for (int b0 = 0; b0 < ns;) {
+        if (np == Smem::kPend) {
+          __syncthreads();
+          rerank_pending(np);
+          np = 0;
+        }
+        const int nb = min(ns - b0, Smem::kPend - np);
+        for (int s = tid; s < nb; s += NT) {
+          const int e = surv[b0 + s], r = e >> 6, g = e & 63;
           const int64_t slot = (ch0 + c) * CH + r;
           const float rx = crx[c * CH + r], exv = cex[c * CH + r];
-          const float p = vdump[(g & 31) * NT + r + CH * (g >> 5)];  // all levels
+          float p = vdump[(g & 31) * NT + r + CH * (g >> 5)];  // all levels
+          if (FP8) p *= cfr[c * CH + r];
+          const float under = FP8 ? 2.f * s_cunder * rx : 0.f;
           const float A = qnq[g] + a.xn2[slot] - 2.f * p;
           const float Ss = qrq[g] + rx;
-          const float lr = sqrtf(fmaxf(A - g_slack * Ss * Ss, 0.f)) - (qeq[g] + exv);
+          const float slack = fmaf(g_slack * Ss, Ss, under);
+          const float lr = sqrtf(fmaxf(A - slack, 0.f)) - (qeq[g] + exv);
           pslot[np + s] = slot;
           pq[np + s] = qid[g];
           pid[np + s] = cid[c * CH + r];
           plb[np + s] = lr > 0.f ? lr * lr * a.lb_scale : 0.f;
-          const float ru = __fadd_ru(__fsqrt_ru(fmaxf(A + g_slack * Ss * Ss, 0.f)), qeq[g] + exv);
+          const float ru = __fadd_ru(__fsqrt_ru(fmaxf(A + slack, 0.f)), qeq[g] + exv);
           pub[np + s] = __fmul_ru(__fmul_ru(ru, ru), a.ub_scale);
         }
-      } else {  // too many to defer: re-rank them now
-        for (int s = warp; s < ns; s += NT / 32) {
-          const int r = surv[s] >> 6, g = surv[s] & 63;
-          const int q = qid[g];
-          const int64_t slot = (ch0 + c) * CH + r;
-          const float dist =
-              exact_sqdist_warp_wide(a.qorig + (int64_t)q * d, a.rows + slot * d, d);
-          topk_insert_warp(a.topk + (int64_t)q * a.k_max, qk[g], make_key(dist, cid[c * CH + r]));
-        }
-        if (a.collect && tid == 0) s_stat[4] += ns;
+        np += nb;
+        b0 += nb;
       }
       tc::fence_before_sync();
       __syncthreads();
       tc::fence_after_sync();
-      if (tid == 0) s_npend = ns <= Smem::kPend ? np + ns : np;
+      if (tid == 0) s_npend = np;
     }
     // the scratch written through the generic proxy is refilled by
     // bulk-async copies in the next item
@@ -745,7 +937,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   }
   if (!s_fail) {  // the last deferred survivors
     __syncthreads();
-    rerank_pending();
+    rerank_pending(s_npend);
   }
   if (s_fail && tid == 0) atomicOr(a.err, kErrTimeout);
   __syncthreads();
@@ -779,9 +971,20 @@ int launch_pack_bf16(const float* xt, const float* rows, const int64_t* perm, in
   return PANO_OK;
 }
 
-size_t verify_tc_smem(int max_w) {
+int launch_pack_fp8(const float* xt, const float* rows, const int64_t* perm, int64_t chunk0,
+                    int64_t nchunks, int d, int L, const int32_t* level_off, const float* mu,
+                    double c_trans, uint8_t* slices, float* tails, float* xn2, float* ex,
+                    float* xscale, int32_t* ids, cudaStream_t st) {
+  PANO_CHECK(d % 32 == 0 && d <= 8192, PANO_EINVAL, "fp8 storage needs d % 32 == 0, d <= 8192");
+  pack_fp8_kernel<<<(unsigned)nchunks, 256, 0, st>>>(xt, rows, perm, chunk0, d, L, level_off, mu,
+                                                     c_trans, slices, tails, xn2, ex, xscale, ids);
+  PANO_CUDA(cudaGetLastError());
+  return PANO_OK;
+}
+
+size_t verify_tc_smem(int max_w, bool fp8) {
   // at most two CTAs per SM: each owns 256 of the 512 TMEM columns
-  return std::max<size_t>(Smem(max_w).total + 1024, 80 * 1024);
+  return std::max<size_t>(Smem(max_w, fp8 ? 1 : 2).total + 1024, 80 * 1024);
 }
 
 int launch_verify_tc(const VerifyTCArgs& a, cudaStream_t st) {
@@ -791,17 +994,18 @@ int launch_verify_tc(const VerifyTCArgs& a, cudaStream_t st) {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa;
-    attr_err = cudaFuncGetAttributes(&fa, verify_tc_kernel);
-    if (attr_err == cudaSuccess)
-      attr_err = cudaFuncSetAttribute(verify_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      optin - (int)fa.sharedSizeBytes);
-    if (attr_err == cudaSuccess)
-      attr_err = cudaFuncSetAttribute(verify_tc_kernel,
-                                      cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    for (const void* k : {(const void*)verify_tc_kernel<false>, (const void*)verify_tc_kernel<true>}) {
+      cudaFuncAttributes fa;
+      if (attr_err == cudaSuccess) attr_err = cudaFuncGetAttributes(&fa, k);
+      if (attr_err == cudaSuccess)
+        attr_err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        optin - (int)fa.sharedSizeBytes);
+      if (attr_err == cudaSuccess)
+        attr_err = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
   });
   PANO_CUDA(attr_err);
-  const size_t smem = verify_tc_smem(a.max_w);
+  const size_t smem = verify_tc_smem(a.max_w, a.fp8 != 0);
   int dev = 0, sms = 0, optin = 0;
   PANO_CUDA(cudaGetDevice(&dev));
   PANO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -813,7 +1017,10 @@ int launch_verify_tc(const VerifyTCArgs& a, cudaStream_t st) {
   // memory carveout, which switches only when a launch asks for more.  A
   // persistent CTA that cannot be resident yet starts later and finds the
   // queue drained, so over-provisioning is harmless.
-  verify_tc_kernel<<<sms * 2, NT, smem, st>>>(a);
+  if (a.fp8)
+    verify_tc_kernel<true><<<sms * 2, NT, smem, st>>>(a);
+  else
+    verify_tc_kernel<false><<<sms * 2, NT, smem, st>>>(a);
   PANO_CUDA(cudaGetLastError());
   return PANO_OK;
 }

@@ -1,4 +1,4 @@
-// Launchers of the BF16 tensor-core path (verify_tc.cu).
+// Launchers of the BF16 / FP8 tensor-core path (verify_tc.cu).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -15,6 +15,7 @@ struct VerifyTCArgs {
   const float* xn2;
   const float* ex;
   const int32_t* ids;
+  const float* xscale;  // FP8: per-vector power-of-two scale s_x
   const float* rows;
   const int64_t* chunk_off;
   const float* qt;
@@ -39,6 +40,7 @@ struct VerifyTCArgs {
   int collect;
   int phase;  // 0: phase A (its dims are also counted apart)
   float eps;  // Eq. 4: the query tail term of the pruning test is scaled by eps
+  int fp8;    // 1: E4M3 level tiles (kind::f8f6f4), 0: BF16
   int32_t level_off[65];
 };
 
@@ -46,7 +48,11 @@ int launch_pack_bf16(const float* xt, const float* rows, const int64_t* perm, in
                      int64_t nchunks, int d, int L, const int32_t* level_off, const float* mu,
                      double c_trans, uint8_t* slices, float* tails, float* xn2, float* ex,
                      int32_t* ids, cudaStream_t st);
+int launch_pack_fp8(const float* xt, const float* rows, const int64_t* perm, int64_t chunk0,
+                    int64_t nchunks, int d, int L, const int32_t* level_off, const float* mu,
+                    double c_trans, uint8_t* slices, float* tails, float* xn2, float* ex,
+                    float* xscale, int32_t* ids, cudaStream_t st);
 int launch_verify_tc(const VerifyTCArgs& a, cudaStream_t st);
-size_t verify_tc_smem(int max_w);
+size_t verify_tc_smem(int max_w, bool fp8);
 
 }  // namespace pano

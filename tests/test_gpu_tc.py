@@ -1,9 +1,10 @@
-"""Tensor-core building blocks of the BF16 verify kernel in isolation:
-swizzled K-major shared-memory tiles, tcgen05.mma accumulation in tensor
-memory over two passes, tcgen05.ld read-back.  D = 2 A B^T is compared with
-an FP64 product of the same bf16 values; products of bf16 are exact in FP32,
-so only the accumulation rounds.  The bound used by the pruning margin is
-n_mma * 2^-20 * sum |a b| per output (n_mma = MMA instructions accumulated)."""
+"""Tensor-core building blocks of the BF16 and FP8 verify kernels in
+isolation: swizzled K-major shared-memory tiles, tcgen05.mma accumulation in
+tensor memory over two passes, tcgen05.ld read-back.  D = 2 A B^T is compared
+with an FP64 product of the same bf16 (or E4M3) values; their products are
+exact in FP32, so only the accumulation rounds.  The bound used by the
+pruning margin is n_mma * 2^-20 * sum |a b| per output (n_mma = MMA
+instructions accumulated: 16 K elements each for bf16, 32 for E4M3)."""
 import numpy as np
 import pytest
 import torch
@@ -52,3 +53,44 @@ def test_tc_gemm_cancellation():
     ref = 2.0 * (A.double() @ B.double().T)
     mag = 2.0 * (A.double().abs() @ B.double().abs().T)
     assert torch.all((D - ref).abs() <= (2 * K // 16) * 2.0 ** -20 * mag)
+
+
+E4M3 = torch.float8_e4m3fn
+
+
+def _fp8_check(A, B):
+    D = pano.panorama_debug_tc_gemm_fp8(A.view(torch.uint8).cuda(),
+                                        B.view(torch.uint8).cuda()).cpu().double()
+    a, b = A.double(), B.double()
+    ref = 2.0 * (a @ b.T)
+    mag = 2.0 * (a.abs() @ b.abs().T)
+    n_mma = 2 * A.shape[1] // 32
+    err = (D - ref).abs()
+    assert torch.all(err <= n_mma * 2.0 ** -20 * mag + 1e-30), float((err / mag).max())
+    return float((err / mag.clamp_min(1e-300)).max())
+
+
+@pytest.mark.parametrize("N,K", [(16, 32), (64, 64), (32, 128), (256, 128), (48, 384),
+                                 (64, 512)])
+def test_tc_gemm_fp8_matches_fp64(N, K):
+    g = torch.Generator().manual_seed(N * 1000 + K)
+    A = (torch.randn(128, K, generator=g) * torch.exp(-0.01 * torch.arange(K))).to(E4M3)
+    B = torch.randn(N, K, generator=g).to(E4M3)
+    assert _fp8_check(A, B) < 1e-6
+
+
+def test_tc_gemm_fp8_wide_range_and_cancellation():
+    """Products over 2^40 of dynamic range (subnormal E4M3 included), and
+    large terms that cancel: the error stays within the per-MMA model."""
+    g = torch.Generator().manual_seed(7)
+    scale_a = torch.pow(2.0, torch.randint(-12, 8, (128, 256), generator=g).float())
+    scale_b = torch.pow(2.0, torch.randint(-12, 8, (64, 256), generator=g).float())
+    A = (torch.randn(128, 256, generator=g) * scale_a).clamp(-448, 448).to(E4M3)
+    B = (torch.randn(64, 256, generator=g) * scale_b).clamp(-448, 448).to(E4M3)
+    _fp8_check(A, B)
+    a = torch.zeros(128, 128)
+    a[:, 0::2] = 448.0
+    a[:, 1::2] = -448.0
+    b = torch.ones(32, 128)
+    b[:, 1::2] = 1.125
+    assert _fp8_check(a.to(E4M3), b.to(E4M3)) == 0.0
