@@ -245,6 +245,40 @@ int panorama_search_noalloc(const pano_index* idx, const float* queries, int64_t
 /* Counters of this thread's last search_ex with collect_stats = 1. */
 int panorama_search_stats(pano_search_stats* out);
 
+/* ------------------------------------------------------------------ refine
+ * panorama_build_flat -- flat index for refining candidate-id lists, the
+ * paper's no-batch (B = 1) variant [Section 6.4 "IndexRefinePanorama",
+ * Table 1]: every vector transformed and stored row-major (a candidate's
+ * level slice is contiguous), with rounded-up tail norms, norms, error bounds
+ * and the original FP32 rows for the exact re-ranking.
+ *   t, X, n, opts: as panorama_build_ivf (opts: level split; precision must
+ *   be PANO_FP32; no k-means).  Vector i gets id i.  panorama_search rejects
+ *   a flat index; panorama_save / panorama_load keep it.
+ * Errors: PANO_EINVAL, PANO_ENOMEM, PANO_ECUDA, PANO_ENODEV. */
+int panorama_build_flat(const pano_transform* t, const float* X, int64_t n,
+                        const pano_build_opts* opts, void* stream, pano_index** out);
+
+/* panorama_refine -- exact k nearest neighbours of each query among its own
+ * candidate ids (e.g. another index's top-k'), by Algorithm 1 with B = 1:
+ * the first k candidates' exact distances seed the threshold, every other
+ * candidate is refined level by level and abandoned at the first level
+ * whose margined Eq. 3 lower bound exceeds the running k-th distance; the
+ * rest are re-ranked exactly on the original rows.
+ *   idx:       a flat index (panorama_build_flat).
+ *   queries:   device, nq x d FP32 row-major.
+ *   cand_ids:  device, nq x kprime int64; -1 = no candidate; an id may repeat
+ *              (kept once).
+ *   k:         1..1024.  epsilon: Eq. 4 (0 or 1 = exact; as search).
+ *   out_ids / out_dists: device, nq x k, ascending (distance, id), padded
+ *              with (-1, +inf) when a query has fewer than k distinct ids.
+ *   Statistics of the call (pairs = candidates, dims_scanned, reranked) are
+ *   read with panorama_search_stats.  Blocks until the results are written.
+ * Errors: PANO_EINVAL (not a flat index, sizes, an id outside [-1, n)),
+ *         PANO_ENOMEM, PANO_ECUDA, PANO_ENODEV. */
+int panorama_refine(const pano_index* idx, const float* queries, int64_t nq,
+                    const int64_t* cand_ids, int32_t kprime, int32_t k, int64_t* out_ids,
+                    float* out_dists, float epsilon, void* stream);
+
 /* panorama_probe -- the coarse step alone: the nprobe nearest lists of each
  * query by (original-space squared distance, list id) [Section 6.1].
  *   queries: device nq x d; out_lists: device nq x nprobe int32, ascending. */

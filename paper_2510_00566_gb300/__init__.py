@@ -15,7 +15,8 @@ from typing import Optional
 __all__ = ["lib", "LibraryError", "Transform", "Index", "SearchStats",
            "panorama_fit_transform", "panorama_build_ivf", "panorama_search",
            "panorama_search_ex", "panorama_probe", "panorama_save",
-           "panorama_load", "PANO_FP32", "PANO_BF16", "PANO_FP8",
+           "panorama_load", "panorama_build_flat", "panorama_refine",
+           "PANO_FP32", "PANO_BF16", "PANO_FP8",
            "library_path"]
 
 PANO_FP32, PANO_BF16, PANO_FP8 = 0, 1, 2
@@ -116,6 +117,9 @@ SIGNATURES = {
     "panorama_free_index": (None, [_P]),
     "panorama_last_error": (ctypes.c_char_p, []),
     "panorama_version": (ctypes.c_char_p, []),
+    "panorama_build_flat": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P]),
+    "panorama_refine": (ctypes.c_int, [_P, _P, _I64, _P, _I32, _I32, _P, _P, ctypes.c_float,
+                                       _P]),
     "panorama_debug_tc_gemm": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _P]),
     "panorama_debug_tc_gemm_fp8": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _P]),
     "panorama_plan_create": (ctypes.c_int, [_P, _P, _I64, _P, _I32, _P, _I32, _I32,
@@ -168,7 +172,8 @@ def _host_f32(a):
     import torch
     if isinstance(a, torch.Tensor):
         if a.is_cuda:
-            return a.contiguous(), a.contiguous().data_ptr()
+            keep = a.contiguous()
+            return keep, keep.data_ptr()
         a = a.numpy()
     a = np.ascontiguousarray(a, dtype=np.float32)
     return a, a.ctypes.data
@@ -278,6 +283,39 @@ def panorama_probe(idx: "Index", queries, nprobe: int, stream=None):
 
 def panorama_save(idx: "Index", path: str):
     _check(lib().panorama_save(idx.handle, path.encode()))
+
+
+def panorama_build_flat(t: "Transform", X, n_levels=8, level_widths=None, stream=None):
+    """Flat index for refining candidate-id lists (B = 1); see
+    panorama_build_flat.  Vector i gets id i."""
+    keep, ptr = _host_f32(X)
+    n, d = keep.shape
+    widths = None
+    if level_widths is not None:
+        widths = (ctypes.c_int32 * len(level_widths))(*level_widths)
+        n_levels = len(level_widths)
+    opts = BuildOpts(n_levels=n_levels, level_widths=widths, precision=PANO_FP32)
+    out = ctypes.c_void_p()
+    _check(lib().panorama_build_flat(t.handle, ptr, n, ctypes.byref(opts),
+                                     _stream_ptr(stream), ctypes.byref(out)))
+    return Index(out.value)
+
+
+def panorama_refine(index: "Index", queries, cand_ids, k: int, epsilon=1.0, stream=None):
+    """Exact top-k of each query among its candidate ids (CUDA tensors:
+    queries nq x d float32, cand_ids nq x k' int64 with -1 = none) on a flat
+    index; returns (ids int64 nq x k, dists float32 nq x k)."""
+    import torch
+    q = queries.contiguous()
+    c = cand_ids.to(torch.int64).contiguous()
+    nq = q.shape[0]
+    kp = c.shape[1] if c.dim() == 2 else 0
+    ids = torch.empty((nq, k), dtype=torch.int64, device=q.device)
+    dists = torch.empty((nq, k), dtype=torch.float32, device=q.device)
+    _check(lib().panorama_refine(index.handle, q.data_ptr(), nq, c.data_ptr() if kp else None,
+                                 kp, k, ids.data_ptr(), dists.data_ptr(), float(epsilon),
+                                 _stream_ptr(stream)))
+    return ids, dists
 
 
 def panorama_load(path: str) -> "Index":
@@ -509,6 +547,9 @@ class Index:
 
     def search(self, queries, nprobe, k, k_max=None, **kw):
         return panorama_search_ex(self, queries, nprobe, k, k_max, **kw)
+
+    def refine(self, queries, cand_ids, k, epsilon=1.0, stream=None):
+        return panorama_refine(self, queries, cand_ids, k, epsilon=epsilon, stream=stream)
 
     def free(self):
         if getattr(self, "handle", None) and _lib is not None:

@@ -204,6 +204,20 @@ int panorama_search_ex(const pano_index* idx, const float* queries, int64_t nq,
                 (cudaStream_t)stream, opts);
 }
 
+int panorama_build_flat(const pano_transform* t, const float* X, int64_t n,
+                        const pano_build_opts* opts, void* stream, pano_index** out) {
+  clear_error();
+  return build_flat(t, X, n, opts, (cudaStream_t)stream, out);
+}
+
+int panorama_refine(const pano_index* idx, const float* queries, int64_t nq,
+                    const int64_t* cand_ids, int32_t kprime, int32_t k, int64_t* out_ids,
+                    float* out_dists, float epsilon, void* stream) {
+  clear_error();
+  return refine(idx, queries, nq, cand_ids, kprime, k, out_ids, out_dists, epsilon,
+                (cudaStream_t)stream);
+}
+
 int panorama_search_stats(pano_search_stats* out) {
   PANO_CHECK(out, PANO_EINVAL, "null stats");
   *out = last_stats();
@@ -329,9 +343,11 @@ int panorama_load(const char* path, pano_index** out) {
                     I.nlist <= I.n && I.L >= 1 && I.L <= 64 &&
                     ((I.precision == PANO_FP32 && I.chunk == 64) ||
                      ((I.precision == PANO_BF16 || I.precision == PANO_FP8) &&
-                      I.chunk == 128)) &&
+                      I.chunk == 128) ||
+                     (I.precision == PANO_FP32 && I.chunk == 1 && I.nlist == 1)) &&
                     I.n_chunks >= 0 && I.n_chunks <= I.n + I.nlist;
   PANO_CHECK(sane, PANO_ECORRUPT, "header fields out of range");
+  I.flat = I.chunk == 1 ? 1 : 0;  // a flat (refine) index: one row per "chunk"
   const uint64_t d = I.d, n = I.n, nl = I.nlist;
   r.vec(I.widths, 64);
   r.vec(I.offs, 65);

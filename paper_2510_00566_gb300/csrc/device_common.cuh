@@ -131,7 +131,7 @@ __device__ __forceinline__ void topk_insert_thread(unsigned long long* slots, in
   }
   for (int j = start; j < k; ++j) {
     unsigned long long old = atomicMin(slots + j, key);
-    if (old == kEmptyKey) return;
+    if (old == kEmptyKey || old == key) return;  // an equal key is the same pair: kept once
     key = old > key ? old : key;
   }
 }

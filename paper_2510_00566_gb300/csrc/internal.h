@@ -78,6 +78,10 @@ struct pano_index {
   int64_t n = 0;
   int32_t d = 0, nlist = 0, L = 0, precision = 0, chunk = 64;
   int32_t max_w = 0;
+  // 1: flat row-major index for refining candidate-id lists (B = 1): slices
+  // holds the x~ rows [n][d] FP32, tails [n][L+1], xn2 / ex [n], rows [n][d]
+  // the original rows; the id of a vector is its row.  0: IVF, level-major.
+  int32_t flat = 0;
   std::vector<int32_t> widths, offs;  // offs[l] = m_l, l = 0..L
   int64_t n_chunks = 0;
   double eta = 0.0;     // orthogonality defect of T~
@@ -112,6 +116,7 @@ struct pano_index {
   int64_t fp32_chunk_rows() const { return (int64_t)d + L + 3; }
   int32_t fp32_row_off(int l) const { return l == 0 ? 0 : offs[l] + l + 3; }
   size_t slices_bytes() const {
+    if (flat) return (size_t)n * d * 4;
     return precision == PANO_FP32  ? (size_t)n_chunks * chunk * fp32_chunk_rows() * 4
            : precision == PANO_BF16 ? (size_t)n_chunks * chunk * d * 2
                                     : (size_t)n_chunks * chunk * d;

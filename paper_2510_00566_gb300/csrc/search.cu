@@ -1319,6 +1319,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
            void* ext_ws, size_t ext_cap) {
   PANO_CHECK(ip, PANO_EINVAL, "null index");
   const pano_index& I = *ip;
+  PANO_CHECK(!I.flat, PANO_EINVAL, "a flat index is searched with panorama_refine");
   PANO_CHECK(nq >= 0 && nq < (1LL << 31), PANO_EINVAL, "nq out of range");
   PANO_CHECK(nq == 0 || (queries && out_ids && out_dists), PANO_EINVAL, "null argument");
   PANO_CHECK(k_max >= 1 && k_max <= 1024, PANO_EINVAL, "k_max must be in [1, 1024]");
@@ -1699,5 +1700,24 @@ int probe_only(const pano_index* ip, const float* queries, int64_t nq, int32_t n
 }
 
 const pano_search_stats& last_stats() { return t_stats; }
+pano_search_stats& stats_slot() { return t_stats; }
+
+// a1 for callers outside the IVF search (the refine path): q~ = T~(q - mu~),
+// then norms, rounded-up tails and e_q (query_norms_kernel).
+int transform_queries(const pano_index& I, const float* queries, int64_t nq, float* qt,
+                      float4* qinfo, float* qtail, float* qn2, cudaStream_t st) {
+  const int d = I.d, L = I.L;
+  if (nq == 0) return PANO_OK;
+  PANO_CUDA(gemm_nt(kStore, (int)nq, d, d, queries, d, I.mu32.as<float>(), I.T32.as<float>(), d,
+                    qt, d, nullptr, nullptr, st));
+  float c_trans_up = (float)I.c_trans;
+  if ((double)c_trans_up < I.c_trans) c_trans_up = std::nextafter(c_trans_up, INFINITY);
+  query_norms_kernel<<<(unsigned)((nq + kNormRows - 1) / kNormRows), kNormRows * 32,
+                       d <= kNormMaxD ? (size_t)kNormRows * d * 4 : 0, st>>>(
+      queries, qt, nq, d, L, I.level_off_d.as<int32_t>(), I.mu32.as<float>(), c_trans_up, qinfo,
+      qtail, qn2);
+  PANO_CUDA(cudaGetLastError());
+  return PANO_OK;
+}
 
 }  // namespace pano

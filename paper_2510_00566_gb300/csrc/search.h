@@ -12,6 +12,14 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
 int probe_only(const pano_index* ip, const float* queries, int64_t nq, int32_t nprobe,
                int32_t* out, cudaStream_t st);
 const pano_search_stats& last_stats();
+pano_search_stats& stats_slot();  // the calling thread's last-call statistics
+int transform_queries(const pano_index& I, const float* queries, int64_t nq, float* qt,
+                      float4* qinfo, float* qtail, float* qn2, cudaStream_t st);
+int build_flat(const pano_transform* t, const float* X, int64_t n, const pano_build_opts* o,
+               cudaStream_t st, pano_index** out);
+int refine(const pano_index* ip, const float* queries, int64_t nq, const int64_t* cand,
+           int32_t kprime, int32_t k, int64_t* out_ids, float* out_dists, float epsilon,
+           cudaStream_t st);
 int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
               const pano_build_opts* o, cudaStream_t st, pano_index** out);
 int make_levels(int d, const pano_build_opts* o, std::vector<int32_t>& widths,
