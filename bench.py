@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-bf16", action="store_true",
                    help="skip the BF16-storage run on FP32 workloads")
+    p.add_argument("--no-refine", action="store_true",
+                   help="skip the candidate-list refine run on FP32 IVF workloads")
     p.add_argument("--no-fp8", action="store_true",
                    help="skip the FP8-storage run on FP32 and BF16 workloads")
     p.add_argument("--no-serve", action="store_true",
@@ -449,6 +451,39 @@ def main():
         del idxq
         return out
 
+    # the refine workload (point-centric, B = 1): each query's top-1000 of the
+    # pruned IVF search as its candidate-id list, refined to the top-k on a
+    # flat index of the same data and levels
+    refine = None
+    if s.precision == "fp32" and not args.no_refine and s.nlist > 1 and s.d % s.n_levels == 0:
+        kprime = 1000
+        cand, _ = idx.search(Q, npa, kprime, k_max=kprime)
+        flat = pano.panorama_build_flat(t, X, level_widths=[s.d // s.n_levels] * s.n_levels)
+        for _ in range(args.warmup):
+            flat.refine(Q, cand, k)
+        torch.cuda.synchronize()
+        totr = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            flat.refine(Q, cand, k)
+            e1.record(stream)
+            e1.synchronize()
+            totr += e0.elapsed_time(e1)
+        tr = torch.tensor([totr], device=dev)
+        if world > 1:
+            dist.all_reduce(tr, op=dist.ReduceOp.MAX)
+        msr = tr.item() / args.steps
+        str_ = pano.last_stats().as_dict()
+        refine = {"kprime": kprime, "k": k, "ms_per_step": msr,
+                  "value": nq * kprime * world / (msr / 1e3), "unit": "candidates/s",
+                  "qps": nq * world / (msr / 1e3),
+                  "dims_scanned_frac": str_["dims_scanned"] / max(1, str_["pairs"] * s.d),
+                  "reranked": str_["reranked"]}
+        del flat, cand
+
     bf16 = fp8 = None
     if s.precision == "fp32" and not args.no_bf16 and s.d % 64 == 0:
         bf16 = quantised_run(pano.PANO_BF16)
@@ -512,6 +547,7 @@ def main():
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": nq * k * 12},
             "bf16_pruned": bf16,
             "fp8_pruned": fp8,
+            "refine": refine,
             "autotune": tune,
             "serving": serving,
             "gpu_launches": (KERNELS_PER_SEARCH if s.nlist > 1 else KERNELS_PER_SEARCH - 2)
