@@ -630,10 +630,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     section(0);
     for (int l = 0; l < L; ++l) {
       const int w = a.level_off[l + 1] - a.level_off[l];
-      // the bound is tested at levels 0 and 1, then every other level, and at
-      // the last: a test costs the epilogue ~4x an untested level, while a
-      // pair it misses is caught one level later
-      const bool test = l == L - 1 || (a.prune && (l < 2 || (l & 1)));
+      const bool test = a.prune || l == L - 1;
       const bool has_next = l + 1 < L;
       uint32_t live_mask = 0;
       for (int c = 0; c < nch; ++c)
