@@ -56,6 +56,9 @@ class Spec:
     k: int | tuple = 10           # int, or tuple of values drawn uniformly
     n_levels: int = 8
     precision: str = "fp32"       # "fp32", "bf16" or "fp8"
+    query_decay: Optional[float] = None  # queries' own eigen-decay (out of
+                                         # distribution, same total energy);
+                                         # None = decay
 
     @property
     def level_width(self) -> int:
@@ -200,7 +203,12 @@ def generate(s: Spec, device="cpu", block: int = 1 << 18,
         qlabels = torch.multinomial(weights.to(torch.float32).to(device),
                                     s.n_queries, replacement=True,
                                     generator=gq)
-    Qm = _draw(s.n_queries, qlabels, O32, sd32, C32, gq, device, block)
+    sdq32 = sd32
+    if s.query_decay is not None:  # same basis and total energy, another decay
+        lam_q = torch.exp(-s.query_decay * torch.arange(s.d, dtype=torch.float64))
+        lam_q *= lam.sum() / lam_q.sum()
+        sdq32 = lam_q.sqrt().to(torch.float32).to(device)
+    Qm = _draw(s.n_queries, qlabels, O32, sdq32, C32, gq, device, block)
 
     gp = torch.Generator().manual_seed(4000 + s.cfg)
     if isinstance(s.nprobe, tuple):

@@ -1,0 +1,84 @@
+"""Out-of-distribution queries (Proposition 5.2): queries whose tail energy
+decays at a rate alpha_q other than the database's alpha_x (same basis, same
+total energy, so only the compaction changes).  The model puts the cost at
+2 / (alpha_q + alpha_x) of the in-distribution one's 1 / alpha_x, i.e. the
+ratio R = 2 alpha_x / (alpha_q + alpha_x).  On finite d and levels the
+measured ratio r = frac(alpha_q) / frac(alpha_x) moves in the model's
+direction by at most its factor: r lies between 1 and R (the first level is
+always read and near neighbours are read in full, which damps the effect).
+
+The CPU test pins the oracle's Algorithm 1 to that behaviour; the GPU test
+checks that the GPU path reads about as many coordinates as the oracle on
+the same out-of-distribution queries."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+D, BETA_X = 128, 0.05          # alpha_x = BETA_X * D = 6.4
+BETAS_Q = (0.0125, 0.05, 0.2)  # alpha_q = 1.6, 6.4, 25.6
+WIDTHS = [16] * 8
+
+
+def _oracle_frac(s, X, Q, T, mu):
+    m = oracle.level_thresholds(D, WIDTHS)
+    tX = oracle.transform(T, mu, X)
+    tQ = oracle.transform(T, mu, Q)
+    ids = np.arange(len(X))
+    return float(np.mean([oracle.refine(tQ[i], tX, ids, m, 10, B=1024)[2].mean() / D
+                          for i in range(len(Q))]))
+
+
+def _workload(beta_q, n_queries=20):
+    s = synth.scaled(1, n=3000, n_queries=n_queries, nlist=1, query_decay=beta_q)
+    return s, synth.generate(s)
+
+
+def test_ood_cost_follows_the_arithmetic_mean_rate():
+    fr = {}
+    mu = T = None
+    for bq in BETAS_Q:
+        s, w = _workload(bq)
+        X, Q = w.X.numpy(), w.Q.numpy()
+        if T is None:
+            mu, T, _ = oracle.pca_fit(X)  # the database is the same for every beta_q
+        fr[bq] = _oracle_frac(s, X, Q, T, mu)
+    assert fr[BETAS_Q[0]] > fr[BETAS_Q[1]] > fr[BETAS_Q[2]], fr
+    ax = BETA_X * D
+    for bq in (BETAS_Q[0], BETAS_Q[2]):
+        R = 2 * ax / (bq * D + ax)
+        r = fr[bq] / fr[BETA_X]
+        assert min(1.0, R) - 0.02 <= r <= max(1.0, R) + 0.02, (bq, r, R)
+
+
+def test_query_decay_changes_only_the_queries():
+    s0, w0 = _workload(None)
+    s1, w1 = _workload(0.2)
+    assert torch.equal(w0.X, w1.X)
+    e0 = (w0.Q.double() ** 2).sum(1).mean()
+    e1 = (w1.Q.double() ** 2).sum(1).mean()
+    assert abs(float(e1 / e0) - 1.0) < 0.15  # same total energy (sampling noise)
+
+
+@pytest.mark.gpu
+def test_gpu_reads_what_the_oracle_reads_on_ood_queries():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2510_00566_gb300 as pano
+    from paper_2510_00566_gb300 import _build
+    _build.build()
+    s, w = _workload(BETAS_Q[0])
+    X = w.X.numpy()
+    mu, T, _ = oracle.pca_fit(X)
+    t = pano.panorama_fit_transform(X, n_levels=len(WIDTHS))
+    idx = pano.panorama_build_ivf(t, w.X.to("cuda:0"), nlist=1, level_widths=WIDTHS)
+    for bq in BETAS_Q:
+        s, w = _workload(bq)
+        Q = w.Q.numpy()
+        idx.search(w.Q.to("cuda:0"), 1, 10, collect_stats=True)
+        st = pano.last_stats()
+        gpu = st.dims_scanned / (st.pairs * D)
+        ref = _oracle_frac(s, X, Q, T, mu)
+        assert gpu <= 1.2 * ref + 0.03, (bq, gpu, ref)
