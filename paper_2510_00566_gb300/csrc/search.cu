@@ -367,11 +367,11 @@ constexpr int kSeedWarps = 8;
 __global__ void __launch_bounds__(kSeedWarps * 32) seed_tau_kernel(
     const float* __restrict__ q, int d, const int32_t* __restrict__ probes, int stride,
     const int64_t* __restrict__ chunk_off, const int32_t* __restrict__ list_size, int chunk,
-    const float* __restrict__ rows, const int32_t* __restrict__ kq, float slack,
-    float* __restrict__ tau_seed) {
+    const float* __restrict__ rows, const int32_t* __restrict__ kq,
+    const int32_t* __restrict__ order, float slack, float* __restrict__ tau_seed) {
   extern __shared__ float4 qs4[];  // the query row (d floats)
   __shared__ float dist[kSeedMax];
-  const int64_t row = blockIdx.x;
+  const int64_t row = order ? order[blockIdx.x] : blockIdx.x;
   const int k = kq[row];
   const int c = probes[row * stride];
   const int n = c >= 0 ? list_size[c] : 0;
@@ -443,6 +443,108 @@ __global__ void __launch_bounds__(kSeedWarps * 32) seed_tau_kernel(
   if (warp == 0) {
     const float t = warp_kth_smallest(dist, ns, k);
     if (lane == 0) tau_seed[row] = t;
+  }
+}
+
+// The same seeds for up to 16 queries of one phase-A work item at once
+// (two-phase searches, d <= 1024, d % 4 == 0): the queries sit in shared
+// memory and each warp reads one of the list's first rows into registers
+// (8 float4 per lane) and computes its distances to all of them, so a list's
+// rows are read once per 16 queries instead of once per query.  Per query
+// and row, each lane sums fl(q_j - x_j)^2 by FMA over its (at most 32) dims
+// into four interleaved sums, then the warp adds the lanes' sums: each term
+// meets at most m = ceil(d/128) + 8 roundings, as in seed_tau_kernel, whose
+// slack is reused.  CTA b takes sub-group b % nsub of item b / nsub; only
+// an item's first segment computes (the queries of a group are the same in
+// every segment).
+constexpr int kSeedSub = 16;
+
+__global__ void __launch_bounds__(kSeedWarps * 32) seed_group_kernel(
+    const float* __restrict__ q, int d, const int4* __restrict__ items,
+    const int* __restrict__ n_items, int64_t items_cap, int nsub,
+    const int32_t* __restrict__ bucket, const int64_t* __restrict__ chunk_off,
+    const int32_t* __restrict__ list_size, int chunk, const float* __restrict__ rows,
+    const int32_t* __restrict__ kq, float slack, float* __restrict__ tau_seed) {
+  extern __shared__ float4 sg_raw[];
+  const int64_t item = blockIdx.x / nsub;
+  const int sub = blockIdx.x % nsub;
+  if (item >= imin64(*n_items, items_cap)) return;
+  const int4 it = items[item];
+  if (it.y != 0) return;
+  const int g0 = sub * kSeedSub, G = min(kSeedSub, it.w - g0);
+  if (G <= 0) return;
+  const int c = it.x, n = list_size[c];
+  const int d4 = d >> 2;
+  float4* qs = sg_raw;                                                // [G][d/4]
+  float* dist = reinterpret_cast<float*>(sg_raw + (size_t)kSeedSub * d4);  // [G][kSeedMax]
+  __shared__ int s_q[kSeedSub], s_k[kSeedSub], s_ns[kSeedSub];
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
+  if (tid < G) {
+    const int qi = bucket[it.z + g0 + tid];
+    const int k = kq[qi];
+    s_q[tid] = qi;
+    s_k[tid] = k;
+    s_ns[tid] = min(n, min(kSeedMax, max(4 * k, 64)));
+  }
+  __syncthreads();
+  int nsmax = 0;
+  for (int g = 0; g < G; ++g) nsmax = max(nsmax, s_ns[g]);
+  for (int e = tid; e < G * d4; e += kSeedWarps * 32) {
+    const int g = e / d4, j = e % d4;
+    qs[e] = reinterpret_cast<const float4*>(q + (int64_t)s_q[g] * d)[j];
+  }
+  __syncthreads();
+  const int64_t base = chunk_off[c] * chunk;  // a list's members are its first slots
+  // two rows per warp in registers: each query float4 read from shared
+  // memory serves both (the loop is bound by those reads)
+  for (int r0 = 2 * warp; r0 < nsmax; r0 += 2 * kSeedWarps) {
+    float4 xv[2][8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float4* x4 = reinterpret_cast<const float4*>(rows + (base + r0 + h) * d);
+      const bool ok = r0 + h < nsmax;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = lane + 32 * u;
+        xv[h][u] = ok && j < d4 ? x4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    for (int g = 0; g < G; ++g) {
+      float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = lane + 32 * u;
+        if (j < d4) {
+          const float4 qv = qs[g * d4 + j];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float t;
+            t = qv.x - xv[h][u].x;
+            acc[h][0] = fmaf(t, t, acc[h][0]);
+            t = qv.y - xv[h][u].y;
+            acc[h][1] = fmaf(t, t, acc[h][1]);
+            t = qv.z - xv[h][u].z;
+            acc[h][2] = fmaf(t, t, acc[h][2]);
+            t = qv.w - xv[h][u].w;
+            acc[h][3] = fmaf(t, t, acc[h][3]);
+          }
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float sum = (acc[h][0] + acc[h][1]) + (acc[h][2] + acc[h][3]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+        if (lane == 0 && r0 + h < s_ns[g])
+          dist[g * kSeedMax + r0 + h] = __fadd_ru(__fmul_ru(sum, slack), 0x1p-126f);
+      }
+    }
+  }
+  __syncthreads();
+  for (int g = warp; g < G; g += kSeedWarps) {
+    const int k = s_k[g], ns = s_ns[g];
+    const float t = (k <= 0) ? -1.f : (ns < k ? INFINITY : warp_kth_smallest(dist + g * kSeedMax, ns, k));
+    if (lane == 0) tau_seed[s_q[g]] = t;
   }
 }
 
@@ -1461,14 +1563,6 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     }
     // a3 (and the Alg. 1 warm start of the threshold)
     mark(2);
-    const double seed_m = (d + 127) / 128 + 8;
-    const double seed_sl = 1.0 + 2.0 * (seed_m + 3.0) * kU32;
-    float seed_slack = (float)seed_sl;
-    if ((double)seed_slack < seed_sl) seed_slack = std::nextafter(seed_slack, INFINITY);
-    seed_tau_kernel<<<(unsigned)nq, kSeedWarps * 32, (size_t)d * 4, st>>>(
-        queries, d, probes, stride, I.chunk_off_d.as<int64_t>(), I.list_size_d.as<int32_t>(),
-        I.chunk, I.rows.as<float>(), kq, seed_slack, tau_seed);
-    PANO_CUDA(cudaGetLastError());
     const int64_t ne = nq * stride;
     // Phase A (each query's nearest list, verified first for a tight
     // threshold) pays off unless its query groups are nearly empty: on the
@@ -1488,6 +1582,27 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
                                           boff, ioff, tot, capA, itA, err);
     inv_emit_kernel<<<1024, 256, 0, st>>>(1, cnt, nlist, I.chunk_off_d.as<int64_t>(), SEG, QBB,
                                           boff, ioff, tot, capB, itB, err);
+    PANO_CUDA(cudaGetLastError());
+    // the warm-start seeds, in phase A's order when there is a phase A (its
+    // bucket lists every query once, grouped by nearest list, so the CTAs
+    // that read one list's first rows run together and share them in L2)
+    const double seed_m = (d + 127) / 128 + 8;
+    const double seed_sl = 1.0 + 2.0 * (seed_m + 3.0) * kU32;
+    float seed_slack = (float)seed_sl;
+    if ((double)seed_slack < seed_sl) seed_slack = std::nextafter(seed_slack, INFINITY);
+    if (!one_pass && d <= 1024 && (d & 3) == 0 &&
+        (reinterpret_cast<uintptr_t>(queries) & 15) == 0) {
+      const int nsub = (QBA + kSeedSub - 1) / kSeedSub;
+      const size_t gsm = (size_t)kSeedSub * d * 4 + (size_t)kSeedSub * kSeedMax * 4;
+      PANO_CUDA(allow_dynamic_smem((const void*)seed_group_kernel));
+      seed_group_kernel<<<(unsigned)(capA * nsub), kSeedWarps * 32, gsm, st>>>(
+          queries, d, itA, tot + 1, capA, nsub, bucket, I.chunk_off_d.as<int64_t>(),
+          I.list_size_d.as<int32_t>(), I.chunk, I.rows.as<float>(), kq, seed_slack, tau_seed);
+    } else {
+      seed_tau_kernel<<<(unsigned)nq, kSeedWarps * 32, (size_t)d * 4, st>>>(
+          queries, d, probes, stride, I.chunk_off_d.as<int64_t>(), I.list_size_d.as<int32_t>(),
+          I.chunk, I.rows.as<float>(), kq, one_pass ? nullptr : bucket, seed_slack, tau_seed);
+    }
     PANO_CUDA(cudaGetLastError());
     // a4-a10
     if (tcpath) {
