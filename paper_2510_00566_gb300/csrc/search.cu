@@ -653,7 +653,8 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
   constexpr int TQ = QB / 4;
   constexpr int NW = NTH / 32;
   static_assert(TQ * (CB / 4) == NTH, "4x4 register tile per thread");
-  static_assert(TQ <= 32 && (32 % TQ) == 0, "query blocks of a candidate block share a warp");
+  static_assert(TQ <= 32 && (32 % TQ) == 0 && (TQ < 8 || TQ % 8 == 0),
+                "a warp holds whole query-row groups");
   static_assert(NCH <= 32, "live-chunk mask");
   // the thread that issues bulk copies: a warp with no per-query setup work
   constexpr int ISSUER = 32 * ((QB + 31) / 32 < NW ? (QB + 31) / 32 : NW - 1);
@@ -690,7 +691,13 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
   __shared__ uint32_t s_live[2];
 
   const int tid = threadIdx.x;
-  const int tq = tid % TQ, tc = tid / TQ;
+  // thread -> (tq, tc): a warp holds WQ = min(TQ, 8) query rows x 32 / WQ
+  // candidate blocks, so its float4 query loads touch at most 8 rows (one
+  // 128-byte wavefront with the odd row stride) and its candidate loads
+  // 16 B x 32 / WQ; a warp's candidates (16 or 32) lie in one chunk
+  constexpr int WQ = TQ >= 8 ? 8 : TQ, WC = 32 / WQ, NWQ = TQ / WQ;
+  const int tq = (tid & 31) % WQ + WQ * ((tid >> 5) % NWQ);
+  const int tc = (tid & 31) / WQ + WC * ((tid >> 5) / NWQ);
   const int warp = tid / 32, lane = tid & 31;
   // counters (collect_stats) live in shared memory, off the registers:
   // [0] pair-levels, [1] dims, [2] tile-levels, [3] bytes, [4] reranked
@@ -977,11 +984,9 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
       section(0);
 
       for (int l = 0; l < L; ++l) {
-        // chunks with a live pair (any query of the group)
-        uint32_t cm = alive;
-#pragma unroll
-        for (int off = 1; off < TQ; off <<= 1) cm |= __shfl_xor_sync(0xffffffffu, cm, off);
-        if (tq == 0 && cm) atomicOr(&s_live[l & 1], 1u << my_ch);
+        // chunks with a live pair (a warp's pairs all lie in chunk my_ch)
+        const bool wl = __any_sync(0xffffffffu, alive != 0);
+        if ((tid & 31) == 0 && wl) atomicOr(&s_live[l & 1], 1u << my_ch);
         const int any = __syncthreads_or(alive != 0);
         if (!any) {
           completed = false;
@@ -1017,7 +1022,7 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
           break;
         }
         section(1);
-        if (cm != 0) {
+        if (wl) {
           float acc[4][4];
 #pragma unroll
           for (int ai = 0; ai < 4; ++ai)
