@@ -702,6 +702,10 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
   // counters (collect_stats) live in shared memory, off the registers:
   // [0] pair-levels, [1] dims, [2] tile-levels, [3] bytes, [4] reranked
   __shared__ unsigned long long s_stat[5], s_sec[8];
+  // per warp: its live pairs (lane << 4 | bit) and their level dot products
+  // when few are live (the sparse path of the level loop)
+  __shared__ uint16_t s_pair[NTH / 32][32];
+  __shared__ float s_pdot[NTH / 32][32];
   __shared__ long long s_tmark, s_tkernel;
   if (tid == 0) {
     for (int b = 0; b < NST; ++b) mbar_init(&bar[b], 1);
@@ -1022,13 +1026,55 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
           break;
         }
         section(1);
-        if (wl) {
+        const float* xb = stage_x(cur) + (size_t)my_ch * BR + my_i;  // this thread's candidates
+        const int nalive = wl ? (int)__reduce_add_sync(0xffffffffu, (unsigned)__popc(alive)) : 0;
+        if (wl && l > 0 && nalive <= 32) {
+          // few live pairs in the warp: they are listed in lane order and each
+          // lane computes one pair's level dot product, which its owner adds
+          // (the same sequential sum over the level's dims as the dense path
+          // below, so the partial products are identical)
+          const int lane = tid & 31, wrp = tid >> 5, cnt = __popc(alive);
+          int pre = cnt;
+#pragma unroll
+          for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, pre, off);
+            if (lane >= off) pre += y;
+          }
+          const int base = pre - cnt;
+          uint16_t* slot = s_pair[wrp];
+          float* res = s_pdot[wrp];
+          {
+            uint32_t m = alive;
+            for (int k = base; m; ++k) {
+              slot[k] = (uint16_t)((lane << 4) | (__ffs(m) - 1));
+              m &= m - 1;
+            }
+          }
+          __syncwarp();
+          if (lane < nalive) {
+            const int code = slot[lane], src = code >> 4, bit = code & 15;
+            const int stq = src % WQ + WQ * (wrp % NWQ), stc = src / WQ + WC * (wrp / NWQ);
+            const float* qr = qslice(l) + (size_t)(stq + TQ * (bit >> 2)) * QS;
+            const float* xc =
+                stage_x(cur) + (size_t)((4 * stc) / CH) * BR + (4 * stc) % CH + (bit & 3);
+            float dt = 0.f;
+            for (int j = 0; j < w; ++j) dt = fmaf(qr[j], xc[j * CH], dt);
+            res[lane] = dt;
+          }
+          __syncwarp();
+#pragma unroll
+          for (int ai = 0; ai < 4; ++ai)
+#pragma unroll
+            for (int bi = 0; bi < 4; ++bi) {
+              const int b = 4 * ai + bi;
+              if (alive & (1u << b)) p[ai][bi] += res[base + __popc(alive & ((1u << b) - 1u))];
+            }
+        } else if (wl) {
           float acc[4][4];
 #pragma unroll
           for (int ai = 0; ai < 4; ++ai)
 #pragma unroll
             for (int bi = 0; bi < 4; ++bi) acc[ai][bi] = 0.f;
-          const float* xb = stage_x(cur) + (size_t)my_ch * BR + my_i;
           const float* qb = qslice(l) + tq * QS;
           const int w4 = w & ~3;
 #pragma unroll 2
@@ -1071,6 +1117,8 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
           for (int ai = 0; ai < 4; ++ai)
 #pragma unroll
             for (int bi = 0; bi < 4; ++bi) p[ai][bi] += acc[ai][bi];
+        }
+        if (wl) {
           if (a.collect) {
             const unsigned np = __reduce_add_sync(__activemask(), (unsigned)__popc(alive));
             if ((threadIdx.x & 31) == __ffs(__activemask()) - 1) {
