@@ -929,11 +929,13 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
 
     for (int64_t tile = ch0; tile < ch1; tile += NCH) {
       const int nch = (int)imin64(NCH, ch1 - tile);
+      section(0);
       wait_stage(cur);
       if (__syncthreads_or(failed)) {
         failed = true;
         break;
       }
+      section(1);  // the tile's first stage landed: a staging wait
       // the next tile's first levels go out before this tile's arithmetic
       const bool has_next = tile + NCH < ch1;
       int n0 = -1, n1 = -1;
