@@ -13,6 +13,11 @@ What is here, all in FP64 unless stated:
   (batched iterative refinement), IVF assignment/probing (Section 6.1), the
   energy-compaction diagnostic E(m) and its decay alpha (Section 4.1), and the
   brute-force definition of the answer (Problem 1).
+* ``pq.py`` -- IVFPQ Panorama: spectrum shaping (Section 4.3, Robin Hood
+  inter-level shaping and intra-level Haar isotropisation), product
+  quantisation of IVF residuals, asymmetric distances, the Eq. 3 bounds in
+  partial-distance form and Algorithm 1 over asymmetric distances
+  (Section 6.3).
 * ``topk.c`` -- the brute-force answer of Problem 1 over an IVF candidate set,
   plain C, FP64, one thread per host core; compiled by ``build_native()``.
 
