@@ -58,6 +58,8 @@ def parse():
                    help="skip the candidate-list refine run on FP32 IVF workloads")
     p.add_argument("--no-fp8", action="store_true",
                    help="skip the FP8-storage run on FP32 and BF16 workloads")
+    p.add_argument("--no-pq", action="store_true",
+                   help="skip the IVFPQ line (shaped PCA, M = d/2, levels as the headline)")
     p.add_argument("--no-serve", action="store_true",
                    help="skip the arrival traces of the serving workload")
     p.add_argument("--serve-requests", type=int, default=20000)
@@ -484,6 +486,56 @@ def main():
                   "reranked": str_["reranked"]}
         del flat, cand
 
+    # the IVFPQ workload (Section 6.3): the same data, lists and queries; the
+    # PCA basis shaped for PQ (Section 4.3, kappa = 4, seeded Haar draws),
+    # M = d / 2 subquantisers of 8 bits (2-d subvectors), codebooks and codes
+    # trained by the library; pruned search vs the plain PQ scan
+    ivfpq = None
+    if (s.precision == "fp32" and not args.no_pq and s.nlist > 1 and s.d % s.n_levels == 0
+            and (s.d // 2) % s.n_levels == 0 and isinstance(s.nprobe, int)):
+        import time as _time
+        gd = np.random.default_rng(7000 + s.cfg).standard_normal((2, s.d, s.d))
+        b0 = _time.time()
+        tsh, blocks = pano.panorama_shape_transform(t, s.n_levels, 4.0, gd)
+        idxp = pano.panorama_build_ivfpq(tsh, X, s.nlist, s.d // 2, s.n_levels,
+                                         centroids=idx.centroids(), assign=idx.assignment())
+        build_s = _time.time() - b0
+        del gd
+
+        def pq_timed(mode, steps):
+            for _ in range(args.warmup):
+                idxp.search_pq(Q, s.nprobe, k, mode=mode)
+            torch.cuda.synchronize()
+            tot = 0.0
+            for _ in range(steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                idxp.search_pq(Q, s.nprobe, k, mode=mode)
+                e1.record(stream)
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
+            tp = torch.tensor([tot], device=dev)
+            if world > 1:
+                dist.all_reduce(tp, op=dist.ReduceOp.MAX)
+            return tp.item() / steps
+
+        msp = pq_timed(0, args.steps)
+        msp_scan = pq_timed(1, args.scan_steps)
+        idxp.search_pq(Q, s.nprobe, k, collect_stats=True)
+        stp = pano.last_stats().as_dict()
+        ivfpq = {"M": s.d // 2, "nbits": 8, "levels": f"{s.n_levels}x{s.d // s.n_levels}",
+                 "kappa": 4.0, "robin_hood_blocks": blocks, "ms_per_step": msp,
+                 "value": stp["pairs"] * world / (msp / 1e3), "unit": "candidates/s",
+                 "qps": nq * world / (msp / 1e3),
+                 "plain_pq_scan": {"ms_per_step": msp_scan, "qps": nq * world / (msp_scan / 1e3),
+                                   "speedup_of_pruned": msp_scan / msp},
+                 "dims_scanned_frac": stp["dims_scanned"] / max(1, stp["pairs"] * s.d),
+                 "tables_built": stp["tile_levels"], "pairs": stp["pairs"],
+                 "index_gb": idxp.info().device_bytes / 1e9, "build_s": build_s}
+        del idxp, tsh
+
     bf16 = fp8 = None
     if s.precision == "fp32" and not args.no_bf16 and s.d % 64 == 0:
         bf16 = quantised_run(pano.PANO_BF16)
@@ -548,6 +600,7 @@ def main():
             "bf16_pruned": bf16,
             "fp8_pruned": fp8,
             "refine": refine,
+            "ivfpq": ivfpq,
             "autotune": tune,
             "serving": serving,
             "gpu_launches": (KERNELS_PER_SEARCH if s.nlist > 1 else KERNELS_PER_SEARCH - 2)

@@ -16,10 +16,13 @@ __all__ = ["lib", "LibraryError", "Transform", "Index", "SearchStats",
            "panorama_fit_transform", "panorama_build_ivf", "panorama_search",
            "panorama_search_ex", "panorama_probe", "panorama_save",
            "panorama_load", "panorama_build_flat", "panorama_refine",
-           "PANO_FP32", "PANO_BF16", "PANO_FP8",
+           "PANO_FP32", "PANO_BF16", "PANO_FP8", "PANO_PQ",
+           "panorama_transform_import", "panorama_shape_transform",
+           "panorama_build_ivfpq", "panorama_search_pq", "panorama_pq_export",
+           "panorama_debug_pq_encode",
            "library_path"]
 
-PANO_FP32, PANO_BF16, PANO_FP8 = 0, 1, 2
+PANO_FP32, PANO_BF16, PANO_FP8, PANO_PQ = 0, 1, 2, 3
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT",
            -5: "ECORRUPT", -6: "ENODEV"}
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -91,7 +94,17 @@ class IndexInfo(ctypes.Structure):
                 ("eta", ctypes.c_double)]
 
 
-# name -> (restype, argtypes); the exported C-ABI (include/panorama.h)
+class PQBuildOpts(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int32), ("n_levels", ctypes.c_int32),
+                ("kmeans_iters", ctypes.c_int32), ("pq_iters", ctypes.c_int32),
+                ("kmeans_sample", ctypes.c_int64), ("pq_sample", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("centroids", ctypes.c_void_p),
+                ("assign", ctypes.c_void_p), ("codebooks", ctypes.c_void_p),
+                ("codes", ctypes.c_void_p)]
+
+
+# name -> (restype, argtypes); the exported C-ABI (include/panorama.h,
+# include/panorama_pq.h)
 _P, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
 SIGNATURES = {
     "panorama_partition_lists": (ctypes.c_int, [_P, _I32, _I32, _P]),
@@ -121,6 +134,12 @@ SIGNATURES = {
     "panorama_refine": (ctypes.c_int, [_P, _P, _I64, _P, _I32, _I32, _P, _P, ctypes.c_float,
                                        _P]),
     "panorama_debug_tc_gemm": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _P]),
+    "panorama_transform_import": (ctypes.c_int, [_P, _P, _P, _I32, _P]),
+    "panorama_shape_transform": (ctypes.c_int, [_P, _I32, ctypes.c_double, _P, _P, _P]),
+    "panorama_build_ivfpq": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _P]),
+    "panorama_search_pq": (ctypes.c_int, [_P, _P, _I64, _I32, _I32, _P, _P, _I32, _I32, _P]),
+    "panorama_pq_export": (ctypes.c_int, [_P, _P, _P, _P]),
+    "panorama_debug_pq_encode": (ctypes.c_int, [_P, _I64, _I32, _I32, _P, _P, _P]),
     "panorama_debug_tc_gemm_fp8": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _P]),
     "panorama_plan_create": (ctypes.c_int, [_P, _P, _I64, _P, _I32, _P, _I32, _I32,
                                             _P, _P, _I32, _P]),
@@ -351,6 +370,113 @@ def panorama_debug_tc_gemm_fp8(A, B, stream=None):
     return D
 
 
+# ------------------------------------------------------------------ IVFPQ
+def panorama_transform_import(T, mu, lam) -> "Transform":
+    """A transform from FP64 arrays: T (d x d, orthogonal), mu (d), lam (d
+    expected coordinate variances)."""
+    import numpy as np
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    d = T.shape[0]
+    out = ctypes.c_void_p()
+    _check(lib().panorama_transform_import(T.ctypes.data, mu.ctypes.data, lam.ctypes.data, d,
+                                           ctypes.byref(out)))
+    return Transform(out.value, d)
+
+
+def panorama_shape_transform(t: "Transform", n_levels: int, kappa: float, gauss):
+    """U R T of spectrum shaping; gauss: 2 x d x d standard normal draws
+    (G1, G2).  Returns (shaped Transform, list of (start, size) blocks)."""
+    import numpy as np
+    g = np.ascontiguousarray(gauss, dtype=np.float64)
+    assert g.size == 2 * t.d * t.d
+    blocks = np.full(2 * n_levels, -1, dtype=np.int32)
+    out = ctypes.c_void_p()
+    _check(lib().panorama_shape_transform(t.handle, n_levels, float(kappa), g.ctypes.data,
+                                          blocks.ctypes.data, ctypes.byref(out)))
+    bl = [(int(blocks[2 * i]), int(blocks[2 * i + 1])) for i in range(n_levels)
+          if blocks[2 * i] >= 0]
+    return Transform(out.value, t.d), bl
+
+
+def panorama_build_ivfpq(t: "Transform", X, nlist: int, M: int, n_levels: int,
+                         centroids=None, assign=None, codebooks=None, codes=None,
+                         kmeans_iters=0, pq_iters=0, kmeans_sample=0, pq_sample=0,
+                         seed=1234, stream=None) -> "Index":
+    """IVFPQ index of X (CUDA tensor or host array); optional host arrays:
+    centroids (nlist x d), assign (n int32), codebooks (M x 256 x d/M float32
+    in the basis of t), codes (n x M uint8)."""
+    import numpy as np
+    keep, ptr = _host_f32(X)
+    n = keep.shape[0]
+    o = PQBuildOpts(M=M, n_levels=n_levels, kmeans_iters=kmeans_iters, pq_iters=pq_iters,
+                    kmeans_sample=kmeans_sample, pq_sample=pq_sample, seed=seed)
+    hold = []
+
+    def host(a, dt):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a.cpu().numpy() if hasattr(a, "cpu") else a, dtype=dt)
+        hold.append(a)
+        return a.ctypes.data
+
+    o.centroids = host(centroids, np.float32)
+    o.assign = host(assign, np.int32)
+    o.codebooks = host(codebooks, np.float32)
+    o.codes = host(codes, np.uint8)
+    out = ctypes.c_void_p()
+    _check(lib().panorama_build_ivfpq(t.handle, ptr, n, nlist, ctypes.byref(o),
+                                      _stream_ptr(stream), ctypes.byref(out)))
+    del hold
+    return Index(out.value)
+
+
+def panorama_search_pq(idx: "Index", queries, nprobe: int, k: int, mode=0,
+                       collect_stats=False, stream=None, out=None):
+    """(ids int64 [nq, k], dists float32 [nq, k]) on the GPU; mode 1 = plain
+    scan."""
+    import torch
+    q = queries.contiguous()
+    assert q.is_cuda and q.dtype == torch.float32
+    nq = q.shape[0]
+    if out is None:
+        ids = torch.empty((nq, k), dtype=torch.int64, device=q.device)
+        dists = torch.empty((nq, k), dtype=torch.float32, device=q.device)
+    else:
+        ids, dists = out
+    _check(lib().panorama_search_pq(idx.handle, q.data_ptr(), nq, int(nprobe), int(k),
+                                    ids.data_ptr(), dists.data_ptr(), int(mode),
+                                    1 if collect_stats else 0, _stream_ptr(stream)))
+    return ids, dists
+
+
+def panorama_pq_export(idx: "Index"):
+    """(codebooks M x 256 x d/M float32, codes n x M uint8) host copies."""
+    import numpy as np
+    info = idx.info()
+    M = ctypes.c_int32()
+    _check(lib().panorama_pq_export(idx.handle, None, None, ctypes.byref(M)))
+    cb = np.empty((M.value, 256, info.d // M.value), dtype=np.float32)
+    codes = np.empty((info.n, M.value), dtype=np.uint8)
+    _check(lib().panorama_pq_export(idx.handle, cb.ctypes.data, codes.ctypes.data, None))
+    return cb, codes
+
+
+def panorama_debug_pq_encode(R, codebooks, stream=None):
+    """Codes (n x M uint8 CUDA tensor) of residual rows R (n x d float32 CUDA)
+    by the build's encoder; codebooks M x 256 x d/M float32 CUDA."""
+    import torch
+    R = R.contiguous()
+    cb = codebooks.contiguous()
+    n, d = R.shape
+    M = cb.shape[0]
+    codes = torch.empty((n, M), dtype=torch.uint8, device=R.device)
+    _check(lib().panorama_debug_pq_encode(R.data_ptr(), n, d, M, cb.data_ptr(),
+                                          codes.data_ptr(), _stream_ptr(stream)))
+    return codes
+
+
 class Plan:
     """One search of a fixed batch shape captured into a CUDA graph.
 
@@ -550,6 +676,9 @@ class Index:
 
     def refine(self, queries, cand_ids, k, epsilon=1.0, stream=None):
         return panorama_refine(self, queries, cand_ids, k, epsilon=epsilon, stream=stream)
+
+    def search_pq(self, queries, nprobe, k, **kw):
+        return panorama_search_pq(self, queries, nprobe, k, **kw)
 
     def free(self):
         if getattr(self, "handle", None) and _lib is not None:

@@ -30,7 +30,7 @@ def _nvcc() -> str:
 def _headers():
     return glob.glob(os.path.join(CSRC, "*.h")) + \
         glob.glob(os.path.join(CSRC, "*.cuh")) + \
-        [os.path.join(ROOT, "include", "panorama.h")]
+        glob.glob(os.path.join(ROOT, "include", "*.h"))
 
 
 def sources():

@@ -263,6 +263,7 @@ int panorama_index_assignment(const pano_index* idx, int32_t* out) {
 int panorama_save(const pano_index* idx, const char* path) {
   clear_error();
   PANO_CHECK(idx && path, PANO_EINVAL, "null argument");
+  PANO_CHECK(idx->pq_M == 0, PANO_EINVAL, "an IVFPQ index cannot be saved");
   Writer w;
   w.f.open(path, std::ios::binary | std::ios::trunc);
   PANO_CHECK((bool)w.f, PANO_EINVAL, std::string("cannot open ") + path);

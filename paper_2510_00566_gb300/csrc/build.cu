@@ -358,61 +358,12 @@ int make_levels(int d, const pano_build_opts* o, std::vector<int32_t>& widths,
   return PANO_OK;
 }
 
-int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
-              const pano_build_opts* o, cudaStream_t st, pano_index** out) {
-  PANO_CHECK(t && X && out, PANO_EINVAL, "null argument");
-  const int d = t->d;
-  PANO_CHECK(n >= 1 && nlist >= 1 && nlist <= n, PANO_EINVAL, "need 1 <= nlist <= n");
-  PANO_CHECK(n < ((int64_t)1 << 31) - 1, PANO_EINVAL, "at most 2^31-2 vectors");
-  int precision = o ? o->precision : PANO_FP32;
-  PANO_CHECK(precision == PANO_FP32 || precision == PANO_BF16 || precision == PANO_FP8,
-             PANO_EINVAL, "storage precision must be PANO_FP32, PANO_BF16 or PANO_FP8");
-  PANO_CHECK(d <= 8192, PANO_EINVAL, "dimension must be at most 8192");
-  int dev = 0;
-  int rc = check_device(&dev);
-  if (rc) return rc;
-  auto idx = std::make_unique<pano_index>();
-  pano_index& I = *idx;
-  I.device = dev;
-  I.n = n;
-  I.d = d;
-  I.nlist = nlist;
-  I.precision = precision;
-  const int CHK = precision == PANO_FP32 ? CH : TC_CHUNK;  // vectors per chunk
-  I.chunk = CHK;
-  I.tf = *t;
-  rc = make_levels(d, o, I.widths, I.offs);
-  if (rc) return rc;
-  if (precision == PANO_BF16)
-    for (int w : I.widths)
-      PANO_CHECK(w == 16 || w == 32 || w % 64 == 0, PANO_EINVAL,
-                 "bf16 level widths must be 16, 32 or multiples of 64");
-  if (precision == PANO_FP8)  // the byte layout of bf16 tiles of half the width
-    for (int w : I.widths)
-      PANO_CHECK(w == 32 || w == 64 || w % 128 == 0, PANO_EINVAL,
-                 "fp8 level widths must be 32, 64 or multiples of 128");
-  I.L = (int)I.widths.size();
-  I.max_w = *std::max_element(I.widths.begin(), I.widths.end());
-  I.eta = t->eta;
-  // transform error: blocked FP32 dot products of |T~| rows with |v - mu~|
-  // (||T~||_F <= sqrt(d (1 + eta)) bounds the 2-norm of |T~|) plus the
-  // rounding of the subtraction.
-  double nu = std::sqrt((double)d * (1.0 + t->eta));
-  I.c_trans = t->identity ? 0.0 : (gamma_n(gemm_rounds(d)) * nu + 1.01 * kU32 * (1.0 + t->eta));
-
-  // ---- data on the device
-  const float* Xd = X;
-  Tmp t_x;
-  cudaPointerAttributes pa;
-  if (cudaPointerGetAttributes(&pa, X) != cudaSuccess || pa.type == cudaMemoryTypeHost ||
-      pa.type == cudaMemoryTypeUnregistered) {
-    cudaGetLastError();
-    PANO_CUDA(cudaMalloc(&t_x.p, (size_t)n * d * sizeof(float)));
-    PANO_CUDA(cudaMemcpyAsync(t_x.p, X, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, st));
-    Xd = (const float*)t_x.p;
-  }
-
-  // ---- coarse quantiser
+// Centroids (given, the sample mean for one list, or k-means) and each
+// vector's nearest centroid (IVF, Section 6.1): fills I.centroids, I.cmax,
+// I.cent, I.cent_n2 and I.assign.  Xd: device rows n x d.
+int coarse_lists(const float* Xd, int64_t n, int d, int nlist, const pano_build_opts* o,
+                 cudaStream_t st, pano_index& I) {
+  int rc = PANO_OK;
   if (o && o->centroids) {
     I.centroids.assign(o->centroids, o->centroids + (size_t)nlist * d);
   } else if (nlist == 1) {
@@ -470,6 +421,66 @@ int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
     PANO_CUDA(cudaMemcpyAsync(I.assign.data(), t_asg.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     PANO_CUDA(cudaStreamSynchronize(st));
   }
+  return PANO_OK;
+}
+
+int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
+              const pano_build_opts* o, cudaStream_t st, pano_index** out) {
+  PANO_CHECK(t && X && out, PANO_EINVAL, "null argument");
+  const int d = t->d;
+  PANO_CHECK(n >= 1 && nlist >= 1 && nlist <= n, PANO_EINVAL, "need 1 <= nlist <= n");
+  PANO_CHECK(n < ((int64_t)1 << 31) - 1, PANO_EINVAL, "at most 2^31-2 vectors");
+  int precision = o ? o->precision : PANO_FP32;
+  PANO_CHECK(precision == PANO_FP32 || precision == PANO_BF16 || precision == PANO_FP8,
+             PANO_EINVAL, "storage precision must be PANO_FP32, PANO_BF16 or PANO_FP8");
+  PANO_CHECK(d <= 8192, PANO_EINVAL, "dimension must be at most 8192");
+  int dev = 0;
+  int rc = check_device(&dev);
+  if (rc) return rc;
+  auto idx = std::make_unique<pano_index>();
+  pano_index& I = *idx;
+  I.device = dev;
+  I.n = n;
+  I.d = d;
+  I.nlist = nlist;
+  I.precision = precision;
+  const int CHK = precision == PANO_FP32 ? CH : TC_CHUNK;  // vectors per chunk
+  I.chunk = CHK;
+  I.tf = *t;
+  rc = make_levels(d, o, I.widths, I.offs);
+  if (rc) return rc;
+  if (precision == PANO_BF16)
+    for (int w : I.widths)
+      PANO_CHECK(w == 16 || w == 32 || w % 64 == 0, PANO_EINVAL,
+                 "bf16 level widths must be 16, 32 or multiples of 64");
+  if (precision == PANO_FP8)  // the byte layout of bf16 tiles of half the width
+    for (int w : I.widths)
+      PANO_CHECK(w == 32 || w == 64 || w % 128 == 0, PANO_EINVAL,
+                 "fp8 level widths must be 32, 64 or multiples of 128");
+  I.L = (int)I.widths.size();
+  I.max_w = *std::max_element(I.widths.begin(), I.widths.end());
+  I.eta = t->eta;
+  // transform error: blocked FP32 dot products of |T~| rows with |v - mu~|
+  // (||T~||_F <= sqrt(d (1 + eta)) bounds the 2-norm of |T~|) plus the
+  // rounding of the subtraction.
+  double nu = std::sqrt((double)d * (1.0 + t->eta));
+  I.c_trans = t->identity ? 0.0 : (gamma_n(gemm_rounds(d)) * nu + 1.01 * kU32 * (1.0 + t->eta));
+
+  // ---- data on the device
+  const float* Xd = X;
+  Tmp t_x;
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, X) != cudaSuccess || pa.type == cudaMemoryTypeHost ||
+      pa.type == cudaMemoryTypeUnregistered) {
+    cudaGetLastError();
+    PANO_CUDA(cudaMalloc(&t_x.p, (size_t)n * d * sizeof(float)));
+    PANO_CUDA(cudaMemcpyAsync(t_x.p, X, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, st));
+    Xd = (const float*)t_x.p;
+  }
+
+  // ---- coarse quantiser and assignment
+  rc = coarse_lists(Xd, n, d, nlist, o, st, I);
+  if (rc) return rc;
 
   // ---- list layout (host)
   I.list_size.assign(nlist, 0);
@@ -551,5 +562,6 @@ int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
 size_t pano_index::device_bytes() const {
   return T32.bytes + mu32.bytes + cent.bytes + cent_n2.bytes + chunk_off_d.bytes +
          list_size_d.bytes + level_off_d.bytes + slices.bytes + tails.bytes + xn2.bytes +
-         ex.bytes + ids.bytes + rows.bytes + xscale.bytes;
+         ex.bytes + ids.bytes + rows.bytes + xscale.bytes + pq_codes.bytes + pq_codebook.bytes +
+         pq_cent_t.bytes;
 }

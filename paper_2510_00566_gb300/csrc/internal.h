@@ -110,6 +110,11 @@ struct pano_index {
   pano::DevBuf ids;      // [chunk][CH] int32 original id, -1 = padding
   pano::DevBuf xscale;   // FP8: [chunk][CH] power-of-two scale s_x of each vector
   pano::DevBuf rows;     // [chunk * CH][d] original FP32 rows (re-ranking)
+  // IVFPQ (precision PANO_PQ, chunk = 256): codes [block][M][256] u8, tails
+  // [block][L][256] (in `tails`), ids [block][256] (in `ids`), the codebooks
+  // [M][256][dsub] and the transformed centroids [nlist][d]
+  int32_t pq_M = 0, pq_dsub = 0;
+  pano::DevBuf pq_codes, pq_codebook, pq_cent_t;
   size_t device_bytes() const;
   // FP32 slice layout: rows (of 64 floats) per chunk, and the first row of
   // level l's block within a chunk
@@ -117,6 +122,7 @@ struct pano_index {
   int32_t fp32_row_off(int l) const { return l == 0 ? 0 : offs[l] + l + 3; }
   size_t slices_bytes() const {
     if (flat) return (size_t)n * d * 4;
+    if (pq_M) return 0;
     return precision == PANO_FP32  ? (size_t)n_chunks * chunk * fp32_chunk_rows() * 4
            : precision == PANO_BF16 ? (size_t)n_chunks * chunk * d * 2
                                     : (size_t)n_chunks * chunk * d;

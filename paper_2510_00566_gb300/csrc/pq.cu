@@ -1,0 +1,1112 @@
+// IVFPQ Panorama: spectrum shaping (Section 4.3), the IVFPQ build and the
+// level-wise bounded asymmetric-distance search (Section 6.3).
+//
+// Search: one thread block per (query, probed list) pair.  The block forms
+// the query residual r = q~ - c~ in shared memory, its level tail energies in
+// FP64, and walks the list in slabs of PQ_S candidates, level by level.  A
+// level's subvector terms e_m = ||r_m - C_m[code_m]||^2 come from a table of
+// the 256 terms of each of the level's subquantisers, built in shared memory
+// while many candidates are live (the paper's per-level look-up tables), and
+// straight from the codebook once few are (the same arithmetic, so the same
+// values).  The codes of one level of a block of 256 vectors are M / L rows
+// of 256 bytes (subquantiser-major), so the live candidates of a warp read
+// neighbouring bytes of one row per subquantiser.  Survivors are compacted
+// with warp ballots into the next level's list.  The query's top-k is a
+// sorted array of (distance, id) keys shared by all of its pairs; its k-th
+// key is the pruning threshold (Algorithm 1's running k-th distance), seeded
+// before the scan with the first members of the query's nearest list.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/panorama_pq.h"
+#include "device_common.cuh"
+#include "gemm.h"
+#include "internal.h"
+#include "search.h"
+
+namespace pano {
+namespace {
+
+constexpr int PQ_KSUB = 256;     // codewords per subquantiser (8-bit codes)
+constexpr int PQ_B = 256;        // vector slots per layout block
+constexpr int PQ_S = 2048;       // candidates per slab of one (query, list) pair
+constexpr int PQ_NT = 256;       // threads of the verify kernel
+constexpr int PQ_MAXML = 64;     // subquantisers per level
+constexpr int PQ_MAXDSUB = 32;   // coordinates per subvector
+constexpr int PQ_LUT_MIN = 384;  // live candidates from which a level's table is built
+constexpr int PQ_SEED = 64;      // nearest-list members that seed each query's top-k
+constexpr int PQ_MAXL = 64;
+
+// ------------------------------------------------------------------ host
+// Q of G = QR with diag(R) > 0 (Householder reflections in FP64), G the
+// n x n block at g with row stride ld: a Haar-distributed rotation when G
+// is standard normal (Mezzadri 2007).  Q row-major n x n.
+void haar_q(const double* g, int64_t ld, int n, std::vector<double>& Q) {
+  std::vector<double> A((size_t)n * n), V((size_t)n * n, 0.0), beta(n, 0.0), rdiag(n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) A[(size_t)i * n + j] = g[(size_t)i * ld + j];
+  for (int k = 0; k < n; ++k) {
+    double nrm = 0.0;
+    for (int i = k; i < n; ++i) nrm += A[(size_t)i * n + k] * A[(size_t)i * n + k];
+    nrm = std::sqrt(nrm);
+    const double x0 = A[(size_t)k * n + k];
+    const double alpha = x0 >= 0.0 ? -nrm : nrm;
+    double vn = 0.0;
+    for (int i = k; i < n; ++i) {
+      double v = A[(size_t)i * n + k] - (i == k ? alpha : 0.0);
+      V[(size_t)i * n + k] = v;
+      vn += v * v;
+    }
+    beta[k] = vn > 0.0 ? 2.0 / vn : 0.0;
+    for (int j = k; j < n; ++j) {
+      double s = 0.0;
+      for (int i = k; i < n; ++i) s += V[(size_t)i * n + k] * A[(size_t)i * n + j];
+      s *= beta[k];
+      for (int i = k; i < n; ++i) A[(size_t)i * n + j] -= s * V[(size_t)i * n + k];
+    }
+    rdiag[k] = A[(size_t)k * n + k];
+  }
+  // Q = H_0 H_1 ... H_{n-1}
+  Q.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+  for (int k = n - 1; k >= 0; --k) {
+    if (beta[k] == 0.0) continue;
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int i = k; i < n; ++i) s += V[(size_t)i * n + k] * Q[(size_t)i * n + j];
+      s *= beta[k];
+      for (int i = k; i < n; ++i) Q[(size_t)i * n + j] -= s * V[(size_t)i * n + k];
+    }
+  }
+  for (int j = 0; j < n; ++j)
+    if (rdiag[j] < 0.0)
+      for (int i = 0; i < n; ++i) Q[(size_t)i * n + j] = -Q[(size_t)i * n + j];
+}
+
+// rows a..a+n of M (d columns) <- Q * rows a..a+n of M
+void rotate_rows(std::vector<double>& Mx, int d, int a, int n, const std::vector<double>& Q) {
+  std::vector<double> out((size_t)n * d, 0.0);
+  parallel_for(n, [&](int64_t b, int64_t e) {
+    for (int64_t i = b; i < e; ++i) {
+      double* o = out.data() + i * d;
+      for (int t = 0; t < n; ++t) {
+        const double q = Q[(size_t)i * n + t];
+        const double* src = Mx.data() + (size_t)(a + t) * d;
+        for (int j = 0; j < d; ++j) o[j] += q * src[j];
+      }
+    }
+  });
+  std::memcpy(Mx.data() + (size_t)a * d, out.data(), out.size() * 8);
+}
+
+void finish_transform(pano_transform& t) {
+  const int d = t.d;
+  t.T32.resize((size_t)d * d);
+  t.mu32.resize(d);
+  for (size_t i = 0; i < t.T.size(); ++i) t.T32[i] = (float)t.T[i];
+  for (int i = 0; i < d; ++i) t.mu32[i] = (float)t.mu[i];
+  t.eta = orthogonality_defect(t.T32.data(), d) * (1.0 + 1e-6) + 1e-15;
+}
+
+uint64_t mix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// k distinct indices of [0, n), ascending (partial Fisher-Yates).
+std::vector<int64_t> sample_rows(int64_t n, int64_t k, uint64_t seed) {
+  k = std::min(k, n);
+  std::vector<int64_t> out;
+  if (k == n) {
+    out.resize(n);
+    std::iota(out.begin(), out.end(), 0);
+    return out;
+  }
+  std::vector<int64_t> perm(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  uint64_t s = seed;
+  for (int64_t i = 0; i < k; ++i) {
+    int64_t j = i + (int64_t)(mix64(s) % (uint64_t)(n - i));
+    std::swap(perm[i], perm[j]);
+  }
+  out.assign(perm.begin(), perm.begin() + k);
+  std::sort(out.begin(), out.end());
+  return out;
+}
+
+struct DTmp {
+  void* p = nullptr;
+  ~DTmp() {
+    if (p) cudaFree(p);
+  }
+};
+
+// ---------------------------------------------------------------- device
+// The subvector term sum_t fl(fl(r_t - c_t)^2), left to right (no fused
+// multiply-add: every kernel, and the encoder, gets the same bits).
+__device__ __forceinline__ float pq_term(const float* __restrict__ r,
+                                         const float* __restrict__ c, int dsub) {
+  float t = __fsub_rn(r[0], c[0]);
+  float s = __fmul_rn(t, t);
+  for (int j = 1; j < dsub; ++j) {
+    t = __fsub_rn(r[j], c[j]);
+    s = __fadd_rn(s, __fmul_rn(t, t));
+  }
+  return s;
+}
+
+__global__ void pq_gather_kernel(const float* __restrict__ X, int d,
+                                 const int64_t* __restrict__ rows, int64_t n,
+                                 float* __restrict__ out) {
+  const int64_t i = blockIdx.x;
+  if (i >= n) return;
+  const int64_t r = rows[i];
+  for (int j = threadIdx.x; j < d; j += blockDim.x)
+    out[i * d + j] = r >= 0 ? X[r * d + j] : 0.f;
+}
+
+// R[i] = xt[i] - ct[list[i]] (rows with list -1: zero)
+__global__ void pq_residual_kernel(float* __restrict__ xt, int64_t n, int d,
+                                   const float* __restrict__ ct,
+                                   const int32_t* __restrict__ list) {
+  const int64_t i = blockIdx.x;
+  if (i >= n) return;
+  const int c = list[i];
+  for (int j = threadIdx.x; j < d; j += blockDim.x)
+    xt[i * d + j] = c >= 0 ? __fsub_rn(xt[i * d + j], ct[(size_t)c * d + j]) : 0.f;
+}
+
+// Nearest codeword of each (row, subquantiser), ties to the lower index.
+// Grid (ceil(n / 256), M); the subquantiser's codebook in shared memory.
+// layout != 0: codes go to [(i / 256) * M + m][256] + i % 256 (the index
+// layout, i = slot), else to [i][M].  Rows with skip[i] < 0 are left alone.
+__global__ void __launch_bounds__(256) pq_encode_kernel(const float* __restrict__ R, int64_t n,
+                                                        int d, int M, int dsub,
+                                                        const float* __restrict__ cb,
+                                                        const int32_t* __restrict__ skip,
+                                                        int layout, uint8_t* __restrict__ codes) {
+  extern __shared__ float s_cb[];
+  const int m = blockIdx.y;
+  for (int t = threadIdx.x; t < PQ_KSUB * dsub; t += blockDim.x)
+    s_cb[t] = cb[(size_t)m * PQ_KSUB * dsub + t];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || (skip && skip[i] < 0)) return;
+  float r[PQ_MAXDSUB];
+  for (int t = 0; t < dsub; ++t) r[t] = R[i * d + (int64_t)m * dsub + t];
+  float best = INFINITY;
+  int bj = 0;
+  for (int j = 0; j < PQ_KSUB; ++j) {
+    const float e = pq_term(r, s_cb + j * dsub, dsub);
+    if (e < best) {
+      best = e;
+      bj = j;
+    }
+  }
+  if (layout)
+    codes[((i / PQ_B) * M + m) * PQ_B + (i % PQ_B)] = (uint8_t)bj;
+  else
+    codes[i * M + m] = (uint8_t)bj;
+}
+
+// One Lloyd step of every subquantiser: assign each sampled subvector to its
+// nearest codeword (as the encoder) and accumulate FP64 sums and counts.
+__global__ void __launch_bounds__(256) pq_kmeans_accum_kernel(
+    const float* __restrict__ R, int64_t n, int d, int dsub, const float* __restrict__ cb,
+    double* __restrict__ sums, int* __restrict__ cnt) {
+  extern __shared__ float s_cb[];
+  const int m = blockIdx.y;
+  for (int t = threadIdx.x; t < PQ_KSUB * dsub; t += blockDim.x)
+    s_cb[t] = cb[(size_t)m * PQ_KSUB * dsub + t];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float r[PQ_MAXDSUB];
+  for (int t = 0; t < dsub; ++t) r[t] = R[i * d + (int64_t)m * dsub + t];
+  float best = INFINITY;
+  int bj = 0;
+  for (int j = 0; j < PQ_KSUB; ++j) {
+    const float e = pq_term(r, s_cb + j * dsub, dsub);
+    if (e < best) {
+      best = e;
+      bj = j;
+    }
+  }
+  const size_t cell = (size_t)m * PQ_KSUB + bj;
+  for (int t = 0; t < dsub; ++t) atomicAdd(sums + cell * dsub + t, (double)r[t]);
+  atomicAdd(cnt + cell, 1);
+}
+
+__global__ void pq_kmeans_update_kernel(int M, int dsub, const double* __restrict__ sums,
+                                        const int* __restrict__ cnt, float* __restrict__ cb) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)M * PQ_KSUB * dsub) return;
+  const int c = cnt[i / dsub];
+  if (c > 0) cb[i] = (float)(sums[i] / c);  // an empty cell keeps its codeword
+}
+
+// ||C_m[j]||^2 in FP64
+__global__ void pq_cnorm_kernel(int M, int dsub, const float* __restrict__ cb,
+                                double* __restrict__ cn) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)M * PQ_KSUB) return;
+  double s = 0.0;
+  for (int t = 0; t < dsub; ++t) {
+    const double v = cb[i * dsub + t];
+    s += v * v;
+  }
+  cn[i] = s;
+}
+
+// Scatter caller codes (vector-id order) into the block layout.
+__global__ void pq_scatter_codes_kernel(const uint8_t* __restrict__ src, int M,
+                                        const int64_t* __restrict__ perm, int64_t nslots,
+                                        uint8_t* __restrict__ codes) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nslots * M) return;
+  const int64_t slot = i / M;
+  const int m = (int)(i % M);
+  const int64_t id = perm[slot];
+  codes[((slot / PQ_B) * M + m) * PQ_B + (slot % PQ_B)] = id >= 0 ? src[id * M + m] : 0;
+}
+
+// ids and tail norms of every slot: tails[(block L + l) 256 + lane] =
+// sqrt(sum over the subquantisers of levels > l of ||C_m[code_m]||^2).
+__global__ void pq_tails_kernel(const uint8_t* __restrict__ codes,
+                                const int64_t* __restrict__ perm, int64_t nslots, int M,
+                                int L, const double* __restrict__ cn, float* __restrict__ tails,
+                                int32_t* __restrict__ ids) {
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= nslots) return;
+  const int64_t blk = slot / PQ_B;
+  const int lane = (int)(slot % PQ_B);
+  const int64_t id = perm[slot];
+  ids[slot] = (int32_t)id;
+  const int ML = M / L;
+  double acc = 0.0;
+  for (int l = L - 1; l >= 0; --l) {
+    tails[(blk * L + l) * PQ_B + lane] = id >= 0 ? (float)sqrt(acc) : 0.f;
+    if (id < 0) continue;
+    for (int mm = 0; mm < ML; ++mm) {
+      const int m = l * ML + mm;
+      acc += cn[(size_t)m * PQ_KSUB + codes[(blk * M + m) * PQ_B + lane]];
+    }
+  }
+}
+
+// ---- search
+struct PqArgs {
+  const uint8_t* codes;
+  const float* xtail;
+  const int32_t* ids;
+  const int64_t* blk_off;
+  const int32_t* list_size;
+  const float* codebook;
+  const float* cent_t;
+  const float* qt;
+  const int2* pairs;  // (query, list), nearest lists first, then by list
+  unsigned long long* topk;
+  unsigned long long* stats;
+  int d, M, dsub, L, ML, b, k, prune, collect;
+  float lo;    // (1 - gamma) factor of the lower bound, rounded down
+  float erel;  // relative allowance for the roundings of s_q, s_x and |s_q - s_x|
+};
+
+// Bytes of dynamic shared memory of the verify kernel.
+size_t pq_verify_smem(int d, int L, int ML) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    o = (o + 15) & ~(size_t)15;
+    o += bytes;
+  };
+  take((size_t)d * 4);                 // r
+  take((size_t)L * 8);                 // level energies (FP64)
+  take((size_t)L * 4);                 // s_q per level
+  take((size_t)ML * PQ_KSUB * 4);      // level table
+  take((size_t)2 * PQ_S * 4);          // partial distances (two lists)
+  take((size_t)2 * PQ_S * 2);          // live candidates (two lists)
+  take(64);                            // counters, threshold
+  return o;
+}
+
+__device__ __forceinline__ float threshold_of(const unsigned long long* slots, int k) {
+  const unsigned long long key = ld_volatile_u64(slots + k - 1);
+  return key == kEmptyKey ? INFINITY : key_dist(key);
+}
+
+__global__ void __launch_bounds__(PQ_NT) pq_verify_kernel(const PqArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int d = a.d, L = a.L, ML = a.ML, M = a.M, dsub = a.dsub;
+  size_t o = 0;
+  auto carve = [&](size_t bytes) {
+    o = (o + 15) & ~(size_t)15;
+    unsigned char* p = smem + o;
+    o += bytes;
+    return p;
+  };
+  float* r = (float*)carve((size_t)d * 4);
+  double* eq = (double*)carve((size_t)L * 8);
+  float* sq = (float*)carve((size_t)L * 4);
+  float* lut = (float*)carve((size_t)ML * PQ_KSUB * 4);
+  float* pacc = (float*)carve((size_t)2 * PQ_S * 4);
+  uint16_t* live = (uint16_t*)carve((size_t)2 * PQ_S * 2);
+  int* ctr = (int*)carve(64);  // [0] survivors of the level, [2] threshold bits
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  const int2 pr = a.pairs[blockIdx.x];
+  const int q = pr.x, c = pr.y;
+  const int nc = a.list_size[c];
+  if (nc == 0) return;
+  const int64_t blk0 = a.blk_off[c];
+  unsigned long long* slots = a.topk + (size_t)q * a.k;
+
+  for (int j = tid; j < d; j += PQ_NT)
+    r[j] = __fsub_rn(a.qt[(size_t)q * d + j], a.cent_t[(size_t)c * d + j]);
+  __syncthreads();
+  // FP64 level energies of the residual, one warp per level
+  for (int l = warp; l < L; l += PQ_NT / 32) {
+    double s = 0.0;
+    for (int j = lane; j < a.b; j += 32) {
+      const double v = r[l * a.b + j];
+      s += v * v;
+    }
+    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) eq[l] = s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double tail = 0.0;
+    for (int l = L - 1; l >= 0; --l) {
+      sq[l] = (float)sqrt(tail);  // after level l
+      tail += eq[l];
+    }
+  }
+  __syncthreads();
+
+  unsigned long long n_dims = 0, n_lv = 0, n_full = 0, n_lut = 0;
+  for (int s0 = 0; s0 < nc; s0 += PQ_S) {
+    const int ns = min(PQ_S, nc - s0);
+    int nl = ns, cur = 0;
+    for (int l = 0; l < L && nl > 0; ++l) {
+      const bool last = l == L - 1;
+      if (tid == 0) {
+        ctr[0] = 0;
+        ctr[2] = __float_as_int(threshold_of(slots, a.k));
+      }
+      const bool use_lut = nl >= PQ_LUT_MIN;
+      if (use_lut) {
+        for (int e = tid; e < ML * PQ_KSUB; e += PQ_NT) {
+          const int m = l * ML + e / PQ_KSUB;
+          lut[e] = pq_term(r + m * dsub, a.codebook + ((size_t)m * PQ_KSUB + (e % PQ_KSUB)) * dsub,
+                           dsub);
+        }
+      }
+      __syncthreads();
+      const float tau = __int_as_float(ctr[2]);
+      const float sql = sq[l];
+      const int nxt = cur ^ 1;
+      for (int i0 = 0; i0 < nl; i0 += PQ_NT) {
+        const int i = i0 + tid;
+        bool keep = false;
+        int cand = 0;
+        float P = 0.f;
+        if (i < nl) {
+          cand = l == 0 ? i : live[cur * PQ_S + i];
+          if (l > 0) P = pacc[cur * PQ_S + i];
+          const int g = s0 + cand;
+          const int64_t blk = blk0 + g / PQ_B;
+          const int ln = g % PQ_B;
+          const uint8_t* cp = a.codes + (blk * M + (int64_t)l * ML) * PQ_B + ln;
+          float S = 0.f;
+          for (int mm = 0; mm < ML; ++mm) {
+            const int code = cp[(size_t)mm * PQ_B];
+            const int m = l * ML + mm;
+            const float e = use_lut ? lut[mm * PQ_KSUB + code]
+                                    : pq_term(r + m * dsub,
+                                              a.codebook + ((size_t)m * PQ_KSUB + code) * dsub,
+                                              dsub);
+            S = mm == 0 ? e : __fadd_rn(S, e);
+          }
+          P = __fadd_rn(P, S);
+          if (last) {
+            const unsigned long long key = make_key(P, a.ids[blk * PQ_B + ln]);
+            if (key < ld_volatile_u64(slots + a.k - 1)) topk_insert_thread(slots, a.k, key);
+          } else {
+            keep = true;
+            if (a.prune) {
+              const float sx = a.xtail[(blk * L + l) * PQ_B + ln];
+              float gap = fabsf(__fsub_rn(sql, sx)) - a.erel * (sql + sx);
+              gap = fmaxf(gap, 0.f);
+              const float lb = __fmaf_rn(gap, gap, P);
+              keep = !(lb * a.lo > tau);
+            }
+          }
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, keep);
+        if (ball) {
+          int base = 0;
+          if (lane == 0) base = atomicAdd(&ctr[0], __popc(ball));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (keep) {
+            const int at = base + __popc(ball & ((1u << lane) - 1));
+            live[nxt * PQ_S + at] = (uint16_t)cand;
+            pacc[nxt * PQ_S + at] = P;
+          }
+        }
+      }
+      __syncthreads();
+      if (a.collect && tid == 0) {
+        n_dims += (unsigned long long)nl * a.b;
+        n_lv += nl;
+        if (last) n_full += nl;
+        if (use_lut) ++n_lut;
+      }
+      nl = last ? 0 : ctr[0];
+      cur = nxt;
+      __syncthreads();
+    }
+  }
+  if (a.collect && tid == 0) {
+    atomicAdd(a.stats + 0, (unsigned long long)nc);
+    atomicAdd(a.stats + 1, n_dims);
+    atomicAdd(a.stats + 2, n_lv);
+    atomicAdd(a.stats + 3, n_full);
+    atomicAdd(a.stats + 4, n_lut);
+    atomicAdd(a.stats + 5, 1ULL);
+  }
+}
+
+// Seeds each query's top-k with the first PQ_SEED members of its nearest
+// list, distances computed exactly as pq_verify_kernel computes them (level
+// sums in subquantiser order, added in level order), so that the verify
+// kernel's insert of the same candidate meets an equal key and is dropped.
+__global__ void __launch_bounds__(256) pq_seed_kernel(const PqArgs a,
+                                                      const int32_t* __restrict__ probes,
+                                                      int nprobe) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int d = a.d, L = a.L, ML = a.ML, dsub = a.dsub;
+  float* r = (float*)smem;
+  float* part = r + ((d + 3) & ~3);  // [PQ_SEED][L]
+  const int q = blockIdx.x;
+  const int c = probes[(size_t)q * nprobe];
+  const int ns = min(PQ_SEED, a.list_size[c]);
+  if (ns == 0) return;
+  const int64_t blk0 = a.blk_off[c];
+  for (int j = threadIdx.x; j < d; j += blockDim.x)
+    r[j] = __fsub_rn(a.qt[(size_t)q * d + j], a.cent_t[(size_t)c * d + j]);
+  __syncthreads();
+  for (int e = threadIdx.x; e < ns * L; e += blockDim.x) {
+    const int cand = e / L, l = e % L;
+    const int64_t blk = blk0 + cand / PQ_B;
+    const int ln = cand % PQ_B;
+    const uint8_t* cp = a.codes + (blk * a.M + (int64_t)l * ML) * PQ_B + ln;
+    float S = 0.f;
+    for (int mm = 0; mm < ML; ++mm) {
+      const int m = l * ML + mm;
+      const float v = pq_term(r + m * dsub,
+                              a.codebook + ((size_t)m * PQ_KSUB + cp[(size_t)mm * PQ_B]) * dsub,
+                              dsub);
+      S = mm == 0 ? v : __fadd_rn(S, v);
+    }
+    part[cand * L + l] = S;
+  }
+  __syncthreads();
+  for (int cand = threadIdx.x; cand < ns; cand += blockDim.x) {
+    float P = 0.f;
+    for (int l = 0; l < L; ++l) P = __fadd_rn(P, part[cand * L + l]);
+    const int64_t blk = blk0 + cand / PQ_B;
+    topk_insert_thread(a.topk + (size_t)q * a.k, a.k,
+                       make_key(P, a.ids[blk * PQ_B + cand % PQ_B]));
+  }
+}
+
+// Pair order: each query's nearest list first (grouped by list), then the
+// other probes (grouped by list).  bucket b = (rank > 0) * nlist + list.
+__global__ void pq_pair_count_kernel(const int32_t* __restrict__ probes, int64_t nq, int nprobe,
+                                     int nlist, int* __restrict__ cnt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq * nprobe) return;
+  const int rank = (int)(i % nprobe);
+  atomicAdd(cnt + (rank > 0) * nlist + probes[i], 1);
+}
+
+__global__ void __launch_bounds__(1024) pq_pair_scan_kernel(const int* __restrict__ cnt, int nb,
+                                                            int* __restrict__ off) {
+  __shared__ int s_part[1024];
+  const int per = (nb + 1023) / 1024;
+  const int b0 = threadIdx.x * per;
+  int sum = 0;
+  for (int b = b0; b < min(nb, b0 + per); ++b) sum += cnt[b];
+  s_part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int st = 1; st < 1024; st <<= 1) {
+    const int v = threadIdx.x >= st ? s_part[threadIdx.x - st] : 0;
+    __syncthreads();
+    s_part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = s_part[threadIdx.x] - sum;
+  for (int b = b0; b < min(nb, b0 + per); ++b) {
+    off[b] = run;
+    run += cnt[b];
+  }
+}
+
+__global__ void pq_pair_scatter_kernel(const int32_t* __restrict__ probes, int64_t nq, int nprobe,
+                                       int nlist, int* __restrict__ fill,
+                                       const int* __restrict__ off, int2* __restrict__ pairs) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq * nprobe) return;
+  const int rank = (int)(i % nprobe);
+  const int c = probes[i];
+  const int b = (rank > 0) * nlist + c;
+  const int at = off[b] + atomicAdd(fill + b, 1);
+  pairs[at] = make_int2((int)(i / nprobe), c);
+}
+
+__global__ void pq_decode_kernel(const unsigned long long* __restrict__ topk, int64_t n,
+                                 int64_t* __restrict__ ids, float* __restrict__ dists) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned long long key = topk[i];
+  ids[i] = key == kEmptyKey ? -1 : (int64_t)key_id(key);
+  dists[i] = key == kEmptyKey ? INFINITY : key_dist(key);
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ build
+int build_ivfpq(const pano_transform* t, const float* X, int64_t n, int nlist,
+                const pano_pq_build_opts* o, cudaStream_t st, pano_index** out) {
+  PANO_CHECK(t && X && out && o, PANO_EINVAL, "null argument");
+  const int d = t->d, M = o->M, L = o->n_levels;
+  PANO_CHECK(n >= 1 && nlist >= 1 && nlist <= n, PANO_EINVAL, "need 1 <= nlist <= n");
+  PANO_CHECK(n < ((int64_t)1 << 31) - 1, PANO_EINVAL, "at most 2^31-2 vectors");
+  PANO_CHECK(L >= 1 && L <= PQ_MAXL && d % L == 0, PANO_EINVAL,
+             "n_levels must divide d (at most 64 levels)");
+  PANO_CHECK(M >= 1 && d % M == 0 && M % L == 0, PANO_EINVAL,
+             "M must divide d and be a multiple of n_levels");
+  const int dsub = d / M, ML = M / L;
+  PANO_CHECK(ML <= PQ_MAXML, PANO_EINVAL, "at most 64 subquantisers per level");
+  PANO_CHECK(dsub <= PQ_MAXDSUB, PANO_EINVAL, "at most 32 coordinates per subvector");
+  PANO_CHECK(o->codebooks || n >= PQ_KSUB, PANO_EINVAL,
+             "training codebooks needs at least 256 vectors");
+  int dev = 0;
+  int rc = check_device(&dev);
+  if (rc) return rc;
+  auto idx = std::make_unique<pano_index>();
+  pano_index& I = *idx;
+  I.device = dev;
+  I.n = n;
+  I.d = d;
+  I.nlist = nlist;
+  I.precision = PANO_PQ;
+  I.chunk = PQ_B;
+  I.L = L;
+  I.pq_M = M;
+  I.pq_dsub = dsub;
+  I.tf = *t;
+  I.eta = t->eta;
+  I.widths.assign(L, d / L);
+  I.offs.assign(L + 1, 0);
+  for (int l = 0; l < L; ++l) I.offs[l + 1] = I.offs[l] + d / L;
+  I.max_w = d / L;
+
+  const float* Xd = X;
+  DTmp t_x;
+  if (!is_device_ptr(X)) {
+    PANO_CUDA(cudaMalloc(&t_x.p, (size_t)n * d * 4));
+    PANO_CUDA(cudaMemcpyAsync(t_x.p, X, (size_t)n * d * 4, cudaMemcpyHostToDevice, st));
+    Xd = (const float*)t_x.p;
+  }
+
+  // ---- coarse quantiser and lists
+  if (o->assign) {
+    PANO_CHECK(o->centroids, PANO_EINVAL, "an assignment needs its centroids");
+    for (int64_t i = 0; i < n; ++i)
+      PANO_CHECK(o->assign[i] >= 0 && o->assign[i] < nlist, PANO_EINVAL,
+                 "assignment out of range");
+  }
+  pano_build_opts co;
+  std::memset(&co, 0, sizeof(co));
+  co.kmeans_iters = o->kmeans_iters;
+  co.kmeans_sample = o->kmeans_sample;
+  co.seed = o->seed ? o->seed : 1234;
+  co.centroids = o->centroids;
+  if (o->assign) {
+    // centroids and lists given: only the centroid arrays are needed
+    I.centroids.assign(o->centroids, o->centroids + (size_t)nlist * d);
+    std::vector<float> hcn(nlist);
+    float cmax = 0.f;
+    for (int c = 0; c < nlist; ++c) {
+      double s = 0;
+      for (int j = 0; j < d; ++j)
+        s += (double)I.centroids[(size_t)c * d + j] * I.centroids[(size_t)c * d + j];
+      hcn[c] = (float)s;
+      cmax = std::max(cmax, (float)std::sqrt(s));
+    }
+    I.cmax = cmax;
+    if ((rc = I.cent.alloc((size_t)nlist * d * 4)) || (rc = I.cent_n2.alloc(nlist * 4))) return rc;
+    PANO_CUDA(cudaMemcpyAsync(I.cent.p, I.centroids.data(), (size_t)nlist * d * 4,
+                              cudaMemcpyHostToDevice, st));
+    PANO_CUDA(cudaMemcpyAsync(I.cent_n2.p, hcn.data(), nlist * 4, cudaMemcpyHostToDevice, st));
+    I.assign.assign(o->assign, o->assign + n);
+  } else {
+    rc = coarse_lists(Xd, n, d, nlist, &co, st, I);
+    if (rc) return rc;
+  }
+
+  // ---- list layout (host): blocks of PQ_B slots, ascending id within a list
+  I.list_size.assign(nlist, 0);
+  for (int64_t i = 0; i < n; ++i) I.list_size[I.assign[i]]++;
+  I.list_chunk_off.assign(nlist + 1, 0);
+  for (int c = 0; c < nlist; ++c)
+    I.list_chunk_off[c + 1] = I.list_chunk_off[c] + (I.list_size[c] + PQ_B - 1) / PQ_B;
+  I.n_chunks = I.list_chunk_off[nlist];
+  const int64_t nslots = I.n_chunks * PQ_B;
+  std::vector<int64_t> perm(nslots, -1);
+  std::vector<int32_t> slot_list(nslots, -1);
+  {
+    std::vector<int64_t> fill(nlist, 0);
+    for (int64_t i = 0; i < n; ++i) {
+      const int c = I.assign[i];
+      const int64_t s = I.list_chunk_off[c] * PQ_B + fill[c]++;
+      perm[s] = i;
+      slot_list[s] = c;
+    }
+  }
+  if ((rc = I.chunk_off_d.alloc((nlist + 1) * 8)) || (rc = I.list_size_d.alloc(nlist * 4)) ||
+      (rc = I.level_off_d.alloc((L + 1) * 4)) || (rc = I.T32.alloc((size_t)d * d * 4)) ||
+      (rc = I.mu32.alloc(d * 4)) || (rc = I.pq_cent_t.alloc((size_t)nlist * d * 4)) ||
+      (rc = I.pq_codebook.alloc((size_t)M * PQ_KSUB * dsub * 4)) ||
+      (rc = I.pq_codes.alloc((size_t)std::max<int64_t>(nslots, 1) * M)) ||
+      (rc = I.tails.alloc((size_t)std::max<int64_t>(nslots, 1) * L * 4)) ||
+      (rc = I.ids.alloc((size_t)std::max<int64_t>(nslots, 1) * 4)))
+    return rc;
+  PANO_CUDA(cudaMemcpyAsync(I.chunk_off_d.p, I.list_chunk_off.data(), (nlist + 1) * 8,
+                            cudaMemcpyHostToDevice, st));
+  PANO_CUDA(cudaMemcpyAsync(I.list_size_d.p, I.list_size.data(), nlist * 4,
+                            cudaMemcpyHostToDevice, st));
+  PANO_CUDA(cudaMemcpyAsync(I.level_off_d.p, I.offs.data(), (L + 1) * 4, cudaMemcpyHostToDevice,
+                            st));
+  PANO_CUDA(cudaMemcpyAsync(I.T32.p, t->T32.data(), (size_t)d * d * 4, cudaMemcpyHostToDevice, st));
+  PANO_CUDA(cudaMemcpyAsync(I.mu32.p, t->mu32.data(), d * 4, cudaMemcpyHostToDevice, st));
+  // c~ = T~(c - mu~)
+  PANO_CUDA(gemm_nt(kStore, nlist, d, d, I.cent.as<float>(), d, I.mu32.as<float>(),
+                    I.T32.as<float>(), d, I.pq_cent_t.as<float>(), d, nullptr, nullptr, st));
+
+  DTmp t_perm, t_sl;
+  PANO_CUDA(cudaMalloc(&t_perm.p, std::max<int64_t>(nslots, 1) * 8));
+  PANO_CUDA(cudaMalloc(&t_sl.p, std::max<int64_t>(nslots, 1) * 4));
+  PANO_CUDA(cudaMemcpyAsync(t_perm.p, perm.data(), nslots * 8, cudaMemcpyHostToDevice, st));
+  PANO_CUDA(cudaMemcpyAsync(t_sl.p, slot_list.data(), nslots * 4, cudaMemcpyHostToDevice, st));
+  const size_t cbsm = (size_t)PQ_KSUB * dsub * 4;
+
+  // rows (or sampled rows) -> transformed residuals, in blocks of rows
+  auto residuals = [&](const int64_t* rows_d, const int32_t* lists_d, int64_t m,
+                       float* out_r) -> int {
+    if (m == 0) return PANO_OK;
+    pq_gather_kernel<<<(unsigned)m, 128, 0, st>>>(Xd, d, rows_d, m, out_r);
+    PANO_CUDA(cudaGetLastError());
+    // in place: the GEMM reads rows and writes x~ to a second buffer
+    DTmp t_xt;
+    PANO_CUDA(cudaMalloc(&t_xt.p, (size_t)m * d * 4));
+    PANO_CUDA(gemm_nt(kStore, (int)m, d, d, out_r, d, I.mu32.as<float>(), I.T32.as<float>(), d,
+                      (float*)t_xt.p, d, nullptr, nullptr, st));
+    pq_residual_kernel<<<(unsigned)m, 128, 0, st>>>((float*)t_xt.p, m, d,
+                                                    I.pq_cent_t.as<float>(), lists_d);
+    PANO_CUDA(cudaGetLastError());
+    PANO_CUDA(cudaMemcpyAsync(out_r, t_xt.p, (size_t)m * d * 4, cudaMemcpyDeviceToDevice, st));
+    PANO_CUDA(cudaStreamSynchronize(st));
+    return PANO_OK;
+  };
+
+  // ---- codebooks
+  if (o->codebooks) {
+    PANO_CUDA(cudaMemcpyAsync(I.pq_codebook.p, o->codebooks, (size_t)M * PQ_KSUB * dsub * 4,
+                              cudaMemcpyHostToDevice, st));
+  } else {
+    const int64_t ns = std::min<int64_t>(n, o->pq_sample > 0 ? o->pq_sample : 65536);
+    std::vector<int64_t> rows = sample_rows(n, std::max<int64_t>(ns, PQ_KSUB),
+                                            (o->seed ? o->seed : 1234) ^ 0x5051ULL);
+    const int64_t m = (int64_t)rows.size();
+    std::vector<int32_t> lists(m);
+    for (int64_t i = 0; i < m; ++i) lists[i] = I.assign[rows[i]];
+    DTmp t_rows, t_lists, t_r, t_sums, t_cnt;
+    PANO_CUDA(cudaMalloc(&t_rows.p, m * 8));
+    PANO_CUDA(cudaMalloc(&t_lists.p, m * 4));
+    PANO_CUDA(cudaMalloc(&t_r.p, (size_t)m * d * 4));
+    PANO_CUDA(cudaMalloc(&t_sums.p, (size_t)M * PQ_KSUB * dsub * 8));
+    PANO_CUDA(cudaMalloc(&t_cnt.p, (size_t)M * PQ_KSUB * 4));
+    PANO_CUDA(cudaMemcpyAsync(t_rows.p, rows.data(), m * 8, cudaMemcpyHostToDevice, st));
+    PANO_CUDA(cudaMemcpyAsync(t_lists.p, lists.data(), m * 4, cudaMemcpyHostToDevice, st));
+    rc = residuals((const int64_t*)t_rows.p, (const int32_t*)t_lists.p, m, (float*)t_r.p);
+    if (rc) return rc;
+    // initial codewords: 256 distinct sampled rows' subvectors
+    std::vector<int64_t> init = sample_rows(m, PQ_KSUB, (o->seed ? o->seed : 1234) ^ 0xC0DEULL);
+    std::vector<float> hr((size_t)m * d);
+    PANO_CUDA(cudaMemcpyAsync(hr.data(), t_r.p, hr.size() * 4, cudaMemcpyDeviceToHost, st));
+    PANO_CUDA(cudaStreamSynchronize(st));
+    std::vector<float> cb((size_t)M * PQ_KSUB * dsub);
+    for (int mq = 0; mq < M; ++mq)
+      for (int j = 0; j < PQ_KSUB; ++j)
+        for (int tt = 0; tt < dsub; ++tt)
+          cb[((size_t)mq * PQ_KSUB + j) * dsub + tt] = hr[(size_t)init[j] * d + mq * dsub + tt];
+    PANO_CUDA(cudaMemcpyAsync(I.pq_codebook.p, cb.data(), cb.size() * 4, cudaMemcpyHostToDevice,
+                              st));
+    const int iters = o->pq_iters > 0 ? o->pq_iters : 16;
+    for (int it = 0; it < iters; ++it) {
+      PANO_CUDA(cudaMemsetAsync(t_sums.p, 0, (size_t)M * PQ_KSUB * dsub * 8, st));
+      PANO_CUDA(cudaMemsetAsync(t_cnt.p, 0, (size_t)M * PQ_KSUB * 4, st));
+      pq_kmeans_accum_kernel<<<dim3((unsigned)((m + 255) / 256), M), 256, cbsm, st>>>(
+          (const float*)t_r.p, m, d, dsub, I.pq_codebook.as<float>(), (double*)t_sums.p,
+          (int*)t_cnt.p);
+      PANO_CUDA(cudaGetLastError());
+      const int64_t tot = (int64_t)M * PQ_KSUB * dsub;
+      pq_kmeans_update_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+          M, dsub, (const double*)t_sums.p, (const int*)t_cnt.p, I.pq_codebook.as<float>());
+      PANO_CUDA(cudaGetLastError());
+    }
+  }
+
+  // ---- codes, in the block layout
+  if (o->codes) {
+    DTmp t_codes;
+    PANO_CUDA(cudaMalloc(&t_codes.p, (size_t)n * M));
+    PANO_CUDA(cudaMemcpyAsync(t_codes.p, o->codes, (size_t)n * M, cudaMemcpyHostToDevice, st));
+    const int64_t tot = nslots * M;
+    if (tot > 0)
+      pq_scatter_codes_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+          (const uint8_t*)t_codes.p, M, (const int64_t*)t_perm.p, nslots,
+          I.pq_codes.as<uint8_t>());
+    PANO_CUDA(cudaGetLastError());
+    PANO_CUDA(cudaStreamSynchronize(st));
+  } else {
+    PANO_CUDA(cudaMemsetAsync(I.pq_codes.p, 0, (size_t)std::max<int64_t>(nslots, 1) * M, st));
+    // blocks of slots (a multiple of PQ_B): 64 MB of residuals each
+    const int64_t step =
+        std::max<int64_t>(PQ_B, (((int64_t)1 << 24) / d) / PQ_B * PQ_B);
+    DTmp t_r;
+    PANO_CUDA(cudaMalloc(&t_r.p, (size_t)std::min(step, std::max<int64_t>(nslots, 1)) * d * 4));
+    for (int64_t s0 = 0; s0 < nslots; s0 += step) {
+      const int64_t m = std::min(step, nslots - s0);
+      rc = residuals((const int64_t*)t_perm.p + s0, (const int32_t*)t_sl.p + s0, m,
+                     (float*)t_r.p);
+      if (rc) return rc;
+      pq_encode_kernel<<<dim3((unsigned)((m + 255) / 256), M), 256, cbsm, st>>>(
+          (const float*)t_r.p, m, d, M, dsub, I.pq_codebook.as<float>(),
+          (const int32_t*)t_sl.p + s0, 1, I.pq_codes.as<uint8_t>() + s0 * M);
+      PANO_CUDA(cudaGetLastError());
+    }
+  }
+
+  // ---- ids and tail norms
+  {
+    DTmp t_cn;
+    PANO_CUDA(cudaMalloc(&t_cn.p, (size_t)M * PQ_KSUB * 8));
+    pq_cnorm_kernel<<<(unsigned)((M * PQ_KSUB + 255) / 256), 256, 0, st>>>(
+        M, dsub, I.pq_codebook.as<float>(), (double*)t_cn.p);
+    if (nslots > 0)
+      pq_tails_kernel<<<(unsigned)((nslots + 255) / 256), 256, 0, st>>>(
+          I.pq_codes.as<uint8_t>(), (const int64_t*)t_perm.p, nslots, M, L,
+          (const double*)t_cn.p, I.tails.as<float>(), I.ids.as<int32_t>());
+    PANO_CUDA(cudaGetLastError());
+    PANO_CUDA(cudaStreamSynchronize(st));
+  }
+  *out = idx.release();
+  return PANO_OK;
+}
+
+// ----------------------------------------------------------------- search
+int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe, int k,
+              int64_t* out_ids, float* out_dists, int mode, int collect, cudaStream_t st) {
+  PANO_CHECK(ip, PANO_EINVAL, "null index");
+  const pano_index& I = *ip;
+  PANO_CHECK(I.pq_M > 0, PANO_EINVAL, "not an IVFPQ index (panorama_build_ivfpq)");
+  PANO_CHECK(nq >= 0 && nq < (1LL << 31), PANO_EINVAL, "nq out of range");
+  PANO_CHECK(nq == 0 || (queries && out_ids && out_dists), PANO_EINVAL, "null argument");
+  PANO_CHECK(k >= 1 && k <= 1024, PANO_EINVAL, "k must be in [1, 1024]");
+  PANO_CHECK(nprobe >= 1 && nprobe <= I.nlist, PANO_EINVAL, "nprobe must be in [1, nlist]");
+  PANO_CHECK((int64_t)nq * nprobe < (1LL << 31), PANO_EINVAL, "too many (query, list) pairs");
+  pano_search_stats& S = stats_slot();
+  std::memset(&S, 0, sizeof(S));
+  S.n_queries = nq;
+  if (nq == 0) return PANO_OK;
+  int cur = 0;
+  PANO_CUDA(cudaGetDevice(&cur));
+  PANO_CHECK(cur == I.device, PANO_EINVAL, "current device differs from the index's device");
+  const int d = I.d, L = I.L, M = I.pq_M, dsub = I.pq_dsub, ML = M / L, nlist = I.nlist;
+  const int64_t npairs = nq * nprobe;
+
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    size_t at = off;
+    off += bytes;
+    return at;
+  };
+  const size_t o_qt = take((size_t)nq * d * 4);
+  const size_t o_pr = take((size_t)npairs * 4);
+  const size_t o_pairs = take((size_t)npairs * 8);
+  const size_t o_cnt = take((size_t)2 * nlist * 4);
+  const size_t o_fill = take((size_t)2 * nlist * 4);
+  const size_t o_off = take((size_t)2 * nlist * 4);
+  const size_t o_topk = take((size_t)nq * k * 8);
+  const size_t o_stats = take(8 * 8);
+  void* ws = nullptr;
+  PANO_CUDA(cudaMallocAsync(&ws, off, st));
+  char* W = (char*)ws;
+  float* qt = (float*)(W + o_qt);
+  int32_t* probes = (int32_t*)(W + o_pr);
+  int2* pairs = (int2*)(W + o_pairs);
+  int* cnt = (int*)(W + o_cnt);
+  int* fill = (int*)(W + o_fill);
+  int* poff = (int*)(W + o_off);
+  unsigned long long* topk = (unsigned long long*)(W + o_topk);
+  unsigned long long* stats = (unsigned long long*)(W + o_stats);
+
+  auto body = [&]() -> int {
+    PANO_CUDA(cudaMemsetAsync(cnt, 0, (size_t)2 * nlist * 4, st));
+    PANO_CUDA(cudaMemsetAsync(fill, 0, (size_t)2 * nlist * 4, st));
+    PANO_CUDA(cudaMemsetAsync(topk, 0xff, (size_t)nq * k * 8, st));
+    PANO_CUDA(cudaMemsetAsync(stats, 0, 8 * 8, st));
+    // q~ = T~(q - mu~)
+    PANO_CUDA(gemm_nt(kStore, (int)nq, d, d, queries, d, I.mu32.as<float>(), I.T32.as<float>(),
+                      d, qt, d, nullptr, nullptr, st));
+    int rc = probe_only(ip, queries, nq, nprobe, probes, st);
+    if (rc) return rc;
+    const unsigned pg = (unsigned)((npairs + 255) / 256);
+    pq_pair_count_kernel<<<pg, 256, 0, st>>>(probes, nq, nprobe, nlist, cnt);
+    pq_pair_scan_kernel<<<1, 1024, 0, st>>>(cnt, 2 * nlist, poff);
+    pq_pair_scatter_kernel<<<pg, 256, 0, st>>>(probes, nq, nprobe, nlist, fill, poff, pairs);
+    PANO_CUDA(cudaGetLastError());
+
+    PqArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.codes = I.pq_codes.as<uint8_t>();
+    a.xtail = I.tails.as<float>();
+    a.ids = I.ids.as<int32_t>();
+    a.blk_off = I.chunk_off_d.as<int64_t>();
+    a.list_size = I.list_size_d.as<int32_t>();
+    a.codebook = I.pq_codebook.as<float>();
+    a.cent_t = I.pq_cent_t.as<float>();
+    a.qt = qt;
+    a.pairs = pairs;
+    a.topk = topk;
+    a.stats = stats;
+    a.d = d;
+    a.M = M;
+    a.dsub = dsub;
+    a.L = L;
+    a.ML = ML;
+    a.b = d / L;
+    a.k = k;
+    a.prune = mode == 0 ? 1 : 0;
+    a.collect = collect ? 1 : 0;
+    // D~ >= (1-u)^(L + ML + dsub + 2) (D_head~ + (sqrt R_q - sqrt R_x)^2) (level
+    // and subquantiser sums of non-negative terms, each term's subtraction,
+    // square and additions); the computed bound and its scaling add three
+    // roundings up: lo = 1 - gamma_{L + ML + dsub + 6}, rounded down.
+    const double lo = 1.0 - gamma_n((double)L + ML + dsub + 6);
+    float lo32 = (float)lo;
+    if ((double)lo32 > lo) lo32 = std::nextafter(lo32, 0.f);
+    a.lo = lo32;
+    // s_q, s_x: FP64 sums rounded to FP32 (u each), |s_q - s_x| and the
+    // allowance itself (u each): 8u of (s_q + s_x) covers them with margin.
+    a.erel = (float)(8.0 * kU32);
+
+    const size_t ssm = (size_t)((d + 3) & ~3) * 4 + (size_t)PQ_SEED * L * 4;
+    PANO_CUDA(cudaFuncSetAttribute(pq_seed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)ssm));
+    pq_seed_kernel<<<(unsigned)nq, 256, ssm, st>>>(a, probes, nprobe);
+    PANO_CUDA(cudaGetLastError());
+    const size_t vsm = pq_verify_smem(d, L, ML);
+    PANO_CUDA(cudaFuncSetAttribute(pq_verify_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)vsm));
+    pq_verify_kernel<<<(unsigned)npairs, PQ_NT, vsm, st>>>(a);
+    PANO_CUDA(cudaGetLastError());
+    pq_decode_kernel<<<(unsigned)((nq * k + 255) / 256), 256, 0, st>>>(topk, nq * k, out_ids,
+                                                                      out_dists);
+    PANO_CUDA(cudaGetLastError());
+    unsigned long long hs[8] = {};
+    PANO_CUDA(cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    PANO_CUDA(cudaStreamSynchronize(st));
+    if (collect) {
+      S.pairs = (int64_t)hs[0];
+      S.dims_scanned = (int64_t)hs[1];
+      S.pair_levels = (int64_t)hs[2];
+      S.reranked = (int64_t)hs[3];
+      S.tile_levels = (int64_t)hs[4];
+      S.work_items = (int64_t)hs[5];
+    }
+    return PANO_OK;
+  };
+  int rc = body();
+  cudaFreeAsync(ws, st);
+  return rc;
+}
+
+int debug_pq_encode(const float* R, int64_t n, int d, int M, const float* cb, uint8_t* codes,
+                    cudaStream_t st) {
+  PANO_CHECK(R && cb && codes, PANO_EINVAL, "null argument");
+  PANO_CHECK(n >= 0 && M >= 1 && d % M == 0 && d / M <= PQ_MAXDSUB, PANO_EINVAL,
+             "M must divide d with at most 32 coordinates per subvector");
+  if (n == 0) return PANO_OK;
+  const int dsub = d / M;
+  pq_encode_kernel<<<dim3((unsigned)((n + 255) / 256), M), 256, (size_t)PQ_KSUB * dsub * 4, st>>>(
+      R, n, d, M, dsub, cb, nullptr, 0, codes);
+  PANO_CUDA(cudaGetLastError());
+  PANO_CUDA(cudaStreamSynchronize(st));
+  return PANO_OK;
+}
+
+}  // namespace pano
+
+using namespace pano;
+
+extern "C" {
+
+int panorama_transform_import(const double* T, const double* mu, const double* lam, int32_t d,
+                              pano_transform** out) {
+  clear_error();
+  PANO_CHECK(T && mu && lam && out && d >= 1, PANO_EINVAL, "bad arguments to transform_import");
+  auto t = std::make_unique<pano_transform>();
+  t->d = d;
+  t->T.assign(T, T + (size_t)d * d);
+  t->mu.assign(mu, mu + d);
+  t->lam.assign(lam, lam + d);
+  for (double v : t->T) PANO_CHECK(std::isfinite(v), PANO_EINVAL, "non-finite T");
+  for (double v : t->mu) PANO_CHECK(std::isfinite(v), PANO_EINVAL, "non-finite mu");
+  for (double v : t->lam) PANO_CHECK(std::isfinite(v) && v >= 0, PANO_EINVAL, "bad lam");
+  finish_transform(*t);
+  *out = t.release();
+  return PANO_OK;
+}
+
+int panorama_shape_transform(const pano_transform* t, int32_t n_levels, double kappa,
+                             const double* gauss, int32_t* blocks, pano_transform** out) {
+  clear_error();
+  PANO_CHECK(t && gauss && out, PANO_EINVAL, "null argument");
+  const int d = t->d, L = n_levels;
+  PANO_CHECK(L >= 1 && d % L == 0, PANO_EINVAL, "n_levels must divide d");
+  PANO_CHECK(std::isfinite(kappa) && kappa >= 1.0, PANO_EINVAL, "kappa must be >= 1");
+  PANO_CHECK((int)t->lam.size() == d, PANO_EINVAL, "the transform has no coordinate variances");
+  for (size_t i = 0; i < (size_t)2 * d * d; ++i)
+    PANO_CHECK(std::isfinite(gauss[i]), PANO_EINVAL, "non-finite Gaussian draw");
+  const int b = d / L;
+  const double* G1 = gauss;
+  const double* G2 = gauss + (size_t)d * d;
+  std::vector<double> v(t->lam);
+  double tot = 0.0;
+  for (double x : v) tot += x;
+  const double cap = kappa * tot / L;
+  const double tie = 1e-12;
+  auto tn = std::make_unique<pano_transform>();
+  tn->d = d;
+  tn->mu = t->mu;
+  tn->T = t->T;
+  std::vector<std::pair<int, int>> bl;
+  std::vector<double> Q;
+  // Procedure 1: Robin Hood inter-level shaping
+  for (int l = 0; l < L; ++l) {
+    const int a = l * b;
+    double E = 0.0;
+    for (int j = a; j < a + b; ++j) E += v[j];
+    if (E <= cap * (1 + tie)) continue;
+    int s = 1;
+    double sum = E + v[a + b];
+    while (a + b + s < d && (double)b * sum > cap * (b + s) * (1 + tie)) {
+      sum += v[a + b + s];
+      ++s;
+    }
+    const int nb = b + s;
+    haar_q(G1 + (size_t)a * d + a, d, nb, Q);
+    rotate_rows(tn->T, d, a, nb, Q);
+    double bs = 0.0;
+    for (int j = a; j < a + nb; ++j) bs += v[j];
+    for (int j = a; j < a + nb; ++j) v[j] = bs / nb;
+    bl.emplace_back(a, nb);
+  }
+  // Procedure 2: intra-level isotropisation
+  for (int l = 0; l < L; ++l) {
+    const int a = l * b;
+    haar_q(G2 + (size_t)a * d + a, d, b, Q);
+    rotate_rows(tn->T, d, a, b, Q);
+    double E = 0.0;
+    for (int j = a; j < a + b; ++j) E += v[j];
+    for (int j = a; j < a + b; ++j) v[j] = E / b;
+  }
+  tn->lam = v;
+  finish_transform(*tn);
+  if (blocks) {
+    for (int i = 0; i < 2 * L; ++i) blocks[i] = -1;
+    for (size_t i = 0; i < bl.size() && (int)i < L; ++i) {
+      blocks[2 * i] = bl[i].first;
+      blocks[2 * i + 1] = bl[i].second;
+    }
+  }
+  *out = tn.release();
+  return PANO_OK;
+}
+
+int panorama_build_ivfpq(const pano_transform* t, const float* X, int64_t n, int32_t nlist,
+                         const pano_pq_build_opts* opts, void* stream, pano_index** out) {
+  clear_error();
+  return build_ivfpq(t, X, n, nlist, opts, (cudaStream_t)stream, out);
+}
+
+int panorama_search_pq(const pano_index* idx, const float* queries, int64_t nq, int32_t nprobe,
+                       int32_t k, int64_t* out_ids, float* out_dists, int32_t mode,
+                       int32_t collect_stats, void* stream) {
+  clear_error();
+  return search_pq(idx, queries, nq, nprobe, k, out_ids, out_dists, mode, collect_stats,
+                   (cudaStream_t)stream);
+}
+
+int panorama_pq_export(const pano_index* idx, float* codebooks, uint8_t* codes, int32_t* M_out) {
+  clear_error();
+  PANO_CHECK(idx && idx->pq_M > 0, PANO_EINVAL, "not an IVFPQ index");
+  const pano_index& I = *idx;
+  const int M = I.pq_M;
+  if (M_out) *M_out = M;
+  if (codebooks)
+    PANO_CUDA(cudaMemcpy(codebooks, I.pq_codebook.p, (size_t)M * PQ_KSUB * I.pq_dsub * 4,
+                         cudaMemcpyDeviceToHost));
+  if (codes) {
+    const int64_t nslots = I.n_chunks * PQ_B;
+    std::vector<uint8_t> lay((size_t)std::max<int64_t>(nslots, 1) * M);
+    std::vector<int32_t> ids((size_t)std::max<int64_t>(nslots, 1));
+    PANO_CUDA(cudaMemcpy(lay.data(), I.pq_codes.p, (size_t)nslots * M, cudaMemcpyDeviceToHost));
+    PANO_CUDA(cudaMemcpy(ids.data(), I.ids.p, (size_t)nslots * 4, cudaMemcpyDeviceToHost));
+    for (int64_t s = 0; s < nslots; ++s) {
+      if (ids[s] < 0) continue;
+      for (int m = 0; m < M; ++m)
+        codes[(size_t)ids[s] * M + m] = lay[((s / PQ_B) * M + m) * PQ_B + s % PQ_B];
+    }
+  }
+  return PANO_OK;
+}
+
+int panorama_debug_pq_encode(const float* R, int64_t n, int32_t d, int32_t M,
+                             const float* codebooks, uint8_t* codes, void* stream) {
+  clear_error();
+  return debug_pq_encode(R, n, d, M, codebooks, codes, (cudaStream_t)stream);
+}
+
+}  // extern "C"

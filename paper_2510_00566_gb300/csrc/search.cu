@@ -1477,6 +1477,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
   PANO_CHECK(ip, PANO_EINVAL, "null index");
   const pano_index& I = *ip;
   PANO_CHECK(!I.flat, PANO_EINVAL, "a flat index is searched with panorama_refine");
+  PANO_CHECK(!I.pq_M, PANO_EINVAL, "an IVFPQ index is searched with panorama_search_pq");
   PANO_CHECK(nq >= 0 && nq < (1LL << 31), PANO_EINVAL, "nq out of range");
   PANO_CHECK(nq == 0 || (queries && out_ids && out_dists), PANO_EINVAL, "null argument");
   PANO_CHECK(k_max >= 1 && k_max <= 1024, PANO_EINVAL, "k_max must be in [1, 1024]");

@@ -25,4 +25,6 @@ int build_ivf(const pano_transform* t, const float* X, int64_t n, int nlist,
 int make_levels(int d, const pano_build_opts* o, std::vector<int32_t>& widths,
                 std::vector<int32_t>& offs);
 int check_device(int* dev_out);
+int coarse_lists(const float* Xd, int64_t n, int d, int nlist, const pano_build_opts* o,
+                 cudaStream_t st, pano_index& I);
 }  // namespace pano

@@ -1,5 +1,5 @@
 """CPU-side checks of the C-ABI library: it loads, exports every symbol that
-include/panorama.h declares, reports errors, and its host-only PCA fit agrees
+include/*.h declares, reports errors, and its host-only PCA fit agrees
 with the oracle (no GPU compute is called here)."""
 import ctypes
 import re
@@ -21,7 +21,9 @@ def L():
 
 
 def declared_functions():
-    text = open(HEADER).read() + open(HEADER.replace("panorama.h", "panorama_debug.h")).read()
+    import glob
+    text = "".join(open(h).read() for h in
+                   sorted(glob.glob(_build.os.path.join(_build.ROOT, "include", "*.h"))))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(panorama_\w+)\s*\(", text)))
 

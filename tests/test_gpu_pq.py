@@ -1,0 +1,233 @@
+"""GPU parity of IVFPQ Panorama (Section 6.3) with spectrum shaping (Section
+4.3).  The oracle supplies the shaped transform, centroids, lists, codebooks
+and codes (or checks the library's own), and computes the FP64 answer; the
+library's pruned search must equal its plain scan bit for bit, and both must
+match the oracle: ids equal except where FP64 distances tie within 2e-5
+(two FP32 sums of M terms, each within 1e-5, may swap), distances within
+1e-5 relative."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import pq
+import paper_2510_00566_gb300 as pano
+import synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+RTOL_D = 1e-5
+RTOL_TIE = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_00566_gb300 import _build
+    _build.build()
+    pano.lib()
+
+
+def _oracle_dists(Q, Ts, mu, C, lists, cb, codes, probes):
+    """Per query: candidate ids and FP64 asymmetric distances over its probes."""
+    tq = oracle.transform(Ts, mu, Q)
+    tc = oracle.transform(Ts, mu, C)
+    xh = pq.pq_reconstruct(codes, cb)
+    out = []
+    for i in range(len(Q)):
+        mem = np.concatenate([np.nonzero(lists == c)[0] for c in probes[i]])
+        own = lists[mem]
+        D = ((tq[i][None] - tc[own] - xh[mem]) ** 2).sum(1)
+        out.append((mem, D))
+    return out
+
+
+def _check(got_i, got_d, cand, k, keep):
+    got_i, got_d = got_i.cpu().numpy(), got_d.cpu().numpy().astype(np.float64)
+    worst = 0.0
+    for i in np.nonzero(keep)[0]:
+        mem, D = cand[i]
+        order = np.lexsort((mem, D))[:k]
+        nv = order.size
+        assert np.all(got_i[i, nv:] == -1) and np.all(np.isinf(got_d[i, nv:])), i
+        g = got_i[i, :nv]
+        assert len(set(g.tolist())) == nv and np.all(np.isin(g, mem)), (i, g)
+        pos = {int(v): j for j, v in enumerate(mem)}
+        true = D[[pos[int(v)] for v in g]]
+        rel = np.abs(got_d[i, :nv] - true) / np.maximum(true, 1e-30)
+        worst = max(worst, float(rel.max()))
+        assert np.all(rel <= RTOL_D), (i, rel.max())
+        mism = g != mem[order]
+        if mism.any():
+            gap = np.abs(true[mism] - D[order][mism]) / np.maximum(D[order][mism], 1e-30)
+            assert np.all(gap <= RTOL_TIE), (i, g[mism], mem[order][mism], gap)
+        assert np.all(np.diff(got_d[i, :nv]) >= 0)
+    return worst
+
+
+def _shaped(X, L, kappa, seed):
+    mu, T, lam = oracle.pca_fit(X[:65536])
+    G = np.random.default_rng(seed).standard_normal((2, X.shape[1], X.shape[1]))
+    Ts, vs, _ = pq.shape_transform(T, lam, L, kappa, G[0], G[1])
+    return Ts, mu, vs
+
+
+def _search_both(idx, Q, nprobe, k):
+    q = torch.from_numpy(Q).to(DEV)
+    a = idx.search_pq(q, nprobe, k, mode=0, collect_stats=True)
+    st0 = pano.last_stats()
+    b = idx.search_pq(q, nprobe, k, mode=1, collect_stats=True)
+    st1 = pano.last_stats()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]), "pruned != plain scan"
+    return a, st0, st1
+
+
+def test_pq_960d_shaped_parity_and_pruning():
+    """The 1M x 960 workload's recipe at 12k vectors: 16 lists, M = 480
+    (2-d subvectors), 16 levels of 60 coordinates, kappa = 4."""
+    s = synth.scaled(2, n=12_000, n_queries=40, nlist=16, n_clusters=16)
+    w = synth.generate(s)
+    X, Q = w.X.numpy(), w.Q.numpy()
+    d, L, M, nl = 960, 16, 480, 16
+    Ts, mu, vs = _shaped(X, L, 4.0, 11)
+    C = synth.initial_centroids(w.X, nl, seed=3002).numpy()
+    lists, _ = oracle.assign(X, C)
+    R = oracle.transform(Ts, mu, X) - oracle.transform(Ts, mu, C)[lists]
+    g = np.random.default_rng(12)
+    cb = pq.pq_train(R[g.choice(len(R), 2000, replace=False)], M, iters=1, seed=13)
+    codes = pq.pq_encode32(R.astype(np.float32), cb)
+    t = pano.panorama_transform_import(Ts, mu, vs)
+    idx = pano.panorama_build_ivfpq(t, w.X.to(DEV), nl, M, L, centroids=C, assign=lists,
+                                    codebooks=cb, codes=codes)
+    info = idx.info()
+    assert info.precision == pano.PANO_PQ and info.chunk == 256
+    k, nprobe = 10, 4
+    (ids, dd), st0, st1 = _search_both(idx, Q, nprobe, k)
+    probes, gap = oracle.probe(Q, C, nprobe)
+    cand = _oracle_dists(Q, Ts, mu, C, lists, cb, codes, probes)
+    worst = _check(ids, dd, cand, k, gap >= 1e-6)
+    assert worst < RTOL_D
+    pairs = sum(len(c[0]) for c in cand)
+    assert st1.pairs == pairs and st1.dims_scanned == pairs * d
+    assert st0.pairs == pairs and st0.dims_scanned < 0.9 * st1.dims_scanned
+    # Algorithm 1 over the same codes (lists in probe order, batches of 1024)
+    tq = oracle.transform(Ts, mu, Q)
+    tc = oracle.transform(Ts, mu, C)
+    xh = pq.pq_reconstruct(codes, cb)
+    m = oracle.level_thresholds(d, [d // L] * L)
+    dims = 0
+    for i in range(len(Q)):
+        mems = [np.nonzero(lists == c)[0] for c in probes[i]]
+        _, _, di = pq.ivfpq_panorama([tq[i] - tc[c] for c in probes[i]],
+                                     [xh[mm] for mm in mems], mems, m, k)
+        dims += di
+    assert st0.dims_scanned <= 1.5 * dims + 0.02 * pairs * d, (st0.dims_scanned, dims)
+
+
+def test_pq_ragged_lists_slabs_and_padding():
+    """Lists of 4500 (three slabs), 1, 0 and the rest of 7000 vectors; random
+    codes; k from 1 to 100; a query whose only probed list has one member."""
+    g = np.random.default_rng(20)
+    d, L, M = 64, 4, 32
+    n = 7000
+    X = (g.standard_normal((n, d)) * np.exp(-0.04 * np.arange(d))).astype(np.float32)
+    lists = np.full(n, 3, np.int32)
+    lists[:4500] = 0
+    lists[4500] = 1
+    C = np.stack([X[lists == 0].mean(0), X[4500], 5 + X[:10].mean(0), X[lists == 3].mean(0)])
+    C = C.astype(np.float32)
+    C[0] += 0.3
+    Ts, mu, vs = _shaped(X, L, 2.0, 21)
+    cb = (g.standard_normal((M, 256, d // M)) * 0.3).astype(np.float32)
+    codes = g.integers(0, 256, (n, M)).astype(np.uint8)
+    t = pano.panorama_transform_import(Ts, mu, vs)
+    idx = pano.panorama_build_ivfpq(t, X, 4, M, L, centroids=C, assign=lists, codebooks=cb,
+                                    codes=codes)
+    Q = np.concatenate([g.standard_normal((30, d)).astype(np.float32) * 0.5,
+                        X[4500:4501] + 1e-3]).astype(np.float32)
+    for nprobe, k in ((1, 1), (1, 10), (2, 10), (4, 100), (3, 37)):
+        (ids, dd), _, _ = _search_both(idx, Q, nprobe, k)
+        probes, gap = oracle.probe(Q, C, nprobe)
+        cand = _oracle_dists(Q, Ts, mu, C, lists, cb, codes, probes)
+        _check(ids, dd, cand, k, gap >= 1e-6)
+    ids, dd = idx.search_pq(torch.from_numpy(Q[-1:]).to(DEV), 1, 10)
+    assert ids[0, 0].item() == 4500 and torch.all(ids[0, 1:] == -1)
+
+
+@pytest.mark.parametrize("dsub", [1, 2, 3, 8])
+def test_pq_encoder_bit_exact(dsub):
+    g = np.random.default_rng(30 + dsub)
+    M, n = 12, 3000
+    d = M * dsub
+    cb = g.standard_normal((M, 256, dsub)).astype(np.float32)
+    cb[:, 200] = cb[:, 17]  # duplicated codewords: the lower index wins
+    R = g.standard_normal((n, d)).astype(np.float32)
+    R[:50] = cb[:, 17].reshape(-1)[None, :]
+    got = pano.panorama_debug_pq_encode(torch.from_numpy(R).to(DEV),
+                                        torch.from_numpy(cb).to(DEV)).cpu().numpy()
+    want = pq.pq_encode32(R, cb)
+    assert np.array_equal(got, want)
+    assert np.all(got[:50] == 17)
+
+
+def test_pq_library_trained_index():
+    """No quantiser given: k-means lists, PQ k-means and the device encoder.
+    Codes are the nearest codewords of the FP64 residuals up to FP32
+    rounding; the pruned search equals the plain scan; recall of the exact
+    neighbours among the probed candidates is that of a working PQ."""
+    s = synth.scaled(4, n=20_000, n_queries=60, nlist=20, n_clusters=20)
+    w = synth.generate(s)
+    X, Q = w.X.numpy(), w.Q.numpy()
+    d, L, M = X.shape[1], 8, 96
+    mu, T, lam = oracle.pca_fit(X)
+    t0 = pano.panorama_transform_import(T, mu, lam)
+    G = np.random.default_rng(40).standard_normal((2, d, d))
+    t, _ = pano.panorama_shape_transform(t0, L, 2.0, G)
+    Ts, _, vs = t.export()
+    idx = pano.panorama_build_ivfpq(t, w.X.to(DEV), 20, M, L, pq_iters=8)
+    C = idx.centroids()
+    lists = idx.assignment()
+    cb, codes = pano.panorama_pq_export(idx)
+    R = oracle.transform(Ts, mu, X) - oracle.transform(Ts, mu, C)[lists]
+    dsub = d // M
+    for m in range(0, M, 7):
+        sub = R[:, m * dsub:(m + 1) * dsub]
+        dd = ((sub[:, None, :] - cb[m][None].astype(np.float64)) ** 2).sum(-1)
+        got = dd[np.arange(len(R)), codes[:, m]]
+        assert np.all(got <= dd.min(1) + 1e-4 * (1 + dd.min(1))), m
+    k, nprobe = 10, 5
+    (ids, dd), _, _ = _search_both(idx, Q, nprobe, k)
+    probes, gap = oracle.probe(Q, C, nprobe)
+    cand = _oracle_dists(Q, Ts, mu, C, lists, cb, codes, probes)
+    _check(ids, dd, cand, k, gap >= 1e-6)
+    ids = ids.cpu().numpy()
+    rec = []
+    for i in range(len(Q)):
+        mem = cand[i][0]
+        ex = ((X[mem].astype(np.float64) - Q[i]) ** 2).sum(1)
+        true = mem[np.argsort(ex)[:k]]
+        rec.append(len(set(true) & set(ids[i])) / k)
+    assert np.mean(rec) >= 0.4, np.mean(rec)
+
+
+def test_pq_argument_errors(tmp_path):
+    g = np.random.default_rng(50)
+    X = g.standard_normal((600, 32)).astype(np.float32)
+    t = pano.panorama_fit_transform(X, n_levels=4)
+    for M, L in ((5, 4), (8, 3), (12, 4)):
+        with pytest.raises(pano.LibraryError):
+            pano.panorama_build_ivfpq(t, X, 2, M, L)
+    idx = pano.panorama_build_ivfpq(t, X, 2, 16, 4, pq_iters=2)
+    q = torch.from_numpy(X[:4]).to(DEV)
+    with pytest.raises(pano.LibraryError):
+        idx.search(q, 1, 5)
+    with pytest.raises(pano.LibraryError):
+        idx.search_pq(q, 3, 5)  # nprobe > nlist
+    with pytest.raises(pano.LibraryError):
+        pano.panorama_save(idx, str(tmp_path / "pq.pano"))
+    flat = pano.panorama_build_ivf(t, X, 2, n_levels=4)
+    with pytest.raises(pano.LibraryError):
+        flat.search_pq(q, 1, 5)
+    ids, dd = idx.search_pq(q, 2, 5)
+    assert torch.all(ids[:, 0] >= 0)
