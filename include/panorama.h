@@ -289,7 +289,7 @@ int panorama_probe(const pano_index* idx, const float* queries, int64_t nq,
  * A plan is one search of a fixed batch shape captured into a CUDA graph:
  * workspace allocation, memsets, transform and probe GEMMs, work inversion,
  * the two persistent verify kernels and the decode replay with a single
- * cudaGraphLaunch (SURVEY "persistent graph-captured scheduler").
+ * cudaGraphLaunch.
  * panorama_plan_create runs the search once eagerly (so kernel attributes
  * are settled), then captures it on a private stream.  The device pointers
  * (queries, nprobe, k, out_ids, out_dists) are baked into the graph: every

@@ -341,6 +341,59 @@ __device__ __forceinline__ float threshold_of(const unsigned long long* slots, i
   return key == kEmptyKey ? INFINITY : key_dist(key);
 }
 
+// One level's partial distance of one candidate whose codes start at cp
+// (subquantiser rows PQ_B bytes apart), terms added in subquantiser order;
+// codes are loaded eight at a time so their latencies overlap.
+template <bool LUT>
+__device__ __forceinline__ float level_sum1(const uint8_t* __restrict__ cp, int ML, int m0,
+                                            const float* lut, const float* r,
+                                            const float* __restrict__ cb, int dsub) {
+  float S = 0.f;
+  for (int mm0 = 0; mm0 < ML; mm0 += 8) {
+    int code[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) code[u] = mm0 + u < ML ? __ldg(cp + (size_t)(mm0 + u) * PQ_B) : 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (mm0 + u < ML) {
+        const int m = m0 + mm0 + u;
+        const float e = LUT ? lut[(mm0 + u) * PQ_KSUB + code[u]]
+                            : pq_term(r + m * dsub, cb + ((size_t)m * PQ_KSUB + code[u]) * dsub,
+                                      dsub);
+        S = mm0 + u == 0 ? e : __fadd_rn(S, e);
+      }
+    }
+  }
+  return S;
+}
+
+// The same for four consecutive candidates (one 32-bit load carries their
+// four codes of a subquantiser), four subquantisers per round.
+template <bool LUT>
+__device__ __forceinline__ void level_sum4(const uint32_t* __restrict__ cp, int ML, int m0,
+                                           const float* lut, const float* r,
+                                           const float* __restrict__ cb, int dsub, float S[4]) {
+  for (int mm0 = 0; mm0 < ML; mm0 += 4) {
+    uint32_t w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) w[u] = mm0 + u < ML ? __ldg(cp + (size_t)(mm0 + u) * (PQ_B / 4)) : 0u;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (mm0 + u < ML) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int code = (w[u] >> (8 * c)) & 255;
+          const int m = m0 + mm0 + u;
+          const float e = LUT ? lut[(mm0 + u) * PQ_KSUB + code]
+                              : pq_term(r + m * dsub, cb + ((size_t)m * PQ_KSUB + code) * dsub,
+                                        dsub);
+          S[c] = mm0 + u == 0 ? e : __fadd_rn(S[c], e);
+        }
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(PQ_NT) pq_verify_kernel(const PqArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int d = a.d, L = a.L, ML = a.ML, M = a.M, dsub = a.dsub;
@@ -412,52 +465,86 @@ __global__ void __launch_bounds__(PQ_NT) pq_verify_kernel(const PqArgs a) {
       const float tau = __int_as_float(ctr[2]);
       const float sql = sq[l];
       const int nxt = cur ^ 1;
-      for (int i0 = 0; i0 < nl; i0 += PQ_NT) {
+      // Eq. 3 in partial-distance form, margined (see search_pq): keep unless
+      // (1 - gamma) (P + max(0, |s_q - s_x| - 8u (s_q + s_x))^2) > tau
+      auto passes = [&](float P, float sx) {
+        if (!a.prune) return true;
+        float gap = fabsf(__fsub_rn(sql, sx)) - a.erel * (sql + sx);
+        gap = fmaxf(gap, 0.f);
+        const float lb = __fmaf_rn(gap, gap, P);
+        return !(lb * a.lo > tau);
+      };
+      // level 0 visits every candidate of the slab: four consecutive ones per
+      // thread (one 32-bit code load per subquantiser); deeper levels visit
+      // the live list, one candidate per thread
+      const bool dense = l == 0;
+      const int nunits = dense ? (ns + 3) >> 2 : nl;
+      for (int i0 = 0; i0 < nunits; i0 += PQ_NT) {
         const int i = i0 + tid;
-        bool keep = false;
-        int cand = 0;
-        float P = 0.f;
-        if (i < nl) {
-          cand = l == 0 ? i : live[cur * PQ_S + i];
-          if (l > 0) P = pacc[cur * PQ_S + i];
-          const int g = s0 + cand;
+        bool keep[4] = {false, false, false, false};
+        float Pv[4] = {0.f, 0.f, 0.f, 0.f};
+        int cand0 = 0;
+        if (i < nunits && dense) {
+          cand0 = 4 * i;
+          const int g = s0 + cand0;
+          const int64_t blk = blk0 + g / PQ_B;
+          const int ln = g % PQ_B;
+          const uint32_t* cp = reinterpret_cast<const uint32_t*>(a.codes + blk * M * PQ_B + ln);
+          float S[4];
+          if (use_lut)
+            level_sum4<true>(cp, ML, 0, lut, r, a.codebook, dsub, S);
+          else
+            level_sum4<false>(cp, ML, 0, lut, r, a.codebook, dsub, S);
+          float sxv[4] = {0.f, 0.f, 0.f, 0.f};
+          if (!last) {
+            const float4 t4 = *reinterpret_cast<const float4*>(a.xtail + blk * L * PQ_B + ln);
+            sxv[0] = t4.x;
+            sxv[1] = t4.y;
+            sxv[2] = t4.z;
+            sxv[3] = t4.w;
+          }
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            if (cand0 + c >= ns) continue;
+            const float P = __fadd_rn(0.f, S[c]);
+            Pv[c] = P;
+            if (last) {
+              const unsigned long long key = make_key(P, a.ids[blk * PQ_B + ln + c]);
+              if (key < ld_volatile_u64(slots + a.k - 1)) topk_insert_thread(slots, a.k, key);
+            } else {
+              keep[c] = passes(P, sxv[c]);
+            }
+          }
+        } else if (i < nunits) {
+          cand0 = live[cur * PQ_S + i];
+          const int g = s0 + cand0;
           const int64_t blk = blk0 + g / PQ_B;
           const int ln = g % PQ_B;
           const uint8_t* cp = a.codes + (blk * M + (int64_t)l * ML) * PQ_B + ln;
-          float S = 0.f;
-          for (int mm = 0; mm < ML; ++mm) {
-            const int code = cp[(size_t)mm * PQ_B];
-            const int m = l * ML + mm;
-            const float e = use_lut ? lut[mm * PQ_KSUB + code]
-                                    : pq_term(r + m * dsub,
-                                              a.codebook + ((size_t)m * PQ_KSUB + code) * dsub,
-                                              dsub);
-            S = mm == 0 ? e : __fadd_rn(S, e);
-          }
-          P = __fadd_rn(P, S);
+          const float S = use_lut ? level_sum1<true>(cp, ML, l * ML, lut, r, a.codebook, dsub)
+                                  : level_sum1<false>(cp, ML, l * ML, lut, r, a.codebook, dsub);
+          const float P = __fadd_rn(pacc[cur * PQ_S + i], S);
+          Pv[0] = P;
           if (last) {
             const unsigned long long key = make_key(P, a.ids[blk * PQ_B + ln]);
             if (key < ld_volatile_u64(slots + a.k - 1)) topk_insert_thread(slots, a.k, key);
           } else {
-            keep = true;
-            if (a.prune) {
-              const float sx = a.xtail[(blk * L + l) * PQ_B + ln];
-              float gap = fabsf(__fsub_rn(sql, sx)) - a.erel * (sql + sx);
-              gap = fmaxf(gap, 0.f);
-              const float lb = __fmaf_rn(gap, gap, P);
-              keep = !(lb * a.lo > tau);
-            }
+            keep[0] = passes(P, a.xtail[(blk * L + l) * PQ_B + ln]);
           }
         }
-        const unsigned ball = __ballot_sync(0xffffffffu, keep);
-        if (ball) {
-          int base = 0;
-          if (lane == 0) base = atomicAdd(&ctr[0], __popc(ball));
-          base = __shfl_sync(0xffffffffu, base, 0);
-          if (keep) {
-            const int at = base + __popc(ball & ((1u << lane) - 1));
-            live[nxt * PQ_S + at] = (uint16_t)cand;
-            pacc[nxt * PQ_S + at] = P;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (c > 0 && !dense) break;
+          const unsigned ball = __ballot_sync(0xffffffffu, keep[c]);
+          if (ball) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&ctr[0], __popc(ball));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (keep[c]) {
+              const int at = base + __popc(ball & ((1u << lane) - 1));
+              live[nxt * PQ_S + at] = (uint16_t)(cand0 + c);
+              pacc[nxt * PQ_S + at] = Pv[c];
+            }
           }
         }
       }
