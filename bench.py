@@ -37,6 +37,7 @@ KERNELS_PER_SEARCH = 14  # see the launch list in profiles/
 # capture of a smaller case of the same kernel scaled to the full launch
 # (profiles/ holds the capture summary); None once the kernel has changed.
 TRAFFIC = {"ivf-1m-d960-fp32": 834.49e6 + 3.38e6}  # phase B, ncu at full size, one pass
+PQ_TRAFFIC = {"ivf-1m-d960-fp32": 768.1e6 + 1.3e6}  # pruned pq_verify_kernel, same capture
 
 
 def parse():
@@ -506,23 +507,24 @@ def main():
             for _ in range(args.warmup):
                 idxp.search_pq(Q, s.nprobe, k, mode=mode)
             torch.cuda.synchronize()
-            tot = 0.0
+            tot, vms = 0.0, []
             for _ in range(steps):
                 flush.zero_()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                idxp.search_pq(Q, s.nprobe, k, mode=mode)
+                idxp.search_pq(Q, s.nprobe, k, mode=mode, collect_timing=True)
                 e1.record(stream)
                 e1.synchronize()
                 tot += e0.elapsed_time(e1)
+                vms.append(pano.last_stats().stage_ms[4])
             tp = torch.tensor([tot], device=dev)
             if world > 1:
                 dist.all_reduce(tp, op=dist.ReduceOp.MAX)
-            return tp.item() / steps
+            return tp.item() / steps, float(np.median(vms))
 
-        msp = pq_timed(0, args.steps)
-        msp_scan = pq_timed(1, args.scan_steps)
+        msp, vmsp = pq_timed(0, args.steps)
+        msp_scan, _ = pq_timed(1, args.scan_steps)
         idxp.search_pq(Q, s.nprobe, k, collect_stats=True)
         stp = pano.last_stats().as_dict()
         ivfpq = {"M": s.d // 2, "nbits": 8, "levels": f"{s.n_levels}x{s.d // s.n_levels}",
@@ -533,6 +535,16 @@ def main():
                                    "speedup_of_pruned": msp_scan / msp},
                  "dims_scanned_frac": stp["dims_scanned"] / max(1, stp["pairs"] * s.d),
                  "tables_built": stp["tile_levels"], "pairs": stp["pairs"],
+                 # the verify kernel: one shared-memory table lookup per
+                 # (live pair, subquantiser); peak = one conflict-free 32-lane
+                 # shared-memory wavefront per SM per clock
+                 "roofline": {"bound": "lsu", "kernel": "pq_verify_kernel",
+                              "achieved": stp["dims_scanned"] / 2 / (vmsp / 1e3),
+                              "peak": 152 * 32 * sm_max * 1e6, "unit": "lookups/s",
+                              "frac": stp["dims_scanned"] / 2 / (vmsp / 1e3)
+                              / (152 * 32 * sm_max * 1e6),
+                              "traffic": PQ_TRAFFIC.get(s.name), "ms_per_launch": vmsp,
+                              "lookups_per_launch": stp["dims_scanned"] / 2},
                  "index_gb": idxp.info().device_bytes / 1e9, "build_s": build_s}
         del idxp, tsh
 

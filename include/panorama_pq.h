@@ -121,10 +121,12 @@ int panorama_build_ivfpq(const pano_transform* t, const float* X, int64_t n, int
  *   out_ids / out_dists: device nq x k, ascending (distance, id), padded with
  *             (-1, +inf) when fewer than k candidates exist.
  *   mode:     0 = pruned, 1 = plain scan (every level of every candidate).
- *   collect_stats: nonzero = count pairs, dims_scanned (coordinates whose
+ *   collect_stats: bit 0 = count pairs, dims_scanned (coordinates whose
  *             subvector terms were added), pair_levels, reranked (candidates
  *             that reached the last level), tile_levels (tables built);
- *             read with panorama_search_stats.
+ *             bit 1 = CUDA-event times of the stages in stage_ms (transform,
+ *             probe, pair order and seeds, -, verify, decode); read with
+ *             panorama_search_stats.
  * Blocks until the results are written.
  * Errors: PANO_EINVAL (not an IVFPQ index, sizes), PANO_ENOMEM, PANO_ECUDA,
  *         PANO_ENODEV, PANO_ETIMEOUT never (no device-side waits). */

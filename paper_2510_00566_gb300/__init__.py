@@ -433,9 +433,10 @@ def panorama_build_ivfpq(t: "Transform", X, nlist: int, M: int, n_levels: int,
 
 
 def panorama_search_pq(idx: "Index", queries, nprobe: int, k: int, mode=0,
-                       collect_stats=False, stream=None, out=None):
+                       collect_stats=False, stream=None, out=None, collect_timing=False):
     """(ids int64 [nq, k], dists float32 [nq, k]) on the GPU; mode 1 = plain
-    scan."""
+    scan; collect_timing fills stage_ms (transform, probe, pairs + seeds, -,
+    verify, decode)."""
     import torch
     q = queries.contiguous()
     assert q.is_cuda and q.dtype == torch.float32
@@ -447,7 +448,8 @@ def panorama_search_pq(idx: "Index", queries, nprobe: int, k: int, mode=0,
         ids, dists = out
     _check(lib().panorama_search_pq(idx.handle, q.data_ptr(), nq, int(nprobe), int(k),
                                     ids.data_ptr(), dists.data_ptr(), int(mode),
-                                    1 if collect_stats else 0, _stream_ptr(stream)))
+                                    (1 if collect_stats else 0) | (2 if collect_timing else 0),
+                                    _stream_ptr(stream)))
     return ids, dists
 
 

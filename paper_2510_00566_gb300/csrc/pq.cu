@@ -935,6 +935,7 @@ int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe
   std::memset(&S, 0, sizeof(S));
   S.n_queries = nq;
   if (nq == 0) return PANO_OK;
+  const bool counts = (collect & 1) != 0, timing = (collect & 2) != 0;
   int cur = 0;
   PANO_CUDA(cudaGetDevice(&cur));
   PANO_CHECK(cur == I.device, PANO_EINVAL, "current device differs from the index's device");
@@ -968,16 +969,25 @@ int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe
   unsigned long long* topk = (unsigned long long*)(W + o_topk);
   unsigned long long* stats = (unsigned long long*)(W + o_stats);
 
+  cudaEvent_t ev[6] = {};
+  if (timing)
+    for (auto& e : ev) PANO_CUDA(cudaEventCreate(&e));
+  auto mark = [&](int i) {
+    if (timing) cudaEventRecord(ev[i], st);
+  };
   auto body = [&]() -> int {
     PANO_CUDA(cudaMemsetAsync(cnt, 0, (size_t)2 * nlist * 4, st));
     PANO_CUDA(cudaMemsetAsync(fill, 0, (size_t)2 * nlist * 4, st));
     PANO_CUDA(cudaMemsetAsync(topk, 0xff, (size_t)nq * k * 8, st));
     PANO_CUDA(cudaMemsetAsync(stats, 0, 8 * 8, st));
     // q~ = T~(q - mu~)
+    mark(0);
     PANO_CUDA(gemm_nt(kStore, (int)nq, d, d, queries, d, I.mu32.as<float>(), I.T32.as<float>(),
                       d, qt, d, nullptr, nullptr, st));
+    mark(1);
     int rc = probe_only(ip, queries, nq, nprobe, probes, st);
     if (rc) return rc;
+    mark(2);
     const unsigned pg = (unsigned)((npairs + 255) / 256);
     pq_pair_count_kernel<<<pg, 256, 0, st>>>(probes, nq, nprobe, nlist, cnt);
     pq_pair_scan_kernel<<<1, 1024, 0, st>>>(cnt, 2 * nlist, poff);
@@ -1005,7 +1015,7 @@ int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe
     a.b = d / L;
     a.k = k;
     a.prune = mode == 0 ? 1 : 0;
-    a.collect = collect ? 1 : 0;
+    a.collect = counts ? 1 : 0;
     // D~ >= (1-u)^(L + ML + dsub + 2) (D_head~ + (sqrt R_q - sqrt R_x)^2) (level
     // and subquantiser sums of non-negative terms, each term's subtraction,
     // square and additions); the computed bound and its scaling add three
@@ -1023,18 +1033,35 @@ int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe
                                    (int)ssm));
     pq_seed_kernel<<<(unsigned)nq, 256, ssm, st>>>(a, probes, nprobe);
     PANO_CUDA(cudaGetLastError());
+    mark(3);
     const size_t vsm = pq_verify_smem(d, L, ML);
     PANO_CUDA(cudaFuncSetAttribute(pq_verify_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)vsm));
     pq_verify_kernel<<<(unsigned)npairs, PQ_NT, vsm, st>>>(a);
     PANO_CUDA(cudaGetLastError());
+    mark(4);
     pq_decode_kernel<<<(unsigned)((nq * k + 255) / 256), 256, 0, st>>>(topk, nq * k, out_ids,
                                                                       out_dists);
     PANO_CUDA(cudaGetLastError());
+    mark(5);
     unsigned long long hs[8] = {};
     PANO_CUDA(cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
     PANO_CUDA(cudaStreamSynchronize(st));
-    if (collect) {
+    if (timing) {
+      // stage_ms: transform, probe, pair order + seeds, -, verify, decode
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      S.stage_ms[0] = ms;
+      cudaEventElapsedTime(&ms, ev[1], ev[2]);
+      S.stage_ms[1] = ms;
+      cudaEventElapsedTime(&ms, ev[2], ev[3]);
+      S.stage_ms[2] = ms;
+      cudaEventElapsedTime(&ms, ev[3], ev[4]);
+      S.stage_ms[4] = ms;
+      cudaEventElapsedTime(&ms, ev[4], ev[5]);
+      S.stage_ms[5] = ms;
+    }
+    if (counts) {
       S.pairs = (int64_t)hs[0];
       S.dims_scanned = (int64_t)hs[1];
       S.pair_levels = (int64_t)hs[2];
@@ -1046,6 +1073,8 @@ int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe
   };
   int rc = body();
   cudaFreeAsync(ws, st);
+  if (timing)
+    for (auto& e : ev) cudaEventDestroy(e);
   return rc;
 }
 
