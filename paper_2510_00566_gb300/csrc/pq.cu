@@ -40,6 +40,7 @@ constexpr int PQ_MAXML = 64;     // subquantisers per level
 constexpr int PQ_MAXDSUB = 32;   // coordinates per subvector
 constexpr int PQ_LUT_MIN = 384;  // live candidates from which a level's table is built
 constexpr int PQ_SEED = 64;      // nearest-list members that seed each query's top-k
+constexpr int PQ_DEEP = 512;     // live candidates from which a slab finishes depth-first
 constexpr int PQ_MAXL = 64;
 
 // ------------------------------------------------------------------ host
@@ -341,6 +342,61 @@ __device__ __forceinline__ float threshold_of(const unsigned long long* slots, i
   return key == kEmptyKey ? INFINITY : key_dist(key);
 }
 
+// Table of one level: lut[mm][j] = term(r_m, C_m[j]) for m = m0 + mm.  Four
+// consecutive codewords per thread (their DS-float rows arrive as DS float4
+// loads, 16-byte aligned since j0 % 4 == 0), stored as one float4.
+template <int DS>
+__device__ __forceinline__ void build_table_v(float* lut, const float* r,
+                                              const float* __restrict__ cb, int m0, int ML) {
+  for (int e4 = threadIdx.x; e4 < ML * (PQ_KSUB / 4); e4 += blockDim.x) {
+    const int mm = e4 / (PQ_KSUB / 4), j0 = (e4 % (PQ_KSUB / 4)) * 4;
+    const int m = m0 + mm;
+    const float4* c4 = reinterpret_cast<const float4*>(cb + ((size_t)m * PQ_KSUB + j0) * DS);
+    float cv[4 * DS];
+#pragma unroll
+    for (int t = 0; t < DS; ++t) {
+      const float4 v = __ldg(c4 + t);
+      cv[4 * t] = v.x;
+      cv[4 * t + 1] = v.y;
+      cv[4 * t + 2] = v.z;
+      cv[4 * t + 3] = v.w;
+    }
+    float rv[DS];
+#pragma unroll
+    for (int t = 0; t < DS; ++t) rv[t] = r[m * DS + t];
+    float o[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) o[u] = pq_term(rv, cv + u * DS, DS);
+    *reinterpret_cast<float4*>(lut + mm * PQ_KSUB + j0) = make_float4(o[0], o[1], o[2], o[3]);
+  }
+}
+
+__device__ __forceinline__ void build_table(float* lut, const float* r,
+                                            const float* __restrict__ cb, int m0, int ML,
+                                            int dsub) {
+  switch (dsub) {
+    case 1: build_table_v<1>(lut, r, cb, m0, ML); break;
+    case 2: build_table_v<2>(lut, r, cb, m0, ML); break;
+    case 4: build_table_v<4>(lut, r, cb, m0, ML); break;
+    case 8: build_table_v<8>(lut, r, cb, m0, ML); break;
+    default:
+      for (int e = threadIdx.x; e < ML * PQ_KSUB; e += blockDim.x) {
+        const int m = m0 + e / PQ_KSUB;
+        lut[e] = pq_term(r + m * dsub, cb + ((size_t)m * PQ_KSUB + (e % PQ_KSUB)) * dsub, dsub);
+      }
+  }
+}
+
+// Eq. 3 in partial-distance form, margined (see search_pq): keep unless
+// (1 - gamma) (P + max(0, |s_q - s_x| - 8u (s_q + s_x))^2) > tau.
+__device__ __forceinline__ bool pq_keep(float P, float sx, float sql, float tau, float erel,
+                                        float lo) {
+  float gap = fabsf(__fsub_rn(sql, sx)) - erel * (sql + sx);
+  gap = fmaxf(gap, 0.f);
+  const float lb = __fmaf_rn(gap, gap, P);
+  return !(lb * lo > tau);
+}
+
 // One level's partial distance of one candidate whose codes start at cp
 // (subquantiser rows PQ_B bytes apart), terms added in subquantiser order;
 // codes are loaded eight at a time so their latencies overlap.
@@ -443,36 +499,60 @@ __global__ void __launch_bounds__(PQ_NT) pq_verify_kernel(const PqArgs a) {
   }
   __syncthreads();
 
+  // counters (every thread keeps its own; summed at the end when collecting)
   unsigned long long n_dims = 0, n_lv = 0, n_full = 0, n_lut = 0;
+  int lut_level = -1;  // the level whose table `lut` holds (uniform)
   for (int s0 = 0; s0 < nc; s0 += PQ_S) {
     const int ns = min(PQ_S, nc - s0);
     int nl = ns, cur = 0;
     for (int l = 0; l < L && nl > 0; ++l) {
       const bool last = l == L - 1;
+      if (l > 0 && a.prune && nl <= PQ_DEEP) {
+        // few survivors: each thread walks its own through the remaining
+        // levels (terms straight from the codebook, the same bits as the
+        // tables), stopping at the first level whose test fails; no block
+        // barrier per level
+        for (int i = tid; i < nl; i += PQ_NT) {
+          const int cand = live[cur * PQ_S + i];
+          float P = pacc[cur * PQ_S + i];
+          const int g = s0 + cand;
+          const int64_t blk = blk0 + g / PQ_B;
+          const int ln = g % PQ_B;
+          for (int ll = l; ll < L; ++ll) {
+            const float tq = threshold_of(slots, a.k);
+            const uint8_t* cp = a.codes + (blk * M + (int64_t)ll * ML) * PQ_B + ln;
+            P = __fadd_rn(P, level_sum1<false>(cp, ML, ll * ML, nullptr, r, a.codebook, dsub));
+            n_dims += a.b;
+            ++n_lv;
+            if (ll == L - 1) {
+              ++n_full;
+              const unsigned long long key = make_key(P, a.ids[blk * PQ_B + ln]);
+              if (key < ld_volatile_u64(slots + a.k - 1)) topk_insert_thread(slots, a.k, key);
+            } else if (!pq_keep(P, a.xtail[(blk * L + ll) * PQ_B + ln], sq[ll], tq, a.erel,
+                                a.lo)) {
+              break;
+            }
+          }
+        }
+        __syncthreads();  // the next slab reuses the live list
+        break;
+      }
       if (tid == 0) {
         ctr[0] = 0;
         ctr[2] = __float_as_int(threshold_of(slots, a.k));
       }
       const bool use_lut = nl >= PQ_LUT_MIN;
-      if (use_lut) {
-        for (int e = tid; e < ML * PQ_KSUB; e += PQ_NT) {
-          const int m = l * ML + e / PQ_KSUB;
-          lut[e] = pq_term(r + m * dsub, a.codebook + ((size_t)m * PQ_KSUB + (e % PQ_KSUB)) * dsub,
-                           dsub);
-        }
+      if (use_lut && lut_level != l) {
+        build_table(lut, r, a.codebook, l * ML, ML, dsub);
+        lut_level = l;
+        if (tid == 0) ++n_lut;
       }
       __syncthreads();
       const float tau = __int_as_float(ctr[2]);
       const float sql = sq[l];
       const int nxt = cur ^ 1;
-      // Eq. 3 in partial-distance form, margined (see search_pq): keep unless
-      // (1 - gamma) (P + max(0, |s_q - s_x| - 8u (s_q + s_x))^2) > tau
       auto passes = [&](float P, float sx) {
-        if (!a.prune) return true;
-        float gap = fabsf(__fsub_rn(sql, sx)) - a.erel * (sql + sx);
-        gap = fmaxf(gap, 0.f);
-        const float lb = __fmaf_rn(gap, gap, P);
-        return !(lb * a.lo > tau);
+        return !a.prune || pq_keep(P, sx, sql, tau, a.erel, a.lo);
       };
       // level 0 visits every candidate of the slab: four consecutive ones per
       // thread (one 32-bit code load per subquantiser); deeper levels visit
@@ -553,20 +633,28 @@ __global__ void __launch_bounds__(PQ_NT) pq_verify_kernel(const PqArgs a) {
         n_dims += (unsigned long long)nl * a.b;
         n_lv += nl;
         if (last) n_full += nl;
-        if (use_lut) ++n_lut;
       }
       nl = last ? 0 : ctr[0];
       cur = nxt;
       __syncthreads();
     }
   }
-  if (a.collect && tid == 0) {
-    atomicAdd(a.stats + 0, (unsigned long long)nc);
-    atomicAdd(a.stats + 1, n_dims);
-    atomicAdd(a.stats + 2, n_lv);
-    atomicAdd(a.stats + 3, n_full);
-    atomicAdd(a.stats + 4, n_lut);
-    atomicAdd(a.stats + 5, 1ULL);
+  if (a.collect) {
+    for (int off = 16; off; off >>= 1) {
+      n_dims += __shfl_xor_sync(0xffffffffu, n_dims, off);
+      n_lv += __shfl_xor_sync(0xffffffffu, n_lv, off);
+      n_full += __shfl_xor_sync(0xffffffffu, n_full, off);
+    }
+    if (lane == 0 && n_lv) {
+      atomicAdd(a.stats + 1, n_dims);
+      atomicAdd(a.stats + 2, n_lv);
+      atomicAdd(a.stats + 3, n_full);
+    }
+    if (tid == 0) {
+      atomicAdd(a.stats + 0, (unsigned long long)nc);
+      atomicAdd(a.stats + 4, n_lut);
+      atomicAdd(a.stats + 5, 1ULL);
+    }
   }
 }
 
@@ -594,15 +682,7 @@ __global__ void __launch_bounds__(256) pq_seed_kernel(const PqArgs a,
     const int64_t blk = blk0 + cand / PQ_B;
     const int ln = cand % PQ_B;
     const uint8_t* cp = a.codes + (blk * a.M + (int64_t)l * ML) * PQ_B + ln;
-    float S = 0.f;
-    for (int mm = 0; mm < ML; ++mm) {
-      const int m = l * ML + mm;
-      const float v = pq_term(r + m * dsub,
-                              a.codebook + ((size_t)m * PQ_KSUB + cp[(size_t)mm * PQ_B]) * dsub,
-                              dsub);
-      S = mm == 0 ? v : __fadd_rn(S, v);
-    }
-    part[cand * L + l] = S;
+    part[cand * L + l] = level_sum1<false>(cp, ML, l * ML, nullptr, r, a.codebook, dsub);
   }
   __syncthreads();
   for (int cand = threadIdx.x; cand < ns; cand += blockDim.x) {
