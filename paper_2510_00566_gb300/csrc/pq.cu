@@ -424,17 +424,24 @@ __device__ __forceinline__ float level_sum1(const uint8_t* __restrict__ cp, int 
 }
 
 // The same for four consecutive candidates (one 32-bit load carries their
-// four codes of a subquantiser), four subquantisers per round.
+// four codes of a subquantiser), eight subquantisers per round, the next
+// round's codes loaded while the current round's terms are summed.
 template <bool LUT>
 __device__ __forceinline__ void level_sum4(const uint32_t* __restrict__ cp, int ML, int m0,
                                            const float* lut, const float* r,
                                            const float* __restrict__ cb, int dsub, float S[4]) {
-  for (int mm0 = 0; mm0 < ML; mm0 += 4) {
-    uint32_t w[4];
+  constexpr int G = 8;
+  uint32_t w[G];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) w[u] = mm0 + u < ML ? __ldg(cp + (size_t)(mm0 + u) * (PQ_B / 4)) : 0u;
+  for (int u = 0; u < G; ++u) w[u] = u < ML ? __ldg(cp + (size_t)u * (PQ_B / 4)) : 0u;
+#pragma unroll 1
+  for (int mm0 = 0; mm0 < ML; mm0 += G) {
+    uint32_t wn[G];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < G; ++u)
+      wn[u] = mm0 + G + u < ML ? __ldg(cp + (size_t)(mm0 + G + u) * (PQ_B / 4)) : 0u;
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
       if (mm0 + u < ML) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -447,6 +454,8 @@ __device__ __forceinline__ void level_sum4(const uint32_t* __restrict__ cp, int 
         }
       }
     }
+#pragma unroll
+    for (int u = 0; u < G; ++u) w[u] = wn[u];
   }
 }
 
