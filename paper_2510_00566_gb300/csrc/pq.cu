@@ -686,8 +686,10 @@ __global__ void __launch_bounds__(256) pq_seed_kernel(const PqArgs a,
   for (int j = threadIdx.x; j < d; j += blockDim.x)
     r[j] = __fsub_rn(a.qt[(size_t)q * d + j], a.cent_t[(size_t)c * d + j]);
   __syncthreads();
+  // neighbouring lanes take neighbouring candidates of one level, so a warp's
+  // code loads hit one 32-byte run per subquantiser
   for (int e = threadIdx.x; e < ns * L; e += blockDim.x) {
-    const int cand = e / L, l = e % L;
+    const int cand = e % ns, l = e / ns;
     const int64_t blk = blk0 + cand / PQ_B;
     const int ln = cand % PQ_B;
     const uint8_t* cp = a.codes + (blk * a.M + (int64_t)l * ML) * PQ_B + ln;
