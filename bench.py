@@ -37,7 +37,7 @@ KERNELS_PER_SEARCH = 14  # see the launch list in profiles/
 # capture of a smaller case of the same kernel scaled to the full launch
 # (profiles/ holds the capture summary); None once the kernel has changed.
 TRAFFIC = {"ivf-1m-d960-fp32": 834.49e6 + 3.38e6}  # phase B, ncu at full size, one pass
-PQ_TRAFFIC = {"ivf-1m-d960-fp32": 769.1e6 + 1.2e6}  # pruned pq_verify_kernel, ncu at full size, one pass
+PQ_TRAFFIC = {}  # pruned pq_verify_kernel: ncu at full size, one pass (none for this version yet)
 
 
 def parse():
@@ -527,6 +527,9 @@ def main():
         msp_scan, _ = pq_timed(1, args.scan_steps)
         idxp.search_pq(Q, s.nprobe, k, collect_stats=True)
         stp = pano.last_stats().as_dict()
+        secs = list(pano.last_stats().section_cycles)[:4]
+        secs_share = {nm: v / max(1, sum(secs)) for nm, v in
+                      zip(("prologue", "level0_tables", "level0_scan", "deeper_levels"), secs)}
         ivfpq = {"M": s.d // 2, "nbits": 8, "levels": f"{s.n_levels}x{s.d // s.n_levels}",
                  "kappa": 4.0, "robin_hood_blocks": blocks, "ms_per_step": msp,
                  "value": stp["pairs"] * world / (msp / 1e3), "unit": "candidates/s",
@@ -535,6 +538,7 @@ def main():
                                    "speedup_of_pruned": msp_scan / msp},
                  "dims_scanned_frac": stp["dims_scanned"] / max(1, stp["pairs"] * s.d),
                  "tables_built": stp["tile_levels"], "pairs": stp["pairs"],
+                 "block_time_share": secs_share,
                  # the verify kernel: one shared-memory table lookup per
                  # (live pair, subquantiser); peak = one conflict-free 32-lane
                  # shared-memory wavefront per SM per clock

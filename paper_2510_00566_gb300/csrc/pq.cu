@@ -38,9 +38,9 @@ constexpr int PQ_S = 2048;       // candidates per slab of one (query, list) pai
 constexpr int PQ_NT = 256;       // threads of the verify kernel
 constexpr int PQ_MAXML = 64;     // subquantisers per level
 constexpr int PQ_MAXDSUB = 32;   // coordinates per subvector
-constexpr int PQ_LUT_MIN = 384;  // live candidates from which a level's table is built
+constexpr int PQ_LUT_MIN = 128;  // live candidates from which a level's table is built
 constexpr int PQ_SEED = 64;      // nearest-list members that seed each query's top-k
-constexpr int PQ_DEEP = 512;     // live candidates from which a slab finishes depth-first
+constexpr int PQ_DEEP = 128;     // live candidates from which a slab finishes depth-first
 constexpr int PQ_MAXL = 64;
 
 // ------------------------------------------------------------------ host
@@ -475,9 +475,25 @@ __global__ void __launch_bounds__(PQ_NT) pq_verify_kernel(const PqArgs a) {
   float* lut = (float*)carve((size_t)ML * PQ_KSUB * 4);
   float* pacc = (float*)carve((size_t)2 * PQ_S * 4);
   uint16_t* live = (uint16_t*)carve((size_t)2 * PQ_S * 2);
-  int* ctr = (int*)carve(64);  // [0] survivors of the level, [2] threshold bits
+  int* ctr = (int*)carve(64);  // [0] survivors of the level, [2] threshold bits,
+                               // [8..15] four 64-bit section clocks
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
+  // section clocks in shared memory (thread 0's view: the block's barriers
+  // align the phases): prologue, level-0 tables, level-0 scan, deeper levels
+  unsigned long long* sec = reinterpret_cast<unsigned long long*>(ctr + 8);
+  long long t_mark = 0;
+  if (a.collect && threadIdx.x == 0) {
+    for (int i = 0; i < 4; ++i) sec[i] = 0;
+    t_mark = clock64();
+  }
+  auto lap = [&](int i) {
+    if (a.collect && threadIdx.x == 0) {
+      const long long t = clock64();
+      sec[i] += (unsigned long long)(t - t_mark);
+      t_mark = t;
+    }
+  };
   const int2 pr = a.pairs[blockIdx.x];
   const int q = pr.x, c = pr.y;
   const int nc = a.list_size[c];
@@ -488,7 +504,8 @@ __global__ void __launch_bounds__(PQ_NT) pq_verify_kernel(const PqArgs a) {
   for (int j = tid; j < d; j += PQ_NT)
     r[j] = __fsub_rn(a.qt[(size_t)q * d + j], a.cent_t[(size_t)c * d + j]);
   __syncthreads();
-  // FP64 level energies of the residual, one warp per level
+  // FP64 level energies of the residual (one warp per level) while the whole
+  // block builds level 0's table (the first slab needs it when it is large)
   for (int l = warp; l < L; l += PQ_NT / 32) {
     double s = 0.0;
     for (int j = lane; j < a.b; j += 32) {
@@ -498,19 +515,26 @@ __global__ void __launch_bounds__(PQ_NT) pq_verify_kernel(const PqArgs a) {
     for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane == 0) eq[l] = s;
   }
-  __syncthreads();
-  if (tid == 0) {
-    double tail = 0.0;
-    for (int l = L - 1; l >= 0; --l) {
-      sq[l] = (float)sqrt(tail);  // after level l
-      tail += eq[l];
-    }
+  int lut_level = -1;  // the level whose table `lut` holds (uniform)
+  unsigned long long n_lut = 0;
+  if (min(PQ_S, nc) >= PQ_LUT_MIN) {
+    build_table(lut, r, a.codebook, 0, ML, dsub);
+    lut_level = 0;
+    n_lut = 1;
   }
   __syncthreads();
+  // tail after level l: one lane per level, FP64 sum, sqrt rounded to FP32
+  if (warp == 0)
+    for (int l = lane; l < L; l += 32) {
+      double tail = 0.0;
+      for (int l2 = L - 1; l2 > l; --l2) tail += eq[l2];
+      sq[l] = (float)sqrt(tail);
+    }
+  __syncthreads();
 
+  lap(0);
   // counters (every thread keeps its own; summed at the end when collecting)
-  unsigned long long n_dims = 0, n_lv = 0, n_full = 0, n_lut = 0;
-  int lut_level = -1;  // the level whose table `lut` holds (uniform)
+  unsigned long long n_dims = 0, n_lv = 0, n_full = 0;
   for (int s0 = 0; s0 < nc; s0 += PQ_S) {
     const int ns = min(PQ_S, nc - s0);
     int nl = ns, cur = 0;
@@ -544,6 +568,7 @@ __global__ void __launch_bounds__(PQ_NT) pq_verify_kernel(const PqArgs a) {
           }
         }
         __syncthreads();  // the next slab reuses the live list
+        lap(3);
         break;
       }
       if (tid == 0) {
@@ -557,6 +582,7 @@ __global__ void __launch_bounds__(PQ_NT) pq_verify_kernel(const PqArgs a) {
         if (tid == 0) ++n_lut;
       }
       __syncthreads();
+      lap(l == 0 ? 1 : 3);
       const float tau = __int_as_float(ctr[2]);
       const float sql = sq[l];
       const int nxt = cur ^ 1;
@@ -646,6 +672,7 @@ __global__ void __launch_bounds__(PQ_NT) pq_verify_kernel(const PqArgs a) {
       nl = last ? 0 : ctr[0];
       cur = nxt;
       __syncthreads();
+      lap(l == 0 ? 2 : 3);
     }
   }
   if (a.collect) {
@@ -663,6 +690,7 @@ __global__ void __launch_bounds__(PQ_NT) pq_verify_kernel(const PqArgs a) {
       atomicAdd(a.stats + 0, (unsigned long long)nc);
       atomicAdd(a.stats + 4, n_lut);
       atomicAdd(a.stats + 5, 1ULL);
+      for (int i = 0; i < 4; ++i) atomicAdd(a.stats + 8 + i, sec[i]);
     }
   }
 }
@@ -1047,7 +1075,7 @@ int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe
   const size_t o_fill = take((size_t)2 * nlist * 4);
   const size_t o_off = take((size_t)2 * nlist * 4);
   const size_t o_topk = take((size_t)nq * k * 8);
-  const size_t o_stats = take(8 * 8);
+  const size_t o_stats = take(16 * 8);
   void* ws = nullptr;
   PANO_CUDA(cudaMallocAsync(&ws, off, st));
   char* W = (char*)ws;
@@ -1070,7 +1098,7 @@ int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe
     PANO_CUDA(cudaMemsetAsync(cnt, 0, (size_t)2 * nlist * 4, st));
     PANO_CUDA(cudaMemsetAsync(fill, 0, (size_t)2 * nlist * 4, st));
     PANO_CUDA(cudaMemsetAsync(topk, 0xff, (size_t)nq * k * 8, st));
-    PANO_CUDA(cudaMemsetAsync(stats, 0, 8 * 8, st));
+    PANO_CUDA(cudaMemsetAsync(stats, 0, 16 * 8, st));
     // q~ = T~(q - mu~)
     mark(0);
     PANO_CUDA(gemm_nt(kStore, (int)nq, d, d, queries, d, I.mu32.as<float>(), I.T32.as<float>(),
@@ -1135,7 +1163,7 @@ int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe
                                                                       out_dists);
     PANO_CUDA(cudaGetLastError());
     mark(5);
-    unsigned long long hs[8] = {};
+    unsigned long long hs[16] = {};
     PANO_CUDA(cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
     PANO_CUDA(cudaStreamSynchronize(st));
     if (timing) {
@@ -1159,6 +1187,8 @@ int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe
       S.reranked = (int64_t)hs[3];
       S.tile_levels = (int64_t)hs[4];
       S.work_items = (int64_t)hs[5];
+      // block clocks: prologue, level-0 tables, level-0 scan, deeper levels
+      for (int i = 0; i < 4; ++i) S.section_cycles[i] = (int64_t)hs[8 + i];
     }
     return PANO_OK;
   };

@@ -211,6 +211,33 @@ def test_pq_library_trained_index():
     assert np.mean(rec) >= 0.4, np.mean(rec)
 
 
+@pytest.mark.parametrize("M,L", [(48, 4), (16, 1), (6, 3), (16, 8), (12, 2)])
+def test_pq_subvector_widths_and_level_counts(M, L):
+    """d = 48 with 1-, 3-, 4- and 8-coordinate subvectors (vector and scalar
+    table builders), a single level (no bound test at all) and up to 8
+    levels; lists large enough for tables at level 0."""
+    g = np.random.default_rng(60 + M + L)
+    d, n = 48, 3000
+    X = (g.standard_normal((n, d)) * np.exp(-0.05 * np.arange(d))).astype(np.float32)
+    C = X[g.choice(n, 3, replace=False)]
+    lists, _ = oracle.assign(X, C)
+    Ts, mu, vs = _shaped(X, L, 2.0, 61)
+    cb = (g.standard_normal((M, 256, d // M)) * 0.2).astype(np.float32)
+    R = oracle.transform(Ts, mu, X) - oracle.transform(Ts, mu, C)[lists]
+    codes = pq.pq_encode32(R.astype(np.float32), cb)
+    t = pano.panorama_transform_import(Ts, mu, vs)
+    idx = pano.panorama_build_ivfpq(t, X, 3, M, L, centroids=C, assign=lists, codebooks=cb,
+                                    codes=codes)
+    Q = (X[:40] + 0.05 * g.standard_normal((40, d))).astype(np.float32)
+    for nprobe, k in ((1, 10), (2, 25)):
+        (ids, dd), st0, st1 = _search_both(idx, Q, nprobe, k)
+        probes, gap = oracle.probe(Q, C, nprobe)
+        cand = _oracle_dists(Q, Ts, mu, C, lists, cb, codes, probes)
+        _check(ids, dd, cand, k, gap >= 1e-6)
+        assert st1.dims_scanned == st1.pairs * d
+        assert st0.dims_scanned <= st1.dims_scanned
+
+
 def test_pq_argument_errors(tmp_path):
     g = np.random.default_rng(50)
     X = g.standard_normal((600, 32)).astype(np.float32)
