@@ -37,7 +37,7 @@ KERNELS_PER_SEARCH = 14  # see the launch list in profiles/
 # capture of a smaller case of the same kernel scaled to the full launch
 # (profiles/ holds the capture summary); None once the kernel has changed.
 TRAFFIC = {"ivf-1m-d960-fp32": 834.49e6 + 3.38e6}  # phase B, ncu at full size, one pass
-PQ_TRAFFIC = {"ivf-1m-d960-fp32": 769.2e6 + 1.3e6}  # pruned pq_verify_kernel, ncu at full size, one pass
+PQ_TRAFFIC = {}  # pruned pq_verify_kernel: ncu at full size, one pass (none for this version yet)
 
 
 def parse():
@@ -59,6 +59,8 @@ def parse():
                    help="skip the candidate-list refine run on FP32 IVF workloads")
     p.add_argument("--no-fp8", action="store_true",
                    help="skip the FP8-storage run on FP32 and BF16 workloads")
+    p.add_argument("--pq-levels", type=int, default=0,
+                   help="levels of the IVFPQ line (default: the workload's)")
     p.add_argument("--no-pq", action="store_true",
                    help="skip the IVFPQ line (shaped PCA, M = d/2, levels as the headline)")
     p.add_argument("--no-serve", action="store_true",
@@ -492,13 +494,14 @@ def main():
     # M = d / 2 subquantisers of 8 bits (2-d subvectors), codebooks and codes
     # trained by the library; pruned search vs the plain PQ scan
     ivfpq = None
-    if (s.precision == "fp32" and not args.no_pq and s.nlist > 1 and s.d % s.n_levels == 0
-            and (s.d // 2) % s.n_levels == 0 and isinstance(s.nprobe, int)):
+    Lp = args.pq_levels or s.n_levels
+    if (s.precision == "fp32" and not args.no_pq and s.nlist > 1 and s.d % Lp == 0
+            and (s.d // 2) % Lp == 0 and isinstance(s.nprobe, int)):
         import time as _time
         gd = np.random.default_rng(7000 + s.cfg).standard_normal((2, s.d, s.d))
         b0 = _time.time()
-        tsh, blocks = pano.panorama_shape_transform(t, s.n_levels, 4.0, gd)
-        idxp = pano.panorama_build_ivfpq(tsh, X, s.nlist, s.d // 2, s.n_levels,
+        tsh, blocks = pano.panorama_shape_transform(t, Lp, 4.0, gd)
+        idxp = pano.panorama_build_ivfpq(tsh, X, s.nlist, s.d // 2, Lp,
                                          centroids=idx.centroids(), assign=idx.assignment())
         build_s = _time.time() - b0
         del gd
@@ -530,7 +533,7 @@ def main():
         secs = list(pano.last_stats().section_cycles)[:4]
         secs_share = {nm: v / max(1, sum(secs)) for nm, v in
                       zip(("prologue", "level0_tables", "level0_scan", "deeper_levels"), secs)}
-        ivfpq = {"M": s.d // 2, "nbits": 8, "levels": f"{s.n_levels}x{s.d // s.n_levels}",
+        ivfpq = {"M": s.d // 2, "nbits": 8, "levels": f"{Lp}x{s.d // Lp}",
                  "kappa": 4.0, "robin_hood_blocks": blocks, "ms_per_step": msp,
                  "value": stp["pairs"] * world / (msp / 1e3), "unit": "candidates/s",
                  "qps": nq * world / (msp / 1e3),

@@ -423,6 +423,53 @@ __device__ __forceinline__ float level_sum1(const uint8_t* __restrict__ cp, int 
   return S;
 }
 
+// level_sum1 without a table for a compile-time subvector width: the eight
+// codewords of a round are loaded together (after their codes) before any
+// term is formed, so a round costs two load latencies, not eight.
+template <int DS>
+__device__ __forceinline__ float level_sum1_direct(const uint8_t* __restrict__ cp, int ML, int m0,
+                                                   const float* r,
+                                                   const float* __restrict__ cb) {
+  float S = 0.f;
+  for (int mm0 = 0; mm0 < ML; mm0 += 8) {
+    int code[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) code[u] = mm0 + u < ML ? __ldg(cp + (size_t)(mm0 + u) * PQ_B) : 0;
+    float cv[8][DS];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int m = min(m0 + mm0 + u, m0 + ML - 1);
+      const float* c = cb + ((size_t)m * PQ_KSUB + code[u]) * DS;
+#pragma unroll
+      for (int t = 0; t < DS; ++t) cv[u][t] = __ldg(c + t);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (mm0 + u < ML) {
+        const int m = m0 + mm0 + u;
+        float rv[DS];
+#pragma unroll
+        for (int t = 0; t < DS; ++t) rv[t] = r[m * DS + t];
+        const float e = pq_term(rv, cv[u], DS);
+        S = mm0 + u == 0 ? e : __fadd_rn(S, e);
+      }
+    }
+  }
+  return S;
+}
+
+// A level's partial distance without a table, any subvector width.
+__device__ __forceinline__ float level_sum_direct(const uint8_t* __restrict__ cp, int ML, int m0,
+                                                  const float* r,
+                                                  const float* __restrict__ cb, int dsub) {
+  switch (dsub) {
+    case 1: return level_sum1_direct<1>(cp, ML, m0, r, cb);
+    case 2: return level_sum1_direct<2>(cp, ML, m0, r, cb);
+    case 4: return level_sum1_direct<4>(cp, ML, m0, r, cb);
+    default: return level_sum1<false>(cp, ML, m0, nullptr, r, cb, dsub);
+  }
+}
+
 // The same for four consecutive candidates (one 32-bit load carries their
 // four codes of a subquantiser), eight subquantisers per round, the next
 // round's codes loaded while the current round's terms are summed.
@@ -459,7 +506,7 @@ __device__ __forceinline__ void level_sum4(const uint32_t* __restrict__ cp, int 
   }
 }
 
-__global__ void __launch_bounds__(PQ_NT) pq_verify_kernel(const PqArgs a) {
+__global__ void __launch_bounds__(PQ_NT, 3) pq_verify_kernel(const PqArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int d = a.d, L = a.L, ML = a.ML, M = a.M, dsub = a.dsub;
   size_t o = 0;
@@ -554,7 +601,7 @@ __global__ void __launch_bounds__(PQ_NT) pq_verify_kernel(const PqArgs a) {
           for (int ll = l; ll < L; ++ll) {
             const float tq = threshold_of(slots, a.k);
             const uint8_t* cp = a.codes + (blk * M + (int64_t)ll * ML) * PQ_B + ln;
-            P = __fadd_rn(P, level_sum1<false>(cp, ML, ll * ML, nullptr, r, a.codebook, dsub));
+            P = __fadd_rn(P, level_sum_direct(cp, ML, ll * ML, r, a.codebook, dsub));
             n_dims += a.b;
             ++n_lv;
             if (ll == L - 1) {
@@ -637,7 +684,7 @@ __global__ void __launch_bounds__(PQ_NT) pq_verify_kernel(const PqArgs a) {
           const int ln = g % PQ_B;
           const uint8_t* cp = a.codes + (blk * M + (int64_t)l * ML) * PQ_B + ln;
           const float S = use_lut ? level_sum1<true>(cp, ML, l * ML, lut, r, a.codebook, dsub)
-                                  : level_sum1<false>(cp, ML, l * ML, lut, r, a.codebook, dsub);
+                                  : level_sum_direct(cp, ML, l * ML, r, a.codebook, dsub);
           const float P = __fadd_rn(pacc[cur * PQ_S + i], S);
           Pv[0] = P;
           if (last) {
@@ -721,7 +768,7 @@ __global__ void __launch_bounds__(256) pq_seed_kernel(const PqArgs a,
     const int64_t blk = blk0 + cand / PQ_B;
     const int ln = cand % PQ_B;
     const uint8_t* cp = a.codes + (blk * a.M + (int64_t)l * ML) * PQ_B + ln;
-    part[cand * L + l] = level_sum1<false>(cp, ML, l * ML, nullptr, r, a.codebook, dsub);
+    part[cand * L + l] = level_sum_direct(cp, ML, l * ML, r, a.codebook, dsub);
   }
   __syncthreads();
   for (int cand = threadIdx.x; cand < ns; cand += blockDim.x) {
