@@ -42,7 +42,10 @@ Pins (tests/test_pq_oracle.py): hand-derived Robin Hood examples
 cap, minimality of each suffix, Haar moments by Monte Carlo, the encoder's
 codes against an FP64 argmin, ADC equal to the exact distance when the
 codebooks hold the data, LB <= ADC <= UB with equality at the last level, the
-Eq. 3 identity, and Algorithm 1 over ADC equal to the plain ADC top-k.
+Eq. 3 identity, Algorithm 1 over ADC equal to the plain ADC top-k, the
+invariance of every level bound under Procedure 2, and the trade Procedure 1
+makes (more coordinates read by Algorithm 1, lower PQ reconstruction error
+than the PCA basis at the same bit budget).
 """
 from __future__ import annotations
 

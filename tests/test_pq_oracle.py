@@ -220,3 +220,54 @@ def test_ivfpq_search_reduces_to_ivf_flat_when_codes_are_exact():
     want = ref.ivf_search(Xr.astype(np.float64), Q, C, 2, 7, lists_of_vector=lists)
     assert np.array_equal(got["ids"], want["ids"])
     np.testing.assert_allclose(got["dists"], want["dists"], rtol=1e-9)
+
+
+def test_procedure2_leaves_every_level_bound_unchanged():
+    """A rotation inside each level keeps every level's head distance and
+    tail energy, so the bounds of Eq. 3 are the same before and after
+    Procedure 2 (only the coordinates within a level mix)."""
+    g = np.random.default_rng(10)
+    d, L = 40, 5
+    m = ref.level_thresholds(d, [d // L] * L)
+    lam = np.exp(-0.1 * np.arange(d))
+    q = g.standard_normal(d) * np.sqrt(lam)
+    X = g.standard_normal((200, d)) * np.sqrt(lam)
+    U = pq.isotropize(d, L, g.standard_normal((d, d)))
+    lb0, ub0 = pq.pq_level_bounds(q, X, m)
+    lb1, ub1 = pq.pq_level_bounds(U @ q, X @ U.T, m)
+    np.testing.assert_allclose(lb1, lb0, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(ub1, ub0, rtol=1e-9, atol=1e-9)
+
+
+def test_robin_hood_trades_pruning_for_pq_balance():
+    """Section 4.3's trade: on a fast-decaying spectrum, kappa = 1 moves energy
+    out of the leading level, so Algorithm 1 reads more coordinates than in
+    the PCA basis, while product quantisation with the same bit budget
+    reconstructs the vectors better (equal-bit codebooks fit a flat profile)."""
+    g = np.random.default_rng(11)
+    d, L, M, n = 32, 4, 8, 3000
+    lam = np.exp(-0.2 * np.arange(d))
+    X = g.standard_normal((n, d)) * np.sqrt(lam)  # already in its PCA basis
+    q = g.standard_normal((20, d)) * np.sqrt(lam)
+    m = ref.level_thresholds(d, [d // L] * L)
+    G = g.standard_normal((2, d, d))
+    Ts, vs, blocks = pq.shape_transform(np.eye(d), lam, L, 1.0, G[0], G[1])
+    assert blocks and pq.level_energies(vs, L).max() <= lam.sum() / L * (1 + 1e-9)
+
+    def dims(T):
+        tot = 0
+        for i in range(len(q)):
+            tq, tX = T @ q[i], X @ T.T
+            _, _, r = ref.refine(tq, tX, np.arange(n), m, 10, B=256)
+            tot += r.sum()
+        return tot
+
+    assert dims(Ts) > dims(np.eye(d))
+
+    def pq_mse(T):
+        R = X @ T.T
+        cb = pq.pq_train(R[:2000], M, iters=6, seed=3)
+        codes = pq.pq_encode32(R.astype(np.float32), cb)
+        return float(((pq.pq_reconstruct(codes, cb) - R) ** 2).sum(1).mean())
+
+    assert pq_mse(Ts) < pq_mse(np.eye(d))
