@@ -381,7 +381,9 @@ int panorama_index_assignment(const pano_index* idx, int32_t* out);
 
 /* ------------------------------------------------------ persistence
  * panorama_save writes a versioned little-endian file with an FNV-1a 64-bit
- * checksum; panorama_load rebuilds the index on the current device.
+ * checksum; panorama_load rebuilds the index on the current device.  Every
+ * index kind is kept: IVF (FP32 / BF16 / FP8), flat, and IVFPQ
+ * (panorama_pq.h).
  * Errors: PANO_EINVAL, PANO_ENOMEM, PANO_ECUDA, PANO_ECORRUPT (bad magic,
  *         version, sizes or checksum), and I/O failures as PANO_EINVAL. */
 int panorama_save(const pano_index* idx, const char* path);

@@ -98,6 +98,8 @@ typedef struct {
  * [L][256] FP32 (FP64 sums from the codebook, rounded to nearest; level L-1's
  * entry is 0) and the ids [256] int32 (-1 = padding); the codebooks
  * [M][256][d / M] FP32 and the transformed centroids [nlist][d] FP32.
+ * panorama_save / panorama_load keep an IVFPQ index (its quantiser arrays in
+ * place of the level slices); panorama_search rejects it.
  * Errors: PANO_EINVAL (sizes above, assign or nlist out of range, fewer than
  *         256 vectors to train codebooks on), PANO_ENOMEM, PANO_ECUDA,
  *         PANO_ENODEV. */

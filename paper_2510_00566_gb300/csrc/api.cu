@@ -5,6 +5,7 @@
 #include <cstring>
 #include <fstream>
 
+#include "../../include/panorama_pq.h"
 #include "internal.h"
 #include "search.h"
 
@@ -263,7 +264,6 @@ int panorama_index_assignment(const pano_index* idx, int32_t* out) {
 int panorama_save(const pano_index* idx, const char* path) {
   clear_error();
   PANO_CHECK(idx && path, PANO_EINVAL, "null argument");
-  PANO_CHECK(idx->pq_M == 0, PANO_EINVAL, "an IVFPQ index cannot be saved");
   Writer w;
   w.f.open(path, std::ios::binary | std::ios::trunc);
   PANO_CHECK((bool)w.f, PANO_EINVAL, std::string("cannot open ") + path);
@@ -297,10 +297,17 @@ int panorama_save(const pano_index* idx, const char* path) {
   w.vec(I.list_chunk_off);
   w.vec(I.list_size);
   int rc;
-  if ((rc = w.dev(I.slices)) || (rc = w.dev(I.tails)) || (rc = w.dev(I.xn2)) ||
-      (rc = w.dev(I.ex)) || (rc = w.dev(I.ids)) || (rc = w.dev(I.rows)) ||
-      (I.precision == PANO_FP8 && (rc = w.dev(I.xscale))))
+  if (I.precision == PANO_PQ) {  // the quantiser in place of the slices
+    w.pod(I.pq_M);
+    w.pod(I.pq_dsub);
+    if ((rc = w.dev(I.pq_codes)) || (rc = w.dev(I.tails)) || (rc = w.dev(I.ids)) ||
+        (rc = w.dev(I.pq_codebook)) || (rc = w.dev(I.pq_cent_t)))
+      return rc;
+  } else if ((rc = w.dev(I.slices)) || (rc = w.dev(I.tails)) || (rc = w.dev(I.xn2)) ||
+             (rc = w.dev(I.ex)) || (rc = w.dev(I.ids)) || (rc = w.dev(I.rows)) ||
+             (I.precision == PANO_FP8 && (rc = w.dev(I.xscale)))) {
     return rc;
+  }
   uint64_t h = w.fnv.h;
   w.f.write(reinterpret_cast<const char*>(&h), 8);
   PANO_CHECK(w.ok && (bool)w.f, PANO_EINVAL, std::string("write failed: ") + path);
@@ -345,7 +352,8 @@ int panorama_load(const char* path, pano_index** out) {
                     ((I.precision == PANO_FP32 && I.chunk == 64) ||
                      ((I.precision == PANO_BF16 || I.precision == PANO_FP8) &&
                       I.chunk == 128) ||
-                     (I.precision == PANO_FP32 && I.chunk == 1 && I.nlist == 1)) &&
+                     (I.precision == PANO_FP32 && I.chunk == 1 && I.nlist == 1) ||
+                     (I.precision == PANO_PQ && I.chunk == 256)) &&
                     I.n_chunks >= 0 && I.n_chunks <= I.n + I.nlist;
   PANO_CHECK(sane, PANO_ECORRUPT, "header fields out of range");
   I.flat = I.chunk == 1 ? 1 : 0;  // a flat (refine) index: one row per "chunk"
@@ -370,7 +378,18 @@ int panorama_load(const char* path, pano_index** out) {
                  I.list_chunk_off[nl] == I.n_chunks,
              PANO_ECORRUPT, "truncated or inconsistent index file");
   const uint64_t CHK = (uint64_t)I.chunk, ns = (uint64_t)I.n_chunks * CHK;
-  if ((rc = r.dev(I.slices, I.slices_bytes())) ||
+  if (I.precision == PANO_PQ) {
+    r.pod(I.pq_M);
+    r.pod(I.pq_dsub);
+    const int M = I.pq_M, ds = I.pq_dsub;
+    PANO_CHECK(r.ok && M >= 1 && ds >= 1 && ds <= 32 && (uint64_t)M * ds == d && M % I.L == 0 &&
+                   M / I.L <= 64 && d % I.L == 0,
+               PANO_ECORRUPT, "IVFPQ fields out of range");
+    if ((rc = r.dev(I.pq_codes, ns * M)) || (rc = r.dev(I.tails, ns * I.L * 4)) ||
+        (rc = r.dev(I.ids, ns * 4)) || (rc = r.dev(I.pq_codebook, (uint64_t)M * 256 * ds * 4)) ||
+        (rc = r.dev(I.pq_cent_t, nl * d * 4)))
+      return rc;
+  } else if ((rc = r.dev(I.slices, I.slices_bytes())) ||
       (rc = r.dev(I.tails, (uint64_t)I.n_chunks * (I.L + 1) * CHK * 4)) ||
       (rc = r.dev(I.xn2, ns * 4)) || (rc = r.dev(I.ex, ns * 4)) || (rc = r.dev(I.ids, ns * 4)) ||
       (rc = r.dev(I.rows, ns * d * 4)) ||

@@ -238,7 +238,7 @@ def test_pq_subvector_widths_and_level_counts(M, L):
         assert st0.dims_scanned <= st1.dims_scanned
 
 
-def test_pq_argument_errors(tmp_path):
+def test_pq_argument_errors_and_save_load(tmp_path):
     g = np.random.default_rng(50)
     X = g.standard_normal((600, 32)).astype(np.float32)
     t = pano.panorama_fit_transform(X, n_levels=4)
@@ -251,8 +251,17 @@ def test_pq_argument_errors(tmp_path):
         idx.search(q, 1, 5)
     with pytest.raises(pano.LibraryError):
         idx.search_pq(q, 3, 5)  # nprobe > nlist
+    path = str(tmp_path / "pq.pano")
+    pano.panorama_save(idx, path)  # the quantiser survives a round trip bit for bit
+    idx2 = pano.panorama_load(path)
+    assert idx2.info().precision == pano.PANO_PQ
+    a, b = idx.search_pq(q, 2, 5), idx2.search_pq(q, 2, 5)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    cb1, c1 = pano.panorama_pq_export(idx)
+    cb2, c2 = pano.panorama_pq_export(idx2)
+    assert np.array_equal(cb1, cb2) and np.array_equal(c1, c2)
     with pytest.raises(pano.LibraryError):
-        pano.panorama_save(idx, str(tmp_path / "pq.pano"))
+        idx2.search(q, 1, 5)
     flat = pano.panorama_build_ivf(t, X, 2, n_levels=4)
     with pytest.raises(pano.LibraryError):
         flat.search_pq(q, 1, 5)
