@@ -129,12 +129,16 @@ int panorama_build_ivfpq(const pano_transform* t, const float* X, int64_t n, int
  *             bit 1 = CUDA-event times of the stages in stage_ms (transform,
  *             probe, pair order and seeds, -, verify, decode); read with
  *             panorama_search_stats.
+ *   epsilon:  Eq. 4; in (0, 1) the lower bound becomes
+ *             D_head + s_q^2 + s_x^2 - 2 epsilon s_q s_x (no rounding
+ *             allowance): faster, approximate recall; returned distances are
+ *             still the computed ones.  0 or 1 = the exact, margined test.
  * Blocks until the results are written.
  * Errors: PANO_EINVAL (not an IVFPQ index, sizes), PANO_ENOMEM, PANO_ECUDA,
  *         PANO_ENODEV, PANO_ETIMEOUT never (no device-side waits). */
 int panorama_search_pq(const pano_index* idx, const float* queries, int64_t nq, int32_t nprobe,
                        int32_t k, int64_t* out_ids, float* out_dists, int32_t mode,
-                       int32_t collect_stats, void* stream);
+                       int32_t collect_stats, float epsilon, void* stream);
 
 /* panorama_pq_export -- host copies of an IVFPQ index's quantiser.
  *   codebooks: M x 256 x (d / M) FP32, or NULL.

@@ -137,7 +137,8 @@ SIGNATURES = {
     "panorama_transform_import": (ctypes.c_int, [_P, _P, _P, _I32, _P]),
     "panorama_shape_transform": (ctypes.c_int, [_P, _I32, ctypes.c_double, _P, _P, _P]),
     "panorama_build_ivfpq": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _P]),
-    "panorama_search_pq": (ctypes.c_int, [_P, _P, _I64, _I32, _I32, _P, _P, _I32, _I32, _P]),
+    "panorama_search_pq": (ctypes.c_int, [_P, _P, _I64, _I32, _I32, _P, _P, _I32, _I32,
+                                          ctypes.c_float, _P]),
     "panorama_pq_export": (ctypes.c_int, [_P, _P, _P, _P]),
     "panorama_debug_pq_encode": (ctypes.c_int, [_P, _I64, _I32, _I32, _P, _P, _P]),
     "panorama_debug_tc_gemm_fp8": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _P]),
@@ -433,10 +434,11 @@ def panorama_build_ivfpq(t: "Transform", X, nlist: int, M: int, n_levels: int,
 
 
 def panorama_search_pq(idx: "Index", queries, nprobe: int, k: int, mode=0,
-                       collect_stats=False, stream=None, out=None, collect_timing=False):
+                       collect_stats=False, stream=None, out=None, collect_timing=False,
+                       epsilon=1.0):
     """(ids int64 [nq, k], dists float32 [nq, k]) on the GPU; mode 1 = plain
     scan; collect_timing fills stage_ms (transform, probe, pairs + seeds, -,
-    verify, decode)."""
+    verify, decode); epsilon < 1: Eq. 4's relaxed pruning (approximate)."""
     import torch
     q = queries.contiguous()
     assert q.is_cuda and q.dtype == torch.float32
@@ -449,7 +451,7 @@ def panorama_search_pq(idx: "Index", queries, nprobe: int, k: int, mode=0,
     _check(lib().panorama_search_pq(idx.handle, q.data_ptr(), nq, int(nprobe), int(k),
                                     ids.data_ptr(), dists.data_ptr(), int(mode),
                                     (1 if collect_stats else 0) | (2 if collect_timing else 0),
-                                    _stream_ptr(stream)))
+                                    float(epsilon), _stream_ptr(stream)))
     return ids, dists
 
 

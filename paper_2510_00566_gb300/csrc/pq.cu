@@ -318,6 +318,7 @@ struct PqArgs {
   int d, M, dsub, L, ML, b, k, prune, collect;
   float lo;    // (1 - gamma) factor of the lower bound, rounded down
   float erel;  // relative allowance for the roundings of s_q, s_x and |s_q - s_x|
+  float eps;   // Eq. 4 (1 = the exact, margined test)
 };
 
 // Bytes of dynamic shared memory of the verify kernel.
@@ -389,11 +390,19 @@ __device__ __forceinline__ void build_table(float* lut, const float* r,
 
 // Eq. 3 in partial-distance form, margined (see search_pq): keep unless
 // (1 - gamma) (P + max(0, |s_q - s_x| - 8u (s_q + s_x))^2) > tau.
+// eps < 1: Eq. 4, the Cauchy-Schwarz term scaled by eps,
+// LB_eps = P + s_q^2 + s_x^2 - 2 eps s_q s_x (approximate by design: no
+// rounding allowance; what is returned still carries its computed distance).
 __device__ __forceinline__ bool pq_keep(float P, float sx, float sql, float tau, float erel,
-                                        float lo) {
-  float gap = fabsf(__fsub_rn(sql, sx)) - erel * (sql + sx);
-  gap = fmaxf(gap, 0.f);
-  const float lb = __fmaf_rn(gap, gap, P);
+                                        float lo, float eps) {
+  float lb;
+  if (eps < 1.f) {
+    lb = P + fmaxf(0.f, fmaf(sql, sql, sx * sx) - 2.f * eps * sql * sx);
+  } else {
+    float gap = fabsf(__fsub_rn(sql, sx)) - erel * (sql + sx);
+    gap = fmaxf(gap, 0.f);
+    lb = __fmaf_rn(gap, gap, P);
+  }
   return !(lb * lo > tau);
 }
 
@@ -609,7 +618,7 @@ __global__ void __launch_bounds__(PQ_NT, 3) pq_verify_kernel(const PqArgs a) {
               const unsigned long long key = make_key(P, a.ids[blk * PQ_B + ln]);
               if (key < ld_volatile_u64(slots + a.k - 1)) topk_insert_thread(slots, a.k, key);
             } else if (!pq_keep(P, a.xtail[(blk * L + ll) * PQ_B + ln], sq[ll], tq, a.erel,
-                                a.lo)) {
+                                a.lo, a.eps)) {
               break;
             }
           }
@@ -634,7 +643,7 @@ __global__ void __launch_bounds__(PQ_NT, 3) pq_verify_kernel(const PqArgs a) {
       const float sql = sq[l];
       const int nxt = cur ^ 1;
       auto passes = [&](float P, float sx) {
-        return !a.prune || pq_keep(P, sx, sql, tau, a.erel, a.lo);
+        return !a.prune || pq_keep(P, sx, sql, tau, a.erel, a.lo, a.eps);
       };
       // level 0 visits every candidate of the slab: four consecutive ones per
       // thread (one 32-bit code load per subquantiser); deeper levels visit
@@ -1088,7 +1097,8 @@ int build_ivfpq(const pano_transform* t, const float* X, int64_t n, int nlist,
 
 // ----------------------------------------------------------------- search
 int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe, int k,
-              int64_t* out_ids, float* out_dists, int mode, int collect, cudaStream_t st) {
+              int64_t* out_ids, float* out_dists, int mode, int collect, float epsilon,
+              cudaStream_t st) {
   PANO_CHECK(ip, PANO_EINVAL, "null index");
   const pano_index& I = *ip;
   PANO_CHECK(I.pq_M > 0, PANO_EINVAL, "not an IVFPQ index (panorama_build_ivfpq)");
@@ -1193,6 +1203,7 @@ int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe
     // s_q, s_x: FP64 sums rounded to FP32 (u each), |s_q - s_x| and the
     // allowance itself (u each): 8u of (s_q + s_x) covers them with margin.
     a.erel = (float)(8.0 * kU32);
+    a.eps = (epsilon > 0.f && epsilon < 1.f) ? epsilon : 1.f;
 
     const size_t ssm = (size_t)((d + 3) & ~3) * 4 + (size_t)PQ_SEED * L * 4;
     PANO_CUDA(cudaFuncSetAttribute(pq_seed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1357,9 +1368,9 @@ int panorama_build_ivfpq(const pano_transform* t, const float* X, int64_t n, int
 
 int panorama_search_pq(const pano_index* idx, const float* queries, int64_t nq, int32_t nprobe,
                        int32_t k, int64_t* out_ids, float* out_dists, int32_t mode,
-                       int32_t collect_stats, void* stream) {
+                       int32_t collect_stats, float epsilon, void* stream) {
   clear_error();
-  return search_pq(idx, queries, nq, nprobe, k, out_ids, out_dists, mode, collect_stats,
+  return search_pq(idx, queries, nq, nprobe, k, out_ids, out_dists, mode, collect_stats, epsilon,
                    (cudaStream_t)stream);
 }
 

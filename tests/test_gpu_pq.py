@@ -211,6 +211,42 @@ def test_pq_library_trained_index():
     assert np.mean(rec) >= 0.4, np.mean(rec)
 
 
+def test_pq_epsilon_relaxed_pruning():
+    """Eq. 4 on the IVFPQ path: epsilon = 0.5 reads no more subvector terms
+    than the exact test, keeps most of the exact top-k, and every returned
+    candidate carries its computed distance (as the plain scan computes it)."""
+    s = synth.scaled(5, n=15_000, n_queries=60, nlist=8)
+    w = synth.generate(s)
+    X, Q = w.X.numpy(), w.Q.numpy()
+    d, L, M = X.shape[1], 8, X.shape[1] // 2
+    Ts, mu, vs = _shaped(X, L, 2.0, 71)
+    C = synth.initial_centroids(w.X, 8, seed=72).numpy()
+    lists, _ = oracle.assign(X, C)
+    R = oracle.transform(Ts, mu, X) - oracle.transform(Ts, mu, C)[lists]
+    cb = pq.pq_train(R[:2000], M, iters=2, seed=73)
+    codes = pq.pq_encode32(R.astype(np.float32), cb)
+    t = pano.panorama_transform_import(Ts, mu, vs)
+    idx = pano.panorama_build_ivfpq(t, X, 8, M, L, centroids=C, assign=lists, codebooks=cb,
+                                    codes=codes)
+    q = torch.from_numpy(Q).to(DEV)
+    ids1, d1 = idx.search_pq(q, 3, 10, collect_stats=True)
+    dims1 = pano.last_stats().dims_scanned
+    ids_e, d_e = idx.search_pq(q, 3, 10, collect_stats=True, epsilon=0.5)
+    assert pano.last_stats().dims_scanned <= dims1
+    probes, _ = oracle.probe(Q, C, 3)
+    cand = _oracle_dists(Q, Ts, mu, C, lists, cb, codes, probes)
+    ids_e, d_e = ids_e.cpu().numpy(), d_e.cpu().numpy().astype(np.float64)
+    ids1 = ids1.cpu().numpy()
+    rec = np.mean([len(set(ids_e[i]) & set(ids1[i])) / 10 for i in range(len(Q))])
+    assert rec >= 0.5, rec
+    for i in range(len(Q)):
+        mem, D = cand[i]
+        pos = {int(v): j for j, v in enumerate(mem)}
+        v = ids_e[i] >= 0
+        true = D[[pos[int(x)] for x in ids_e[i][v]]]
+        assert np.allclose(d_e[i][v], true, rtol=RTOL_D)
+
+
 @pytest.mark.parametrize("M,L", [(48, 4), (16, 1), (6, 3), (16, 8), (12, 2)])
 def test_pq_subvector_widths_and_level_counts(M, L):
     """d = 48 with 1-, 3-, 4- and 8-coordinate subvectors (vector and scalar
