@@ -2,19 +2,22 @@
 // level-wise bounded asymmetric-distance search (Section 6.3).
 //
 // Search: one thread block per (query, probed list) pair.  The block forms
-// the query residual r = q~ - c~ in shared memory, its level tail energies in
-// FP64, and walks the list in slabs of PQ_S candidates, level by level.  A
+// the query residual r = q~ - c~ in shared memory and its level tail
+// energies (FP64), then walks the list in slabs of PQ_S candidates.  A
 // level's subvector terms e_m = ||r_m - C_m[code_m]||^2 come from a table of
-// the 256 terms of each of the level's subquantisers, built in shared memory
-// while many candidates are live (the paper's per-level look-up tables), and
+// the 256 terms of each of the level's subquantisers in shared memory (the
+// paper's per-level look-up tables) while many candidates are live, and
 // straight from the codebook once few are (the same arithmetic, so the same
 // values).  The codes of one level of a block of 256 vectors are M / L rows
-// of 256 bytes (subquantiser-major), so the live candidates of a warp read
-// neighbouring bytes of one row per subquantiser.  Survivors are compacted
-// with warp ballots into the next level's list.  The query's top-k is a
-// sorted array of (distance, id) keys shared by all of its pairs; its k-th
-// key is the pruning threshold (Algorithm 1's running k-th distance), seeded
-// before the scan with the first members of the query's nearest list.
+// of 256 bytes (subquantiser-major): at level 0 every thread takes four
+// consecutive candidates, whose codes of one subquantiser are one 32-bit
+// word.  Survivors are compacted with warp ballots into the next level's
+// list; levels stay in step across the block while more than PQ_DEEP
+// candidates live, after which each thread walks its survivors through the
+// remaining levels alone.  The query's top-k is a sorted array of
+// (distance, id) keys shared by all of its pairs; its k-th key is the
+// pruning threshold (Algorithm 1's running k-th distance), seeded before the
+// scan with the first members of the query's nearest list.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
