@@ -61,6 +61,8 @@ def parse():
                    help="skip the FP8-storage run on FP32 and BF16 workloads")
     p.add_argument("--pq-levels", type=int, default=0,
                    help="levels of the IVFPQ line (default: the workload's)")
+    p.add_argument("--no-pq-sweep", action="store_true",
+                   help="skip the IVFPQ kappa sweep (Section 4.3's shaping trade)")
     p.add_argument("--no-pq", action="store_true",
                    help="skip the IVFPQ line (shaped PCA, M = d/2, levels as the headline)")
     p.add_argument("--no-serve", action="store_true",
@@ -553,7 +555,50 @@ def main():
                               "traffic": PQ_TRAFFIC.get(s.name), "ms_per_launch": vmsp,
                               "lookups_per_launch": stp["dims_scanned"] / 2},
                  "index_gb": idxp.info().device_bytes / 1e9, "build_s": build_s}
-        del idxp, tsh
+        # recall@k against the exact top-k over the same lists: the IVFFlat
+        # search of the same index lists and queries returns it
+        ref_ids, _ = idx.search(Q, s.nprobe, k)
+        ref_ids = ref_ids.cpu().numpy()
+
+        def recall_of(ids):
+            ids = ids.cpu().numpy()
+            return float(np.mean([len(set(ids[i]) & set(ref_ids[i])) / k for i in range(nq)]))
+
+        ivfpq["recall_at_k"] = recall_of(idxp.search_pq(Q, s.nprobe, k)[0])
+        del idxp
+        # the kappa trade of spectrum shaping (Section 4.3): a larger cap
+        # keeps more energy up front (more pruning, less even PQ subspaces)
+        if not args.no_pq_sweep:
+            sweep = []
+            for kap in (1.0, 2.0, 4.0, 16.0):
+                gk = np.random.default_rng(7000 + s.cfg).standard_normal((2, s.d, s.d))
+                tk, bk = pano.panorama_shape_transform(t, Lp, kap, gk)
+                del gk
+                ik = pano.panorama_build_ivfpq(tk, X, s.nlist, s.d // 2, Lp,
+                                               centroids=idx.centroids(),
+                                               assign=idx.assignment())
+                for _ in range(2):
+                    ik.search_pq(Q, s.nprobe, k)
+                torch.cuda.synchronize()
+                tot = 0.0
+                for _ in range(3):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ids_k, _ = ik.search_pq(Q, s.nprobe, k)
+                    e1.record(stream)
+                    e1.synchronize()
+                    tot += e0.elapsed_time(e1)
+                ik.search_pq(Q, s.nprobe, k, collect_stats=True)
+                stk = pano.last_stats().as_dict()
+                sweep.append({"kappa": kap, "robin_hood_blocks": bk, "ms_per_step": tot / 3,
+                              "qps": nq * world / (tot / 3 / 1e3),
+                              "recall_at_k": recall_of(ids_k),
+                              "dims_scanned_frac": stk["dims_scanned"] / max(1, stk["pairs"] * s.d)})
+                del ik, tk
+            ivfpq["kappa_sweep"] = sweep
+        del tsh
 
     bf16 = fp8 = None
     if s.precision == "fp32" and not args.no_bf16 and s.d % 64 == 0:
