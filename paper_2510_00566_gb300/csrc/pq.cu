@@ -872,6 +872,12 @@ int build_ivfpq(const pano_transform* t, const float* X, int64_t n, int nlist,
   PANO_CHECK(dsub <= PQ_MAXDSUB, PANO_EINVAL, "at most 32 coordinates per subvector");
   PANO_CHECK(o->codebooks || n >= PQ_KSUB, PANO_EINVAL,
              "training codebooks needs at least 256 vectors");
+  if (o->assign) {
+    PANO_CHECK(o->centroids, PANO_EINVAL, "an assignment needs its centroids");
+    for (int64_t i = 0; i < n; ++i)
+      PANO_CHECK(o->assign[i] >= 0 && o->assign[i] < nlist, PANO_EINVAL,
+                 "assignment out of range");
+  }
   int dev = 0;
   int rc = check_device(&dev);
   if (rc) return rc;
@@ -902,12 +908,6 @@ int build_ivfpq(const pano_transform* t, const float* X, int64_t n, int nlist,
   }
 
   // ---- coarse quantiser and lists
-  if (o->assign) {
-    PANO_CHECK(o->centroids, PANO_EINVAL, "an assignment needs its centroids");
-    for (int64_t i = 0; i < n; ++i)
-      PANO_CHECK(o->assign[i] >= 0 && o->assign[i] < nlist, PANO_EINVAL,
-                 "assignment out of range");
-  }
   pano_build_opts co;
   std::memset(&co, 0, sizeof(co));
   co.kmeans_iters = o->kmeans_iters;

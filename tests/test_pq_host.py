@@ -79,3 +79,31 @@ def test_shaping_argument_errors():
     for L, kappa in ((3, 2.0), (4, 0.5), (4, float("nan"))):
         with pytest.raises(pano.LibraryError):
             pano.panorama_shape_transform(t, L, kappa, G)
+
+
+def test_ivfpq_argument_checks_before_any_device_work():
+    """Sizes the IVFPQ build and search reject on the host (no GPU needed):
+    the C entry points are called directly with a null stream."""
+    import ctypes
+    L_ = pano.lib()
+
+    def build(d, M, L, n=600, nlist=2, assign=None):
+        t = pano.panorama_transform_import(np.eye(d), np.zeros(d), np.ones(d))
+        X = np.zeros((n, d), np.float32)
+        o = pano.PQBuildOpts(M=M, n_levels=L)
+        if assign is not None:
+            o.assign = assign.ctypes.data
+        out = ctypes.c_void_p()
+        return L_.panorama_build_ivfpq(t.handle, X.ctypes.data, n, nlist, ctypes.byref(o),
+                                       None, ctypes.byref(out))
+
+    for M, L in ((5, 4), (8, 3), (12, 4), (32, 64), (1, 2)):
+        assert build(32, M, L) == -1, (M, L)
+    assert build(130, 130, 2) == -1      # 65 subquantisers per level
+    assert build(32, 16, 4, nlist=0) == -1
+    assert build(32, 16, 4, n=100) == -1  # codebooks to train on fewer than 256 rows
+    a = np.zeros(600, np.int32)
+    assert build(32, 16, 4, assign=a) == -1  # an assignment without its centroids
+    assert L_.panorama_search_pq(None, None, 0, 1, 1, None, None, 0, 0, 1.0, None) == -1
+    assert L_.panorama_pq_export(None, None, None, None) == -1
+    assert L_.panorama_debug_pq_encode(None, 0, 32, 5, None, None, None) == -1
