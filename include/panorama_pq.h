@@ -140,6 +140,22 @@ int panorama_search_pq(const pano_index* idx, const float* queries, int64_t nq, 
                        int32_t k, int64_t* out_ids, float* out_dists, int32_t mode,
                        int32_t collect_stats, float epsilon, void* stream);
 
+/* panorama_search_pq_ex -- panorama_search_pq with per-query probes and k
+ * (as panorama_search_ex):
+ *   nprobe:   device nq int32 (each clamped to [1, nprobe_scalar]; a
+ *             nprobe_scalar < 1 means nlist), or NULL for nprobe_scalar.
+ *   k:        device nq int32 (each clamped to [0, k_max]), or NULL for
+ *             k_scalar in [0, k_max].
+ *   k_max:    1..1024, the row length of out_ids / out_dists (nq x k_max;
+ *             a row's entries past its k are (-1, +inf)).
+ *   opts:     mode, collect_stats, collect_timing and epsilon are used
+ *             (NULL = pruned, exact, no statistics).
+ * Errors: as panorama_search_pq. */
+int panorama_search_pq_ex(const pano_index* idx, const float* queries, int64_t nq,
+                          const int32_t* nprobe, int32_t nprobe_scalar, const int32_t* k,
+                          int32_t k_scalar, int32_t k_max, int64_t* out_ids, float* out_dists,
+                          const pano_search_opts* opts, void* stream);
+
 /* panorama_pq_export -- host copies of an IVFPQ index's quantiser.
  *   codebooks: M x 256 x (d / M) FP32, or NULL.
  *   codes:     n x M uint8 in vector-id order, or NULL.

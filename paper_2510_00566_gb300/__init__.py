@@ -139,6 +139,8 @@ SIGNATURES = {
     "panorama_build_ivfpq": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _P]),
     "panorama_search_pq": (ctypes.c_int, [_P, _P, _I64, _I32, _I32, _P, _P, _I32, _I32,
                                           ctypes.c_float, _P]),
+    "panorama_search_pq_ex": (ctypes.c_int, [_P, _P, _I64, _P, _I32, _P, _I32, _I32, _P, _P,
+                                             _P, _P]),
     "panorama_pq_export": (ctypes.c_int, [_P, _P, _P, _P]),
     "panorama_debug_pq_encode": (ctypes.c_int, [_P, _I64, _I32, _I32, _P, _P, _P]),
     "panorama_debug_tc_gemm_fp8": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _P]),
@@ -433,25 +435,46 @@ def panorama_build_ivfpq(t: "Transform", X, nlist: int, M: int, n_levels: int,
     return Index(out.value)
 
 
-def panorama_search_pq(idx: "Index", queries, nprobe: int, k: int, mode=0,
+def panorama_search_pq(idx: "Index", queries, nprobe, k, k_max=None, mode=0,
                        collect_stats=False, stream=None, out=None, collect_timing=False,
                        epsilon=1.0):
-    """(ids int64 [nq, k], dists float32 [nq, k]) on the GPU; mode 1 = plain
-    scan; collect_timing fills stage_ms (transform, probe, pairs + seeds, -,
-    verify, decode); epsilon < 1: Eq. 4's relaxed pruning (approximate)."""
+    """(ids int64 [nq, k_max], dists float32 [nq, k_max]) on the GPU.
+
+    nprobe / k: python ints, or CUDA int32 tensors with one value per query
+    (then k_max defaults to max(k)); mode 1 = plain scan; collect_timing
+    fills stage_ms (transform, probe, pairs + seeds, -, verify, decode);
+    epsilon < 1: Eq. 4's relaxed pruning (approximate)."""
     import torch
     q = queries.contiguous()
     assert q.is_cuda and q.dtype == torch.float32
     nq = q.shape[0]
+    np_ptr, np_scalar = None, 0
+    if isinstance(nprobe, torch.Tensor):
+        nprobe = nprobe.to(device=q.device, dtype=torch.int32).contiguous()
+        np_ptr, np_scalar = nprobe.data_ptr(), int(nprobe.max()) if nq else 1
+    else:
+        np_scalar = int(nprobe)
+    k_ptr, k_scalar = None, 0
+    if isinstance(k, torch.Tensor):
+        k = k.to(device=q.device, dtype=torch.int32).contiguous()
+        k_ptr = k.data_ptr()
+        if k_max is None:
+            k_max = max(1, int(k.max())) if nq else 1
+    else:
+        k_scalar = int(k)
+        if k_max is None:
+            k_max = max(1, k_scalar)
     if out is None:
-        ids = torch.empty((nq, k), dtype=torch.int64, device=q.device)
-        dists = torch.empty((nq, k), dtype=torch.float32, device=q.device)
+        ids = torch.empty((nq, k_max), dtype=torch.int64, device=q.device)
+        dists = torch.empty((nq, k_max), dtype=torch.float32, device=q.device)
     else:
         ids, dists = out
-    _check(lib().panorama_search_pq(idx.handle, q.data_ptr(), nq, int(nprobe), int(k),
-                                    ids.data_ptr(), dists.data_ptr(), int(mode),
-                                    (1 if collect_stats else 0) | (2 if collect_timing else 0),
-                                    float(epsilon), _stream_ptr(stream)))
+    opts = SearchOpts(mode=mode, synchronize=1, collect_stats=1 if collect_stats else 0,
+                      collect_timing=1 if collect_timing else 0, epsilon=float(epsilon))
+    _check(lib().panorama_search_pq_ex(idx.handle, q.data_ptr(), nq, np_ptr, np_scalar,
+                                       k_ptr, k_scalar, k_max, ids.data_ptr(),
+                                       dists.data_ptr(), ctypes.byref(opts),
+                                       _stream_ptr(stream)))
     return ids, dists
 
 

@@ -315,10 +315,11 @@ struct PqArgs {
   const float* codebook;
   const float* cent_t;
   const float* qt;
-  const int2* pairs;  // (query, list), nearest lists first, then by list
+  const int2* pairs;  // (query, list), nearest lists first, then by list; x < 0: none
+  const int32_t* kq;  // per-query k (<= k_max); a query's top-k row holds k_max slots
   unsigned long long* topk;
   unsigned long long* stats;
-  int d, M, dsub, L, ML, b, k, prune, collect;
+  int d, M, dsub, L, ML, b, k_max, prune, collect;
   float lo;    // (1 - gamma) factor of the lower bound, rounded down
   float erel;  // relative allowance for the roundings of s_q, s_x and |s_q - s_x|
   float eps;   // Eq. 4 (1 = the exact, margined test)
@@ -534,7 +535,7 @@ __global__ void __launch_bounds__(PQ_NT, 3) pq_verify_kernel(const PqArgs a) {
   float* lut = (float*)carve((size_t)ML * PQ_KSUB * 4);
   float* pacc = (float*)carve((size_t)2 * PQ_S * 4);
   uint16_t* live = (uint16_t*)carve((size_t)2 * PQ_S * 2);
-  int* ctr = (int*)carve(64);  // [0] survivors of the level, [2] threshold bits,
+  int* ctr = (int*)carve(64);  // [0] survivors of the level, [2] threshold bits, [3] k,
                                // [8..15] four 64-bit section clocks
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -554,11 +555,16 @@ __global__ void __launch_bounds__(PQ_NT, 3) pq_verify_kernel(const PqArgs a) {
     }
   };
   const int2 pr = a.pairs[blockIdx.x];
+  if (pr.x < 0) return;  // a slot of a query that probes fewer lists
   const int q = pr.x, c = pr.y;
   const int nc = a.list_size[c];
-  if (nc == 0) return;
+  if (nc == 0 || a.kq[q] == 0) return;
   const int64_t blk0 = a.blk_off[c];
-  unsigned long long* slots = a.topk + (size_t)q * a.k;
+  unsigned long long* slots = a.topk + (size_t)q * a.k_max;
+  // the query's k, read from shared memory where it is used (kept out of
+  // the registers the level loops need)
+  volatile int* s_kq = ctr + 3;
+  if (tid == 0) *s_kq = a.kq[q];
 
   for (int j = tid; j < d; j += PQ_NT)
     r[j] = __fsub_rn(a.qt[(size_t)q * d + j], a.cent_t[(size_t)c * d + j]);
@@ -611,7 +617,7 @@ __global__ void __launch_bounds__(PQ_NT, 3) pq_verify_kernel(const PqArgs a) {
           const int64_t blk = blk0 + g / PQ_B;
           const int ln = g % PQ_B;
           for (int ll = l; ll < L; ++ll) {
-            const float tq = threshold_of(slots, a.k);
+            const float tq = threshold_of(slots, *s_kq);
             const uint8_t* cp = a.codes + (blk * M + (int64_t)ll * ML) * PQ_B + ln;
             P = __fadd_rn(P, level_sum_direct(cp, ML, ll * ML, r, a.codebook, dsub));
             n_dims += a.b;
@@ -619,7 +625,7 @@ __global__ void __launch_bounds__(PQ_NT, 3) pq_verify_kernel(const PqArgs a) {
             if (ll == L - 1) {
               ++n_full;
               const unsigned long long key = make_key(P, a.ids[blk * PQ_B + ln]);
-              if (key < ld_volatile_u64(slots + a.k - 1)) topk_insert_thread(slots, a.k, key);
+              if (key < ld_volatile_u64(slots + *s_kq - 1)) topk_insert_thread(slots, *s_kq, key);
             } else if (!pq_keep(P, a.xtail[(blk * L + ll) * PQ_B + ln], sq[ll], tq, a.erel,
                                 a.lo, a.eps)) {
               break;
@@ -632,7 +638,7 @@ __global__ void __launch_bounds__(PQ_NT, 3) pq_verify_kernel(const PqArgs a) {
       }
       if (tid == 0) {
         ctr[0] = 0;
-        ctr[2] = __float_as_int(threshold_of(slots, a.k));
+        ctr[2] = __float_as_int(threshold_of(slots, *s_kq));
       }
       const bool use_lut = nl >= PQ_LUT_MIN;
       if (use_lut && lut_level != l) {
@@ -684,7 +690,7 @@ __global__ void __launch_bounds__(PQ_NT, 3) pq_verify_kernel(const PqArgs a) {
             Pv[c] = P;
             if (last) {
               const unsigned long long key = make_key(P, a.ids[blk * PQ_B + ln + c]);
-              if (key < ld_volatile_u64(slots + a.k - 1)) topk_insert_thread(slots, a.k, key);
+              if (key < ld_volatile_u64(slots + *s_kq - 1)) topk_insert_thread(slots, *s_kq, key);
             } else {
               keep[c] = passes(P, sxv[c]);
             }
@@ -701,7 +707,7 @@ __global__ void __launch_bounds__(PQ_NT, 3) pq_verify_kernel(const PqArgs a) {
           Pv[0] = P;
           if (last) {
             const unsigned long long key = make_key(P, a.ids[blk * PQ_B + ln]);
-            if (key < ld_volatile_u64(slots + a.k - 1)) topk_insert_thread(slots, a.k, key);
+            if (key < ld_volatile_u64(slots + *s_kq - 1)) topk_insert_thread(slots, *s_kq, key);
           } else {
             keep[0] = passes(P, a.xtail[(blk * L + l) * PQ_B + ln]);
           }
@@ -768,7 +774,8 @@ __global__ void __launch_bounds__(256) pq_seed_kernel(const PqArgs a,
   const int q = blockIdx.x;
   const int c = probes[(size_t)q * nprobe];
   const int ns = min(PQ_SEED, a.list_size[c]);
-  if (ns == 0) return;
+  const int kq = a.kq[q];
+  if (ns == 0 || kq == 0) return;
   const int64_t blk0 = a.blk_off[c];
   for (int j = threadIdx.x; j < d; j += blockDim.x)
     r[j] = __fsub_rn(a.qt[(size_t)q * d + j], a.cent_t[(size_t)c * d + j]);
@@ -787,17 +794,36 @@ __global__ void __launch_bounds__(256) pq_seed_kernel(const PqArgs a,
     float P = 0.f;
     for (int l = 0; l < L; ++l) P = __fadd_rn(P, part[cand * L + l]);
     const int64_t blk = blk0 + cand / PQ_B;
-    topk_insert_thread(a.topk + (size_t)q * a.k, a.k,
+    topk_insert_thread(a.topk + (size_t)q * a.k_max, kq,
                        make_key(P, a.ids[blk * PQ_B + cand % PQ_B]));
   }
 }
 
 // Pair order: each query's nearest list first (grouped by list), then the
 // other probes (grouped by list).  bucket b = (rank > 0) * nlist + list.
-__global__ void pq_pair_count_kernel(const int32_t* __restrict__ probes, int64_t nq, int nprobe,
-                                     int nlist, int* __restrict__ cnt) {
+// Per-query probe counts and k, clamped to [1, cap] and [0, k_max].
+__global__ void pq_prep_kernel(int64_t nq, const int32_t* __restrict__ npq_in, int cap,
+                               const int32_t* __restrict__ kq_in, int k, int k_max,
+                               int32_t* __restrict__ npq, int32_t* __restrict__ kq) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nq * nprobe) return;
+  if (i >= nq) return;
+  npq[i] = npq_in ? min(max(npq_in[i], 1), cap) : cap;
+  kq[i] = kq_in ? min(max(kq_in[i], 0), k_max) : k;
+}
+
+// A probe slot makes a pair when its rank is below the query's nprobe and
+// the query wants at least one result.
+__device__ __forceinline__ bool pq_pair_live(int64_t i, int nprobe, const int32_t* npq,
+                                             const int32_t* kq) {
+  const int64_t q = i / nprobe;
+  return (int)(i % nprobe) < npq[q] && kq[q] > 0;
+}
+
+__global__ void pq_pair_count_kernel(const int32_t* __restrict__ probes, int64_t nq, int nprobe,
+                                     int nlist, const int32_t* __restrict__ npq,
+                                     const int32_t* __restrict__ kq, int* __restrict__ cnt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq * nprobe || !pq_pair_live(i, nprobe, npq, kq)) return;
   const int rank = (int)(i % nprobe);
   atomicAdd(cnt + (rank > 0) * nlist + probes[i], 1);
 }
@@ -825,10 +851,11 @@ __global__ void __launch_bounds__(1024) pq_pair_scan_kernel(const int* __restric
 }
 
 __global__ void pq_pair_scatter_kernel(const int32_t* __restrict__ probes, int64_t nq, int nprobe,
-                                       int nlist, int* __restrict__ fill,
+                                       int nlist, const int32_t* __restrict__ npq,
+                                       const int32_t* __restrict__ kq, int* __restrict__ fill,
                                        const int* __restrict__ off, int2* __restrict__ pairs) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nq * nprobe) return;
+  if (i >= nq * nprobe || !pq_pair_live(i, nprobe, npq, kq)) return;
   const int rank = (int)(i % nprobe);
   const int c = probes[i];
   const int b = (rank > 0) * nlist + c;
@@ -1099,15 +1126,19 @@ int build_ivfpq(const pano_transform* t, const float* X, int64_t n, int nlist,
 }
 
 // ----------------------------------------------------------------- search
-int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe, int k,
-              int64_t* out_ids, float* out_dists, int mode, int collect, float epsilon,
-              cudaStream_t st) {
+// npq_in / kq_in: device per-query nprobe / k (clamped), or null for the
+// scalars; with npq_in, nprobe is the cap of every query's probes.
+int search_pq(const pano_index* ip, const float* queries, int64_t nq, const int32_t* npq_in,
+              int nprobe, const int32_t* kq_in, int k, int k_max, int64_t* out_ids,
+              float* out_dists, int mode, int collect, float epsilon, cudaStream_t st) {
   PANO_CHECK(ip, PANO_EINVAL, "null index");
   const pano_index& I = *ip;
   PANO_CHECK(I.pq_M > 0, PANO_EINVAL, "not an IVFPQ index (panorama_build_ivfpq)");
   PANO_CHECK(nq >= 0 && nq < (1LL << 31), PANO_EINVAL, "nq out of range");
   PANO_CHECK(nq == 0 || (queries && out_ids && out_dists), PANO_EINVAL, "null argument");
-  PANO_CHECK(k >= 1 && k <= 1024, PANO_EINVAL, "k must be in [1, 1024]");
+  PANO_CHECK(k_max >= 1 && k_max <= 1024, PANO_EINVAL, "k_max must be in [1, 1024]");
+  if (!kq_in) PANO_CHECK(k >= 0 && k <= k_max, PANO_EINVAL, "k must be in [0, k_max]");
+  if (npq_in) nprobe = nprobe >= 1 ? std::min(nprobe, I.nlist) : I.nlist;
   PANO_CHECK(nprobe >= 1 && nprobe <= I.nlist, PANO_EINVAL, "nprobe must be in [1, nlist]");
   PANO_CHECK((int64_t)nq * nprobe < (1LL << 31), PANO_EINVAL, "too many (query, list) pairs");
   pano_search_stats& S = stats_slot();
@@ -1134,7 +1165,9 @@ int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe
   const size_t o_cnt = take((size_t)2 * nlist * 4);
   const size_t o_fill = take((size_t)2 * nlist * 4);
   const size_t o_off = take((size_t)2 * nlist * 4);
-  const size_t o_topk = take((size_t)nq * k * 8);
+  const size_t o_topk = take((size_t)nq * k_max * 8);
+  const size_t o_npq = take((size_t)nq * 4);
+  const size_t o_kq = take((size_t)nq * 4);
   const size_t o_stats = take(16 * 8);
   void* ws = nullptr;
   PANO_CUDA(cudaMallocAsync(&ws, off, st));
@@ -1147,6 +1180,8 @@ int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe
   int* poff = (int*)(W + o_off);
   unsigned long long* topk = (unsigned long long*)(W + o_topk);
   unsigned long long* stats = (unsigned long long*)(W + o_stats);
+  int32_t* npq = (int32_t*)(W + o_npq);
+  int32_t* kq = (int32_t*)(W + o_kq);
 
   cudaEvent_t ev[6] = {};
   if (timing)
@@ -1157,8 +1192,11 @@ int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe
   auto body = [&]() -> int {
     PANO_CUDA(cudaMemsetAsync(cnt, 0, (size_t)2 * nlist * 4, st));
     PANO_CUDA(cudaMemsetAsync(fill, 0, (size_t)2 * nlist * 4, st));
-    PANO_CUDA(cudaMemsetAsync(topk, 0xff, (size_t)nq * k * 8, st));
+    PANO_CUDA(cudaMemsetAsync(topk, 0xff, (size_t)nq * k_max * 8, st));
+    PANO_CUDA(cudaMemsetAsync(pairs, 0xff, (size_t)npairs * 8, st));  // (-1, -1): no pair
     PANO_CUDA(cudaMemsetAsync(stats, 0, 16 * 8, st));
+    pq_prep_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(nq, npq_in, nprobe, kq_in, k,
+                                                                k_max, npq, kq);
     // q~ = T~(q - mu~)
     mark(0);
     PANO_CUDA(gemm_nt(kStore, (int)nq, d, d, queries, d, I.mu32.as<float>(), I.T32.as<float>(),
@@ -1168,9 +1206,10 @@ int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe
     if (rc) return rc;
     mark(2);
     const unsigned pg = (unsigned)((npairs + 255) / 256);
-    pq_pair_count_kernel<<<pg, 256, 0, st>>>(probes, nq, nprobe, nlist, cnt);
+    pq_pair_count_kernel<<<pg, 256, 0, st>>>(probes, nq, nprobe, nlist, npq, kq, cnt);
     pq_pair_scan_kernel<<<1, 1024, 0, st>>>(cnt, 2 * nlist, poff);
-    pq_pair_scatter_kernel<<<pg, 256, 0, st>>>(probes, nq, nprobe, nlist, fill, poff, pairs);
+    pq_pair_scatter_kernel<<<pg, 256, 0, st>>>(probes, nq, nprobe, nlist, npq, kq, fill, poff,
+                                               pairs);
     PANO_CUDA(cudaGetLastError());
 
     PqArgs a;
@@ -1192,7 +1231,8 @@ int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe
     a.L = L;
     a.ML = ML;
     a.b = d / L;
-    a.k = k;
+    a.kq = kq;
+    a.k_max = k_max;
     a.prune = mode == 0 ? 1 : 0;
     a.collect = counts ? 1 : 0;
     // D~ >= (1-u)^(L + ML + dsub + 2) (D_head~ + (sqrt R_q - sqrt R_x)^2) (level
@@ -1220,7 +1260,7 @@ int search_pq(const pano_index* ip, const float* queries, int64_t nq, int nprobe
     pq_verify_kernel<<<(unsigned)npairs, PQ_NT, vsm, st>>>(a);
     PANO_CUDA(cudaGetLastError());
     mark(4);
-    pq_decode_kernel<<<(unsigned)((nq * k + 255) / 256), 256, 0, st>>>(topk, nq * k, out_ids,
+    pq_decode_kernel<<<(unsigned)((nq * k_max + 255) / 256), 256, 0, st>>>(topk, nq * k_max, out_ids,
                                                                       out_dists);
     PANO_CUDA(cudaGetLastError());
     mark(5);
@@ -1373,7 +1413,19 @@ int panorama_search_pq(const pano_index* idx, const float* queries, int64_t nq, 
                        int32_t k, int64_t* out_ids, float* out_dists, int32_t mode,
                        int32_t collect_stats, float epsilon, void* stream) {
   clear_error();
-  return search_pq(idx, queries, nq, nprobe, k, out_ids, out_dists, mode, collect_stats, epsilon,
+  PANO_CHECK(k >= 1 && k <= 1024, PANO_EINVAL, "k must be in [1, 1024]");
+  return search_pq(idx, queries, nq, nullptr, nprobe, nullptr, k, k, out_ids, out_dists, mode,
+                   collect_stats, epsilon, (cudaStream_t)stream);
+}
+
+int panorama_search_pq_ex(const pano_index* idx, const float* queries, int64_t nq,
+                          const int32_t* nprobe, int32_t nprobe_scalar, const int32_t* k,
+                          int32_t k_scalar, int32_t k_max, int64_t* out_ids, float* out_dists,
+                          const pano_search_opts* opts, void* stream) {
+  clear_error();
+  const int collect = opts ? ((opts->collect_stats ? 1 : 0) | (opts->collect_timing ? 2 : 0)) : 0;
+  return search_pq(idx, queries, nq, nprobe, nprobe_scalar, k, k_scalar, k_max, out_ids,
+                   out_dists, opts ? opts->mode : 0, collect, opts ? opts->epsilon : 1.f,
                    (cudaStream_t)stream);
 }
 

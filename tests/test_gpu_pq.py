@@ -247,6 +247,38 @@ def test_pq_epsilon_relaxed_pruning():
         assert np.allclose(d_e[i][v], true, rtol=RTOL_D)
 
 
+def test_pq_per_query_nprobe_and_k():
+    """Each query its own nprobe (1..6 of 6 lists) and k (0, 1, 10 or 37) in
+    rows of k_max = 40: every row matches the oracle for its own probes and
+    k, and is padded past it; the pruned search equals the plain scan."""
+    g = np.random.default_rng(80)
+    d, L, M, n, nl, nq = 64, 4, 32, 8000, 6, 50
+    X = (g.standard_normal((n, d)) * np.exp(-0.04 * np.arange(d))).astype(np.float32)
+    C = X[g.choice(n, nl, replace=False)]
+    lists, _ = oracle.assign(X, C)
+    Ts, mu, vs = _shaped(X, L, 2.0, 81)
+    R = oracle.transform(Ts, mu, X) - oracle.transform(Ts, mu, C)[lists]
+    cb = pq.pq_train(R[:2000], M, iters=2, seed=82)
+    codes = pq.pq_encode32(R.astype(np.float32), cb)
+    t = pano.panorama_transform_import(Ts, mu, vs)
+    idx = pano.panorama_build_ivfpq(t, X, nl, M, L, centroids=C, assign=lists, codebooks=cb,
+                                    codes=codes)
+    Q = (X[:nq] + 0.05 * g.standard_normal((nq, d))).astype(np.float32)
+    npq = g.integers(1, nl + 1, nq).astype(np.int32)
+    kq = g.choice([0, 1, 10, 37], nq).astype(np.int32)
+    q = torch.from_numpy(Q).to(DEV)
+    a = idx.search_pq(q, torch.from_numpy(npq).to(DEV), torch.from_numpy(kq).to(DEV), k_max=40)
+    b = idx.search_pq(q, torch.from_numpy(npq).to(DEV), torch.from_numpy(kq).to(DEV), k_max=40,
+                      mode=1)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    assert a[0].shape == (nq, 40)
+    probes, gap = oracle.probe(Q, C, npq)
+    cand = _oracle_dists(Q, Ts, mu, C, lists, cb, codes, probes)
+    for i in range(nq):
+        if gap[i] >= 1e-6:
+            _check(a[0][i:i + 1], a[1][i:i + 1], [cand[i]], int(kq[i]), np.array([True]))
+
+
 @pytest.mark.parametrize("M,L", [(48, 4), (16, 1), (6, 3), (16, 8), (12, 2)])
 def test_pq_subvector_widths_and_level_counts(M, L):
     """d = 48 with 1-, 3-, 4- and 8-coordinate subvectors (vector and scalar
