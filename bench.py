@@ -37,7 +37,7 @@ KERNELS_PER_SEARCH = 14  # see the launch list in profiles/
 # capture of a smaller case of the same kernel scaled to the full launch
 # (profiles/ holds the capture summary); None once the kernel has changed.
 TRAFFIC = {"ivf-1m-d960-fp32": 834.49e6 + 3.38e6}  # phase B, ncu at full size, one pass
-PQ_TRAFFIC = {"ivf-1m-d960-fp32": 768.4e6 + 1.3e6}  # pruned pq_verify_kernel, ncu at full size, one pass
+PQ_TRAFFIC = {}  # pruned pq_verify_kernel: ncu at full size, one pass (none for this version)
 
 
 def parse():

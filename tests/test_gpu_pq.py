@@ -51,6 +51,8 @@ def _check(got_i, got_d, cand, k, keep):
         order = np.lexsort((mem, D))[:k]
         nv = order.size
         assert np.all(got_i[i, nv:] == -1) and np.all(np.isinf(got_d[i, nv:])), i
+        if nv == 0:
+            continue
         g = got_i[i, :nv]
         assert len(set(g.tolist())) == nv and np.all(np.isin(g, mem)), (i, g)
         pos = {int(v): j for j, v in enumerate(mem)}
