@@ -176,14 +176,15 @@ def test_epsilon_relaxed_pruning(ivf960):
     ids_e, d_e = idx.search(q, 8, 10, epsilon=0.5, collect_stats=True)
     dims_e = pano.last_stats().dims_scanned
     ids_e, d_e, ids1 = ids_e.cpu().numpy(), d_e.cpu().numpy(), ids1.cpu().numpy()
-    lists = idx.assignment()
+    lists, agap = oracle.assign(X, C)
     probes, gap = oracle.probe(Q, C, 8)
     hits = 0
     for i in range(len(Q)):
         g = ids_e[i][ids_e[i] >= 0]
         assert len(set(g.tolist())) == len(g)
         if gap[i] >= 1e-6:  # (a probe near-tie may be ordered either way)
-            assert np.all(np.isin(lists[g], probes[i]))
+            # in a probed list of the oracle's assignment (or an assignment near-tie)
+            assert np.all(np.isin(lists[g], probes[i]) | (agap[g] < 1e-6))
         true_d = ((X[g].astype(np.float64) - Q[i]) ** 2).sum(1)
         assert np.all(np.abs(d_e[i][:len(g)] - true_d) <= 1e-5 * np.maximum(true_d, 1e-30))
         assert np.all(np.diff(d_e[i][:len(g)]) >= 0)
