@@ -45,7 +45,9 @@ codebooks hold the data, LB <= ADC <= UB with equality at the last level, the
 Eq. 3 identity, Algorithm 1 over ADC equal to the plain ADC top-k, the
 invariance of every level bound under Procedure 2, and the trade Procedure 1
 makes (more coordinates read by Algorithm 1, lower PQ reconstruction error
-than the PCA basis at the same bit budget).
+than the PCA basis at the same bit budget), and pq_train's Lloyd steps (the
+blob means as the fixed point on separated blobs, a non-increasing
+quantisation error).
 """
 from __future__ import annotations
 

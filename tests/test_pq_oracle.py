@@ -271,3 +271,25 @@ def test_robin_hood_trades_pruning_for_pq_balance():
         return float(((pq.pq_reconstruct(codes, cb) - R) ** 2).sum(1).mean())
 
     assert pq_mse(Ts) < pq_mse(np.eye(d))
+
+
+def test_pq_train_lloyd_properties():
+    """pq_train is Lloyd's algorithm per subspace: on two well-separated blobs
+    with two codewords its fixed point is the pair of blob means (closed
+    form), and more iterations never raise the quantisation error (each
+    step cannot increase the objective)."""
+    g = np.random.default_rng(12)
+    A = g.standard_normal((500, 2)) * 0.1 + 10.0
+    B = g.standard_normal((700, 2)) * 0.1 - 10.0
+    X = np.concatenate([A, B])
+    cb = pq.pq_train(X, 1, ksub=2, iters=10, seed=1)[0].astype(np.float64)
+    cb = cb[np.argsort(cb[:, 0])]
+    np.testing.assert_allclose(cb, np.stack([B.mean(0), A.mean(0)]), atol=1e-6)
+    Y = g.standard_normal((4000, 8)) * np.exp(-0.2 * np.arange(8))
+    errs = []
+    for it in (0, 1, 3, 8):
+        cb = pq.pq_train(Y, 2, iters=it, seed=2)
+        codes = pq.pq_encode32(Y.astype(np.float32), cb)
+        errs.append(((pq.pq_reconstruct(codes, cb) - Y) ** 2).sum(1).mean())
+    assert all(b <= a * (1 + 1e-6) for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < errs[0]
