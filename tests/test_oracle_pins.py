@@ -91,6 +91,55 @@ def test_spectrum_recovery_and_alpha_on_128d_workload():
     assert 5.5 < alpha < 7.5
 
 
+def test_fit_alpha_recovers_an_exact_exponential():
+    """lambda_i = exp(-beta i) with beta d = 50: E(m) equals exp(-50 m / d)
+    up to exp(-50) ~ 2e-22, so the fit must return alpha = 50 to 1e-6 and a
+    vanishing error."""
+    d, beta = 1000, 0.05
+    alpha, mae = oracle.fit_alpha(np.exp(-beta * np.arange(d)))
+    assert abs(alpha - beta * d) < 1e-6 * beta * d, alpha
+    assert mae < 1e-9
+
+
+def test_fit_alpha_least_squares_optimum_by_hand():
+    """Two levels (d = 2): E = (1, r, 0).  The squared error of exp(-a m / 2)
+    over m = 0..2 is (r - u)^2 + u^4 with u = exp(-a / 2); it is least where
+    2 u^3 + u - r = 0.  Taking u = 0.35 gives r = 0.43575, i.e. the spectrum
+    (0.56425, 0.43575), alpha = -2 ln 0.35, and the mean absolute error over
+    the three points (0 + 2u^3 + u^2) / 3 = 0.0694166...  A fit of log E, or
+    an error averaged over m = 1..d only, gives other numbers."""
+    u = 0.35
+    r = 2 * u ** 3 + u
+    alpha, mae = oracle.fit_alpha(np.array([1.0 - r, r]))
+    assert abs(alpha - (-2.0 * np.log(u))) < 1e-6, alpha
+    assert abs(mae - (2 * u ** 3 + u ** 2) / 3) < 1e-9, mae
+
+
+def test_candidate_topk_golden():
+    """tests/golden/refine_candidates.txt: hand-derived answers of Problem 1
+    over explicit candidate lists with repeats, -1 padding, ties and an empty
+    set (the refine workload's reading of a candidate list)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "refine_candidates.txt")
+    X, cases = {}, []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        if line.startswith("X "):
+            f = line.split()
+            X[int(f[1])] = (float(f[2]), float(f[3]))
+        else:
+            q, cand, k, ids, dists = [p.split() for p in line[2:].split("|")]
+            cases.append((np.array(q, float), np.array(cand, np.int64), int(k[0]),
+                          np.array(ids, np.int64), np.array([float(v) for v in dists])))
+    Xa = np.array([X[i] for i in range(len(X))], dtype=np.float32)
+    assert len(cases) == 4
+    for q, cand, k, ids, dists in cases:
+        gi, gd = oracle.candidate_topk(Xa, q[None].astype(np.float32), cand[None], k)
+        np.testing.assert_array_equal(gi[0], ids)
+        np.testing.assert_array_equal(gd[0], dists)
+
+
 def test_energy_fraction_closed_form():
     # geometric spectrum: E(m) = r^m (1 - r^(d-m)) / (1 - r^d)
     d, r = 50, 0.9
