@@ -234,9 +234,10 @@ int panorama_search_ex(const pano_index* idx, const float* queries,
  * a call whose workspace would exceed it fails with PANO_EINVAL before any
  * work is queued (the workspace grows with nq x (d + nlist + nprobe + k_max)).
  * The array's device address is looked up on the first call on each device
- * (make that call before any stream capture).  Every call reuses the same
- * array, so calls that overlap on the GPU race; serialise them on one
- * stream. */
+ * (make that call before any stream capture).  The call returns once the
+ * search has finished: it synchronizes the stream and reads the device
+ * error word, like panorama_search.  Every call reuses the same array, so
+ * calls that overlap on the GPU race; serialise them on one stream. */
 int panorama_search_noalloc(const pano_index* idx, const float* queries, int64_t nq,
                             const int32_t* nprobe, int32_t nprobe_scalar,
                             const int32_t* k, int32_t k_scalar, int32_t k_max,
@@ -244,6 +245,14 @@ int panorama_search_noalloc(const pano_index* idx, const float* queries, int64_t
 
 /* Counters of this thread's last search_ex with collect_stats = 1. */
 int panorama_search_stats(pano_search_stats* out);
+/* Status code of a device error word (pano_search_stats.device_error, or
+ * the word a caller copied back itself): word & 1 (a bounded device-side
+ * wait gave up; the top-k may be partial) -> PANO_ETIMEOUT; word & 4 (a
+ * per-query value out of range was clamped, or an FP8 query exceeds the
+ * format's range) -> PANO_EINVAL; otherwise PANO_OK (word & 2, a capacity
+ * bound reached with the result still valid, is not an error).  Pure host
+ * function; the serving loop maps each batch's word with it. */
+int panorama_status_of_device_error(int32_t word);
 
 /* ------------------------------------------------------------------ refine
  * panorama_build_flat -- flat index for refining candidate-id lists, the

@@ -121,6 +121,7 @@ SIGNATURES = {
     "panorama_search_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _I32, _P, _I32,
                                                 _I32, _P, _P, _P]),
     "panorama_search_stats": (ctypes.c_int, [_P]),
+    "panorama_status_of_device_error": (ctypes.c_int, [_I32]),
     "panorama_probe": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P]),
     "panorama_index_info": (ctypes.c_int, [_P, _P]),
     "panorama_index_centroids": (ctypes.c_int, [_P, _P]),

@@ -225,6 +225,8 @@ int panorama_search_stats(pano_search_stats* out) {
   return PANO_OK;
 }
 
+int panorama_status_of_device_error(int32_t word) { return status_of_device_error(word); }
+
 int panorama_probe(const pano_index* idx, const float* queries, int64_t nq, int32_t nprobe,
                    int32_t* out_lists, void* stream) {
   clear_error();

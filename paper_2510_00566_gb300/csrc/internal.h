@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <functional>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -44,6 +45,33 @@ constexpr int GEMM_KT = 16;
 inline double gemm_rounds(int K) { return GEMM_KT + (K + GEMM_KT - 1) / GEMM_KT + 1; }
 
 // ------------------------------------------------------------ host helpers
+// Runs a set-up step once per device (the current one at the call): kernel
+// attributes such as the dynamic shared-memory limit belong to the device's
+// context, so a process that searches on several devices sets them on each.
+// Returns that device's result (an error is kept, not retried).
+class PerDeviceOnce {
+ public:
+  template <class F>
+  cudaError_t run(F&& setup) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu_);
+    if (!done_[dev]) {
+      err_[dev] = setup();
+      done_[dev] = true;
+    }
+    return err_[dev];
+  }
+
+ private:
+  static constexpr int kMaxDevices = 64;
+  std::mutex mu_;
+  bool done_[kMaxDevices] = {};
+  cudaError_t err_[kMaxDevices] = {};
+};
+
 void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& fn);
 int fit_pca(const float* X, int64_t n, int d, std::vector<double>& mu,
             std::vector<double>& T, std::vector<double>& lam, std::string& err);

@@ -1391,20 +1391,18 @@ constexpr TileCfg kTilesB[] = {{64, 64, 256, 4}, {32, 64, 128, 4}, {16, 64, 64, 
 
 template <int QB, int CB, int NTH, int NST>
 cudaError_t tile_kernel_attrs(const void** kern, size_t* static_smem) {
-  static std::once_flag once;
-  static cudaError_t err = cudaSuccess;
-  static size_t st_smem = 0;
+  static PerDeviceOnce once;
   auto k = verify_fp32_kernel<QB, CB, NTH, NST>;
-  std::call_once(once, [&] {
-    err = allow_dynamic_smem((const void*)k);
-    if (err == cudaSuccess)
-      err = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncAttributes fa;
-    if (err == cudaSuccess) err = cudaFuncGetAttributes(&fa, k);
-    if (err == cudaSuccess) st_smem = fa.sharedSizeBytes;
+  cudaError_t err = once.run([&] {
+    cudaError_t e = allow_dynamic_smem((const void*)k);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
   });
+  cudaFuncAttributes fa;
+  if (err == cudaSuccess) err = cudaFuncGetAttributes(&fa, k);
   *kern = (const void*)k;
-  *static_smem = st_smem;
+  *static_smem = err == cudaSuccess ? fa.sharedSizeBytes : 0;
   return err;
 }
 
@@ -1468,12 +1466,70 @@ struct Carver {
 
 thread_local pano_search_stats t_stats;
 
+// Pieces of one search's workspace (byte offsets into one allocation): the
+// tiles of the FP32 verify phases, the work-item capacities and the carve.
+struct SearchLayout {
+  TileCfg tileA{TC_QG, 0, 0, 0}, tileB{TC_QG, 0, 0, 0};
+  int bpsA = 0, bpsB = 0;
+  int64_t capA = 0, capB = 0;
+  size_t o_qt, o_qinfo, o_qtail, o_qn2, o_pd, o_pr, o_npq, o_kq, o_seed, o_cnt, o_fill, o_boff,
+      o_ioff, o_tot, o_bucket, o_itA, o_itB, o_topk, o_err, o_stats;
+  size_t total = 0;
+};
+
+int plan_layout(const pano_index& I, int64_t nq, int stride, int k_max, SearchLayout* out) {
+  SearchLayout& y = *out;
+  const int d = I.d, L = I.L, nlist = I.nlist;
+  const bool tcpath = I.precision != PANO_FP32;
+  if (!tcpath) {
+    int r = pick_tile(kTilesA, 3, I.max_w, L, &y.tileA, &y.bpsA);
+    if (!r) r = pick_tile(kTilesB, 3, I.max_w, L, &y.tileB, &y.bpsB);
+    if (r) return r;
+  }
+  const int QBA = y.tileA.QB, QBB = y.tileB.QB;
+  const int SEG = tcpath ? TC_SEG : SEG_CHUNKS;
+  // work-item capacity: groups x segments, plus one partial group per list
+  int64_t max_seg = 1, tot_seg = 0;
+  for (int c = 0; c < nlist; ++c) {
+    int64_t nch = I.list_chunk_off[c + 1] - I.list_chunk_off[c];
+    int64_t s = (nch + SEG - 1) / SEG;
+    max_seg = std::max(max_seg, s);
+    tot_seg += s;
+  }
+  y.capA = ((nq + QBA - 1) / QBA) * max_seg + tot_seg;
+  y.capB = ((nq * stride + QBB - 1) / QBB) * max_seg + tot_seg;
+  Carver cv;
+  y.o_qt = cv.take<float>((size_t)nq * d);
+  y.o_qinfo = cv.take<float4>(nq);
+  y.o_qtail = cv.take<float>((size_t)nq * (L + 1));
+  y.o_qn2 = cv.take<float>(nq);
+  y.o_pd = nlist > 1 ? cv.take<float>((size_t)nq * nlist) : 0;
+  y.o_pr = cv.take<int32_t>((size_t)nq * stride);
+  y.o_npq = cv.take<int32_t>(nq);
+  y.o_kq = cv.take<int32_t>(nq);
+  y.o_seed = cv.take<float>(nq);
+  y.o_cnt = cv.take<int>(2 * (size_t)nlist);
+  y.o_fill = cv.take<int>(2 * (size_t)nlist);
+  y.o_boff = cv.take<int>(2 * (size_t)(nlist + 1));
+  y.o_ioff = cv.take<int>(2 * (size_t)(nlist + 1));
+  y.o_tot = cv.take<int>(8);
+  y.o_bucket = cv.take<int32_t>((size_t)nq * stride);
+  y.o_itA = cv.take<int4>(y.capA);
+  y.o_itB = cv.take<int4>(std::max<int64_t>(y.capB, 1));
+  y.o_topk = cv.take<unsigned long long>((size_t)nq * k_max);
+  y.o_err = cv.take<int>(4);
+  y.o_stats = cv.take<unsigned long long>(kStatWords);
+  y.total = cv.off;
+  return PANO_OK;
+}
+
+
 }  // namespace
 
 int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t* nprobe,
            int32_t nprobe_scalar, const int32_t* k, int32_t k_scalar, int32_t k_max,
            int64_t* out_ids, float* out_dists, cudaStream_t st, const pano_search_opts* opts,
-           void* ext_ws, size_t ext_cap) {
+           void* ext_ws, size_t ext_cap, int* err_host) {
   PANO_CHECK(ip, PANO_EINVAL, "null index");
   const pano_index& I = *ip;
   PANO_CHECK(!I.flat, PANO_EINVAL, "a flat index is searched with panorama_refine");
@@ -1503,47 +1559,20 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
                             : nprobe_scalar;
   const int stride = np_cap;
   const bool tcpath = I.precision != PANO_FP32;
-  TileCfg tileA{TC_QG, 0, 0, 0}, tileB{TC_QG, 0, 0, 0};
-  int bpsA = 0, bpsB = 0;
-  if (!tcpath) {
-    int r = pick_tile(kTilesA, 3, I.max_w, L, &tileA, &bpsA);
-    if (!r) r = pick_tile(kTilesB, 3, I.max_w, L, &tileB, &bpsB);
-    if (r) return r;
-  }
+  SearchLayout lay;
+  if (int r = plan_layout(I, nq, stride, k_max, &lay)) return r;
+  const TileCfg tileA = lay.tileA, tileB = lay.tileB;
+  const int bpsA = lay.bpsA, bpsB = lay.bpsB;
   const int QBA = tileA.QB, QBB = tileB.QB;
   const int SEG = tcpath ? TC_SEG : SEG_CHUNKS;
-  // work-item capacity: groups x segments, plus one partial group per list
-  int64_t max_seg = 1, tot_seg = 0;
-  for (int c = 0; c < nlist; ++c) {
-    int64_t nch = I.list_chunk_off[c + 1] - I.list_chunk_off[c];
-    int64_t s = (nch + SEG - 1) / SEG;
-    max_seg = std::max(max_seg, s);
-    tot_seg += s;
-  }
-  const int64_t capA = ((nq + QBA - 1) / QBA) * max_seg + tot_seg;
-  const int64_t capB = ((nq * stride + QBB - 1) / QBB) * max_seg + tot_seg;
-
+  const int64_t capA = lay.capA, capB = lay.capB;
+  const size_t o_qt = lay.o_qt, o_qinfo = lay.o_qinfo, o_qtail = lay.o_qtail, o_qn2 = lay.o_qn2,
+               o_pd = lay.o_pd, o_pr = lay.o_pr, o_npq = lay.o_npq, o_kq = lay.o_kq,
+               o_seed = lay.o_seed, o_cnt = lay.o_cnt, o_fill = lay.o_fill, o_boff = lay.o_boff,
+               o_ioff = lay.o_ioff, o_tot = lay.o_tot, o_bucket = lay.o_bucket, o_itA = lay.o_itA,
+               o_itB = lay.o_itB, o_topk = lay.o_topk, o_err = lay.o_err, o_stats = lay.o_stats;
   Carver cv;
-  size_t o_qt = cv.take<float>((size_t)nq * d);
-  size_t o_qinfo = cv.take<float4>(nq);
-  size_t o_qtail = cv.take<float>((size_t)nq * (L + 1));
-  size_t o_qn2 = cv.take<float>(nq);
-  size_t o_pd = nlist > 1 ? cv.take<float>((size_t)nq * nlist) : 0;
-  size_t o_pr = cv.take<int32_t>((size_t)nq * stride);
-  size_t o_npq = cv.take<int32_t>(nq);
-  size_t o_kq = cv.take<int32_t>(nq);
-  size_t o_seed = cv.take<float>(nq);
-  size_t o_cnt = cv.take<int>(2 * (size_t)nlist);
-  size_t o_fill = cv.take<int>(2 * (size_t)nlist);
-  size_t o_boff = cv.take<int>(2 * (size_t)(nlist + 1));
-  size_t o_ioff = cv.take<int>(2 * (size_t)(nlist + 1));
-  size_t o_tot = cv.take<int>(8);
-  size_t o_bucket = cv.take<int32_t>((size_t)nq * stride);
-  size_t o_itA = cv.take<int4>(capA);
-  size_t o_itB = cv.take<int4>(std::max<int64_t>(capB, 1));
-  size_t o_topk = cv.take<unsigned long long>((size_t)nq * k_max);
-  size_t o_err = cv.take<int>(4);
-  size_t o_stats = cv.take<unsigned long long>(kStatWords);
+  cv.off = lay.total;
   void* ws = ext_ws;
   if (ext_ws) {
     PANO_CHECK(cv.off <= ext_cap, PANO_EINVAL,
@@ -1783,6 +1812,9 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
                                                                 out_dists);
     PANO_CUDA(cudaGetLastError());
     mark(6);
+    // the device error word for a caller that does not synchronize (it maps
+    // the word to a status once the stream has passed this copy)
+    if (err_host) PANO_CUDA(cudaMemcpyAsync(err_host, err, 4, cudaMemcpyDeviceToHost, st));
     if (collect) {
       pair_count_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
           nq, probes, stride, npq, I.list_size_d.as<int32_t>(), one_pass ? 0 : 1, stats + 4,
@@ -1822,6 +1854,21 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
   cudaError_t fe = ext_ws ? cudaSuccess : cudaFreeAsync(ws, st);
   if (rc == PANO_OK && fe != cudaSuccess) return cuda_fail(fe, "cudaFreeAsync");
   return rc;
+}
+
+int search_workspace_bytes(const pano_index* ip, int64_t nq, int32_t stride, int32_t k_max,
+                           size_t* out) {
+  PANO_CHECK(ip && out && nq >= 0 && stride >= 1 && k_max >= 1, PANO_EINVAL, "bad argument");
+  SearchLayout lay;
+  if (int r = plan_layout(*ip, nq, std::min(stride, ip->nlist), k_max, &lay)) return r;
+  *out = lay.total;
+  return PANO_OK;
+}
+
+int status_of_device_error(int word) {
+  if (word & kErrTimeout) return PANO_ETIMEOUT;
+  if (word & kErrBadInput) return PANO_EINVAL;
+  return PANO_OK;
 }
 
 int probe_only(const pano_index* ip, const float* queries, int64_t nq, int32_t nprobe,

@@ -8,7 +8,14 @@ namespace pano {
 int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t* nprobe,
            int32_t nprobe_scalar, const int32_t* k, int32_t k_scalar, int32_t k_max,
            int64_t* out_ids, float* out_dists, cudaStream_t st, const pano_search_opts* opts,
-           void* ext_ws = nullptr, size_t ext_cap = 0);
+           void* ext_ws = nullptr, size_t ext_cap = 0, int* err_host = nullptr);
+// Bytes of the device workspace one search of nq queries (probe stride
+// `stride`, k_max results) carves, as search() computes it.
+int search_workspace_bytes(const pano_index* ip, int64_t nq, int32_t stride, int32_t k_max,
+                           size_t* out);
+// Status code of a device error word (kErrTimeout -> PANO_ETIMEOUT,
+// kErrBadInput -> PANO_EINVAL, otherwise PANO_OK).
+int status_of_device_error(int word);
 int probe_only(const pano_index* ip, const float* queries, int64_t nq, int32_t nprobe,
                int32_t* out, cudaStream_t st);
 const pano_search_stats& last_stats();

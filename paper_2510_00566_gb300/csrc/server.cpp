@@ -7,11 +7,14 @@
 // queue is non-empty and the memory budget admits the batch (its search
 // workspace, estimated from the batch shape, plus the slot buffers), the
 // worker moves up to max_batch queued requests into the slot, copies them to
-// the device, enqueues the search and the copy-back, and records the event.
+// the device, enqueues the search, the copy-back of the results and of the
+// search's device error word, and records the event.
 // Batches in different slots overlap on the device; requests that arrive
 // while batches run are admitted to the next free slot.  Finished slots are
-// retired by polling their events: results are handed to the waiting
-// callers and the request latency (submit -> results on the host) recorded.
+// retired by polling their events: the error word decides the batch's status
+// (a bounded device wait that gave up, or an FP8 query out of range, fails
+// every request of the batch), results are handed to the waiting callers and
+// the request latency (submit -> results on the host) recorded.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -51,6 +54,7 @@ struct Slot {
   int32_t *d_np = nullptr, *h_np = nullptr, *d_k = nullptr, *h_k = nullptr;
   int64_t *d_ids = nullptr, *h_ids = nullptr;
   float *d_dists = nullptr, *h_dists = nullptr;
+  int* h_err = nullptr;  // the batch's device error word (pinned), copied after its search
   std::vector<Request> reqs;
   bool busy = false;
   int64_t bytes = 0;  // admitted memory
@@ -80,17 +84,19 @@ struct pano_server {
 
   ~pano_server();
   void run();
-  int64_t batch_bytes(int nq) const;
+  int64_t batch_bytes(int nq, int nprobe_max) const;
 };
 
-int64_t pano_server::batch_bytes(int nq) const {
-  // the search workspace of a batch (see search.cu) plus the slot buffers
-  const int64_t d = idx->d, L = idx->L, nlist = idx->nlist, km = o.k_max;
-  int64_t w = nq * (d * 4 + 16 + (L + 1) * 4 + 4 + (nlist > 1 ? nlist * 4 : 0) +
-                    nlist * 4 * 2 + 12 + km * 8 + 3 * 4) +
-              16 * nlist + 4096 * 32;
-  w += nq * (int64_t)nlist * 4;  // probes + buckets at stride <= nlist
-  return w + (int64_t)o.max_batch * (d * 4 + 8 + km * 12);
+int64_t pano_server::batch_bytes(int nq, int nprobe_max) const {
+  // the search workspace of the batch, as the search carves it, plus the
+  // slot buffers; the search's own layout at the largest stride if its
+  // sizing fails (it then fails in the search as well)
+  size_t ws = 0;
+  if (pano::search_workspace_bytes(idx, nq, nprobe_max, o.k_max, &ws) != PANO_OK &&
+      pano::search_workspace_bytes(idx, nq, idx->nlist, o.k_max, &ws) != PANO_OK)
+    ws = 0;
+  const int64_t d = idx->d, km = o.k_max;
+  return (int64_t)ws + (int64_t)o.max_batch * (d * 4 + 8 + km * 12);
 }
 
 pano_server::~pano_server() {
@@ -113,6 +119,7 @@ pano_server::~pano_server() {
     cudaFreeHost(s.h_k);
     cudaFreeHost(s.h_ids);
     cudaFreeHost(s.h_dists);
+    cudaFreeHost(s.h_err);
     if (s.ev) cudaEventDestroy(s.ev);
     if (s.stream) cudaStreamDestroy(s.stream);
   }
@@ -128,6 +135,9 @@ void pano_server::run() {
     for (Slot& s : slots) {
       if (!s.busy) continue;
       if (s.status == PANO_OK && cudaEventQuery(s.ev) == cudaErrorNotReady) continue;
+      // a bounded device wait that gave up (partial top-k) or a query the
+      // storage format cannot hold fails every request of the batch
+      if (s.status == PANO_OK) s.status = pano::status_of_device_error(*s.h_err);
       const auto now = Clock::now();
       for (size_t i = 0; i < s.reqs.size(); ++i) {
         Result& r = results[s.reqs[i].ticket];
@@ -158,7 +168,9 @@ void pano_server::run() {
       if (queue.empty()) break;
       if (s.busy) continue;
       const int nb = (int)std::min<size_t>(queue.size(), (size_t)o.max_batch);
-      const int64_t bytes = batch_bytes(nb);
+      int np_batch = 1;
+      for (int i = 0; i < nb; ++i) np_batch = std::max(np_batch, queue[i].nprobe);
+      const int64_t bytes = batch_bytes(nb, np_batch);
       const bool any_busy =
           std::any_of(slots.begin(), slots.end(), [](const Slot& x) { return x.busy; });
       if (any_busy && in_flight_bytes + bytes > o.memory_budget) break;  // wait for memory
@@ -187,8 +199,9 @@ void pano_server::run() {
       if (rc == PANO_OK) {
         pano_search_opts so{};
         so.synchronize = 0;
+        *s.h_err = 0;
         rc = pano::search(idx, s.d_q, nb, s.d_np, std::min(np_max, idx->nlist), s.d_k, 0, km,
-                          s.d_ids, s.d_dists, s.stream, &so);
+                          s.d_ids, s.d_dists, s.stream, &so, nullptr, 0, s.h_err);
       }
       if (rc == PANO_OK) {
         e = cudaMemcpyAsync(s.h_ids, s.d_ids, (size_t)nb * km * 8, cudaMemcpyDeviceToHost, s.stream);
@@ -253,6 +266,8 @@ int panorama_server_create(const pano_index* idx, const pano_server_opts* opts,
     PANO_CUDA(cudaMallocHost(&sl.h_k, mb * 4));
     PANO_CUDA(cudaMallocHost(&sl.h_ids, (size_t)mb * km * 8));
     PANO_CUDA(cudaMallocHost(&sl.h_dists, (size_t)mb * km * 4));
+    PANO_CUDA(cudaMallocHost(&sl.h_err, sizeof(int)));
+    *sl.h_err = 0;
   }
   pano_server* raw = s.get();
   s->worker = std::thread([raw] { raw->run(); });

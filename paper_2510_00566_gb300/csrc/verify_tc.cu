@@ -988,23 +988,23 @@ size_t verify_tc_smem(int max_w, bool fp8) {
 }
 
 int launch_verify_tc(const VerifyTCArgs& a, cudaStream_t st) {
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [&] {
+  static PerDeviceOnce once;
+  PANO_CUDA(once.run([] {
     int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     for (const void* k : {(const void*)verify_tc_kernel<false>, (const void*)verify_tc_kernel<true>}) {
       cudaFuncAttributes fa;
-      if (attr_err == cudaSuccess) attr_err = cudaFuncGetAttributes(&fa, k);
-      if (attr_err == cudaSuccess)
-        attr_err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        optin - (int)fa.sharedSizeBytes);
-      if (attr_err == cudaSuccess)
-        attr_err = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     }
-  });
-  PANO_CUDA(attr_err);
+    return e;
+  }));
   const size_t smem = verify_tc_smem(a.max_w, a.fp8 != 0);
   int dev = 0, sms = 0, optin = 0;
   PANO_CUDA(cudaGetDevice(&dev));

@@ -79,3 +79,15 @@ def test_host_pca_fit_on_constructed_spectrum(L):
     np.testing.assert_allclose(ev, lam, rtol=1e-5)
     np.testing.assert_allclose(np.abs(T @ O), np.eye(d), atol=1e-4)
     assert all(T[r, np.argmax(np.abs(T[r]))] > 0 for r in range(d))
+
+
+def test_device_error_word_maps_to_status(L):
+    """The serving loop retires each batch with the status of its device
+    error word: a bounded wait that gave up -> PANO_ETIMEOUT, an input the
+    search had to clamp or cannot represent -> PANO_EINVAL, a capacity note
+    alone -> success."""
+    f = L.panorama_status_of_device_error
+    assert f(0) == 0
+    assert f(1) == -4 and f(1 | 2) == -4 and f(1 | 4) == -4
+    assert f(4) == -1 and f(4 | 2) == -1
+    assert f(2) == 0

@@ -41,23 +41,8 @@ def _candidates(X, Q, kp, n_true, seed):
     return out
 
 
-def _reference(X, Q, cand, k):
-    """FP64 top-k over each query's distinct valid candidates, ties by id."""
-    ids = np.full((len(Q), k), -1, np.int64)
-    dists = np.full((len(Q), k), np.inf)
-    for i, q in enumerate(Q):
-        c = np.unique(cand[i][cand[i] >= 0])
-        if len(c) == 0:
-            continue
-        d = ((X[c].astype(np.float64) - q.astype(np.float64)) ** 2).sum(1)
-        order = np.lexsort((c, d))[:k]
-        ids[i, :len(order)] = c[order]
-        dists[i, :len(order)] = d[order]
-    return ids, dists
-
-
 def _check(X, Q, cand, k, got_i, got_d):
-    ref_i, ref_d = _reference(X, Q, cand, k)
+    ref_i, ref_d = oracle.candidate_topk(X, Q, cand, k)
     gam = [np.unique(c[c >= 0]) for c in cand]
     check_topk(X, Q, got_i.cpu().numpy(), got_d.cpu().numpy(), ref_i, ref_d, k,
                gamma_rows=gam)
@@ -135,7 +120,7 @@ def test_refine_epsilon_relaxed_keeps_exact_distances():
     dims_e = pano.last_stats().dims_scanned
     assert dims_e <= dims1
     ids, d = ids.cpu().numpy(), d.cpu().numpy()
-    ref_i, _ = _reference(X, Q, cand, 10)
+    ref_i, _ = oracle.candidate_topk(X, Q, cand, 10)
     recall = np.mean([len(set(ids[i]) & set(ref_i[i])) / 10 for i in range(len(Q))])
     assert recall >= 0.5
     for i in range(len(Q)):  # whatever is returned carries its exact distance

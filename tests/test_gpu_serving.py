@@ -1,15 +1,19 @@
 """Serving: continuous batching over a device-resident BF16 index (the
 recipe of the 50M-vector serving workload, d = 128, 8 x 16 levels, at 60k
-vectors).  Each request's result must be the same alone and in the mix
-(ids equal except at FP64-level near-ties, distances within 1e-5
-relative); Poisson arrivals are batched; a tiny memory budget serialises
-batches but still completes every request."""
+vectors, with coarse centroids from the seeded generator).  Every served
+result is checked against the CPU oracle (the FP64 top-k over the query's
+FP64 probe set; ids equal except at near-ties, distances within 1e-5
+relative), and each request's result must also be the same alone and in the
+mix; Poisson arrivals are batched; a tiny memory budget serialises batches
+but still completes every request."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2510_00566_gb300 as pano
 import synth
+from parity import check_topk, gamma_of
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -24,11 +28,27 @@ def serving_index():
     pano.lib()
     s = synth.scaled(5, n=60_000, n_queries=600, nlist=64)
     w = synth.generate(s)
+    C = synth.initial_centroids(w.X, 64, seed=3005).numpy()
     t = pano.panorama_fit_transform(w.X.numpy(), n_levels=8)
     idx = pano.panorama_build_ivf(t, w.X.to(DEV), nlist=64, level_widths=[16] * 8,
-                                  precision=pano.PANO_BF16, kmeans_iters=8)
+                                  precision=pano.PANO_BF16, centroids=C)
     npq = np.clip(w.nprobe.numpy(), 1, 64)
-    return s, w, idx, npq
+    lists, _ = oracle.assign(w.X.numpy(), C)
+    return s, w, idx, npq, C, lists
+
+
+def _check_oracle(w, C, lists, npq, rows, ids, dists, k=10):
+    """The served results of queries `rows` against the oracle's FP64 top-k
+    over each query's FP64 probe set (queries whose nprobe-th and next
+    centroid distances are within 1e-6 are left out, as in every IVF
+    parity test)."""
+    X, Q = w.X.numpy(), w.Q.numpy()[rows]
+    ref = oracle.ivf_search(X, Q, C, npq[rows], k, lists_of_vector=lists)
+    keep = ref["probe_gap"] >= 1e-6
+    assert keep.mean() > 0.9
+    G = gamma_of(lists, [ref["probes"][i] for i in np.nonzero(keep)[0]])
+    check_topk(X, Q[keep], np.asarray(ids)[keep], np.asarray(dists)[keep], ref["ids"][keep],
+               ref["dists"][keep], k, gamma_rows=G)
 
 
 def _alone(idx, q, nprobe, k=10):
@@ -44,8 +64,8 @@ def _same(ia, da, ib, db):
     assert np.all(np.abs(da[diff] - db[diff]) <= 1e-6 * np.abs(da[diff]))
 
 
-def test_results_same_alone_and_in_mix(serving_index):
-    s, w, idx, npq = serving_index
+def test_results_match_oracle_and_alone_in_mix(serving_index):
+    s, w, idx, npq, C, lists = serving_index
     Q = w.Q.numpy()
     srv = pano.Server(idx, max_batch=64, max_inflight=3, k_max=10)
     tickets = [srv.submit(Q[i], int(npq[i]), 10) for i in range(400)]
@@ -53,13 +73,16 @@ def test_results_same_alone_and_in_mix(serving_index):
     st = srv.stats()
     srv.close()
     assert st["completed"] == 400 and st["batches"] >= 400 / 64
+    rows = np.arange(400)
+    _check_oracle(w, C, lists, npq, rows, np.stack([g[0] for g in got]),
+                  np.stack([g[1] for g in got]))
     for i in range(0, 400, 7):
         ia, da = _alone(idx, Q[i], npq[i])
         _same(ia, da, got[i][0], got[i][1])
 
 
 def test_poisson_trace_batches_requests(serving_index):
-    s, w, idx, npq = serving_index
+    s, w, idx, npq, C, lists = serving_index
     Q = w.Q.numpy()
     n = 600
     rng = np.random.default_rng(5005)
@@ -71,13 +94,14 @@ def test_poisson_trace_batches_requests(serving_index):
     assert st["completed"] == n
     assert st["mean_batch"] > 1.0  # arrivals during a batch were grouped
     assert np.all(lat > 0) and st["p99_us"] >= st["p50_us"] > 0
+    _check_oracle(w, C, lists, npq, np.arange(n), ids, d)
     for i in range(0, n, 37):
         ia, da = _alone(idx, Q[i], npq[i])
         _same(ia, da, ids[i], d[i])
 
 
 def test_memory_budget_admits_one_batch_at_a_time(serving_index):
-    s, w, idx, npq = serving_index
+    s, w, idx, npq, C, lists = serving_index
     Q = w.Q.numpy()
     srv = pano.Server(idx, max_batch=32, max_inflight=4, k_max=10, memory_budget=1)
     tickets = [srv.submit(Q[i], int(npq[i]), 10) for i in range(100)]
@@ -85,5 +109,7 @@ def test_memory_budget_admits_one_batch_at_a_time(serving_index):
     st = srv.stats()
     srv.close()
     assert st["completed"] == 100
+    _check_oracle(w, C, lists, npq, np.arange(100), np.stack([g[0] for g in got]),
+                  np.stack([g[1] for g in got]))
     ia, da = _alone(idx, Q[3], npq[3])
     _same(ia, da, got[3][0], got[3][1])

@@ -8,14 +8,15 @@ direction by at most its factor: r lies between 1 and R (the first level is
 always read and near neighbours are read in full, which damps the effect).
 
 The CPU test pins the oracle's Algorithm 1 to that behaviour; the GPU test
-checks that the GPU path reads about as many coordinates as the oracle on
-the same out-of-distribution queries."""
+checks that the GPU path returns the oracle's exact top-k on the same
+out-of-distribution queries and reads about as many coordinates."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 import synth
+from parity import check_topk
 
 D, BETA_X = 128, 0.05          # alpha_x = BETA_X * D = 6.4
 BETAS_Q = (0.0125, 0.05, 0.2)  # alpha_q = 1.6, 6.4, 25.6
@@ -77,8 +78,12 @@ def test_gpu_reads_what_the_oracle_reads_on_ood_queries():
     for bq in BETAS_Q:
         s, w = _workload(bq)
         Q = w.Q.numpy()
-        idx.search(w.Q.to("cuda:0"), 1, 10, collect_stats=True)
+        ids, dists = idx.search(w.Q.to("cuda:0"), 1, 10, collect_stats=True)
         st = pano.last_stats()
+        # the answer on out-of-distribution queries is still the exact top-k
+        ref = oracle.ivf_search(X, Q, np.zeros((1, D)), 1, 10,
+                                lists_of_vector=np.zeros(len(X), dtype=np.int64))
+        check_topk(X, Q, ids.cpu().numpy(), dists.cpu().numpy(), ref["ids"], ref["dists"], 10)
         gpu = st.dims_scanned / (st.pairs * D)
         ref = _oracle_frac(s, X, Q, T, mu)
         assert gpu <= 1.2 * ref + 0.03, (bq, gpu, ref)

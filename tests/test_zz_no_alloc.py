@@ -4,11 +4,12 @@ pool, or an allocation -- which can synchronize or fail under fragmentation
 -- is not allowed on their path).  Its workspace is a fixed array in the
 library's global memory.
 
-The entry point is called through the C-ABI (ctypes) twice in a row; both
-results must match panorama_search's within the parity tolerances used by
-the other GPU tests (ids equal except at near-ties below 1e-6 relative,
-distances within 1e-5 relative).  The second call checks that what the
-first call left in the shared array does not leak into the next result.
+The entry point is called through the C-ABI (ctypes) twice in a row, on two
+different batches; both results must match panorama_search's on the same
+batch within the parity tolerances used by the other GPU tests (ids equal
+except at near-ties below 1e-6 relative, distances within 1e-5 relative).
+The second batch differs in queries, size, nprobe, k and k_max, so what the
+first call left in the shared array would show in the second result.
 This file is collected last; it builds everything it needs, so it also
 passes alone in a fresh process."""
 import ctypes
@@ -61,14 +62,19 @@ def _same(a_ids, a_d, b_ids, b_d):
 
 
 def test_noalloc_matches_search_on_two_calls(index_and_queries):
+    """Two calls in a row with different batches: the second one has other
+    queries, fewer of them, another nprobe, k and k_max, so whatever the
+    first call left in the shared array (top-k keys, counters, work lists)
+    would show up in its result if the search did not clear it."""
     idx, q = index_and_queries
-    ref_ids, ref_d = idx.search(q, 6, 10, k_max=12)
-    for _ in range(2):
-        rc, ids, d = _noalloc(idx, q, 6, 10, 12)
+    calls = [(q[:120], 6, 10, 12), (q[120:], 9, 4, 5)]
+    for qs, nprobe, k, k_max in calls:
+        ref_ids, ref_d = idx.search(qs, nprobe, k, k_max=k_max)
+        rc, ids, d = _noalloc(idx, qs, nprobe, k, k_max)
         torch.cuda.synchronize()
         assert rc == 0, pano.lib().panorama_last_error()
         _same(ref_ids, ref_d, ids, d)
-        assert torch.all(ids[:, 10:] == -1) and torch.all(torch.isinf(d[:, 10:]))
+        assert torch.all(ids[:, k:] == -1) and torch.all(torch.isinf(d[:, k:]))
 
 
 def test_noalloc_rejects_workspace_beyond_scratch(index_and_queries):
