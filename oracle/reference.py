@@ -163,25 +163,45 @@ def _sq_to_centroids_fast(V: np.ndarray, C: np.ndarray,
     return out
 
 
-def assign(X: np.ndarray, C: np.ndarray, block: int = 65536):
+def assign(X: np.ndarray, C: np.ndarray, block: int = 65536, threads: int = 0):
     """Nearest centroid of every vector (IVF, Section 6.1), ties -> lowest id.
 
     Returns (list_of_vector, relative gap between the best and second-best
     centroid distance); gaps below 1e-6 mark assignments that FP32 arithmetic
-    may legitimately resolve the other way.
+    may legitimately resolve the other way.  Distances are the FP64
+    expansion |v|^2 + |c|^2 - 2 v.c (one matmul per block of rows); the
+    argmin (first = lowest id among equal values) and the second-smallest
+    value of each row are taken in parallel over slices of rows.
     """
+    import concurrent.futures as cf
+    import os
     n = X.shape[0]
+    C = np.asarray(C, dtype=np.float64)
+    cn = np.sum(C * C, axis=1)
     lists = np.empty(n, dtype=np.int64)
     gap = np.full(n, np.inf)
-    for s in range(0, n, block):
-        D = _sq_to_centroids_fast(X[s:s + block], C)
-        order = np.argsort(D, axis=1, kind="stable")
-        lists[s:s + block] = order[:, 0]
-        if D.shape[1] > 1:
-            r = np.arange(D.shape[0])
-            d0 = D[r, order[:, 0]]
-            d1 = D[r, order[:, 1]]
-            gap[s:s + block] = (d1 - d0) / np.maximum(d1, 1e-300)
+    nt = threads if threads > 0 else (os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(nt) as ex:
+        for s in range(0, n, block):
+            v = np.asarray(X[s:s + block], dtype=np.float64)
+            vn = np.sum(v * v, axis=1)
+            G = v @ C.T
+
+            def rows(a, b):
+                D = vn[a:b, None] + cn[None, :]
+                D -= 2.0 * G[a:b]
+                best = np.argmin(D, axis=1)
+                r = np.arange(b - a)
+                lists[s + a:s + b] = best
+                if D.shape[1] > 1:
+                    d0 = D[r, best].copy()
+                    D[r, best] = np.inf
+                    d1 = np.min(D, axis=1)
+                    gap[s + a:s + b] = (d1 - d0) / np.maximum(d1, 1e-300)
+
+            step = max(256, -(-v.shape[0] // nt))
+            list(ex.map(lambda a: rows(a, min(a + step, v.shape[0])),
+                        range(0, v.shape[0], step)))
     return lists, gap
 
 
