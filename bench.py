@@ -4,22 +4,28 @@
 A step is one whole search of a batch of synthetic queries through the
 library's C-ABI (query transform, coarse probe, work inversion, level-wise
 verification with pruning, exact re-ranking, top-k) with the index and the
-queries resident in HBM.  The default workload is the 960-d IVF workload:
-N = 1,000,000 FP32 vectors from a 1,024-cluster Gaussian mixture (eigen-decay
-exp(-0.01 i)), nlist = 1024, nprobe = 32, 10,000 queries, 16 levels x 60
-dims, k = 10.
+queries resident in HBM.  The default workload is the 768-d precision
+workload: N = 10,000,000 vectors from one Gaussian (eigen-decay
+exp(-0.008 i)), IVF nlist = 4096, nprobe = 64, 10,000 queries, 12 levels x
+64 dims, k = 10, level slices stored in BF16 (the headline) and in FP8-E4M3,
+compared with the plain scans: the tensor-core scan of the same BF16 index
+and the plain FP32 full-distance scan of an FP32 index of the same data.
 
 Printed (rank 0, one JSON line): candidates verified per second (query,
-candidate pairs resolved per second over all GPUs), QPS, the same through
-host buffers (e2e), the plain FP32 full-distance scan of the same candidate
-sets as the comparator, the roofline of the dominant kernel, the CPU oracle
-baseline and the SM clocks seen during the timed region.
+candidate pairs resolved per second over all GPUs) and QPS of the pruned
+BF16 search, the same through host buffers (e2e), the FP8 and FP32 lines,
+a sampled comparison with the CPU oracle at full size (`parity`), the HBM
+roofline of the dominant kernel, the CPU oracle baseline, the SM clocks
+seen during the timed region, and a secondary line for the 960-d FP32
+workload (with the epsilon sweep of Eq. 4, point-centric refine and IVFPQ).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 2]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 3]
   python bench.py --impl reference ...   # the CPU oracle as the reference arm
 """
 import argparse
+import dataclasses
 import json
+import math
 import os
 import subprocess
 import sys
@@ -32,12 +38,14 @@ METRIC = ("candidates verified/sec and QPS at oracle-exact top-k: "
           "pruned BF16/FP8 vs plain FP32")
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS, FALLBACK_BF16_TFS = 6800.0, 1900.0
-KERNELS_PER_SEARCH = 14  # see the launch list in profiles/
-# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
-# capture of a smaller case of the same kernel scaled to the full launch
-# (profiles/ holds the capture summary); None once the kernel has changed.
-TRAFFIC = {"ivf-1m-d960-fp32": 834.49e6 + 3.38e6}  # phase B, ncu at full size, one pass
-PQ_TRAFFIC = {}  # pruned pq_verify_kernel: ncu at full size, one pass (none for this version)
+# DRAM bytes (read + write) of one launch of the dominant kernel, from one
+# ncu capture of that launch at full size (one pass: dram__bytes_read.sum +
+# dram__bytes_write.sum); the command and figures are in profiles/.  An
+# entry is removed whenever its kernel changes, so the line then reports
+# null instead of a stale figure.
+TRAFFIC = {}
+PQ_TRAFFIC = {}
+EPSILONS = (1.0, 0.9, 0.8, 0.6, 0.5, 0.4)
 
 
 def parse():
@@ -45,45 +53,50 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--config", type=int, default=2)
+    p.add_argument("--config", type=int, default=3)
     p.add_argument("--impl", default="panorama", choices=["panorama", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-parity", action="store_true",
+                   help="skip the sampled comparison with the CPU oracle")
+    p.add_argument("--parity-queries", type=int, default=256)
     p.add_argument("--scan-steps", type=int, default=3)
     p.add_argument("--n", type=int, default=0, help="override N (profiling a smaller case)")
     p.add_argument("--queries", type=int, default=0, help="override the query count")
     p.add_argument("--nlist", type=int, default=0, help="override nlist (and clusters)")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--no-bf16", action="store_true",
-                   help="skip the BF16-storage run on FP32 workloads")
+    p.add_argument("--no-fp8", action="store_true", help="skip the FP8-storage line")
+    p.add_argument("--no-fp32", action="store_true",
+                   help="skip the FP32-storage line of a quantised workload")
+    p.add_argument("--no-secondary", action="store_true",
+                   help="skip the 960-d FP32 workload's secondary line")
+    p.add_argument("--no-eps", action="store_true", help="skip the epsilon sweep")
     p.add_argument("--no-refine", action="store_true",
                    help="skip the candidate-list refine run on FP32 IVF workloads")
-    p.add_argument("--no-fp8", action="store_true",
-                   help="skip the FP8-storage run on FP32 and BF16 workloads")
+    p.add_argument("--no-pq", action="store_true",
+                   help="skip the IVFPQ line (shaped PCA, M = d/2, levels as the workload's)")
+    p.add_argument("--pq-sweep", action="store_true",
+                   help="add the IVFPQ kappa sweep (Section 4.3's shaping trade)")
     p.add_argument("--pq-levels", type=int, default=0,
                    help="levels of the IVFPQ line (default: the workload's)")
-    p.add_argument("--no-pq-sweep", action="store_true",
-                   help="skip the IVFPQ kappa sweep (Section 4.3's shaping trade)")
-    p.add_argument("--no-pq", action="store_true",
-                   help="skip the IVFPQ line (shaped PCA, M = d/2, levels as the headline)")
     p.add_argument("--no-serve", action="store_true",
                    help="skip the arrival traces of the serving workload")
     p.add_argument("--serve-requests", type=int, default=20000)
     return p.parse_args()
 
 
-def workload_spec(args):
-    import dataclasses
+def workload_spec(args, cfg=None):
     import synth
-    s = synth.spec(args.config)
+    s = synth.spec(cfg or args.config)
     upd = {}
-    if args.n:
-        upd["n"] = args.n
-    if args.queries:
-        upd["n_queries"] = args.queries
-    if args.nlist:
-        upd["nlist"] = args.nlist
-        if s.n_clusters:
-            upd["n_clusters"] = args.nlist
+    if cfg is None or cfg == args.config:
+        if args.n:
+            upd["n"] = args.n
+        if args.queries:
+            upd["n_queries"] = args.queries
+        if args.nlist:
+            upd["nlist"] = args.nlist
+            if s.n_clusters:
+                upd["n_clusters"] = args.nlist
     return dataclasses.replace(s, **upd) if upd else s
 
 
@@ -95,9 +108,11 @@ def dist_env():
 
 
 def workload_name(s):
+    npr = s.nprobe if isinstance(s.nprobe, int) else f"U[{s.nprobe[0]},{s.nprobe[1]}]"
+    k = s.k if isinstance(s.k, int) else "{" + ",".join(map(str, s.k)) + "}"
     return (f"{s.name}: N={s.n:,} d={s.d} {s.precision.upper()}, nlist={s.nlist}, "
-            f"nprobe={s.nprobe}, {s.n_queries:,} queries, {s.n_levels}x{s.d // s.n_levels}"
-            f" levels, k={s.k}")
+            f"nprobe={npr}, {s.n_queries:,} queries, {s.n_levels}x{s.d // s.n_levels}"
+            f" levels, k={k}")
 
 
 class Clocks:
@@ -159,30 +174,109 @@ def peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
-def cpu_baseline(X, Q, C, s, sample_queries, npq, kq, target_s=12.0):
-    """The oracle (as it stands) on the host cores: FP64 brute force over each
-    sampled query's candidate set after its own FP64 list assignment.  A
-    first batch of `sample_queries` sizes the timed sample to ~target_s."""
+# --------------------------------------------------------------- the oracle
+class OracleSide:
+    """The CPU oracle's view of a workload: the FP32 host arrays, the
+    coarse centroids the library's build chose, and the oracle's own FP64
+    assignment of every vector to them (Section 6.1); shared by the parity
+    sample and the timed CPU baseline."""
+
+    def __init__(self, X, Q, C):
+        import numpy as np
+        import oracle
+        self.X = np.ascontiguousarray(X, dtype=np.float32)
+        self.Q = np.ascontiguousarray(Q, dtype=np.float32)
+        self.C = np.asarray(C, dtype=np.float32)
+        t0 = time.perf_counter()
+        self.lists, self.agap = oracle.assign(self.X, self.C)
+        self.assign_s = time.perf_counter() - t0
+        self.ptr, self.rows = oracle.ivf_lists(self.lists, self.C.shape[0])
+
+    def answer(self, rows, nprobe, k):
+        """Oracle top-k of queries `rows` over their FP64 probe sets."""
+        import numpy as np
+        import oracle
+        qs = self.Q[rows]
+        probes, pgap = oracle.probe(qs, self.C, nprobe)
+        ids, d = oracle.ivf_topk(self.X, qs, self.ptr, self.rows, probes, k)
+        return ids, d, probes, pgap
+
+
+def parity_report(osd, rows, nprobe, k, got_ids, got_d, gpu_probes, lib_assign):
+    """Element-by-element comparison of the GPU's results for queries `rows`
+    with the oracle's, by the rules of the parity tests: ids equal except
+    where the FP64 distances are within 1e-6 relative (near-ties), each
+    returned distance within 1e-5 relative of the FP64 distance of its id.
+    Queries whose nprobe-th and next FP64 centroid distances are within
+    1e-6 relative are left out (either probe set is correct)."""
+    import numpy as np
+    nq = len(rows)
+    npq = np.broadcast_to(np.asarray(nprobe), (nq,))
+    kq = np.broadcast_to(np.asarray(k), (nq,)).astype(np.int32)
+    ref_i, ref_d, probes, pgap = osd.answer(rows, npq, kq)
+    keep = pgap >= 1e-6
+    probe_mismatch = 0
+    for j in np.nonzero(keep)[0]:
+        if not np.array_equal(np.sort(gpu_probes[j][:npq[j]]), np.sort(probes[j])):
+            probe_mismatch += 1
+    worst, beyond, swaps, bad_pad = 0.0, 0, 0, 0
+    for j in np.nonzero(keep)[0]:
+        kj = int(kq[j])
+        nv = int(np.sum(ref_i[j, :kj] >= 0))
+        g = got_ids[j, :nv]
+        if np.any(got_ids[j, nv:kj] != -1) or np.any(g < 0):
+            bad_pad += 1
+            continue
+        if nv == 0:
+            continue
+        diff = osd.X[g].astype(np.float64) - osd.Q[rows[j]].astype(np.float64)
+        true_d = np.einsum("ij,ij->i", diff, diff)
+        rel = np.abs(got_d[j, :nv].astype(np.float64) - true_d) / np.maximum(true_d, 1e-30)
+        worst = max(worst, float(rel.max()))
+        mism = g != ref_i[j, :nv]
+        if mism.any():
+            r = ref_d[j, :nv][mism]
+            gap = np.abs(true_d[mism] - r) / np.maximum(r, 1e-30)
+            swaps += int(np.sum(gap <= 1e-6))
+            beyond += int(np.sum(gap > 1e-6))
+    am = None
+    if lib_assign is not None:
+        am = int(np.sum((lib_assign != osd.lists) & (osd.agap >= 1e-6)))
+    return {"queries": int(keep.sum()), "excluded_probe_near_ties": int((~keep).sum()),
+            "probe_mismatch": probe_mismatch, "max_rel_err": worst,
+            "id_mismatch_beyond_tie": beyond, "near_tie_swaps": swaps,
+            "bad_padding": bad_pad, "assignment_mismatch_beyond_tie": am,
+            "tolerances": "dist 1e-5 rel vs FP64; ids exact except FP64 near-ties < 1e-6 rel",
+            "oracle": "FP64 brute force over the query's FP64 probe set, vectors assigned "
+                      "to the library's centroids in FP64"}
+
+
+def cpu_baseline(osd, nprobe, k, sample_queries=24, target_s=12.0):
+    """The oracle (as it stands) on the host cores: FP64 probe + brute force
+    over each sampled query's candidate set (the list assignment is done
+    once, untimed).  A first batch of `sample_queries` sizes the timed
+    sample to ~target_s."""
     import numpy as np
     import oracle
-    lists, _ = oracle.assign(X, C)
-    ptr, rows = oracle.ivf_lists(lists, C.shape[0])
+    nq = len(osd.Q)
+    npq = np.broadcast_to(np.asarray(nprobe), (nq,))
+    kq = np.broadcast_to(np.asarray(k), (nq,)).astype(np.int32)
 
-    def run(qs):
+    def run(n):
         t0 = time.perf_counter()
-        probes, _ = oracle.probe(qs, C, npq[:len(qs)])
-        oracle.ivf_topk(X, qs, ptr, rows, probes, kq[:len(qs)])
+        probes, _ = oracle.probe(osd.Q[:n], osd.C, npq[:n])
+        oracle.ivf_topk(osd.X, osd.Q[:n], osd.ptr, osd.rows, probes, kq[:n])
         return time.perf_counter() - t0, probes
 
-    dt0, _ = run(Q[:sample_queries])
-    n = int(min(len(Q), max(sample_queries, sample_queries * target_s / max(dt0, 1e-6))))
-    qs = Q[:n]
-    dt, probes = run(qs)
-    pairs = sum(int(ptr[p + 1].sum() - ptr[p].sum()) for p in probes)
+    dt0, _ = run(sample_queries)
+    n = int(min(nq, max(sample_queries, sample_queries * target_s / max(dt0, 1e-6))))
+    dt, probes = run(n)
+    pairs = sum(int(osd.ptr[p + 1].sum() - osd.ptr[p].sum()) for p in probes)
     return {"value": pairs / dt, "unit": "candidates/s", "cores": os.cpu_count(),
-            "kind": "oracle", "qps": len(qs) / dt,
-            "sample": f"{len(qs)} queries of the workload (probe + FP64 brute force "
-                      f"over their candidate sets; list assignment untimed)",
+            "kind": "oracle", "qps": n / dt,
+            "sample": f"the first {n} queries of the workload (FP64 probe + FP64 brute force "
+                      f"over their candidate sets; the FP64 list assignment to the library's "
+                      f"centroids, {osd.assign_s:.0f} s, untimed)",
             "seconds": dt}
 
 
@@ -195,21 +289,24 @@ def run_reference(args):
     import torch
     import synth
     s = workload_spec(args)
-    w = synth.generate(s, device="cpu")
-    X, Q = w.X.numpy(), w.Q.numpy()
+    dev = "cuda" if torch.cuda.is_available() else "cpu"  # input draws only
+    w = synth.generate(s, device=dev)
+    X, Q = w.X.cpu().numpy(), w.Q.cpu().numpy()
+    del w.X
     npq, kq = w.nprobe.numpy(), w.k.numpy()
-    import oracle
     g = np.random.default_rng(3000 + s.cfg)
     C = X[np.sort(g.choice(len(X), s.nlist, replace=False))].astype(np.float32)
-    lists, _ = oracle.assign(X, C)
-    ptr, rows = oracle.ivf_lists(lists, s.nlist)
+    osd = OracleSide(X, Q, C)
+    import oracle
     per_step = 24
+
     def step(i):
         o = (i * per_step) % len(Q)
-        qs = Q[o:][:per_step]
-        probes, _ = oracle.probe(qs, C, npq[o:][:len(qs)])
-        oracle.ivf_topk(X, qs, ptr, rows, probes, kq[o:][:len(qs)])
-        return sum(int(ptr[p + 1].sum() - ptr[p].sum()) for p in probes)
+        qs = osd.Q[o:][:per_step]
+        probes, _ = oracle.probe(qs, osd.C, npq[o:][:len(qs)])
+        oracle.ivf_topk(osd.X, qs, osd.ptr, osd.rows, probes, kq[o:][:len(qs)])
+        return sum(int(osd.ptr[p + 1].sum() - osd.ptr[p].sum()) for p in probes)
+
     for i in range(args.warmup):
         step(i)
     t0 = time.perf_counter()
@@ -223,7 +320,9 @@ def run_reference(args):
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(s),
-                       "step": f"{per_step} queries (bounded sample of the workload)"},
+                       "step": f"{per_step} queries (bounded sample of the workload); coarse "
+                               f"centroids = {s.nlist} seeded data rows, FP64 assignment "
+                               f"({osd.assign_s:.0f} s, untimed)"},
             "qps": per_step * args.steps / dt,
             "cpu_baseline": {"value": v, "unit": "candidates/s", "cores": os.cpu_count(),
                              "kind": "oracle",
@@ -233,14 +332,55 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def e2e_time(idx, Q, npa, ka, k, args, stream, flush, world, dev):
+# --------------------------------------------------------------- GPU side
+class Timer:
+    """Timed steps on the search stream: W untimed warm-up steps, then K
+    steps each bracketed by CUDA events, a 256 MB buffer written before each
+    (L2 flushed), the max over ranks of the total."""
+
+    def __init__(self, dev, world, stream):
+        import torch
+        self.dev, self.world, self.stream = dev, world, stream
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def run(self, fn, steps, warmup, clocks=False, after=None):
+        import torch
+        import torch.distributed as dist
+        for _ in range(warmup):
+            fn()
+        if self.world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk = Clocks(self.dev.index or 0) if clocks else None
+        if clk:
+            clk.start()
+        total, extra = 0.0, []
+        for _ in range(steps):
+            self.flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            fn()
+            e1.record(self.stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+            if after:
+                extra.append(after())
+        torch.cuda.synchronize()
+        c = clk.stop() if clk else None
+        t = torch.tensor([total], device=self.dev)
+        if self.world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item() / steps, extra, c
+
+
+def e2e_time(idx, Q, npa, ka, k, steps, timer):
     """Per-step time of the public API call with HOST buffers: pinned H2D of
-    the queries, search, D2H of ids and distances, all inside the events."""
+    the queries (and per-query nprobe / k), search, D2H of ids and
+    distances, all inside the events."""
     import torch
-    import torch.distributed as dist
     nq = Q.shape[0]
     qh = Q.cpu().pin_memory()
-    # per-query nprobe / k are inputs of the step too
     par = [(x.cpu().pin_memory(), torch.empty_like(x)) for x in (npa, ka)
            if isinstance(x, torch.Tensor)]
     if par:
@@ -249,36 +389,25 @@ def e2e_time(idx, Q, npa, ka, k, args, stream, flush, world, dev):
     ids_h = torch.empty((nq, k), dtype=torch.int64).pin_memory()
     d_h = torch.empty((nq, k), dtype=torch.float32).pin_memory()
     qd = torch.empty_like(Q)
-    for _ in range(2):
+
+    def step():
         qd.copy_(qh, non_blocking=True)
         for h, dv in par:
             dv.copy_(h, non_blocking=True)
         a, b = idx.search(qd, npa, ka, k_max=k)
         ids_h.copy_(a, non_blocking=True)
         d_h.copy_(b, non_blocking=True)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    total = 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        qd.copy_(qh, non_blocking=True)
-        for h, dv in par:
-            dv.copy_(h, non_blocking=True)
-        a, b = idx.search(qd, npa, ka, k_max=k)
-        ids_h.copy_(a, non_blocking=True)
-        d_h.copy_(b, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        total += e0.elapsed_time(e1)
-    t = torch.tensor([total], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return t.item() / args.steps, Q.numel() * 4 + sum(h.numel() * 4 for h, _ in par)
+
+    ms, _, _ = timer.run(step, steps, 2)
+    return ms, Q.numel() * 4 + sum(h.numel() * 4 for h, _ in par), nq * k * 12
+
+
+def search_launches(pano, st, nlist):
+    """Kernels one search launches: prep, transform GEMM, query norms, probe
+    GEMM + select (IVF), four inversion kernels (emit twice), the threshold
+    seeds, verify phase A (two-phase searches only), verify phase B, decode."""
+    one_pass = st["pairs_a"] == 0
+    return 14 - (2 if nlist <= 1 else 0) - (1 if one_pass else 0)
 
 
 def main():
@@ -304,22 +433,27 @@ def main():
     if world > 1:
         dist.barrier()
     pano.lib()
+    stream = torch.cuda.current_stream()
+    timer = Timer(dev, world, stream)
+    pk, pk_kind = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    check_oracle = rank == 0 and world == 1
 
     s = workload_spec(args)
     # every rank holds a replica of the index and verifies its own query batch
     w = synth.generate(s, device=dev)
     if rank > 0:
-        import dataclasses
         sq = dataclasses.replace(s, cfg=s.cfg + 100 * rank)
         w.Q = synth.generate(sq, device=dev, queries_only=True).Q
     X, Q = w.X, w.Q
+    nq = Q.shape[0]
     t = pano.panorama_fit_transform(X[:65536], n_levels=s.n_levels)
     prec = {"fp32": pano.PANO_FP32, "bf16": pano.PANO_BF16, "fp8": pano.PANO_FP8}[s.precision]
-    # per-query nprobe / k (the batching workload) or scalars
     per_query = not isinstance(s.nprobe, int) or not isinstance(s.k, int)
     npa = w.nprobe.to(dev) if not isinstance(s.nprobe, int) else s.nprobe
     ka = w.k.to(dev) if not isinstance(s.k, int) else s.k
     k = int(w.k.max()) if not isinstance(s.k, int) else s.k  # k_max
+    npmax = int(w.nprobe.max())
     widths, tune = None, None
     if per_query:
         # level widths chosen by the autotuner (median search time of each
@@ -332,287 +466,152 @@ def main():
         tune = {"candidates": [f"{len(c)}x{c[0]}" for c in cands],
                 "ms": [float(x) for x in ms], "chosen": f"{len(widths)}x{widths[0]}",
                 "sample": f"{len(qs)} queries, nprobe 64, k 10"}
+    b0 = time.time()
     idx = pano.panorama_build_ivf(t, X, nlist=s.nlist, n_levels=s.n_levels, seed=3000 + s.cfg,
                                   precision=prec, level_widths=widths)
-    nq = Q.shape[0]
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > L2
-    # the batching workload runs as one graph-captured launch per step
+    torch.cuda.synchronize()
+    build_s = time.time() - b0
+    C = idx.centroids()
     plan = pano.Plan(idx, Q, npa, ka, k_max=k) if per_query else None
 
-    def step(mode=0, timing=False):
-        if plan is not None and mode == 0 and not timing:
-            return plan.launch(stream)
-        return idx.search(Q, npa, ka, k_max=k, mode=mode, collect_timing=timing)
-
     # counters (one instrumented search, outside the timed region)
-    step(0)
+    out = idx.search(Q, npa, ka, k_max=k)
     idx.search(Q, npa, ka, k_max=k, collect_stats=True)
     st = pano.last_stats().as_dict()
-
-    def timed(mode, steps, warmup, timing=True):
-        for _ in range(warmup):
-            step(mode)
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        total, verify_ms = 0.0, []
-        clk = Clocks(local)
-        clk.start()
-        for _ in range(steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step(mode, timing)
-            e1.record(stream)
-            e1.synchronize()
-            total += e0.elapsed_time(e1)
-            if timing:
-                sm = pano.last_stats().stage_ms
-                verify_ms.append((sm[3], sm[4], list(sm)))
-        torch.cuda.synchronize()
-        clocks = clk.stop()
-        t_all = torch.tensor([total], device=dev)
-        if world > 1:
-            dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
-        return t_all.item(), verify_ms, clocks
-
-    total_ms, vms, clocks = timed(0, args.steps, args.warmup, timing=plan is None)
-    if plan is not None:  # stage times from separate, instrumented searches
-        _, vms, _ = timed(0, 3, 1, timing=True)
-    ms_per_step = total_ms / args.steps
     pairs = st["pairs"]
+
+    # the headline: pruned search of the whole batch, timed with the
+    # library's stage events on the search stream
+    def headline():
+        if plan is not None:
+            return plan.launch(stream)
+        return idx.search(Q, npa, ka, k_max=k, collect_timing=True)
+
+    stage_of = (lambda: list(pano.last_stats().stage_ms)) if plan is None else None
+    ms_per_step, stages, clocks = timer.run(headline, args.steps, args.warmup, clocks=True,
+                                           after=stage_of)
+    if plan is not None:  # stage times from separate, instrumented searches
+        _, stages, _ = timer.run(lambda: idx.search(Q, npa, ka, k_max=k, collect_timing=True),
+                                 3, 1, after=lambda: list(pano.last_stats().stage_ms))
+    stage = {n: float(np.median([v[i] for v in stages])) for i, n in
+             enumerate(("transform", "probe", "inversion", "verify_a", "verify_b", "decode"))}
     value = pairs * world / (ms_per_step / 1e3)
     qps = nq * world / (ms_per_step / 1e3)
 
-    # comparator: plain FP32 full-distance scan of the same candidate sets
-    scan_ms, _, _ = timed(1, args.scan_steps, 1, timing=False)
-    scan_per = scan_ms / args.scan_steps
-
-    # e2e: through the public API with host buffers (pinned H2D + D2H)
-    e2e_per, h2d = None, 0
+    # comparator on the same index: the plain scan (no pruning test before
+    # the last level; for BF16/FP8 storage the plain tensor-core scan)
+    scan_ms, _, _ = timer.run(lambda: idx.search(Q, npa, ka, k_max=k, mode=1),
+                              args.scan_steps, 1)
+    e2e = None
     if not args.no_e2e:
-        e2e_per, h2d = e2e_time(idx, Q, npa, ka, k, args, stream, flush, world, dev)
+        e2e_ms, h2d, d2h = e2e_time(idx, Q, npa, ka, k, args.steps, timer)
+        e2e = {"value": pairs * world / (e2e_ms / 1e3), "unit": "candidates/s",
+               "qps": nq * world / (e2e_ms / 1e3), "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    # roofline of the dominant kernel (verify phase B: one launch per step),
-    # its duration measured live above with CUDA events on the search stream
-    pk, pk_kind = peaks()
-    va = float(np.median([v[0] for v in vms]))
-    vb = float(np.median([v[1] for v in vms]))
-    stage = {n: float(np.median([v[2][i] for v in vms])) for i, n in
-             enumerate(("transform", "probe", "inversion", "verify_a", "verify_b", "decode"))}
+    # the oracle side (rank 0 of a 1-GPU run): FP64 assignment to the
+    # library's centroids, then a sampled full-size parity check of every
+    # storage format and the timed CPU baseline
+    osd = None
+    if check_oracle and (not args.no_parity or not args.no_cpu_baseline) and s.nlist > 1:
+        osd = OracleSide(X.cpu().numpy(), Q.cpu().numpy(), C)
+    prow = None
+    if osd is not None and not args.no_parity:
+        g = np.random.default_rng(9000 + s.cfg)
+        prow = np.sort(g.choice(nq, min(nq, args.parity_queries), replace=False))
+    lib_assign = idx.assignment() if osd is not None else None
+    npq_host = w.nprobe.numpy()
+    kq_host = w.k.numpy()
+
+    def parity_of(ix, ids, dists):
+        if prow is None:
+            return None
+        gp = pano.panorama_probe(ix, Q[torch.from_numpy(prow).to(dev)], npmax).cpu().numpy()
+        return parity_report(osd, prow, npq_host[prow], kq_host[prow], ids.cpu().numpy()[prow],
+                             dists.cpu().numpy()[prow], gp, lib_assign)
+
+    parity = parity_of(idx, *out)
+    del out
+
+    # roofline of the dominant kernel: verify phase B (one launch per
+    # search), its device time from the stage events of the timed steps
+    vb = stage["verify_b"]
+    va = stage["verify_a"]
     dims_b = st["dims_scanned"] - st["dims_scanned_a"]
-    flops_b = 2.0 * dims_b  # algorithmic: one FMA per coordinate an alive pair reads
-    sm_max = float(pk.get("sm_max_mhz", 2070.0))
     if s.precision == "fp32":
         peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA pipes
-        bound, kern = "alu", "verify_fp32_kernel<64,64,256,4> (phase B)"
-        src = (f"FP32 FMA: 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
-               f"(max clock of MEASURED_PEAKS.json, {pk_kind})")
+        flops_b = 2.0 * dims_b  # algorithmic: one FMA per coordinate an alive pair reads
+        roof = {"bound": "alu", "kernel": "verify_fp32_kernel (phase B)",
+                "achieved": flops_b / (vb / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops_b / (vb / 1e3) / 1e12 / peak,
+                "traffic": TRAFFIC.get(s.name),
+                "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
+                               f"(max clock of MEASURED_PEAKS.json, {pk_kind})",
+                "flops_per_launch": flops_b, "ms_per_launch": vb,
+                "phase_a": {"ms": va, "flops": 2.0 * st["dims_scanned_a"]}}
     else:
-        peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1900.0)))
-        bound, kern = "tensor", "verify_tc_kernel (phase B)"
-        src = f"dense bf16, sustained ({pk_kind})"
-    achieved = flops_b / (vb / 1e3) / 1e12
-    roof = {"bound": bound, "kernel": kern, "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": TRAFFIC.get(s.name),
-            "peak_source": src, "flops_per_launch": flops_b, "ms_per_launch": vb,
-            "phase_a": {"ms": va, "flops": 2.0 * st["dims_scanned_a"],
-                        "achieved": 2.0 * st["dims_scanned_a"] / (va / 1e3) / 1e12},
-            "slice_bytes_per_step": st["slice_bytes"],
-            "slice_GBps": st["slice_bytes"] / ((va + vb) / 1e3) / 1e9,
-            "hbm_peak_GBps": pk.get("hbm_gbs")}
+        hbm = float(pk.get("hbm_gbs", FALLBACK_HBM_GBS))
+        live_b = st["live_row_bytes"]  # algorithmic: live rows x (w b + 4) per chunk-level
+        ach = live_b / (vb / 1e3) / 1e9
+        eb = 2 if s.precision == "bf16" else 1
+        flops_tc = 2.0 * dims_b * (2 if eb == 2 else 3)  # live pairs, hi+lo (BF16) / 3 terms (FP8)
+        tpk = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", FALLBACK_BF16_TFS)))
+        roof = {"bound": "hbm", "kernel": f"verify_tc_kernel<{'FP8' if eb == 1 else 'BF16'}> "
+                                          f"(phase B)",
+                "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": TRAFFIC.get(s.name),
+                "peak_source": f"STREAM-style copy of MEASURED_PEAKS.json ({pk_kind})",
+                "bytes_per_launch": live_b,
+                "bytes_definition": "per (query group, chunk, level): candidates live for at "
+                                    "least one query of the group x (level width x bytes per "
+                                    "element + 4-byte tail norm)",
+                "ms_per_launch": vb,
+                "staged_bytes_per_launch": st["slice_bytes"],
+                "staged_GBps": st["slice_bytes"] / (vb / 1e3) / 1e9,
+                "tensor": {"achieved_tflops": flops_tc / (vb / 1e3) / 1e12,
+                           "peak_tflops": tpk, "frac": flops_tc / (vb / 1e3) / 1e12 / tpk,
+                           "note": "MMA flops on live (pair, level) coordinates; dense bf16 "
+                                   "sustained peak"}}
 
-    # pruned BF16 and FP8 storage on the same data and queries (the metric's
-    # pruned BF16/FP8 vs plain FP32): d / 64 levels of 64 (valid widths for
-    # both), same transform and centroids
-    def quantised_run(precision):
-        idxq = pano.panorama_build_ivf(t, X, nlist=s.nlist, level_widths=[64] * (s.d // 64),
-                                       precision=precision,
-                                       centroids=idx.centroids() if s.nlist > 1 else None)
-        for _ in range(args.warmup):
-            idxq.search(Q, npa, ka, k_max=k)
-        torch.cuda.synchronize()
-        totq = 0.0
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            idxq.search(Q, npa, ka, k_max=k)
-            e1.record(stream)
-            e1.synchronize()
-            totq += e0.elapsed_time(e1)
-        tq = torch.tensor([totq], device=dev)
-        if world > 1:
-            dist.all_reduce(tq, op=dist.ReduceOp.MAX)
-        msq = tq.item() / args.steps
-        idxq.search(Q, npa, ka, k_max=k, collect_stats=True)
-        stq = pano.last_stats().as_dict()
-        out = {"levels": f"{s.d // 64}x64", "ms_per_step": msq,
-               "value": pairs * world / (msq / 1e3), "qps": nq * world / (msq / 1e3),
-               "speedup_vs_fp32_scan": scan_per / msq if s.precision == "fp32" else None,
-               "dims_scanned_frac": stq["dims_scanned"] / max(1, pairs * s.d),
-               "reranked": stq["reranked"], "index_gb": idxq.info().device_bytes / 1e9}
-        del idxq
-        return out
+    def search_line(ix, precision_name, with_scan=True, eps_runs=False):
+        """Timed pruned search (and plain scan) of another index of the same
+        data and queries, its counters and its parity sample."""
+        o = ix.search(Q, npa, ka, k_max=k)
+        msx, _, _ = timer.run(lambda: ix.search(Q, npa, ka, k_max=k), args.steps, args.warmup)
+        ix.search(Q, npa, ka, k_max=k, collect_stats=True)
+        stx = pano.last_stats().as_dict()
+        line = {"storage": precision_name, "ms_per_step": msx,
+                "value": stx["pairs"] * world / (msx / 1e3), "qps": nq * world / (msx / 1e3),
+                "dims_scanned_frac": stx["dims_scanned"] / max(1, stx["pairs"] * s.d),
+                "reranked": stx["reranked"], "index_gb": ix.info().device_bytes / 1e9}
+        if with_scan:
+            scx, _, _ = timer.run(lambda: ix.search(Q, npa, ka, k_max=k, mode=1),
+                                  args.scan_steps, 1)
+            line["plain_scan"] = {"ms_per_step": scx, "qps": nq * world / (scx / 1e3),
+                                  "value": stx["pairs"] * world / (scx / 1e3),
+                                  "speedup_of_pruned": scx / msx}
+        line["parity"] = parity_of(ix, *o)
+        return line
 
-    # the refine workload (point-centric, B = 1): each query's top-1000 of the
-    # pruned IVF search as its candidate-id list, refined to the top-k on a
-    # flat index of the same data and levels
-    refine = None
-    if s.precision == "fp32" and not args.no_refine and s.nlist > 1 and s.d % s.n_levels == 0:
-        kprime = 1000
-        cand, _ = idx.search(Q, npa, kprime, k_max=kprime)
-        flat = pano.panorama_build_flat(t, X, level_widths=[s.d // s.n_levels] * s.n_levels)
-        for _ in range(args.warmup):
-            flat.refine(Q, cand, k)
-        torch.cuda.synchronize()
-        totr = 0.0
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            flat.refine(Q, cand, k)
-            e1.record(stream)
-            e1.synchronize()
-            totr += e0.elapsed_time(e1)
-        tr = torch.tensor([totr], device=dev)
-        if world > 1:
-            dist.all_reduce(tr, op=dist.ReduceOp.MAX)
-        msr = tr.item() / args.steps
-        str_ = pano.last_stats().as_dict()
-        refine = {"kprime": kprime, "k": k, "ms_per_step": msr,
-                  "value": nq * kprime * world / (msr / 1e3), "unit": "candidates/s",
-                  "qps": nq * world / (msr / 1e3),
-                  "dims_scanned_frac": str_["dims_scanned"] / max(1, str_["pairs"] * s.d),
-                  "reranked": str_["reranked"]}
-        del flat, cand
-
-    # the IVFPQ workload (Section 6.3): the same data, lists and queries; the
-    # PCA basis shaped for PQ (Section 4.3, kappa = 4, seeded Haar draws),
-    # M = d / 2 subquantisers of 8 bits (2-d subvectors), codebooks and codes
-    # trained by the library; pruned search vs the plain PQ scan
-    ivfpq = None
-    Lp = args.pq_levels or s.n_levels
-    if (s.precision == "fp32" and not args.no_pq and s.nlist > 1 and s.d % Lp == 0
-            and (s.d // 2) % Lp == 0 and isinstance(s.nprobe, int)):
-        import time as _time
-        gd = np.random.default_rng(7000 + s.cfg).standard_normal((2, s.d, s.d))
-        b0 = _time.time()
-        tsh, blocks = pano.panorama_shape_transform(t, Lp, 4.0, gd)
-        idxp = pano.panorama_build_ivfpq(tsh, X, s.nlist, s.d // 2, Lp,
-                                         centroids=idx.centroids(), assign=idx.assignment())
-        build_s = _time.time() - b0
-        del gd
-
-        def pq_timed(mode, steps):
-            for _ in range(args.warmup):
-                idxp.search_pq(Q, s.nprobe, k, mode=mode)
-            torch.cuda.synchronize()
-            tot, vms = 0.0, []
-            for _ in range(steps):
-                flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                idxp.search_pq(Q, s.nprobe, k, mode=mode, collect_timing=True)
-                e1.record(stream)
-                e1.synchronize()
-                tot += e0.elapsed_time(e1)
-                vms.append(pano.last_stats().stage_ms[4])
-            tp = torch.tensor([tot], device=dev)
-            if world > 1:
-                dist.all_reduce(tp, op=dist.ReduceOp.MAX)
-            return tp.item() / steps, float(np.median(vms))
-
-        msp, vmsp = pq_timed(0, args.steps)
-        msp_scan, _ = pq_timed(1, args.scan_steps)
-        idxp.search_pq(Q, s.nprobe, k, collect_stats=True)
-        stp = pano.last_stats().as_dict()
-        secs = list(pano.last_stats().section_cycles)[:4]
-        secs_share = {nm: v / max(1, sum(secs)) for nm, v in
-                      zip(("prologue", "level0_tables", "level0_scan", "deeper_levels"), secs)}
-        ivfpq = {"M": s.d // 2, "nbits": 8, "levels": f"{Lp}x{s.d // Lp}",
-                 "kappa": 4.0, "robin_hood_blocks": blocks, "ms_per_step": msp,
-                 "value": stp["pairs"] * world / (msp / 1e3), "unit": "candidates/s",
-                 "qps": nq * world / (msp / 1e3),
-                 "plain_pq_scan": {"ms_per_step": msp_scan, "qps": nq * world / (msp_scan / 1e3),
-                                   "speedup_of_pruned": msp_scan / msp},
-                 "dims_scanned_frac": stp["dims_scanned"] / max(1, stp["pairs"] * s.d),
-                 "tables_built": stp["tile_levels"], "pairs": stp["pairs"],
-                 "block_time_share": secs_share,
-                 # the verify kernel: one shared-memory table lookup per
-                 # (live pair, subquantiser); peak = one conflict-free 32-lane
-                 # shared-memory wavefront per SM per clock
-                 "roofline": {"bound": "lsu", "kernel": "pq_verify_kernel",
-                              "achieved": stp["dims_scanned"] / 2 / (vmsp / 1e3),
-                              "peak": 152 * 32 * sm_max * 1e6, "unit": "lookups/s",
-                              "frac": stp["dims_scanned"] / 2 / (vmsp / 1e3)
-                              / (152 * 32 * sm_max * 1e6),
-                              "traffic": PQ_TRAFFIC.get(s.name), "ms_per_launch": vmsp,
-                              "lookups_per_launch": stp["dims_scanned"] / 2},
-                 "index_gb": idxp.info().device_bytes / 1e9, "build_s": build_s}
-        # recall@k against the exact top-k over the same lists: the IVFFlat
-        # search of the same index lists and queries returns it
-        ref_ids, _ = idx.search(Q, s.nprobe, k)
-        ref_ids = ref_ids.cpu().numpy()
-
-        def recall_of(ids):
-            ids = ids.cpu().numpy()
-            return float(np.mean([len(set(ids[i]) & set(ref_ids[i])) / k for i in range(nq)]))
-
-        ivfpq["recall_at_k"] = recall_of(idxp.search_pq(Q, s.nprobe, k)[0])
-        del idxp
-        # the kappa trade of spectrum shaping (Section 4.3): a larger cap
-        # keeps more energy up front (more pruning, less even PQ subspaces)
-        if not args.no_pq_sweep:
-            sweep = []
-            for kap in (1.0, 2.0, 4.0, 16.0):
-                gk = np.random.default_rng(7000 + s.cfg).standard_normal((2, s.d, s.d))
-                tk, bk = pano.panorama_shape_transform(t, Lp, kap, gk)
-                del gk
-                ik = pano.panorama_build_ivfpq(tk, X, s.nlist, s.d // 2, Lp,
-                                               centroids=idx.centroids(),
-                                               assign=idx.assignment())
-                for _ in range(2):
-                    ik.search_pq(Q, s.nprobe, k)
-                torch.cuda.synchronize()
-                tot = 0.0
-                for _ in range(3):
-                    flush.zero_()
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    ids_k, _ = ik.search_pq(Q, s.nprobe, k)
-                    e1.record(stream)
-                    e1.synchronize()
-                    tot += e0.elapsed_time(e1)
-                ik.search_pq(Q, s.nprobe, k, collect_stats=True)
-                stk = pano.last_stats().as_dict()
-                sweep.append({"kappa": kap, "robin_hood_blocks": bk, "ms_per_step": tot / 3,
-                              "qps": nq * world / (tot / 3 / 1e3),
-                              "recall_at_k": recall_of(ids_k),
-                              "dims_scanned_frac": stk["dims_scanned"] / max(1, stk["pairs"] * s.d)})
-                del ik, tk
-            ivfpq["kappa_sweep"] = sweep
-        del tsh
-
-    bf16 = fp8 = None
-    if s.precision == "fp32" and not args.no_bf16 and s.d % 64 == 0:
-        bf16 = quantised_run(pano.PANO_BF16)
-    if s.precision in ("fp32", "bf16") and not args.no_fp8 and s.d % 64 == 0:
-        fp8 = quantised_run(pano.PANO_FP8)
+    fp8 = fp32 = None
+    if s.precision == "bf16" and not args.no_fp8 and s.d % 64 == 0:
+        ix8 = pano.panorama_build_ivf(t, X, nlist=s.nlist, level_widths=widths or
+                                      [s.d // s.n_levels] * s.n_levels,
+                                      precision=pano.PANO_FP8, centroids=C)
+        fp8 = search_line(ix8, "fp8")
+        del ix8
+    if s.precision != "fp32" and not args.no_fp32:
+        ix32 = pano.panorama_build_ivf(t, X, nlist=s.nlist, level_widths=widths or
+                                       [s.d // s.n_levels] * s.n_levels,
+                                       precision=pano.PANO_FP32, centroids=C)
+        fp32 = search_line(ix32, "fp32")
+        del ix32
 
     # the serving workload: Poisson arrivals through the continuous-batching
     # server (batches of up to 1024 formed from what has arrived, several in
     # flight, admission by memory); QPS and latency percentiles per rate
     serving = None
     if "serving" in s.name and not args.no_serve:
-        import dataclasses
-        import numpy as np
         n_req = args.serve_requests
         sq = dataclasses.replace(s, n_queries=n_req, cfg=s.cfg + 50)
         wq = synth.generate(sq, device="cpu", queries_only=True)
@@ -621,11 +620,11 @@ def main():
         serving = []
         for rate in (20_000, 50_000, 100_000, 200_000):
             arr = np.cumsum(rng.exponential(1e6 / rate, size=n_req))
-            b0 = srv.stats()
+            b0_ = srv.stats()
             _, _, lat = srv.run_trace(wq.Q.numpy(), arr, wq.nprobe.numpy(), wq.k.numpy())
             b1 = srv.stats()
-            nb = b1["batches"] - b0["batches"]
-            nbq = b1["mean_batch"] * b1["batches"] - b0["mean_batch"] * b0["batches"]
+            nb = b1["batches"] - b0_["batches"]
+            nbq = b1["mean_batch"] * b1["batches"] - b0_["mean_batch"] * b0_["batches"]
             span_us = float(np.max(arr + lat) - arr[0])
             serving.append({"offered_qps": rate, "qps": n_req / (span_us / 1e6),
                             "p50_us": float(np.percentile(lat, 50)),
@@ -635,53 +634,211 @@ def main():
         srv.close()
 
     cpu = None
-    if s.n * s.nlist * s.d > 1e13:  # the oracle's FP64 list assignment alone
-        cpu = {"kind": "oracle", "value": None,
-               "skipped": "the oracle's FP64 assignment of N vectors to nlist lists would take "
-                          "hours on the host cores"}
-    elif rank == 0 and world == 1 and not args.no_cpu_baseline:
-        Xh, Qh = X.cpu().numpy(), Q.cpu().numpy()
-        cpu = cpu_baseline(Xh, Qh, idx.centroids(), s, 48, w.nprobe.numpy(), w.k.numpy())
+    if osd is not None and not args.no_cpu_baseline:
+        cpu = cpu_baseline(osd, npq_host, kq_host)
+    launches = search_launches(pano, st, s.nlist) * args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if s.precision == "fp32" else s.precision, "data": "synthetic",
+        "config": {"workload": workload_name(s) + (
+                       f" (levels autotuned: {tune['chosen']})" if tune else ""),
+                   "l2": "index larger than L2, and a 256 MB buffer written between timed "
+                         "steps (L2 flushed)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "qps": qps,
+        "plain_scan": {"storage": s.precision, "what": "plain tensor-core scan of the same "
+                       "index" if s.precision != "fp32" else "plain FP32 full-distance scan",
+                       "value": pairs * world / (scan_ms / 1e3),
+                       "qps": nq * world / (scan_ms / 1e3), "ms_per_step": scan_ms,
+                       "speedup_of_pruned": scan_ms / ms_per_step},
+        "e2e": e2e,
+        "parity": parity,
+        "fp8_pruned": fp8,
+        "fp32": fp32,
+        "speedup_vs_plain_fp32_scan": (fp32["plain_scan"]["ms_per_step"] / ms_per_step
+                                       if fp32 else None),
+        "autotune": tune,
+        "serving": serving,
+        "gpu_launches": launches,
+        "roofline": roof,
+        "stage_ms": stage,
+        "search_stats": {kk: st[kk] for kk in ("pairs", "pair_levels", "dims_scanned",
+                                                 "dims_scanned_a", "tile_levels",
+                                                 "slice_bytes", "live_row_bytes", "reranked",
+                                                 "work_items")},
+        "dims_scanned_frac": st["dims_scanned"] / max(1, pairs * s.d),
+        "build_s": build_s,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    del plan, idx, osd
+    del X, Q, w
+    torch.cuda.empty_cache()
+
+    if s.cfg != 2 and not args.no_secondary:
+        line["secondary"] = secondary(args, timer, dev, world, check_oracle, pk, pk_kind)
     if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if s.precision == "fp32" else s.precision, "data": "synthetic",
-            "config": {"workload": workload_name(s) + (
-                           f" (levels autotuned: {tune['chosen']})" if tune else ""),
-                       "l2": "256 MB buffer written between timed steps (L2 flushed)",
-                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-            "qps": qps,
-            # the comparator: a plain full-distance scan of the same index
-            "plain_scan": {"storage": s.precision, "value": pairs * world / (scan_per / 1e3),
-                           "qps": nq * world / (scan_per / 1e3), "ms_per_step": scan_per,
-                           "speedup_of_pruned": scan_per / ms_per_step},
-            "e2e": None if e2e_per is None else {
-                "value": pairs * world / (e2e_per / 1e3), "unit": "candidates/s",
-                "qps": nq * world / (e2e_per / 1e3), "ms_per_step": e2e_per,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": nq * k * 12},
-            "bf16_pruned": bf16,
-            "fp8_pruned": fp8,
-            "refine": refine,
-            "ivfpq": ivfpq,
-            "autotune": tune,
-            "serving": serving,
-            "gpu_launches": (KERNELS_PER_SEARCH if s.nlist > 1 else KERNELS_PER_SEARCH - 2)
-                            * args.steps,
-            "roofline": roof,
-            "stage_ms": stage,
-            "search_stats": {kk: st[kk] for kk in ("pairs", "pair_levels", "dims_scanned",
-                                                     "dims_scanned_a", "tile_levels",
-                                                     "slice_bytes", "reranked", "work_items")},
-            "dims_scanned_frac": st["dims_scanned"] / max(1, pairs * s.d),
-            "cpu_baseline": cpu,
-            "clocks": clocks,
-        }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def secondary(args, timer, dev, world, check_oracle, pk, pk_kind):
+    """The 960-d FP32 workload (N = 1M from a 1,024-cluster mixture, nlist
+    1024, nprobe 32, 10k queries, 16 x 60 levels, k = 10): pruned FP32
+    search, the plain FP32 scan, the FP32 verify roofline, a parity sample,
+    the epsilon sweep of Eq. 4, point-centric refine and IVFPQ."""
+    import numpy as np
+    import torch
+    import paper_2510_00566_gb300 as pano
+    import synth
+    s = synth.spec(2)
+    rank = int(os.environ.get("RANK", "0"))
+    w = synth.generate(s, device=dev)
+    if rank > 0:
+        w.Q = synth.generate(dataclasses.replace(s, cfg=s.cfg + 100 * rank), device=dev,
+                             queries_only=True).Q
+    X, Q = w.X, w.Q
+    nq, k = Q.shape[0], s.k
+    stream = timer.stream
+    t = pano.panorama_fit_transform(X[:65536], n_levels=s.n_levels)
+    idx = pano.panorama_build_ivf(t, X, nlist=s.nlist, n_levels=s.n_levels, seed=3002)
+    C = idx.centroids()
+    out = idx.search(Q, s.nprobe, k)
+    idx.search(Q, s.nprobe, k, collect_stats=True)
+    st = pano.last_stats().as_dict()
+    pairs = st["pairs"]
+    ms, stages, _ = timer.run(lambda: idx.search(Q, s.nprobe, k, collect_timing=True),
+                              args.steps, args.warmup,
+                              after=lambda: list(pano.last_stats().stage_ms))
+    vb = float(np.median([v[4] for v in stages]))
+    va = float(np.median([v[3] for v in stages]))
+    scan_ms, _, _ = timer.run(lambda: idx.search(Q, s.nprobe, k, mode=1), args.scan_steps, 1)
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    flops_b = 2.0 * (st["dims_scanned"] - st["dims_scanned_a"])
+    sizes = np.bincount(idx.assignment(), minlength=s.nlist)
+    res = {"workload": workload_name(s), "ms_per_step": ms,
+           "value": pairs * world / (ms / 1e3), "unit": "candidates/s",
+           "qps": nq * world / (ms / 1e3),
+           "candidates_per_query": pairs / nq,
+           "list_size_cv": float(sizes.std() / sizes.mean()),
+           "plain_scan": {"storage": "fp32", "ms_per_step": scan_ms,
+                          "qps": nq * world / (scan_ms / 1e3), "speedup_of_pruned": scan_ms / ms},
+           "roofline": {"bound": "alu", "kernel": "verify_fp32_kernel (phase B)",
+                        "achieved": flops_b / (vb / 1e3) / 1e12, "peak": peak,
+                        "unit": "TFLOP/s", "frac": flops_b / (vb / 1e3) / 1e12 / peak,
+                        "traffic": TRAFFIC.get(s.name),
+                        "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
+                                       f"({pk_kind} max clock)",
+                        "ms_per_launch": vb, "phase_a_ms": va},
+           "dims_scanned_frac": st["dims_scanned"] / max(1, pairs * s.d),
+           "gpu_launches": search_launches(pano, st, s.nlist) * args.steps}
+    osd = prow = None
+    if check_oracle and not args.no_parity:
+        osd = OracleSide(X.cpu().numpy(), Q.cpu().numpy(), C)
+        g = np.random.default_rng(9002)
+        prow = np.sort(g.choice(nq, min(nq, args.parity_queries), replace=False))
+        gp = pano.panorama_probe(idx, Q[torch.from_numpy(prow).to(dev)], s.nprobe).cpu().numpy()
+        res["parity"] = parity_report(osd, prow, s.nprobe, k, out[0].cpu().numpy()[prow],
+                                      out[1].cpu().numpy()[prow], gp, idx.assignment())
+    # Eq. 4 / Proposition 5.3: epsilon-relaxed pruning; recall@k against the
+    # oracle's exact top-k on the parity sample, dims read against the model
+    # E[cost_eps] / E[cost_1] = 1 + ln(eps) (valid for eps > 1/e)
+    if not args.no_eps:
+        sweep = []
+        ref_ids = None
+        if osd is not None:
+            ref_ids = osd.answer(prow, s.nprobe, k)[0]
+        d1 = None
+        for eps in EPSILONS:
+            mse, _, _ = timer.run(lambda: idx.search(Q, s.nprobe, k, epsilon=eps),
+                                  max(3, args.scan_steps), 1)
+            ids_e, _ = idx.search(Q, s.nprobe, k, epsilon=eps, collect_stats=True)
+            ste = pano.last_stats().as_dict()
+            d1 = d1 or ste["dims_scanned"]
+            row = {"epsilon": eps, "ms_per_step": mse, "qps": nq * world / (mse / 1e3),
+                   "dims_scanned_frac": ste["dims_scanned"] / max(1, ste["pairs"] * s.d),
+                   "dims_ratio_vs_exact": ste["dims_scanned"] / d1,
+                   "model_ratio_1_plus_ln_eps": 1.0 + math.log(eps)}
+            if ref_ids is not None:
+                got = ids_e.cpu().numpy()[prow]
+                row["recall_at_k"] = float(np.mean(
+                    [len(set(got[i]) & set(ref_ids[i])) / k for i in range(len(prow))]))
+            sweep.append(row)
+        res["epsilon_sweep"] = sweep
+    # the refine workload (point-centric, B = 1): each query's top-1000 of the
+    # pruned IVF search as its candidate-id list, refined to the top-k on a
+    # flat index of the same data and levels
+    if not args.no_refine:
+        kprime = 1000
+        cand, _ = idx.search(Q, s.nprobe, kprime, k_max=kprime)
+        flat = pano.panorama_build_flat(t, X, level_widths=[s.d // s.n_levels] * s.n_levels)
+        msr, _, _ = timer.run(lambda: flat.refine(Q, cand, k), args.steps, args.warmup)
+        str_ = pano.last_stats().as_dict()
+        res["refine"] = {"kprime": kprime, "k": k, "ms_per_step": msr,
+                         "value": nq * kprime * world / (msr / 1e3), "unit": "candidates/s",
+                         "qps": nq * world / (msr / 1e3),
+                         "dims_scanned_frac": str_["dims_scanned"] / max(1, str_["pairs"] * s.d),
+                         "reranked": str_["reranked"]}
+        if osd is not None:
+            rc = cand.cpu().numpy()[prow]
+            import oracle
+            ref_i, ref_d = oracle.candidate_topk(osd.X, osd.Q[prow], rc, k)
+            ids_r, d_r = flat.refine(Q[torch.from_numpy(prow).to(dev)],
+                                     cand[torch.from_numpy(prow).to(dev)], k)
+            ids_r, d_r = ids_r.cpu().numpy(), d_r.cpu().numpy().astype(np.float64)
+            ok = (ids_r == ref_i) | (np.abs(d_r - ref_d) <= 1e-6 * np.maximum(ref_d, 1e-30))
+            fin = np.isfinite(ref_d)
+            res["refine"]["parity"] = {
+                "queries": len(prow), "id_mismatch_beyond_tie": int((~ok).sum()),
+                "max_rel_err": float(np.max(np.abs(d_r[fin] - ref_d[fin]) / ref_d[fin]))}
+        del flat, cand
+    # IVFPQ (Section 6.3): the same data, lists and queries; the PCA basis
+    # shaped for PQ (Section 4.3, kappa = 4, seeded Haar draws), M = d / 2
+    # subquantisers of 8 bits, codebooks and codes trained by the library
+    Lp = args.pq_levels or s.n_levels
+    if not args.no_pq and s.d % Lp == 0 and (s.d // 2) % Lp == 0:
+        gd = np.random.default_rng(7000 + s.cfg).standard_normal((2, s.d, s.d))
+        b0 = time.time()
+        tsh, blocks = pano.panorama_shape_transform(t, Lp, 4.0, gd)
+        idxp = pano.panorama_build_ivfpq(tsh, X, s.nlist, s.d // 2, Lp,
+                                         centroids=C, assign=idx.assignment())
+        build_s = time.time() - b0
+        msp, vm, _ = timer.run(lambda: idxp.search_pq(Q, s.nprobe, k, collect_timing=True),
+                               args.steps, args.warmup,
+                               after=lambda: pano.last_stats().stage_ms[4])
+        vmsp = float(np.median(vm))
+        msp_scan, _, _ = timer.run(lambda: idxp.search_pq(Q, s.nprobe, k, mode=1),
+                                   args.scan_steps, 1)
+        idxp.search_pq(Q, s.nprobe, k, collect_stats=True)
+        stp = pano.last_stats().as_dict()
+        look = stp["dims_scanned"] / 2
+        lpk = 152 * 32 * sm_max * 1e6
+        ref_ids, _ = idx.search(Q, s.nprobe, k)
+        ref_ids = ref_ids.cpu().numpy()
+        pq_ids = idxp.search_pq(Q, s.nprobe, k)[0].cpu().numpy()
+        res["ivfpq"] = {
+            "M": s.d // 2, "nbits": 8, "levels": f"{Lp}x{s.d // Lp}", "kappa": 4.0,
+            "robin_hood_blocks": blocks, "ms_per_step": msp,
+            "value": stp["pairs"] * world / (msp / 1e3), "unit": "candidates/s",
+            "qps": nq * world / (msp / 1e3),
+            "plain_pq_scan": {"ms_per_step": msp_scan, "qps": nq * world / (msp_scan / 1e3),
+                              "speedup_of_pruned": msp_scan / msp},
+            "dims_scanned_frac": stp["dims_scanned"] / max(1, stp["pairs"] * s.d),
+            "recall_at_k_vs_exact_same_lists": float(np.mean(
+                [len(set(pq_ids[i]) & set(ref_ids[i])) / k for i in range(nq)])),
+            "roofline": {"bound": "lsu", "kernel": "pq_verify_kernel",
+                         "achieved": look / (vmsp / 1e3), "peak": lpk, "unit": "lookups/s",
+                         "frac": look / (vmsp / 1e3) / lpk, "traffic": PQ_TRAFFIC.get(s.name),
+                         "ms_per_launch": vmsp},
+            "index_gb": idxp.info().device_bytes / 1e9, "build_s": build_s}
+        del idxp, tsh, gd
+    del idx, osd
+    return res
 
 
 if __name__ == "__main__":

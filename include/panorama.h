@@ -134,6 +134,12 @@ typedef struct {
   int64_t dims_scanned_a; /* the part of dims_scanned read in phase A        */
   int64_t pairs_a;        /* the part of pairs in phase A (0 in one pass)    */
   int64_t section_cycles_a[8]; /* the part of section_cycles from phase A    */
+  int64_t live_row_bytes; /* tensor-core path: sum over (query group, chunk,
+                             level) steps of the candidates live for at
+                             least one query of the group entering the
+                             level x (level width x bytes per element + 4),
+                             the slice and tail-norm bytes the method must
+                             read; 0 on the FP32 path                        */
 } pano_search_stats;
 
 /* Description of a built index. */

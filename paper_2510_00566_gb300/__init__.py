@@ -68,7 +68,8 @@ class SearchStats(ctypes.Structure):
                 ("stage_ms", ctypes.c_float * 6), ("pad2_", ctypes.c_float * 2),
                 ("section_cycles", ctypes.c_int64 * 8),
                 ("dims_scanned_a", ctypes.c_int64), ("pairs_a", ctypes.c_int64),
-                ("section_cycles_a", ctypes.c_int64 * 8)]
+                ("section_cycles_a", ctypes.c_int64 * 8),
+                ("live_row_bytes", ctypes.c_int64)]
 
     STAGES = ("transform", "probe", "inversion", "verify_a", "verify_b",
               "decode")

@@ -32,8 +32,9 @@ namespace {
 constexpr int CH = 64;
 // Device statistics words: [0] pair-levels, [1] tile-levels, [2] slice bytes,
 // [3] reranked, [4] pairs, [5] unused, [6] / [7] dims of phase A / B,
-// [8..15] section cycles, [16..23] their phase-A part, [24] phase-A pairs.
-constexpr int kStatWords = 25;
+// [8..15] section cycles, [16..23] their phase-A part, [24] phase-A pairs,
+// [25] live-row bytes (tensor-core path).
+constexpr int kStatWords = 26;
 constexpr int SEG_CHUNKS = 32;  // chunks per work-item segment
 constexpr int NT = 256;
 
@@ -1841,6 +1842,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
       for (int i = 0; i < 8; ++i) t_stats.section_cycles[i] = (int64_t)hst[8 + i];
       for (int i = 0; i < 8; ++i) t_stats.section_cycles_a[i] = (int64_t)hst[16 + i];
       t_stats.pairs_a = (int64_t)hst[24];
+      t_stats.live_row_bytes = (int64_t)hst[25];
       if (timing)
         for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&t_stats.stage_ms[i], ev[i], ev[i + 1]);
       if (herr[0] & kErrTimeout) return fail(PANO_ETIMEOUT, "a device-side wait timed out");
