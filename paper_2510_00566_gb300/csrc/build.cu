@@ -226,6 +226,77 @@ __global__ void __launch_bounds__(256) pack_fp32_kernel(
   }
 }
 
+// k-means++ seeding (D^2 sampling, Arthur & Vassilvitskii 2007) over m
+// sample rows, on the device.  Round r: every row's squared distance to the
+// newest seed lowers its running minimum d2; each block adds up its rows'
+// d2 (FP64); then one thread draws u ~ U[0, sum d2) from a counter-based
+// hash of (seed, r) and picks the row where the running sum crosses u.
+constexpr int kKppBlocks = 512;
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__global__ void __launch_bounds__(256) kpp_update_kernel(const float* __restrict__ xs, int64_t m,
+                                                         int d, const int64_t* __restrict__ picks,
+                                                         int r, int64_t rpb, float* __restrict__ d2,
+                                                         double* __restrict__ bsum) {
+  const int64_t r0 = (int64_t)blockIdx.x * rpb;
+  const int64_t r1 = r0 + rpb < m ? r0 + rpb : m;
+  const float* c = xs + picks[r] * (int64_t)d;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  double part = 0.0;
+  for (int64_t i = r0 + warp; i < r1; i += blockDim.x / 32) {
+    const float* x = xs + i * (int64_t)d;
+    float s = 0.f;
+    for (int j = lane; j < d; j += 32) {
+      const float t = x[j] - c[j];
+      s = fmaf(t, t, s);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    const float v = r == 0 ? s : fminf(d2[i], s);
+    if (lane == 0) d2[i] = v;
+    part += (double)v;
+  }
+  __shared__ double red[8];
+  if (lane == 0) red[warp] = part;  // lane 0 holds the warp's rows (all lanes add the same)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+__global__ void kpp_pick_kernel(const float* __restrict__ d2, int64_t m, int64_t rpb, int nblk,
+                                const double* __restrict__ bsum, uint64_t seed, int r,
+                                int64_t* __restrict__ picks) {
+  if (threadIdx.x != 0) return;
+  double total = 0.0;
+  for (int b = 0; b < nblk; ++b) total += bsum[b];
+  const double u = (double)(mix64(seed ^ mix64((uint64_t)r + 1)) >> 11) * 0x1.0p-53 * total;
+  int64_t pick = (int64_t)((mix64(seed + 7 * (uint64_t)r) >> 1) % (uint64_t)m);  // all d2 zero
+  if (total > 0.0) {
+    double acc = 0.0;
+    int b = 0;
+    while (b < nblk - 1 && acc + bsum[b] <= u) acc += bsum[b++];
+    const int64_t i0 = (int64_t)b * rpb, i1 = i0 + rpb < m ? i0 + rpb : m;
+    pick = i1 - 1;
+    for (int64_t i = i0; i < i1; ++i) {
+      acc += (double)d2[i];
+      if (acc > u && d2[i] > 0.f) {
+        pick = i;
+        break;
+      }
+    }
+  }
+  picks[r + 1] = pick;
+}
+
 struct Tmp {
   void* p = nullptr;
   ~Tmp() {
@@ -250,14 +321,34 @@ int kmeans(const float* Xd, int64_t n, int d, int nlist, int iters, int64_t ns,
   float* xs = (float*)t_xs.p;
   gather_rows_kernel<<<(unsigned)ns, 128, 0, st>>>(Xd, d, (int64_t*)t_idx.p, ns, xs);
   row_norms_kernel<<<(unsigned)((ns + 7) / 8), 256, 0, st>>>(xs, ns, d, (float*)t_xn.p);
-  // initial centroids: nlist distinct sample rows
-  std::vector<int64_t> init = sample_without_replacement(ns, nlist, seed ^ 0xA5A5A5A5ULL);
-  std::vector<float> hxs_rows((size_t)nlist * d);
-  for (int c = 0; c < nlist; ++c)
-    PANO_CUDA(cudaMemcpyAsync(hxs_rows.data() + (size_t)c * d, xs + init[c] * d,
-                              d * sizeof(float), cudaMemcpyDeviceToHost, st));
-  PANO_CUDA(cudaStreamSynchronize(st));
-  cent = hxs_rows;
+  // initial centroids: k-means++ (D^2) seeding over the first m sample rows
+  // (the sample is already a uniform draw of the data)
+  {
+    const int64_t m = std::min<int64_t>(ns, (int64_t)64 * nlist);
+    const int64_t rpb = (m + kKppBlocks - 1) / kKppBlocks;
+    const int nblk = (int)((m + rpb - 1) / rpb);
+    Tmp t_d2, t_bs, t_pk;
+    PANO_CUDA(cudaMalloc(&t_d2.p, m * sizeof(float)));
+    PANO_CUDA(cudaMalloc(&t_bs.p, nblk * sizeof(double)));
+    PANO_CUDA(cudaMalloc(&t_pk.p, (size_t)(nlist + 1) * sizeof(int64_t)));
+    uint64_t s0 = seed ^ 0xA5A5A5A5ULL;
+    const int64_t first = (int64_t)(splitmix64(s0) % (uint64_t)m);
+    PANO_CUDA(cudaMemcpyAsync(t_pk.p, &first, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    for (int r = 0; r + 1 < nlist; ++r) {
+      kpp_update_kernel<<<nblk, 256, 0, st>>>(xs, m, d, (const int64_t*)t_pk.p, r, rpb,
+                                              (float*)t_d2.p, (double*)t_bs.p);
+      kpp_pick_kernel<<<1, 32, 0, st>>>((const float*)t_d2.p, m, rpb, nblk,
+                                        (const double*)t_bs.p, s0, r, (int64_t*)t_pk.p);
+    }
+    PANO_CUDA(cudaGetLastError());
+    gather_rows_kernel<<<(unsigned)nlist, 128, 0, st>>>(xs, d, (const int64_t*)t_pk.p, nlist,
+                                                        (float*)t_c.p);
+    PANO_CUDA(cudaGetLastError());
+    cent.resize((size_t)nlist * d);
+    PANO_CUDA(cudaMemcpyAsync(cent.data(), t_c.p, cent.size() * sizeof(float),
+                              cudaMemcpyDeviceToHost, st));
+    PANO_CUDA(cudaStreamSynchronize(st));
+  }
   std::vector<double> hsums((size_t)nlist * d);
   std::vector<int> hcnt(nlist);
   std::vector<float> hcn(nlist);
@@ -296,6 +387,27 @@ int kmeans(const float* Xd, int64_t n, int d, int nlist, int iters, int64_t ns,
       }
       hcnt[c] = hcnt[big] / 2;
       hcnt[big] -= hcnt[c];
+    }
+    // balance: while a list holds under half the mean and another over 1.5
+    // times it, the small list's centroid moves to split the large one (at
+    // most nlist / 16 moves per iteration; the last two iterations settle)
+    if (it + 2 < iters && nlist > 1) {
+      const double mean = (double)ns / nlist;
+      std::vector<int> order(nlist);
+      std::iota(order.begin(), order.end(), 0);
+      std::sort(order.begin(), order.end(), [&](int x, int y) { return hcnt[x] < hcnt[y]; });
+      int lo = 0, hi = nlist - 1, moves = 0;
+      while (lo < hi && moves < std::max(1, nlist / 16) && hcnt[order[lo]] < 0.5 * mean &&
+             hcnt[order[hi]] > 1.5 * mean) {
+        const int small = order[lo++], big = order[hi--];
+        for (int j = 0; j < d; ++j) {
+          float base = cent[(size_t)big * d + j];
+          float eps = (float)(1e-4 * ((splitmix64(pert) & 1) ? 1.0 : -1.0)) * (std::fabs(base) + 1e-3f);
+          cent[(size_t)small * d + j] = base + eps;
+          cent[(size_t)big * d + j] = base - eps;
+        }
+        ++moves;
+      }
     }
   }
   return PANO_OK;
