@@ -456,16 +456,22 @@ def main():
     npmax = int(w.nprobe.max())
     widths, tune = None, None
     if per_query:
-        # level widths chosen by the autotuner (median search time of each
-        # candidate split on a query sample, k-means run once)
-        cands = [[w_] * (s.d // w_) for w_ in (16, 32, 64, 128) if s.d % w_ == 0]
+        # storage precision and level split chosen by the autotuner: median
+        # search time of each (precision, split) pair on a query sample,
+        # splits generated per format (uniform and front-loaded), k-means once
         qs = Q[:min(len(Q), 8192)]
-        best, ms = pano.panorama_autotune_levels(t, X, qs, s.nlist, 64, 10, cands,
-                                                 precision=prec, repeats=2)
-        widths = cands[best]
-        tune = {"candidates": [f"{len(c)}x{c[0]}" for c in cands],
-                "ms": [float(x) for x in ms], "chosen": f"{len(widths)}x{widths[0]}",
-                "sample": f"{len(qs)} queries, nprobe 64, k 10"}
+        names = {pano.PANO_FP32: "fp32", pano.PANO_BF16: "bf16", pano.PANO_FP8: "fp8"}
+        t0 = time.time()
+        best, trials = pano.panorama_autotune(
+            t, X, qs, s.nlist, 64, 10,
+            precisions=(pano.PANO_FP32, pano.PANO_BF16, pano.PANO_FP8), repeats=2)
+        widths, prec = trials[best]["widths"], trials[best]["precision"]
+        s = dataclasses.replace(s, precision=names[prec], n_levels=len(widths))
+        tune = {"trials": [{"precision": names[tr["precision"]], "widths": tr["widths"],
+                            "ms": tr["ms"] if math.isfinite(tr["ms"]) else None}
+                           for tr in trials],
+                "chosen": {"precision": names[prec], "widths": widths},
+                "sample": f"{len(qs)} queries, nprobe 64, k 10", "seconds": time.time() - t0}
     b0 = time.time()
     idx = pano.panorama_build_ivf(t, X, nlist=s.nlist, n_levels=s.n_levels, seed=3000 + s.cfg,
                                   precision=prec, level_widths=widths)
@@ -532,6 +538,11 @@ def main():
 
     parity = parity_of(idx, *out)
     del out
+    eps_sweep = None
+    if not args.no_eps and plan is None:
+        ref_ids = osd.answer(prow, npq_host[prow], kq_host[prow])[0] if prow is not None else None
+        eps_sweep = epsilon_sweep(idx, Q, npa, ka, k, s.d, timer, max(3, args.scan_steps),
+                                  ref_ids, prow)
 
     # roofline of the dominant kernel: verify phase B (one launch per
     # search), its device time from the stage events of the timed steps
@@ -593,19 +604,24 @@ def main():
         line["parity"] = parity_of(ix, *o)
         return line
 
+    def other_storage(precision, name):
+        """The same data, centroids, levels and queries in another storage
+        format (a split the format cannot take is reported, not fatal)."""
+        try:
+            ixo = pano.panorama_build_ivf(t, X, nlist=s.nlist, level_widths=widths or
+                                          [s.d // s.n_levels] * s.n_levels,
+                                          precision=precision, centroids=C)
+        except pano.LibraryError as ex:
+            return {"storage": name, "unavailable": str(ex)}
+        line_ = search_line(ixo, name)
+        del ixo
+        return line_
+
     fp8 = fp32 = None
     if s.precision == "bf16" and not args.no_fp8 and s.d % 64 == 0:
-        ix8 = pano.panorama_build_ivf(t, X, nlist=s.nlist, level_widths=widths or
-                                      [s.d // s.n_levels] * s.n_levels,
-                                      precision=pano.PANO_FP8, centroids=C)
-        fp8 = search_line(ix8, "fp8")
-        del ix8
+        fp8 = other_storage(pano.PANO_FP8, "fp8")
     if s.precision != "fp32" and not args.no_fp32:
-        ix32 = pano.panorama_build_ivf(t, X, nlist=s.nlist, level_widths=widths or
-                                       [s.d // s.n_levels] * s.n_levels,
-                                       precision=pano.PANO_FP32, centroids=C)
-        fp32 = search_line(ix32, "fp32")
-        del ix32
+        fp32 = other_storage(pano.PANO_FP32, "fp32")
 
     # the serving workload: Poisson arrivals through the continuous-batching
     # server (batches of up to 1024 formed from what has arrived, several in
@@ -643,7 +659,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if s.precision == "fp32" else s.precision, "data": "synthetic",
         "config": {"workload": workload_name(s) + (
-                       f" (levels autotuned: {tune['chosen']})" if tune else ""),
+                       f" (precision and levels autotuned: {tune['chosen']})" if tune else ""),
                    "l2": "index larger than L2, and a 256 MB buffer written between timed "
                          "steps (L2 flushed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
@@ -655,10 +671,11 @@ def main():
                        "speedup_of_pruned": scan_ms / ms_per_step},
         "e2e": e2e,
         "parity": parity,
+        "epsilon_sweep": eps_sweep,
         "fp8_pruned": fp8,
         "fp32": fp32,
         "speedup_vs_plain_fp32_scan": (fp32["plain_scan"]["ms_per_step"] / ms_per_step
-                                       if fp32 else None),
+                                       if fp32 and "plain_scan" in fp32 else None),
         "autotune": tune,
         "serving": serving,
         "gpu_launches": launches,
@@ -684,6 +701,36 @@ def main():
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def epsilon_sweep(idx, Q, nprobe, k, k_max, d, timer, steps, ref_ids=None, prow=None):
+    """Eq. 4 / Proposition 5.3: epsilon-relaxed pruning.  Per epsilon: time,
+    coordinates read against the model E[cost_eps] / E[cost_1] = 1 + ln(eps)
+    (valid for eps > 1/e), and recall@k against the oracle's exact top-k on
+    the parity sample."""
+    import numpy as np
+    import paper_2510_00566_gb300 as pano
+    nq = Q.shape[0]
+    sweep, d1 = [], None
+    for eps in EPSILONS:
+        mse, _, _ = timer.run(lambda: idx.search(Q, nprobe, k, k_max=k_max, epsilon=eps),
+                              steps, 1)
+        ids_e, _ = idx.search(Q, nprobe, k, k_max=k_max, epsilon=eps, collect_stats=True)
+        ste = pano.last_stats().as_dict()
+        d1 = d1 or ste["dims_scanned"]
+        row = {"epsilon": eps, "ms_per_step": mse, "qps": nq / (mse / 1e3),
+               "dims_scanned_frac": ste["dims_scanned"] / max(1, ste["pairs"] * d),
+               "dims_ratio_vs_exact": ste["dims_scanned"] / d1,
+               "model_ratio_1_plus_ln_eps": 1.0 + math.log(eps)}
+        if ref_ids is not None:
+            got = ids_e.cpu().numpy()[prow]
+            kq = np.broadcast_to(np.asarray(k if isinstance(k, int) else k.cpu().numpy()),
+                                 (nq,))[prow]
+            row["recall_at_k"] = float(np.mean(
+                [len(set(got[i][:kq[i]]) & set(ref_ids[i][:kq[i]])) / max(1, kq[i])
+                 for i in range(len(prow))]))
+        sweep.append(row)
+    return sweep
 
 
 def secondary(args, timer, dev, world, check_oracle, pk, pk_kind):
@@ -749,27 +796,9 @@ def secondary(args, timer, dev, world, check_oracle, pk, pk_kind):
     # oracle's exact top-k on the parity sample, dims read against the model
     # E[cost_eps] / E[cost_1] = 1 + ln(eps) (valid for eps > 1/e)
     if not args.no_eps:
-        sweep = []
-        ref_ids = None
-        if osd is not None:
-            ref_ids = osd.answer(prow, s.nprobe, k)[0]
-        d1 = None
-        for eps in EPSILONS:
-            mse, _, _ = timer.run(lambda: idx.search(Q, s.nprobe, k, epsilon=eps),
-                                  max(3, args.scan_steps), 1)
-            ids_e, _ = idx.search(Q, s.nprobe, k, epsilon=eps, collect_stats=True)
-            ste = pano.last_stats().as_dict()
-            d1 = d1 or ste["dims_scanned"]
-            row = {"epsilon": eps, "ms_per_step": mse, "qps": nq * world / (mse / 1e3),
-                   "dims_scanned_frac": ste["dims_scanned"] / max(1, ste["pairs"] * s.d),
-                   "dims_ratio_vs_exact": ste["dims_scanned"] / d1,
-                   "model_ratio_1_plus_ln_eps": 1.0 + math.log(eps)}
-            if ref_ids is not None:
-                got = ids_e.cpu().numpy()[prow]
-                row["recall_at_k"] = float(np.mean(
-                    [len(set(got[i]) & set(ref_ids[i])) / k for i in range(len(prow))]))
-            sweep.append(row)
-        res["epsilon_sweep"] = sweep
+        ref_ids = osd.answer(prow, s.nprobe, k)[0] if osd is not None else None
+        res["epsilon_sweep"] = epsilon_sweep(idx, Q, s.nprobe, k, k, s.d, timer,
+                                             max(3, args.scan_steps), ref_ids, prow)
     # the refine workload (point-centric, B = 1): each query's top-1000 of the
     # pruned IVF search as its candidate-id list, refined to the top-k on a
     # flat index of the same data and levels

@@ -140,6 +140,11 @@ typedef struct {
                              level x (level width x bytes per element + 4),
                              the slice and tail-norm bytes the method must
                              read; 0 on the FP32 path                        */
+  /* tensor-core path, collect_stats = 1: device cycles each role spent
+   * waiting, summed over CTAs: [0] the MMA warp for staged tiles, [1] the
+   * MMA warp for the epilogue of a chunk's previous level, [2] the first
+   * epilogue warp for MMAs, [3] the producer warp for free stages */
+  int64_t wait_cycles[4];
 } pano_search_stats;
 
 /* Description of a built index. */
@@ -340,6 +345,40 @@ int panorama_autotune_levels(const pano_transform* t, const float* X, int64_t n,
                              const int32_t* widths, const int32_t* n_levels,
                              int32_t n_candidates, int32_t repeats, int32_t* best,
                              float* ms_out, void* stream);
+
+/* panorama_autotune -- picks the storage precision and the level split
+ * (the paper's L ablation of Section 7.5, extended to the precision of the
+ * level slices) that search a sample fastest.
+ *   X, queries, nlist, nprobe, k: as in panorama_autotune_levels;
+ *   precisions: n_prec storage formats to try (PANO_FP32, PANO_BF16,
+ *   PANO_FP8);
+ *   widths / n_levels / n_candidates: candidate splits as in
+ *   panorama_autotune_levels, tried with every precision; n_candidates = 0
+ *   lets the tuner generate them per format: every uniform width (16, 32,
+ *   64, 128, 256) dividing d that the format's kernels take, and
+ *   front-loaded splits whose leading levels are narrow (16, 32 or 64) and
+ *   double towards the widest width the format takes (BF16 128, FP8 and
+ *   FP32 256), the last level taking the rest;
+ *   trials (caller-owned, max_trials entries): one per (precision, split)
+ *   pair in precision-major order, with its median search time over
+ *   `repeats` timed searches (after one warm-up) or +inf when the pair
+ *   cannot be built or staged; *n_trials and *best (index of the fastest)
+ *   are written.  k-means runs once; every candidate is built with its
+ *   centroids.  Errors: PANO_EINVAL for bad arguments, more pairs than
+ *   max_trials, or no searchable pair; build / CUDA errors otherwise. */
+typedef struct {
+  int32_t precision;
+  int32_t n_levels;
+  int32_t widths[64];
+  float ms;
+  int32_t pad_;
+} pano_autotune_trial;
+int panorama_autotune(const pano_transform* t, const float* X, int64_t n,
+                      const float* queries, int64_t nq, int32_t nlist, int32_t nprobe,
+                      int32_t k, const int32_t* precisions, int32_t n_prec,
+                      const int32_t* widths, const int32_t* n_levels, int32_t n_candidates,
+                      int32_t repeats, pano_autotune_trial* trials, int32_t max_trials,
+                      int32_t* n_trials, int32_t* best, void* stream);
 
 /* -------------------------------------------------------------- serving
  * A server batches single-query requests continuously over a device-resident

@@ -19,7 +19,7 @@ __all__ = ["lib", "LibraryError", "Transform", "Index", "SearchStats",
            "PANO_FP32", "PANO_BF16", "PANO_FP8", "PANO_PQ",
            "panorama_transform_import", "panorama_shape_transform",
            "panorama_build_ivfpq", "panorama_search_pq", "panorama_pq_export",
-           "panorama_debug_pq_encode",
+           "panorama_debug_pq_encode", "panorama_autotune",
            "library_path"]
 
 PANO_FP32, PANO_BF16, PANO_FP8, PANO_PQ = 0, 1, 2, 3
@@ -69,7 +69,8 @@ class SearchStats(ctypes.Structure):
                 ("section_cycles", ctypes.c_int64 * 8),
                 ("dims_scanned_a", ctypes.c_int64), ("pairs_a", ctypes.c_int64),
                 ("section_cycles_a", ctypes.c_int64 * 8),
-                ("live_row_bytes", ctypes.c_int64)]
+                ("live_row_bytes", ctypes.c_int64),
+                ("wait_cycles", ctypes.c_int64 * 4)]
 
     STAGES = ("transform", "probe", "inversion", "verify_a", "verify_b",
               "decode")
@@ -77,12 +78,14 @@ class SearchStats(ctypes.Structure):
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_
              if not f.startswith("pad")
-             and f not in ("stage_ms", "section_cycles", "section_cycles_a")}
+             and f not in ("stage_ms", "section_cycles", "section_cycles_a", "wait_cycles")}
         d["stage_ms"] = dict(zip(self.STAGES, list(self.stage_ms)))
         names = ("prologue", "mma_issue", "epilogue", "next_level", "ub_filter", "rerank",
                  "kernel", "ctas")
         d["section_cycles"] = dict(zip(names, list(self.section_cycles)))
         d["section_cycles_a"] = dict(zip(names, list(self.section_cycles_a)))
+        d["wait_cycles"] = dict(zip(("mma_tiles", "mma_epilogue", "epilogue_mma",
+                                     "producer_stages"), list(self.wait_cycles)))
         return d
 
 
@@ -156,6 +159,8 @@ SIGNATURES = {
     "panorama_server_stats": (ctypes.c_int, [_P, _P]),
     "panorama_server_run_trace": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P, _P, _P]),
     "panorama_server_free": (None, [_P]),
+    "panorama_autotune": (ctypes.c_int, [_P, _P, _I64, _P, _I64, _I32, _I32, _I32, _P, _I32,
+                                         _P, _P, _I32, _I32, _P, _I32, _P, _P, _P]),
     "panorama_autotune_levels": (ctypes.c_int, [_P, _P, _I64, _P, _I64, _I32, _I32,
                                                 _I32, _I32, _P, _P, _I32, _I32, _P,
                                                 _P, _P]),
@@ -572,6 +577,43 @@ def panorama_autotune_levels(t: "Transform", X, queries, nlist, nprobe, k,
                                           ctypes.byref(best), ms.ctypes.data,
                                           _stream_ptr(stream)))
     return best.value, ms
+
+
+class AutotuneTrial(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("n_levels", ctypes.c_int32),
+                ("widths", ctypes.c_int32 * 64), ("ms", ctypes.c_float),
+                ("pad_", ctypes.c_int32)]
+
+
+def panorama_autotune(t: "Transform", X, queries, nlist, nprobe, k,
+                      precisions=(PANO_FP32, PANO_BF16, PANO_FP8), candidates=None,
+                      repeats=3, max_trials=64, stream=None):
+    """Fastest (precision, level split) on a query sample.  Returns (best
+    index, trials) with trials a list of dicts (precision, widths, ms)."""
+    import numpy as np
+    keep, ptr = _host_f32(X)
+    n = keep.shape[0]
+    prec = np.ascontiguousarray(precisions, dtype=np.int32)
+    flat = lens = None
+    ncand = 0
+    if candidates:
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(c) for c in candidates]),
+                                    dtype=np.int32)
+        lens = np.ascontiguousarray([len(c) for c in candidates], dtype=np.int32)
+        ncand = len(candidates)
+    trials = (AutotuneTrial * max_trials)()
+    n_tr, best = ctypes.c_int32(0), ctypes.c_int32(-1)
+    q = queries.contiguous()
+    _check(lib().panorama_autotune(t.handle, ptr, n, q.data_ptr(), q.shape[0], nlist, nprobe,
+                                   k, prec.ctypes.data, len(prec),
+                                   None if flat is None else flat.ctypes.data,
+                                   None if lens is None else lens.ctypes.data, ncand, repeats,
+                                   trials, max_trials, ctypes.byref(n_tr), ctypes.byref(best),
+                                   _stream_ptr(stream)))
+    out = [{"precision": trials[i].precision,
+            "widths": list(trials[i].widths[:trials[i].n_levels]), "ms": trials[i].ms}
+           for i in range(n_tr.value)]
+    return best.value, out
 
 
 class ServerOpts(ctypes.Structure):

@@ -70,3 +70,39 @@ def test_autotune_levels_picks_a_valid_split(zipf_index):
     assert all(math.isfinite(x) and x > 0 for x in ms[:3])
     assert math.isinf(ms[3])  # 48-wide bf16 levels are not a supported tile width
     assert ms[best] == min(ms)
+
+
+def test_autotune_precision_and_generated_splits(zipf_index):
+    """The precision x split tuner (generated candidates): every trial is a
+    valid split of d for its storage format, the best is the fastest, and
+    the configuration it picks returns the oracle's exact top-k."""
+    s, w, t, idx = zipf_index
+    X = w.X[:20_000]
+    Qs = w.Q[:128].to(DEV)
+    best, trials = pano.panorama_autotune(
+        t, X.to(DEV), Qs, nlist=32, nprobe=8, k=10,
+        precisions=(pano.PANO_FP32, pano.PANO_BF16, pano.PANO_FP8), repeats=2)
+    assert len(trials) >= 6
+    precs = {tr["precision"] for tr in trials}
+    assert precs == {pano.PANO_FP32, pano.PANO_BF16, pano.PANO_FP8}
+    ok_w = {pano.PANO_BF16: {16, 32, 64, 128}, pano.PANO_FP8: {32, 64, 128, 256}}
+    for tr in trials:
+        assert sum(tr["widths"]) == s.d
+        if tr["precision"] in ok_w:
+            assert set(tr["widths"]) <= ok_w[tr["precision"]]
+    # uniform and front-loaded (non-uniform) splits were both tried
+    assert any(len(set(tr["widths"])) > 1 for tr in trials)
+    finite = [tr["ms"] for tr in trials if math.isfinite(tr["ms"])]
+    assert trials[best]["ms"] == min(finite)
+    # the chosen configuration, built on the same data, answers exactly
+    bt = trials[best]
+    C = synth.initial_centroids(X, 32, seed=3004).numpy()
+    ix = pano.panorama_build_ivf(t, X.to(DEV), nlist=32, level_widths=bt["widths"],
+                                 precision=bt["precision"], centroids=C)
+    ids, d = ix.search(Qs, 8, 10)
+    Xh, Qh = X.numpy(), Qs.cpu().numpy()
+    lists, _ = oracle.assign(Xh, C)
+    ref = oracle.ivf_search(Xh, Qh, C, 8, 10, lists_of_vector=lists)
+    keep = ref["probe_gap"] >= 1e-6
+    check_topk(Xh, Qh[keep], ids.cpu().numpy()[keep], d.cpu().numpy()[keep], ref["ids"][keep],
+               ref["dists"][keep], 10)
