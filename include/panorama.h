@@ -140,11 +140,6 @@ typedef struct {
                              level x (level width x bytes per element + 4),
                              the slice and tail-norm bytes the method must
                              read; 0 on the FP32 path                        */
-  /* tensor-core path, collect_stats = 1: device cycles each role spent
-   * waiting, summed over CTAs: [0] the MMA warp for staged tiles, [1] the
-   * MMA warp for the epilogue of a chunk's previous level, [2] the first
-   * epilogue warp for MMAs, [3] the producer warp for free stages */
-  int64_t wait_cycles[4];
 } pano_search_stats;
 
 /* Description of a built index. */

@@ -69,8 +69,7 @@ class SearchStats(ctypes.Structure):
                 ("section_cycles", ctypes.c_int64 * 8),
                 ("dims_scanned_a", ctypes.c_int64), ("pairs_a", ctypes.c_int64),
                 ("section_cycles_a", ctypes.c_int64 * 8),
-                ("live_row_bytes", ctypes.c_int64),
-                ("wait_cycles", ctypes.c_int64 * 4)]
+                ("live_row_bytes", ctypes.c_int64)]
 
     STAGES = ("transform", "probe", "inversion", "verify_a", "verify_b",
               "decode")
@@ -78,14 +77,12 @@ class SearchStats(ctypes.Structure):
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_
              if not f.startswith("pad")
-             and f not in ("stage_ms", "section_cycles", "section_cycles_a", "wait_cycles")}
+             and f not in ("stage_ms", "section_cycles", "section_cycles_a")}
         d["stage_ms"] = dict(zip(self.STAGES, list(self.stage_ms)))
         names = ("prologue", "mma_issue", "epilogue", "next_level", "ub_filter", "rerank",
                  "kernel", "ctas")
         d["section_cycles"] = dict(zip(names, list(self.section_cycles)))
         d["section_cycles_a"] = dict(zip(names, list(self.section_cycles_a)))
-        d["wait_cycles"] = dict(zip(("mma_tiles", "mma_epilogue", "epilogue_mma",
-                                     "producer_stages"), list(self.wait_cycles)))
         return d
 
 

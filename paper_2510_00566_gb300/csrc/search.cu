@@ -33,8 +33,8 @@ constexpr int CH = 64;
 // Device statistics words: [0] pair-levels, [1] tile-levels, [2] slice bytes,
 // [3] reranked, [4] pairs, [5] unused, [6] / [7] dims of phase A / B,
 // [8..15] section cycles, [16..23] their phase-A part, [24] phase-A pairs,
-// [25] live-row bytes, [26..29] wait cycles per role (tensor-core path).
-constexpr int kStatWords = 30;
+// [25] live-row bytes (tensor-core path).
+constexpr int kStatWords = 26;
 constexpr int SEG_CHUNKS = 32;  // chunks per work-item segment
 constexpr int NT = 256;
 
@@ -1843,7 +1843,6 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
       for (int i = 0; i < 8; ++i) t_stats.section_cycles_a[i] = (int64_t)hst[16 + i];
       t_stats.pairs_a = (int64_t)hst[24];
       t_stats.live_row_bytes = (int64_t)hst[25];
-      for (int i = 0; i < 4; ++i) t_stats.wait_cycles[i] = (int64_t)hst[26 + i];
       if (timing)
         for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&t_stats.stage_ms[i], ev[i], ev[i + 1]);
       if (herr[0] & kErrTimeout) return fail(PANO_ETIMEOUT, "a device-side wait timed out");

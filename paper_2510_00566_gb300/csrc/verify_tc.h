@@ -7,7 +7,7 @@ namespace pano {
 
 constexpr int TC_CHUNK = 128;  // vectors per chunk (MMA M)
 constexpr int TC_QG = 64;      // queries per group (MMA N, padded to 16)
-constexpr int TC_SEG = 8;      // chunks per work-item segment (8 x 64 TMEM columns)
+constexpr int TC_SEG = 4;      // chunks per work-item segment
 
 struct VerifyTCArgs {
   const uint8_t* slices;
@@ -41,8 +41,6 @@ struct VerifyTCArgs {
   int phase;  // 0: phase A (its dims are also counted apart)
   float eps;  // Eq. 4: the query tail term of the pruning test is scaled by eps
   int fp8;    // 1: E4M3 level tiles (kind::f8f6f4), 0: BF16
-  int na;     // stages of the A-tile ring (set by the launcher)
-  int nb;     // query-tile buffers, 2 or 1 (set by the launcher)
   int32_t level_off[65];
 };
 
