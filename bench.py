@@ -478,6 +478,8 @@ def main():
     torch.cuda.synchronize()
     build_s = time.time() - b0
     C = idx.centroids()
+    sizes = np.bincount(idx.assignment(), minlength=s.nlist)
+    list_cv = float(sizes.std() / sizes.mean())  # balance of the k-means lists
     plan = pano.Plan(idx, Q, npa, ka, k_max=k) if per_query else None
 
     # counters (one instrumented search, outside the timed region)
@@ -686,6 +688,8 @@ def main():
                                                  "slice_bytes", "live_row_bytes", "reranked",
                                                  "work_items")},
         "dims_scanned_frac": st["dims_scanned"] / max(1, pairs * s.d),
+        "candidates_per_query": pairs / nq,
+        "list_size_cv": list_cv,
         "build_s": build_s,
         "cpu_baseline": cpu,
         "clocks": clocks,

@@ -351,9 +351,14 @@ __global__ void inv_emit_kernel(int ph, const int* __restrict__ cnt, int nlist,
 // ------------------------------------------------- Alg. 1 warm start (a6)
 // Per query: distances to the first max(4k, 64) (at most 256) members of its
 // nearest list; the k-th smallest is an upper bound on d_k and seeds the
-// threshold before any tile is verified (Algorithm 1 initialises d_k from
-// the first k candidates).  The seeds are not inserted into the top-k: they
-// are verified again like every other candidate.
+// threshold before any tile is verified.  Algorithm 1 also fills its heap
+// with k candidates before pruning anything: the seeds whose bound is at
+// most that k-th one (at least k of them) enter the top-k with their exact
+// distances, computed by the re-ranking's own routine on the same rows, so a
+// later re-rank of the same candidate yields the same key and is kept once.
+// With exact pruning this changes no result; with the epsilon-relaxed bound
+// of Eq. 4, which can prune every candidate of a query, the answer still
+// holds the best k seeds, as Algorithm 1's heap would.
 //
 // The query row sits in shared memory; a warp loads a whole row (up to 1024
 // dims) in one batch and sums fl(q_j - x_j)^2 by FMA into four interleaved
@@ -369,9 +374,11 @@ __global__ void __launch_bounds__(kSeedWarps * 32) seed_tau_kernel(
     const float* __restrict__ q, int d, const int32_t* __restrict__ probes, int stride,
     const int64_t* __restrict__ chunk_off, const int32_t* __restrict__ list_size, int chunk,
     const float* __restrict__ rows, const int32_t* __restrict__ kq,
-    const int32_t* __restrict__ order, float slack, float* __restrict__ tau_seed) {
+    const int32_t* __restrict__ order, float slack, float* __restrict__ tau_seed,
+    const int32_t* __restrict__ ids, unsigned long long* __restrict__ topk, int k_max) {
   extern __shared__ float4 qs4[];  // the query row (d floats)
   __shared__ float dist[kSeedMax];
+  __shared__ float s_t;
   const int64_t row = order ? order[blockIdx.x] : blockIdx.x;
   const int k = kq[row];
   const int c = probes[row * stride];
@@ -443,7 +450,17 @@ __global__ void __launch_bounds__(kSeedWarps * 32) seed_tau_kernel(
   __syncthreads();
   if (warp == 0) {
     const float t = warp_kth_smallest(dist, ns, k);
-    if (lane == 0) tau_seed[row] = t;
+    if (lane == 0) {
+      tau_seed[row] = t;
+      s_t = t;
+    }
+  }
+  __syncthreads();
+  const float t = s_t;
+  for (int i = warp; i < ns; i += kSeedWarps) {
+    if (!(dist[i] <= t)) continue;
+    const float e = exact_sqdist_warp_wide(q + row * d, rows + (base + i) * d, d);
+    topk_insert_warp(topk + row * k_max, k, make_key(e, ids[base + i]));
   }
 }
 
@@ -465,7 +482,8 @@ __global__ void __launch_bounds__(kSeedWarps * 32) seed_group_kernel(
     const int* __restrict__ n_items, int64_t items_cap, int nsub,
     const int32_t* __restrict__ bucket, const int64_t* __restrict__ chunk_off,
     const int32_t* __restrict__ list_size, int chunk, const float* __restrict__ rows,
-    const int32_t* __restrict__ kq, float slack, float* __restrict__ tau_seed) {
+    const int32_t* __restrict__ kq, float slack, float* __restrict__ tau_seed,
+    const int32_t* __restrict__ ids, unsigned long long* __restrict__ topk, int k_max) {
   extern __shared__ float4 sg_raw[];
   const int64_t item = blockIdx.x / nsub;
   const int sub = blockIdx.x % nsub;
@@ -479,6 +497,7 @@ __global__ void __launch_bounds__(kSeedWarps * 32) seed_group_kernel(
   float4* qs = sg_raw;                                                // [G][d/4]
   float* dist = reinterpret_cast<float*>(sg_raw + (size_t)kSeedSub * d4);  // [G][kSeedMax]
   __shared__ int s_q[kSeedSub], s_k[kSeedSub], s_ns[kSeedSub];
+  __shared__ float s_t[kSeedSub];
   const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
   if (tid < G) {
     const int qi = bucket[it.z + g0 + tid];
@@ -545,7 +564,19 @@ __global__ void __launch_bounds__(kSeedWarps * 32) seed_group_kernel(
   for (int g = warp; g < G; g += kSeedWarps) {
     const int k = s_k[g], ns = s_ns[g];
     const float t = (k <= 0) ? -1.f : (ns < k ? INFINITY : warp_kth_smallest(dist + g * kSeedMax, ns, k));
-    if (lane == 0) tau_seed[s_q[g]] = t;
+    if (lane == 0) {
+      tau_seed[s_q[g]] = t;
+      s_t[g] = t;
+    }
+  }
+  __syncthreads();
+  // the seeds within each query's k-th bound enter its top-k (a warp each)
+  for (int e = warp; e < G * kSeedMax; e += kSeedWarps) {
+    const int g = e / kSeedMax, i = e % kSeedMax;
+    if (i >= s_ns[g] || !(dist[g * kSeedMax + i] <= s_t[g])) continue;
+    const int64_t qi = s_q[g];
+    const float ex = exact_sqdist_warp_wide(q + qi * d, rows + (base + i) * d, d);
+    topk_insert_warp(topk + qi * k_max, s_k[g], make_key(ex, ids[base + i]));
   }
 }
 
@@ -1683,11 +1714,13 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
       PANO_CUDA(allow_dynamic_smem((const void*)seed_group_kernel));
       seed_group_kernel<<<(unsigned)(capA * nsub), kSeedWarps * 32, gsm, st>>>(
           queries, d, itA, tot + 1, capA, nsub, bucket, I.chunk_off_d.as<int64_t>(),
-          I.list_size_d.as<int32_t>(), I.chunk, I.rows.as<float>(), kq, seed_slack, tau_seed);
+          I.list_size_d.as<int32_t>(), I.chunk, I.rows.as<float>(), kq, seed_slack, tau_seed,
+          I.ids.as<int32_t>(), topk, k_max);
     } else {
       seed_tau_kernel<<<(unsigned)nq, kSeedWarps * 32, (size_t)d * 4, st>>>(
           queries, d, probes, stride, I.chunk_off_d.as<int64_t>(), I.list_size_d.as<int32_t>(),
-          I.chunk, I.rows.as<float>(), kq, one_pass ? nullptr : bucket, seed_slack, tau_seed);
+          I.chunk, I.rows.as<float>(), kq, one_pass ? nullptr : bucket, seed_slack, tau_seed,
+          I.ids.as<int32_t>(), topk, k_max);
     }
     PANO_CUDA(cudaGetLastError());
     // a4-a10

@@ -194,6 +194,30 @@ def test_epsilon_relaxed_pruning(ivf960):
     assert dims_e <= dims1, (dims_e, dims1)
 
 
+@pytest.mark.gpu
+def test_epsilon_far_below_one_still_answers_k(ivf960):
+    """Eq. 4 with eps = 0.1, where the relaxed bound can prune every candidate
+    of a query: Algorithm 1 fills its heap with k candidates before pruning,
+    so the answer still holds k distinct true candidates (from the query's
+    nearest list at least) with exact distances, in ascending order."""
+    s, X, Q, C, t, idx = ivf960
+    ids_e, d_e = idx.search(torch.from_numpy(Q).to(DEV), 8, 10, epsilon=0.1)
+    ids_e, d_e = ids_e.cpu().numpy(), d_e.cpu().numpy()
+    lists, agap = oracle.assign(X, C)
+    probes, gap = oracle.probe(Q, C, 8)
+    sizes = np.bincount(idx.assignment(), minlength=len(C))
+    for i in range(len(Q)):
+        if gap[i] < 1e-6 or sizes[probes[i][0]] < 10:
+            continue
+        g = ids_e[i]
+        assert np.all(g >= 0), (i, g)
+        assert len(set(g.tolist())) == len(g)
+        assert np.all(np.isin(lists[g], probes[i]) | (agap[g] < 1e-6))
+        true_d = ((X[g].astype(np.float64) - Q[i]) ** 2).sum(1)
+        assert np.all(np.abs(d_e[i] - true_d) <= 1e-5 * np.maximum(true_d, 1e-30))
+        assert np.all(np.diff(d_e[i]) >= 0)
+
+
 def test_ivf_per_query_nprobe_and_k(ivf960):
     s, X, Q, C, t, idx = ivf960
     g = np.random.default_rng(5)
