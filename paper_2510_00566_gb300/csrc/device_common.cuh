@@ -107,7 +107,7 @@ __device__ __forceinline__ void topk_insert(unsigned long long* slots, int k,
   while (j < k && ld_volatile_u64(slots + j) < key) ++j;
   for (; j < k; ++j) {
     unsigned long long old = atomicMin(slots + j, key);
-    if (old == kEmptyKey) return;
+    if (old == kEmptyKey || old == key) return;  // an equal key is the same pair: kept once
     key = old > key ? old : key;
   }
 }
@@ -156,7 +156,7 @@ __device__ __forceinline__ void topk_insert_warp(unsigned long long* slots, int 
   if (lane == 0)
     for (int j = start; j < k; ++j) {
       unsigned long long old = atomicMin(slots + j, key);
-      if (old == kEmptyKey) return;
+      if (old == kEmptyKey || old == key) return;  // an equal key is the same pair: kept once
       key = old > key ? old : key;
     }
 }

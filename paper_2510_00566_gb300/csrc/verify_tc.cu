@@ -41,10 +41,21 @@ namespace {
 constexpr int CH = TC_CHUNK;  // 128 rows (MMA M)
 constexpr int QG = TC_QG;     // 64 queries per group (MMA N, padded to 16)
 constexpr int S = TC_SEG;     // chunks per segment (4 x 64 = 256 TMEM columns)
-// thread t: TMEM lane / chunk row t % 128 and query half t / 128 (queries
-// 32h .. 32h+31 are TMEM columns 32h.. of each chunk's accumulator); warps
-// w and w + 4 share a lane quarter
-constexpr int NT = 256;
+// epilogue thread t < NE: TMEM lane / chunk row t % 128 and query half
+// t / 128 (queries 32h .. 32h+31 are TMEM columns 32h.. of each chunk's
+// accumulator); warps w and w + 4 share a lane quarter.  Warp NE / 32 issues
+// the MMA chains and the tile copies.
+constexpr int NE = 256;
+constexpr int NT = NE + 32;
+constexpr int kIssuer = NE / 32;
+
+// Barrier of the NE epilogue threads alone (named barrier 1).
+__device__ __forceinline__ void epi_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NE) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_plain(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
 // ------------------------------------------------------------------ build
 // One CTA per chunk: bf16 tiles, tail norms / norms of the dequantised
@@ -250,7 +261,7 @@ struct Smem {
 // and top-k insertion, in two passes: first each query's k kept pairs of
 // smallest lower bound (ties by entry), whose exact distances usually set
 // its threshold, then the others that still pass the threshold.  All threads
-// of the CTA call it (one thread per entry at most: kPend <= NT); kept out of
+// epilogue threads call it (one thread per entry at most: kPend <= NE); kept out of
 // line so that it does not add to the level loop's registers.  Returns the
 // number re-ranked (thread 0; 0 elsewhere).
 __device__ __noinline__ int flush_pending(const VerifyTCArgs& a, int np,
@@ -260,9 +271,9 @@ __device__ __noinline__ int flush_pending(const VerifyTCArgs& a, int np,
                                           float* __restrict__ plb,
                                           const float* __restrict__ pub, uint16_t* keep,
                                           uint16_t* rank, int* s_cnt) {
-  const int tid = threadIdx.x, warp = tid / 32, nw = blockDim.x / 32;
+  const int tid = threadIdx.x, warp = tid / 32, nw = NE / 32;
   if (tid == 0) s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
-  __syncthreads();
+  epi_sync();
   auto tau_of = [&](int q, int kk) {
     const unsigned long long key = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + kk - 1);
     return fminf(key == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key), 1.000001f),
@@ -282,7 +293,7 @@ __device__ __noinline__ int flush_pending(const VerifyTCArgs& a, int np,
     }
     if (keep_s) keep[atomicAdd(&s_cnt[0], 1)] = (uint16_t)s;
   }
-  __syncthreads();
+  epi_sync();
   const int nk = s_cnt[0];
   if (tid < nk && (a.d & 3) == 0)  // all kept rows head for L2 at once
     prefetch_l2(a.rows + pslot[keep[tid]] * a.d, (uint32_t)a.d * 4);
@@ -299,7 +310,7 @@ __device__ __noinline__ int flush_pending(const VerifyTCArgs& a, int np,
     rank[tid] = first ? 1 : 0;
     if (first) atomicAdd(&s_cnt[1], 1);
   }
-  __syncthreads();
+  epi_sync();
   // exact distances (a warp each; they replace the lower bounds), then the
   // top-k insertions (a thread each, so their chains overlap)
   auto rerank = [&](const uint16_t* list, int n, const uint16_t* sel) {
@@ -310,12 +321,12 @@ __device__ __noinline__ int flush_pending(const VerifyTCArgs& a, int np,
           exact_sqdist_warp_wide(a.qorig + (int64_t)pq[s] * a.d, a.rows + pslot[s] * a.d, a.d);
       if ((tid & 31) == 0) plb[s] = dist;
     }
-    __syncthreads();
+    epi_sync();
     if (tid < n && (!sel || sel[tid])) {
       const int s = list[tid], q = pq[s];
       topk_insert_thread(a.topk + (int64_t)q * a.k_max, a.kq[q], make_key(plb[s], pid[s]));
     }
-    __syncthreads();
+    epi_sync();
   };
   rerank(keep, nk, rank);
   // the others, against the thresholds of the moment (rank now lists them)
@@ -323,7 +334,7 @@ __device__ __noinline__ int flush_pending(const VerifyTCArgs& a, int np,
     const int s = keep[tid], q = pq[s];
     if (!(plb[s] > tau_of(q, a.kq[q]))) rank[atomicAdd(&s_cnt[2], 1)] = (uint16_t)s;
   }
-  __syncthreads();
+  epi_sync();
   rerank(rank, s_cnt[2], nullptr);
   return tid == 0 ? s_cnt[1] + s_cnt[2] : 0;
 }
@@ -367,7 +378,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   float* qtau = qeq + QG;
   uint16_t* ub16 = reinterpret_cast<uint16_t*>(abuf);  // [QG][S*CH] bf16 bits
   uint16_t* surv = reinterpret_cast<uint16_t*>(abuf);  // [CH * QG], after ub16 is read
-  // [32][NT] each thread's last accumulators (slot j of thread t at j*NT + t)
+  // [32][NE] each thread's last accumulators (slot j of thread t at j*NE + t)
   float* vdump = reinterpret_cast<float*>(abuf + CH * QG * 2);
   // deferred re-rank list: (slot, query, id, lower bound) per pair
   __shared__ int64_t pslot[Smem::kPend];
@@ -375,18 +386,21 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   __shared__ float plb[Smem::kPend], pub[Smem::kPend];
   __shared__ uint16_t keep[Smem::kPend], rnk[Smem::kPend];
   __shared__ int s_flush[3];
-  static_assert(Smem::kPend <= NT, "the flush gives each pending pair one thread");
-  __shared__ __align__(8) uint64_t load_bar[S], mma_bar[S];
+  static_assert(Smem::kPend <= NE, "the flush gives each pending pair one thread");
+  // per chunk: its tile has landed / its MMAs are done / every epilogue warp
+  // has read its accumulator (count NE / 32)
+  __shared__ __align__(8) uint64_t load_bar[S], mma_bar[S], epi_bar[S];
   __shared__ uint32_t tmem_base;
   __shared__ int s_item, s_nsurv, s_fail, s_npend;
   // FP8: the group's largest |q~_j| (as bits), query scale and the absolute
   // bound of the query split's underflow per unit of |x|_2
   __shared__ unsigned int s_qmax;
   __shared__ float s_qs, s_cunder;
-  __shared__ uint32_t rowlive[S][NT / 32];  // per warp: its rows live in its half
+  __shared__ uint32_t rowlive[S][NE / 32];  // per epilogue warp: its rows live in its half
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
   const int row = tid & (CH - 1), half = tid / CH;
+  const bool epi = tid < NE;
   if (warp == 0) {
     tc::tmem_alloc(&tmem_base, TMEM_COLS);
     tc::tmem_relinquish();
@@ -395,6 +409,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     for (int c = 0; c < S; ++c) {
       mbar_init(&load_bar[c], 1);
       mbar_init(&mma_bar[c], 1);
+      mbar_init(&epi_bar[c], NE / 32);
     }
     fence_mbar_init();
     s_fail = 0;
@@ -406,7 +421,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   const uint32_t tbase = tmem_base;
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   const int L = a.L, d = a.d;
-  uint32_t load_bits = 0, mma_bits = 0;
+  uint32_t load_bits = 0, mma_bits = 0, epi_bits = 0;
   // counters (collect_stats) live in shared memory, off the registers:
   // [0] pairs, [1] dims, [2] tiles, [3] bytes, [4] reranked, [5] live-row
   // bytes; section cycles
@@ -445,7 +460,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   auto chunk_live = [&](int c) {
     uint32_t m = 0;
 #pragma unroll
-    for (int i = 0; i < NT / 32; ++i) m |= rowlive[c][i];
+    for (int i = 0; i < NE / 32; ++i) m |= rowlive[c][i];
     return m != 0u;
   };
 
@@ -468,8 +483,9 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     const uint32_t idesc = FP8 ? tc::idesc_e4m3(CH, Npad) : tc::idesc_bf16(CH, Npad);
     const uint8_t* item_src = a.slices + ch0 * (int64_t)CH * d * EB;
 
-    // stage chunk c's level-l tile (live rows only when few rows live);
-    // warp 0 calls it after a CTA barrier, with chunk c's liveness complete
+    // stage chunk c's level-l tile (live rows only when few rows live); the
+    // issue warp calls it once chunk c's liveness words are complete (no
+    // epilogue warp writes them again before this copy has been consumed)
     auto issue_load = [&](int c, int l) {
       const int m = a.level_off[l], w = a.level_off[l + 1] - m;
       const int wl = FP8 ? w / 2 : w;  // width of the bf16 tile with the same bytes
@@ -477,10 +493,12 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       const int rb = tc::row_bytes(wl), npan = wl >= 64 ? wl / 64 : 1;
       unsigned char* dst = abuf + (size_t)c * lay.abytes;
       const uint8_t* src = item_src + (int64_t)c * CH * d * EB + (size_t)m * CH * EB;
-      uint32_t atoms = 0;  // 8-row groups holding a live row
-      for (int t = 0; t < 16; ++t)
-        if (((rowlive[c][t >> 2] | rowlive[c][4 + (t >> 2)]) >> ((t & 3) * 8)) & 0xffu)
-          atoms |= 1u << t;
+      uint32_t atoms = 0;  // 8-row groups holding a live row (lane 0 is the
+      if (lane == 0)       // lane that acquired the liveness words)
+        for (int t = 0; t < 16; ++t)
+          if (((rowlive[c][t >> 2] | rowlive[c][4 + (t >> 2)]) >> ((t & 3) * 8)) & 0xffu)
+            atoms |= 1u << t;
+      atoms = __shfl_sync(0xffffffffu, atoms, 0);
       const int na = __popc(atoms);
       if (l == 0 || na * 4 >= 3 * 16) {
         if (lane == 0) {
@@ -526,7 +544,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     };
     auto build_b = [&](int l, int first_chunk) {
       const int m = a.level_off[l], w = a.level_off[l + 1] - m;
-      for (int e = tid + first_chunk * NT; e < Npad * (w / 8); e += NT) {
+      for (int e = tid + first_chunk * NE; e < Npad * (w / 8); e += NE) {
         const int g = e / (w / 8), c8 = e % (w / 8);
         float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (g < G) {
@@ -587,7 +605,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       s_qs = ldexpf(1.f, -e);
       s_cunder = __fmul_ru(ldexpf(1.f, e - 10), __fsqrt_ru((float)d));
     }
-    {
+    if (epi) {
       uint32_t gm0 = 0, gm1 = 0;
       for (int g = 0; g < G; ++g)
         if (qk[g] > 0) {
@@ -603,7 +621,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       }
     }
     __syncthreads();
-    if (warp == 0)
+    if (warp == kIssuer)
       for (int c = 0; c < nch; ++c)
         if (chunk_live(c)) issue_load(c, 0);
     if (tid < QG) {
@@ -623,7 +641,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       for (int e = tid; e < S * CH; e += NT)
         cfr[e] = e / CH < nch ? a.xscale[(ch0 + e / CH) * CH + (e % CH)] * qinv : 0.f;
     }
-    build_b(0, 0);
+    if (epi) build_b(0, 0);
     fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -652,16 +670,16 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       }
       // prefetch the next level's query slices, tails and thresholds
       float4 pf[2 * PF_CHUNKS];
-      float tail_pf[S * CH / NT];
+      float tail_pf[S * CH / NE];
       unsigned long long key_pf = kEmptyKey;
       float seed_pf = INFINITY, sq_pf = 0.f;
       int m1 = 0, w1 = 16;
-      if (has_next) {
+      if (has_next && epi) {
         m1 = a.level_off[l + 1];
         w1 = a.level_off[l + 2] - m1;
 #pragma unroll
         for (int i = 0; i < PF_CHUNKS; ++i) {
-          const int e = tid + i * NT;
+          const int e = tid + i * NE;
           const int g = e / (w1 / 8), c8 = e % (w1 / 8);
           if (e < Npad * (w1 / 8) && g < G) {
             const float* src = a.qt + (int64_t)qid[g] * d + m1 + c8 * 8;
@@ -672,8 +690,8 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           }
         }
 #pragma unroll
-        for (int u = 0; u < S * CH / NT; ++u) {
-          const int e = tid + u * NT;
+        for (int u = 0; u < S * CH / NE; ++u) {
+          const int e = tid + u * NE;
           tail_pf[u] = e < nch * CH
                            ? a.tails[((ch0 + e / CH) * (L + 1) + l + 2) * CH + (e % CH)]
                            : 0.f;
@@ -687,9 +705,8 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           }
         }
       }
-      // chunk c's MMAs go out before chunk c-1's epilogue, so the tensor
-      // core works while the previous accumulator is tested, and the first
-      // epilogue never waits for the last chunk's tile to land
+      // chunk c's test (epilogue warps): its accumulator once its MMAs are
+      // done, then its liveness for the issue warp
       auto epilogue = [&](int c) {
         const bool ok = wait_phase(&mma_bar[c], mma_bits, c, &s_fail);
         tc::fence_after_sync();
@@ -741,48 +758,67 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         }
         const unsigned bal = __ballot_sync(0xffffffffu, wm != 0);
         if (lane == 0) rowlive[c][warp] = bal;
+        // every lane's accumulator reads are complete before lane 0 tells
+        // the issue warp (which then overwrites the chunk's tile and, at the
+        // next level, its accumulator)
         tc::fence_before_sync();
-        __syncthreads();
-        // the tile stays live: its next level is staged into its (now
-        // free) buffer at once
-        if (warp == 0 && has_next) {
-          const int go = __shfl_sync(0xffffffffu, (chunk_live(c) && !s_fail) ? 1 : 0, 0);
-          if (go) issue_load(c, l + 1);
-        }
+        __syncwarp();
+        if (has_next && lane == 0) mbar_arrive_plain(&epi_bar[c]);
       };
-      int prev = -1;
-      for (int c = 0; c < nch; ++c) {
-        if (!((live_mask >> c) & 1u)) continue;
-        if (tid == 0) {
+      if (warp == kIssuer) {
+        // every live chunk's MMA chain as soon as its tile has landed (the
+        // epilogue warps test chunk c while chunk c + 1's MMAs run) ...
+        if (lane == 0) {
           const uint32_t h0 = smem_u32(bhi), l0 = smem_u32(blo);
-          if (wait_phase(&load_bar[c], load_bits, c, &s_fail)) {
-            const uint32_t a0 = smem_u32(abuf + (size_t)c * lay.abytes);
-            const uint32_t dt = tbase + (uint32_t)(c * QG);
-            if (FP8) {  // 32 elements per K-step; tiles addressed at half width
-              const uint32_t m0 = h0 + (uint32_t)(QG * a.max_w);
-              for (int s = 0; s < w / 32; ++s) {
-                const uint64_t ad = tc::kstep_desc(a0, s, CH, w / 2);
-                tc::mma_e4m3(dt, ad, tc::kstep_desc(h0, s, Npad, w / 2), idesc,
-                             (l > 0 || s > 0) ? 1u : 0u);
-                tc::mma_e4m3(dt, ad, tc::kstep_desc(m0, s, Npad, w / 2), idesc, 1u);
-                tc::mma_e4m3(dt, ad, tc::kstep_desc(l0, s, Npad, w / 2), idesc, 1u);
-              }
-            } else {
-              for (int s = 0; s < w / 16; ++s) {
-                const uint64_t ad = tc::kstep_desc(a0, s, CH, w);
-                tc::mma_bf16(dt, ad, tc::kstep_desc(h0, s, Npad, w), idesc,
-                             (l > 0 || s > 0) ? 1u : 0u);
-                tc::mma_bf16(dt, ad, tc::kstep_desc(l0, s, Npad, w), idesc, 1u);
+          for (int c = 0; c < nch; ++c) {
+            if (!((live_mask >> c) & 1u)) continue;
+            if (wait_phase(&load_bar[c], load_bits, c, &s_fail)) {
+              const uint32_t a0 = smem_u32(abuf + (size_t)c * lay.abytes);
+              const uint32_t dt = tbase + (uint32_t)(c * QG);
+              if (FP8) {  // 32 elements per K-step; tiles addressed at half width
+                const uint32_t m0 = h0 + (uint32_t)(QG * a.max_w);
+                for (int s = 0; s < w / 32; ++s) {
+                  const uint64_t ad = tc::kstep_desc(a0, s, CH, w / 2);
+                  tc::mma_e4m3(dt, ad, tc::kstep_desc(h0, s, Npad, w / 2), idesc,
+                               (l > 0 || s > 0) ? 1u : 0u);
+                  tc::mma_e4m3(dt, ad, tc::kstep_desc(m0, s, Npad, w / 2), idesc, 1u);
+                  tc::mma_e4m3(dt, ad, tc::kstep_desc(l0, s, Npad, w / 2), idesc, 1u);
+                }
+              } else {
+                for (int s = 0; s < w / 16; ++s) {
+                  const uint64_t ad = tc::kstep_desc(a0, s, CH, w);
+                  tc::mma_bf16(dt, ad, tc::kstep_desc(h0, s, Npad, w), idesc,
+                               (l > 0 || s > 0) ? 1u : 0u);
+                  tc::mma_bf16(dt, ad, tc::kstep_desc(l0, s, Npad, w), idesc, 1u);
+                }
               }
             }
+            // committed even after a failed wait, so the epilogue's wait ends
+            tc::mma_commit(&mma_bar[c]);
           }
-          // committed even after a failed wait, so the epilogue's wait ends
-          tc::mma_commit(&mma_bar[c]);
         }
-        if (prev >= 0) epilogue(prev);
-        prev = c;
+        __syncwarp();
+        // ... then each chunk that stays live gets its next level's tile as
+        // soon as every epilogue warp has read its accumulator
+        if (has_next)
+          for (int c = 0; c < nch; ++c) {
+            if (!((live_mask >> c) & 1u)) continue;
+            int ok = 1;
+            if (lane == 0) ok = wait_phase(&epi_bar[c], epi_bits, c, &s_fail) ? 1 : 0;
+            tc::fence_after_sync();
+            // lane 0 decides for the warp (s_fail may change under it)
+            const int go = __shfl_sync(0xffffffffu, (ok && chunk_live(c) && !s_fail) ? 1 : 0, 0);
+            if (go) issue_load(c, l + 1);
+          }
+      } else {
+        for (int c = 0; c < nch; ++c)
+          if ((live_mask >> c) & 1u) epilogue(c);
       }
-      if (prev >= 0) epilogue(prev);
+      // the level's accumulators have been read, its B tiles are free and
+      // the next level's tiles are on their way
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
       if (a.collect && tid == 0) s_stat[2] += __popc(live_mask);
       section(2);
       if (s_fail) {
@@ -790,28 +826,30 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         break;
       }
       if (has_next) {
-        // next level's B tiles, tails and thresholds from the prefetch
+        if (epi) {
+          // next level's B tiles, tails and thresholds from the prefetch
 #pragma unroll
-        for (int i = 0; i < PF_CHUNKS; ++i) {
-          const int e = tid + i * NT;
-          if (e < Npad * (w1 / 8)) {
-            const int g = e / (w1 / 8), c8 = e % (w1 / 8);
-            const float f[8] = {pf[2 * i].x, pf[2 * i].y, pf[2 * i].z, pf[2 * i].w,
-                                pf[2 * i + 1].x, pf[2 * i + 1].y, pf[2 * i + 1].z,
-                                pf[2 * i + 1].w};
-            store_b(g, c8, w1, f);
+          for (int i = 0; i < PF_CHUNKS; ++i) {
+            const int e = tid + i * NE;
+            if (e < Npad * (w1 / 8)) {
+              const int g = e / (w1 / 8), c8 = e % (w1 / 8);
+              const float f[8] = {pf[2 * i].x, pf[2 * i].y, pf[2 * i].z, pf[2 * i].w,
+                                  pf[2 * i + 1].x, pf[2 * i + 1].y, pf[2 * i + 1].z,
+                                  pf[2 * i + 1].w};
+              store_b(g, c8, w1, f);
+            }
           }
-        }
-        if (Npad * (w1 / 8) > PF_CHUNKS * NT) build_b(l + 1, PF_CHUNKS);  // wide levels
+          if (Npad * (w1 / 8) > PF_CHUNKS * NE) build_b(l + 1, PF_CHUNKS);  // wide levels
 #pragma unroll
-        for (int u = 0; u < S * CH / NT; ++u) csx[tid + u * NT] = tail_pf[u];
-        if (tid < QG) {
-          if (qid[tid] >= 0 && qk[tid] > 0) {
-            float tau = key_pf == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key_pf), 1.000001f);
-            set_query_terms(tid, fminf(tau, seed_pf), sq_pf);
+          for (int u = 0; u < S * CH / NE; ++u) csx[tid + u * NE] = tail_pf[u];
+          if (tid < QG) {
+            if (qid[tid] >= 0 && qk[tid] > 0) {
+              float tau = key_pf == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key_pf), 1.000001f);
+              set_query_terms(tid, fminf(tau, seed_pf), sq_pf);
+            }
           }
+          fence_proxy_async_smem();
         }
-        fence_proxy_async_smem();
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
@@ -820,6 +858,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     }
     if (s_fail) break;
     if (!completed) continue;
+    if (!epi) continue;  // the rest of the item is the epilogue warps' (named barrier 1)
 
     // Last level done: the k-th smallest upper bound of each query over the
     // whole segment tightens its threshold (at the last level UB ~ LB ~
@@ -855,8 +894,8 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         for (int j = 0; j < 32; ++j) col[j * S * CH] = 0x7f80u;
       }
     }
-    __syncthreads();
-    for (int g = warp; g < G; g += NT / 32) {
+    epi_sync();
+    for (int g = warp; g < G; g += NE / 32) {
       const float t = warp_kth_smallest_bf16(ub16 + g * S * CH, S * CH, qk[g]);
       // k candidates with upper bounds <= t: a threshold for every later
       // work item of the query too
@@ -865,10 +904,10 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         atomicMin(reinterpret_cast<unsigned int*>(a.tau_seed) + qid[g], __float_as_uint(t));
       }
     }
-    __syncthreads();
+    epi_sync();
     if (tid < G && qk[tid] > 0) set_query_terms(tid, qtau[tid], 0.f);
     tc::fence_before_sync();
-    __syncthreads();
+    epi_sync();
     tc::fence_after_sync();
     section(4);
     // survivors of the tightened test join the deferred re-rank list with
@@ -876,7 +915,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     // checked and re-ranked by all warps at once
     for (int c = 0; c < nch; ++c) {
       if (tid == 0) s_nsurv = 0;
-      __syncthreads();
+      epi_sync();
       uint32_t wm = alive[(c * CH + row) * AW + half];
       const bool any_warp = __any_sync(0xffffffffu, wm != 0);
       if (any_warp) {
@@ -895,14 +934,14 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         wm &= ~pruned;
         if (wm) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) vdump[j * NT + tid] = v[j];
+          for (int j = 0; j < 32; ++j) vdump[j * NE + tid] = v[j];
         }
       }
       for (uint32_t m = wm; m; m &= m - 1) {
         const int j = __ffs(m) - 1;
         surv[atomicAdd(&s_nsurv, 1)] = (uint16_t)((row << 6) | (32 * half + j));
       }
-      __syncthreads();
+      epi_sync();
       const int ns = s_nsurv;
       int np = s_npend;
       // all survivors go through the deferred list, a full list being
@@ -910,16 +949,16 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       // accumulators dumped above stay untouched by a flush)
       for (int b0 = 0; b0 < ns;) {
         if (np == Smem::kPend) {
-          __syncthreads();
+          epi_sync();
           rerank_pending(np);
           np = 0;
         }
         const int nb = min(ns - b0, Smem::kPend - np);
-        for (int s = tid; s < nb; s += NT) {
+        for (int s = tid; s < nb; s += NE) {
           const int e = surv[b0 + s], r = e >> 6, g = e & 63;
           const int64_t slot = (ch0 + c) * CH + r;
           const float rx = crx[c * CH + r], exv = cex[c * CH + r];
-          float p = vdump[(g & 31) * NT + r + CH * (g >> 5)];  // all levels
+          float p = vdump[(g & 31) * NE + r + CH * (g >> 5)];  // all levels
           if (FP8) p *= cfr[c * CH + r];
           const float under = FP8 ? 2.f * s_cunder * rx : 0.f;
           const float A = qnq[g] + a.xn2[slot] - 2.f * p;
@@ -937,7 +976,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         b0 += nb;
       }
       tc::fence_before_sync();
-      __syncthreads();
+      epi_sync();
       tc::fence_after_sync();
       if (tid == 0) s_npend = np;
     }
@@ -946,8 +985,8 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     fence_proxy_async_smem();
     section(5);
   }
-  if (!s_fail) {  // the last deferred survivors
-    __syncthreads();
+  if (!s_fail && epi) {  // the last deferred survivors
+    epi_sync();
     rerank_pending(s_npend);
   }
   if (s_fail && tid == 0) atomicOr(a.err, kErrTimeout);
