@@ -65,6 +65,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, int rb) {
   d |= (uint64_t)layout_code(rb) << 61;
   return d;
 }
+// Start-address offset of K-step s (16 bf16 / 32 E4M3 elements) of an R-row
+// tile, in the descriptor's 16-byte units: (s % 4) 32-byte chunks within a
+// 128-byte panel row and (s / 4) panels of R rows.  Added to a descriptor of
+// the tile's base (the field cannot carry: shared addresses are < 2^18).
+__device__ __forceinline__ uint64_t kstep_off(int s, int R) {
+  return (uint64_t)((uint32_t)(s & 3) * 2u + (uint32_t)(s >> 2) * (uint32_t)R * 8u);
+}
 // Descriptor of K-step s (16 elements) of an R-row tile at `base`.
 __device__ __forceinline__ uint64_t kstep_desc(uint32_t base, int s, int R, int w) {
   const int rb = row_bytes(w);

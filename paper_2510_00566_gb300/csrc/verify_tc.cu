@@ -16,13 +16,13 @@
 // the group's queries are one MMA chain: A = level tile of the chunk, B = the
 // queries' level slices split into bf16 hi + lo parts (two MMAs into the same
 // accumulator), accumulated across levels in tensor memory (4 chunks x 64
-// columns = 256 TMEM columns; two CTAs share an SM).  Candidate row t is
-// owned by two epilogue threads (warps w and w + 4 read the same TMEM lane
-// quarter), one per half of the query group: each reads its 32 accumulators
-// with tcgen05.ld and applies the separable form of the margined Eq. 3 test,
-// which costs three FMAs and a compare per (candidate, query) pair.  Dead rows are not re-staged: at deep
-// levels only live rows are copied (a row-granular gather), or the whole
-// slice when most rows live.
+// columns = 256 TMEM columns; two CTAs share an SM).  One warp of the CTA
+// issues the MMA chains and the tile copies; the other eight test: candidate
+// row t is owned by two epilogue threads (warps w and w + 4 read the same
+// TMEM lane quarter), one per half of the query group, each reading its 32
+// accumulators with tcgen05.ld and applying the separable form of the
+// margined Eq. 3 test (three FMAs and a compare per (candidate, query) pair).
+// A chunk whose rows are all dead is neither copied nor multiplied again.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -221,13 +221,14 @@ __global__ void __launch_bounds__(256) pack_fp8_kernel(
 
 // ------------------------------------------------------------------ search
 // One work item = (list, segment of S chunks, group of <= QG queries).  Each
-// chunk owns an A buffer; a chunk that stays live after level l has its
-// level-(l+1) tile staged right after its epilogue, while the other chunks
-// of level l are still being tested.  A level therefore starts with every
-// live chunk's tile resident: one thread issues all their MMAs back to back,
-// and the epilogues follow as the accumulators complete.  The next level's
-// query slices, tail norms and threshold terms are loaded into registers at
-// the start of a level and written to shared memory at its end.
+// chunk owns an A buffer.  Per level the issue warp issues every live
+// chunk's MMA chain as soon as its tile has landed; the epilogue warps test
+// the chunks in order as their accumulators complete and tell the issue warp
+// (an mbarrier per chunk) when all of them have read one, whereupon a chunk
+// that stays live has its next level's tile staged into its buffer while the
+// other chunks are still tested.  The next level's query slices, tail norms
+// and threshold terms are loaded into the epilogue threads' registers at the
+// start of a level and written to shared memory at its end (a CTA barrier).
 constexpr int TMEM_COLS = S * QG;  // 256: two CTAs share an SM's tensor memory
 constexpr int AW = (QG + 31) / 32;  // alive-mask words per candidate row
 constexpr int PF_CHUNKS = 2;        // 16-byte query chunks prefetched per thread
@@ -483,42 +484,20 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     const uint32_t idesc = FP8 ? tc::idesc_e4m3(CH, Npad) : tc::idesc_bf16(CH, Npad);
     const uint8_t* item_src = a.slices + ch0 * (int64_t)CH * d * EB;
 
-    // stage chunk c's level-l tile (live rows only when few rows live); the
-    // issue warp calls it once chunk c's liveness words are complete (no
-    // epilogue warp writes them again before this copy has been consumed)
+    // stage chunk c's level-l tile: one bulk-async copy of the whole tile
+    // (issue warp).  Copying only the 8-row atoms that still hold a live row
+    // saves bytes, but its one copy instruction per atom on the issue warp's
+    // path cost more than the bytes (HBM is far from busy here), so every
+    // live chunk's tile is copied whole.
     auto issue_load = [&](int c, int l) {
       const int m = a.level_off[l], w = a.level_off[l + 1] - m;
-      const int wl = FP8 ? w / 2 : w;  // width of the bf16 tile with the same bytes
       const uint32_t tbytes = (uint32_t)w * CH * EB;
-      const int rb = tc::row_bytes(wl), npan = wl >= 64 ? wl / 64 : 1;
       unsigned char* dst = abuf + (size_t)c * lay.abytes;
       const uint8_t* src = item_src + (int64_t)c * CH * d * EB + (size_t)m * CH * EB;
-      uint32_t atoms = 0;  // 8-row groups holding a live row (lane 0 is the
-      if (lane == 0)       // lane that acquired the liveness words)
-        for (int t = 0; t < 16; ++t)
-          if (((rowlive[c][t >> 2] | rowlive[c][4 + (t >> 2)]) >> ((t & 3) * 8)) & 0xffu)
-            atoms |= 1u << t;
-      atoms = __shfl_sync(0xffffffffu, atoms, 0);
-      const int na = __popc(atoms);
-      if (l == 0 || na * 4 >= 3 * 16) {
-        if (lane == 0) {
-          mbar_arrive_expect_tx(&load_bar[c], tbytes);
-          bulk_g2s(dst, src, tbytes, &load_bar[c]);
-        }
-        if (a.collect && lane == 0) atomicAdd(&s_stat[3], (unsigned long long)tbytes);
-      } else {
-        const uint32_t abytes_row = (uint32_t)(8 * rb);  // one 8-row atom of one panel
-        if (lane == 0) mbar_arrive_expect_tx(&load_bar[c], (uint32_t)na * npan * abytes_row);
-        __syncwarp();
-        for (int t = lane; t < 16 * npan; t += 32) {
-          const int at = t % 16, p = t / 16;
-          if ((atoms >> at) & 1u) {
-            const uint32_t o = (uint32_t)p * CH * 128 + (uint32_t)at * abytes_row;
-            bulk_g2s(dst + o, src + o, abytes_row, &load_bar[c]);
-          }
-        }
-        if (a.collect && lane == 0)
-          atomicAdd(&s_stat[3], (unsigned long long)na * npan * abytes_row);
+      if (lane == 0) {
+        mbar_arrive_expect_tx(&load_bar[c], tbytes);
+        bulk_g2s(dst, src, tbytes, &load_bar[c]);
+        if (a.collect) atomicAdd(&s_stat[3], (unsigned long long)tbytes);
       }
     };
     // B tiles for level l, 8 query elements at a time: bf16 hi / lo parts,
@@ -769,27 +748,32 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         // every live chunk's MMA chain as soon as its tile has landed (the
         // epilogue warps test chunk c while chunk c + 1's MMAs run) ...
         if (lane == 0) {
-          const uint32_t h0 = smem_u32(bhi), l0 = smem_u32(blo);
+          // the level's descriptors; K-step s adds its offset (16-byte
+          // units) to the start-address field
+          const int rb = tc::row_bytes(FP8 ? w / 2 : w);
+          const uint64_t dh = tc::smem_desc(smem_u32(bhi), rb);
+          const uint64_t dl = tc::smem_desc(smem_u32(blo), rb);
+          const uint64_t dm = tc::smem_desc(smem_u32(bhi) + (uint32_t)(QG * a.max_w), rb);
+          (void)dm;
           for (int c = 0; c < nch; ++c) {
             if (!((live_mask >> c) & 1u)) continue;
             if (wait_phase(&load_bar[c], load_bits, c, &s_fail)) {
-              const uint32_t a0 = smem_u32(abuf + (size_t)c * lay.abytes);
               const uint32_t dt = tbase + (uint32_t)(c * QG);
+              const uint64_t da = tc::smem_desc(smem_u32(abuf + (size_t)c * lay.abytes), rb);
               if (FP8) {  // 32 elements per K-step; tiles addressed at half width
-                const uint32_t m0 = h0 + (uint32_t)(QG * a.max_w);
                 for (int s = 0; s < w / 32; ++s) {
-                  const uint64_t ad = tc::kstep_desc(a0, s, CH, w / 2);
-                  tc::mma_e4m3(dt, ad, tc::kstep_desc(h0, s, Npad, w / 2), idesc,
-                               (l > 0 || s > 0) ? 1u : 0u);
-                  tc::mma_e4m3(dt, ad, tc::kstep_desc(m0, s, Npad, w / 2), idesc, 1u);
-                  tc::mma_e4m3(dt, ad, tc::kstep_desc(l0, s, Npad, w / 2), idesc, 1u);
+                  const uint64_t ad = da + tc::kstep_off(s, CH);
+                  const uint64_t bo = tc::kstep_off(s, Npad);
+                  tc::mma_e4m3(dt, ad, dh + bo, idesc, (l > 0 || s > 0) ? 1u : 0u);
+                  tc::mma_e4m3(dt, ad, dm + bo, idesc, 1u);
+                  tc::mma_e4m3(dt, ad, dl + bo, idesc, 1u);
                 }
               } else {
                 for (int s = 0; s < w / 16; ++s) {
-                  const uint64_t ad = tc::kstep_desc(a0, s, CH, w);
-                  tc::mma_bf16(dt, ad, tc::kstep_desc(h0, s, Npad, w), idesc,
-                               (l > 0 || s > 0) ? 1u : 0u);
-                  tc::mma_bf16(dt, ad, tc::kstep_desc(l0, s, Npad, w), idesc, 1u);
+                  const uint64_t ad = da + tc::kstep_off(s, CH);
+                  const uint64_t bo = tc::kstep_off(s, Npad);
+                  tc::mma_bf16(dt, ad, dh + bo, idesc, (l > 0 || s > 0) ? 1u : 0u);
+                  tc::mma_bf16(dt, ad, dl + bo, idesc, 1u);
                 }
               }
             }
@@ -806,8 +790,9 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
             int ok = 1;
             if (lane == 0) ok = wait_phase(&epi_bar[c], epi_bits, c, &s_fail) ? 1 : 0;
             tc::fence_after_sync();
-            // lane 0 decides for the warp (s_fail may change under it)
-            const int go = __shfl_sync(0xffffffffu, (ok && chunk_live(c) && !s_fail) ? 1 : 0, 0);
+            // lane 0 (which acquired the chunk's liveness words) decides for
+            // the warp (s_fail may change under it)
+            const int go = __shfl_sync(0xffffffffu, (ok && !s_fail && chunk_live(c)) ? 1 : 0, 0);
             if (go) issue_load(c, l + 1);
           }
       } else {
