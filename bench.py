@@ -40,10 +40,16 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS, FALLBACK_BF16_TFS = 6800.0, 1900.0
 # DRAM bytes (read + write) of one launch of the dominant kernel, from one
 # ncu capture of that launch at full size (one pass: dram__bytes_read.sum +
-# dram__bytes_write.sum); the command and figures are in profiles/.  An
+# dram__bytes_write.sum), keyed by the full workload description (so a
+# resized run gets none); the command and figures are in profiles/.  An
 # entry is removed whenever its kernel changes, so the line then reports
 # null instead of a stale figure.
-TRAFFIC = {}
+TRAFFIC = {
+    # verify_tc_kernel<BF16>, phase B of the pruned search (whole-tile copies,
+    # issue warp): 20.61 GB read + 0.065 GB written
+    "ivf-10m-d768-bf16: N=10,000,000 d=768 BF16, nlist=4096, nprobe=64, 10,000 queries, "
+    "12x64 levels, k=10": 20.61e9 + 65.44e6,
+}
 PQ_TRAFFIC = {}
 EPSILONS = (1.0, 0.9, 0.8, 0.6, 0.5, 0.4)
 
@@ -557,7 +563,7 @@ def main():
         roof = {"bound": "alu", "kernel": "verify_fp32_kernel (phase B)",
                 "achieved": flops_b / (vb / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "frac": flops_b / (vb / 1e3) / 1e12 / peak,
-                "traffic": TRAFFIC.get(s.name),
+                "traffic": TRAFFIC.get(workload_name(s)),
                 "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
                                f"(max clock of MEASURED_PEAKS.json, {pk_kind})",
                 "flops_per_launch": flops_b, "ms_per_launch": vb,
@@ -572,7 +578,7 @@ def main():
         roof = {"bound": "hbm", "kernel": f"verify_tc_kernel<{'FP8' if eb == 1 else 'BF16'}> "
                                           f"(phase B)",
                 "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": TRAFFIC.get(s.name),
+                "traffic": TRAFFIC.get(workload_name(s)),
                 "peak_source": f"STREAM-style copy of MEASURED_PEAKS.json ({pk_kind})",
                 "bytes_per_launch": live_b,
                 "bytes_definition": "per (query group, chunk, level): candidates live for at "
@@ -782,7 +788,7 @@ def secondary(args, timer, dev, world, check_oracle, pk, pk_kind):
            "roofline": {"bound": "alu", "kernel": "verify_fp32_kernel (phase B)",
                         "achieved": flops_b / (vb / 1e3) / 1e12, "peak": peak,
                         "unit": "TFLOP/s", "frac": flops_b / (vb / 1e3) / 1e12 / peak,
-                        "traffic": TRAFFIC.get(s.name),
+                        "traffic": TRAFFIC.get(workload_name(s)),
                         "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
                                        f"({pk_kind} max clock)",
                         "ms_per_launch": vb, "phase_a_ms": va},

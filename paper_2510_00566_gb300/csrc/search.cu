@@ -352,13 +352,14 @@ __global__ void inv_emit_kernel(int ph, const int* __restrict__ cnt, int nlist,
 // Per query: distances to the first max(4k, 64) (at most 256) members of its
 // nearest list; the k-th smallest is an upper bound on d_k and seeds the
 // threshold before any tile is verified.  Algorithm 1 also fills its heap
-// with k candidates before pruning anything: the seeds whose bound is at
-// most that k-th one (at least k of them) enter the top-k with their exact
-// distances, computed by the re-ranking's own routine on the same rows, so a
-// later re-rank of the same candidate yields the same key and is kept once.
-// With exact pruning this changes no result; with the epsilon-relaxed bound
-// of Eq. 4, which can prune every candidate of a query, the answer still
-// holds the best k seeds, as Algorithm 1's heap would.
+// with k candidates before pruning anything; that matters once the
+// epsilon-relaxed bound of Eq. 4 can prune every candidate of a query, so
+// an epsilon-relaxed search (topk != nullptr) also enters the seeds whose
+// bound is at most that k-th one (at least k of them) into the top-k with
+// their exact distances, computed by the re-ranking's own routine on the
+// same rows (a later re-rank of the same candidate yields the same key and
+// is kept once).  With exact pruning they would change no result, so exact
+// searches skip those k exact distances.
 //
 // The query row sits in shared memory; a warp loads a whole row (up to 1024
 // dims) in one batch and sums fl(q_j - x_j)^2 by FMA into four interleaved
@@ -456,6 +457,7 @@ __global__ void __launch_bounds__(kSeedWarps * 32) seed_tau_kernel(
     }
   }
   __syncthreads();
+  if (!topk) return;
   const float t = s_t;
   for (int i = warp; i < ns; i += kSeedWarps) {
     if (!(dist[i] <= t)) continue;
@@ -569,6 +571,7 @@ __global__ void __launch_bounds__(kSeedWarps * 32) seed_group_kernel(
       s_t[g] = t;
     }
   }
+  if (!topk) return;
   __syncthreads();
   // the seeds within each query's k-th bound enter its top-k (a warp each)
   for (int e = warp; e < G * kSeedMax; e += kSeedWarps) {
@@ -1715,12 +1718,12 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
       seed_group_kernel<<<(unsigned)(capA * nsub), kSeedWarps * 32, gsm, st>>>(
           queries, d, itA, tot + 1, capA, nsub, bucket, I.chunk_off_d.as<int64_t>(),
           I.list_size_d.as<int32_t>(), I.chunk, I.rows.as<float>(), kq, seed_slack, tau_seed,
-          I.ids.as<int32_t>(), topk, k_max);
+          I.ids.as<int32_t>(), eps < 1.f ? topk : nullptr, k_max);
     } else {
       seed_tau_kernel<<<(unsigned)nq, kSeedWarps * 32, (size_t)d * 4, st>>>(
           queries, d, probes, stride, I.chunk_off_d.as<int64_t>(), I.list_size_d.as<int32_t>(),
           I.chunk, I.rows.as<float>(), kq, one_pass ? nullptr : bucket, seed_slack, tau_seed,
-          I.ids.as<int32_t>(), topk, k_max);
+          I.ids.as<int32_t>(), eps < 1.f ? topk : nullptr, k_max);
     }
     PANO_CUDA(cudaGetLastError());
     // a4-a10
