@@ -250,7 +250,7 @@ struct Smem {
     bbytes = (uint32_t)(QG * max_w * 2 + 1023) & ~1023u;
     off_b_hi = S * abytes;
     off_b_lo = off_b_hi + bbytes;
-    off_alive = off_b_lo + bbytes;                   // [S][CH][AW] u32
+    off_alive = off_b_lo + bbytes;                   // [S][AW][CH] u32 (a warp's rows: consecutive words)
     off_cand = off_alive + S * CH * AW * 4;  // 6 x [S][CH] (Hx, rx, ex, id, sx, FP8 factor)
     off_q = off_cand + 6 * S * CH * 4;       // [QG] float4 + 6 x [QG]
     total = off_q + 10 * QG * 4;
@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       const uint32_t gm = half ? gm1 : gm0;
       for (int c = 0; c < S; ++c) {
         const bool v = c < nch && cid[c * CH + row] >= 0;
-        alive[(c * CH + row) * AW + half] = v ? gm : 0u;
+        alive[(c * AW + half) * CH + row] = v ? gm : 0u;
         const unsigned bal = __ballot_sync(0xffffffffu, v && gm);
         if (lane == 0) rowlive[c][warp] = bal;
       }
@@ -689,19 +689,22 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       auto epilogue = [&](int c) {
         const bool ok = wait_phase(&mma_bar[c], mma_bits, c, &s_fail);
         tc::fence_after_sync();
-        uint32_t wm = alive[(c * CH + row) * AW + half];
-        const bool any_warp = __any_sync(0xffffffffu, wm != 0) && __all_sync(0xffffffffu, ok);
+        uint32_t wm = alive[(c * AW + half) * CH + row];
+        const bool any_live = __any_sync(0xffffffffu, wm != 0);
+        if (a.collect && any_live) {
+          const unsigned np = __reduce_add_sync(0xffffffffu, (unsigned)__popc(wm));
+          if (lane == 0) {
+            atomicAdd(&s_stat[0], (unsigned long long)np);
+            atomicAdd(&s_stat[1], (unsigned long long)np * w);
+          }
+        }
+        // a level without a test (the plain scan's levels before the last)
+        // changes no liveness: its accumulator is not read
+        const bool any_warp = test && any_live && __all_sync(0xffffffffu, ok);
         if (any_warp) {
           const float sx = csx[c * CH + row], rx = crx[c * CH + row], exv = cex[c * CH + row];
           const float Hx = cHx[c * CH + row];
           const float fr = FP8 ? cfr[c * CH + row] : 1.f;
-          if (a.collect) {
-            const unsigned np = __reduce_add_sync(0xffffffffu, (unsigned)__popc(wm));
-            if (lane == 0) {
-              atomicAdd(&s_stat[0], (unsigned long long)np);
-              atomicAdd(&s_stat[1], (unsigned long long)np * w);
-            }
-          }
           if (Npad <= 16) {  // a group of <= 16 queries: 16 columns (half 0 only)
             float v[16];
             tc::tmem_ld16(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
@@ -733,7 +736,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
               wm &= ~pruned;
             }
           }
-          alive[(c * CH + row) * AW + half] = wm;
+          alive[(c * AW + half) * CH + row] = wm;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, wm != 0);
         if (lane == 0) rowlive[c][warp] = bal;
@@ -852,7 +855,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     // bounds) so that all S x CH of them fit next to each other.
     for (int c = 0; c < S; ++c) {
       uint32_t wm = 0;
-      if (c < nch && chunk_live(c)) wm = alive[(c * CH + row) * AW + half];
+      if (c < nch && chunk_live(c)) wm = alive[(c * AW + half) * CH + row];
       const bool any_warp = __any_sync(0xffffffffu, wm != 0);
       uint16_t* col = ub16 + (32 * half) * S * CH + c * CH + row;  // stride S*CH per query
       if (any_warp) {
@@ -901,7 +904,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     for (int c = 0; c < nch; ++c) {
       if (tid == 0) s_nsurv = 0;
       epi_sync();
-      uint32_t wm = alive[(c * CH + row) * AW + half];
+      uint32_t wm = alive[(c * AW + half) * CH + row];
       const bool any_warp = __any_sync(0xffffffffu, wm != 0);
       if (any_warp) {
         const float rx = crx[c * CH + row], exv = cex[c * CH + row], Hx = cHx[c * CH + row];
