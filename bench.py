@@ -380,7 +380,7 @@ class Timer:
         return t.item() / steps, extra, c
 
 
-def e2e_time(idx, Q, npa, ka, k, steps, timer):
+def e2e_time(idx, Q, npa, ka, k, steps, timer, test_every=1):
     """Per-step time of the public API call with HOST buffers: pinned H2D of
     the queries (and per-query nprobe / k), search, D2H of ids and
     distances, all inside the events."""
@@ -400,7 +400,7 @@ def e2e_time(idx, Q, npa, ka, k, steps, timer):
         qd.copy_(qh, non_blocking=True)
         for h, dv in par:
             dv.copy_(h, non_blocking=True)
-        a, b = idx.search(qd, npa, ka, k_max=k)
+        a, b = idx.search(qd, npa, ka, k_max=k, test_every=test_every)
         ids_h.copy_(a, non_blocking=True)
         d_h.copy_(b, non_blocking=True)
 
@@ -461,6 +461,7 @@ def main():
     k = int(w.k.max()) if not isinstance(s.k, int) else s.k  # k_max
     npmax = int(w.nprobe.max())
     widths, tune = None, None
+    test_every = 1  # the bound tested at every level (Algorithm 1) unless tuned
     if per_query:
         # storage precision and level split chosen by the autotuner: median
         # search time of each (precision, split) pair on a query sample,
@@ -472,11 +473,14 @@ def main():
             t, X, qs, s.nlist, 64, 10,
             precisions=(pano.PANO_FP32, pano.PANO_BF16, pano.PANO_FP8), repeats=2)
         widths, prec = trials[best]["widths"], trials[best]["precision"]
+        test_every = max(1, trials[best]["test_every"])
         s = dataclasses.replace(s, precision=names[prec], n_levels=len(widths))
         tune = {"trials": [{"precision": names[tr["precision"]], "widths": tr["widths"],
-                            "ms": tr["ms"] if math.isfinite(tr["ms"]) else None}
+                            "ms": tr["ms"] if math.isfinite(tr["ms"]) else None,
+                            "test_every": tr["test_every"]}
                            for tr in trials],
-                "chosen": {"precision": names[prec], "widths": widths},
+                "chosen": {"precision": names[prec], "widths": widths,
+                           "test_every": test_every},
                 "sample": f"{len(qs)} queries, nprobe 64, k 10", "seconds": time.time() - t0}
     b0 = time.time()
     idx = pano.panorama_build_ivf(t, X, nlist=s.nlist, n_levels=s.n_levels, seed=3000 + s.cfg,
@@ -486,11 +490,11 @@ def main():
     C = idx.centroids()
     sizes = np.bincount(idx.assignment(), minlength=s.nlist)
     list_cv = float(sizes.std() / sizes.mean())  # balance of the k-means lists
-    plan = pano.Plan(idx, Q, npa, ka, k_max=k) if per_query else None
+    plan = pano.Plan(idx, Q, npa, ka, k_max=k, test_every=test_every) if per_query else None
 
     # counters (one instrumented search, outside the timed region)
-    out = idx.search(Q, npa, ka, k_max=k)
-    idx.search(Q, npa, ka, k_max=k, collect_stats=True)
+    out = idx.search(Q, npa, ka, k_max=k, test_every=test_every)
+    idx.search(Q, npa, ka, k_max=k, collect_stats=True, test_every=test_every)
     st = pano.last_stats().as_dict()
     pairs = st["pairs"]
 
@@ -499,13 +503,14 @@ def main():
     def headline():
         if plan is not None:
             return plan.launch(stream)
-        return idx.search(Q, npa, ka, k_max=k, collect_timing=True)
+        return idx.search(Q, npa, ka, k_max=k, collect_timing=True, test_every=test_every)
 
     stage_of = (lambda: list(pano.last_stats().stage_ms)) if plan is None else None
     ms_per_step, stages, clocks = timer.run(headline, args.steps, args.warmup, clocks=True,
                                            after=stage_of)
     if plan is not None:  # stage times from separate, instrumented searches
-        _, stages, _ = timer.run(lambda: idx.search(Q, npa, ka, k_max=k, collect_timing=True),
+        _, stages, _ = timer.run(lambda: idx.search(Q, npa, ka, k_max=k, collect_timing=True,
+                                                    test_every=test_every),
                                  3, 1, after=lambda: list(pano.last_stats().stage_ms))
     stage = {n: float(np.median([v[i] for v in stages])) for i, n in
              enumerate(("transform", "probe", "inversion", "verify_a", "verify_b", "decode"))}
@@ -516,9 +521,24 @@ def main():
     # the last level; for BF16/FP8 storage the plain tensor-core scan)
     scan_ms, _, _ = timer.run(lambda: idx.search(Q, npa, ka, k_max=k, mode=1),
                               args.scan_steps, 1)
+    # the bound-test schedule (which levels test Eq. 3): every level as in
+    # Algorithm 1, every other, every fourth, the last level only
+    schedule_sweep = None
+    if not per_query and not args.no_eps:
+        schedule_sweep = []
+        for te in sorted({1, 2, 4, s.n_levels}):
+            mst, _, _ = timer.run(lambda: idx.search(Q, npa, ka, k_max=k, test_every=te),
+                                  max(3, args.scan_steps), 1)
+            idx.search(Q, npa, ka, k_max=k, test_every=te, collect_stats=True)
+            sts = pano.last_stats().as_dict()
+            schedule_sweep.append({"test_every": te, "ms_per_step": mst,
+                                   "qps": nq * world / (mst / 1e3),
+                                   "tile_levels": sts["tile_levels"],
+                                   "dims_scanned_frac": sts["dims_scanned"] / max(1, pairs * s.d),
+                                   "reranked": sts["reranked"]})
     e2e = None
     if not args.no_e2e:
-        e2e_ms, h2d, d2h = e2e_time(idx, Q, npa, ka, k, args.steps, timer)
+        e2e_ms, h2d, d2h = e2e_time(idx, Q, npa, ka, k, args.steps, timer, test_every)
         e2e = {"value": pairs * world / (e2e_ms / 1e3), "unit": "candidates/s",
                "qps": nq * world / (e2e_ms / 1e3), "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
@@ -680,6 +700,8 @@ def main():
         "e2e": e2e,
         "parity": parity,
         "epsilon_sweep": eps_sweep,
+        "test_schedule_sweep": schedule_sweep,
+        "test_every": test_every,
         "fp8_pruned": fp8,
         "fp32": fp32,
         "speedup_vs_plain_fp32_scan": (fp32["plain_scan"]["ms_per_step"] / ms_per_step

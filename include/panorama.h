@@ -102,6 +102,13 @@ typedef struct {
                              LB; in (0, 1): Eq. 4's relaxed LB_eps = A -
                              2 eps C prunes more and may lose true
                              neighbours (returned distances stay exact)    */
+  int32_t test_every;     /* levels whose bound is tested (mode 0): level l
+                             when (l + 1) % test_every == 0, and always the
+                             last level.  0 or 1 (default) = every level,
+                             as Algorithm 1; larger values test less often,
+                             which can be faster where the work is per tile
+                             and tiles seldom die (panorama_autotune times
+                             it).  The result is exact whatever the value. */
 } pano_search_opts;
 
 /* Counters of the most recent search through this index from this thread
@@ -318,6 +325,13 @@ int panorama_plan_create(const pano_index* idx, const float* queries, int64_t nq
                          const int32_t* k, int32_t k_scalar, int32_t k_max,
                          int64_t* out_ids, float* out_dists, int32_t mode,
                          pano_plan** out);
+/* The same with every search option (mode, test_every, epsilon, ...) taken
+ * from opts (NULL = defaults); synchronize and collect_* are ignored. */
+int panorama_plan_create_ex(const pano_index* idx, const float* queries, int64_t nq,
+                            const int32_t* nprobe, int32_t nprobe_scalar,
+                            const int32_t* k, int32_t k_scalar, int32_t k_max,
+                            int64_t* out_ids, float* out_dists, const pano_search_opts* opts,
+                            pano_plan** out);
 int panorama_plan_launch(pano_plan* plan, void* stream);
 void panorama_plan_free(pano_plan* plan);
 
@@ -356,17 +370,19 @@ int panorama_autotune_levels(const pano_transform* t, const float* X, int64_t n,
  *   FP32 256), the last level taking the rest;
  *   trials (caller-owned, max_trials entries): one per (precision, split)
  *   pair in precision-major order, with its median search time over
- *   `repeats` timed searches (after one warm-up) or +inf when the pair
- *   cannot be built or staged; *n_trials and *best (index of the fastest)
- *   are written.  k-means runs once; every candidate is built with its
+ *   `repeats` timed searches (after one warm-up) at the fastest of the
+ *   bound-test schedules test_every = 1, 2, 4 and n_levels (every level,
+ *   every other, every fourth, the last only), and that schedule, or +inf
+ *   when the pair cannot be built or staged; *n_trials and *best (index of
+ *   the fastest) are written.  k-means runs once; every candidate is built with its
  *   centroids.  Errors: PANO_EINVAL for bad arguments, more pairs than
  *   max_trials, or no searchable pair; build / CUDA errors otherwise. */
 typedef struct {
   int32_t precision;
   int32_t n_levels;
   int32_t widths[64];
-  float ms;
-  int32_t pad_;
+  float ms;          /* at the fastest of the test schedules tried        */
+  int32_t test_every; /* that schedule (pano_search_opts.test_every)      */
 } pano_autotune_trial;
 int panorama_autotune(const pano_transform* t, const float* X, int64_t n,
                       const float* queries, int64_t nq, int32_t nlist, int32_t nprobe,

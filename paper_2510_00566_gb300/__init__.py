@@ -54,7 +54,8 @@ class SearchOpts(ctypes.Structure):
                 ("query_group", ctypes.c_int32),
                 ("collect_timing", ctypes.c_int32),
                 ("single_phase", ctypes.c_int32),
-                ("epsilon", ctypes.c_float)]
+                ("epsilon", ctypes.c_float),
+                ("test_every", ctypes.c_int32)]
 
 
 class SearchStats(ctypes.Structure):
@@ -148,6 +149,8 @@ SIGNATURES = {
     "panorama_debug_tc_gemm_fp8": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _P]),
     "panorama_plan_create": (ctypes.c_int, [_P, _P, _I64, _P, _I32, _P, _I32, _I32,
                                             _P, _P, _I32, _P]),
+    "panorama_plan_create_ex": (ctypes.c_int, [_P, _P, _I64, _P, _I32, _P, _I32, _I32,
+                                               _P, _P, _P, _P]),
     "panorama_plan_launch": (ctypes.c_int, [_P, _P]),
     "panorama_plan_free": (None, [_P]),
     "panorama_server_create": (ctypes.c_int, [_P, _P, _P]),
@@ -249,13 +252,15 @@ def panorama_build_ivf(t: "Transform", X, nlist: int, n_levels=8,
 def panorama_search_ex(idx: "Index", queries, nprobe, k, k_max=None,
                        mode=0, collect_stats=False, synchronize=True,
                        stream=None, out=None, collect_timing=False,
-                       single_phase=None, epsilon=1.0):
+                       single_phase=None, epsilon=1.0, test_every=1):
     """Returns (ids int64 [nq, k_max], dists float32 [nq, k_max]) on the GPU.
 
     nprobe / k: python ints, or CUDA int32 tensors with one value per query.
     single_phase: None = the library chooses, True = one pass, False = each
     query's nearest list first.  epsilon < 1: Eq. 4's relaxed pruning
-    (approximate; exact distances for what is returned).
+    (approximate; exact distances for what is returned).  test_every: the
+    bound is tested at level l when (l + 1) % test_every == 0 and at the
+    last level (1 = every level; the result is exact either way).
     """
     import torch
     q = queries.contiguous()
@@ -286,7 +291,7 @@ def panorama_search_ex(idx: "Index", queries, nprobe, k, k_max=None,
                       collect_stats=1 if collect_stats else 0,
                       collect_timing=1 if collect_timing else 0,
                       single_phase=0 if single_phase is None else (1 if single_phase else 2),
-                      epsilon=float(epsilon))
+                      epsilon=float(epsilon), test_every=int(test_every))
     _check(lib().panorama_search_ex(idx.handle, q.data_ptr(), nq, np_ptr,
                                     np_scalar, k_ptr, k_scalar, k_max,
                                     ids.data_ptr(), dists.data_ptr(),
@@ -515,7 +520,8 @@ class Plan:
     nprobe / k when they are tensors) in place, call ``launch()``, then read
     ``ids`` / ``dists``."""
 
-    def __init__(self, idx: "Index", queries, nprobe, k, k_max=None, mode=0):
+    def __init__(self, idx: "Index", queries, nprobe, k, k_max=None, mode=0, test_every=1,
+                 epsilon=1.0):
         import torch
         self.idx = idx
         self.queries = queries
@@ -538,10 +544,11 @@ class Plan:
         self.ids = torch.empty((nq, k_max), dtype=torch.int64, device=queries.device)
         self.dists = torch.empty((nq, k_max), dtype=torch.float32, device=queries.device)
         out = ctypes.c_void_p()
-        _check(lib().panorama_plan_create(idx.handle, queries.data_ptr(), nq, np_ptr,
-                                          np_scalar, k_ptr, k_scalar, k_max,
-                                          self.ids.data_ptr(), self.dists.data_ptr(),
-                                          mode, ctypes.byref(out)))
+        opts = SearchOpts(mode=mode, test_every=int(test_every), epsilon=float(epsilon))
+        _check(lib().panorama_plan_create_ex(idx.handle, queries.data_ptr(), nq, np_ptr,
+                                             np_scalar, k_ptr, k_scalar, k_max,
+                                             self.ids.data_ptr(), self.dists.data_ptr(),
+                                             ctypes.byref(opts), ctypes.byref(out)))
         self.handle = out.value
 
     def launch(self, stream=None):
@@ -579,14 +586,15 @@ def panorama_autotune_levels(t: "Transform", X, queries, nlist, nprobe, k,
 class AutotuneTrial(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("n_levels", ctypes.c_int32),
                 ("widths", ctypes.c_int32 * 64), ("ms", ctypes.c_float),
-                ("pad_", ctypes.c_int32)]
+                ("test_every", ctypes.c_int32)]
 
 
 def panorama_autotune(t: "Transform", X, queries, nlist, nprobe, k,
                       precisions=(PANO_FP32, PANO_BF16, PANO_FP8), candidates=None,
                       repeats=3, max_trials=64, stream=None):
-    """Fastest (precision, level split) on a query sample.  Returns (best
-    index, trials) with trials a list of dicts (precision, widths, ms)."""
+    """Fastest (precision, level split, bound-test schedule) on a query
+    sample.  Returns (best index, trials) with trials a list of dicts
+    (precision, widths, ms, test_every: the fastest schedule of the split)."""
     import numpy as np
     keep, ptr = _host_f32(X)
     n = keep.shape[0]
@@ -608,7 +616,8 @@ def panorama_autotune(t: "Transform", X, queries, nlist, nprobe, k,
                                    trials, max_trials, ctypes.byref(n_tr), ctypes.byref(best),
                                    _stream_ptr(stream)))
     out = [{"precision": trials[i].precision,
-            "widths": list(trials[i].widths[:trials[i].n_levels]), "ms": trials[i].ms}
+            "widths": list(trials[i].widths[:trials[i].n_levels]), "ms": trials[i].ms,
+            "test_every": trials[i].test_every}
            for i in range(n_tr.value)]
     return best.value, out
 

@@ -34,6 +34,16 @@ int panorama_plan_create(const pano_index* idx, const float* queries, int64_t nq
                          const int32_t* nprobe, int32_t nprobe_scalar, const int32_t* k,
                          int32_t k_scalar, int32_t k_max, int64_t* out_ids, float* out_dists,
                          int32_t mode, pano_plan** out) {
+  pano_search_opts o{};
+  o.mode = mode;
+  return panorama_plan_create_ex(idx, queries, nq, nprobe, nprobe_scalar, k, k_scalar, k_max,
+                                 out_ids, out_dists, &o, out);
+}
+
+int panorama_plan_create_ex(const pano_index* idx, const float* queries, int64_t nq,
+                            const int32_t* nprobe, int32_t nprobe_scalar, const int32_t* k,
+                            int32_t k_scalar, int32_t k_max, int64_t* out_ids, float* out_dists,
+                            const pano_search_opts* opts, pano_plan** out) {
   clear_error();
   PANO_CHECK(idx && out && nq >= 1, PANO_EINVAL, "bad arguments to plan_create");
   auto plan = std::make_unique<pano_plan>();
@@ -42,7 +52,9 @@ int panorama_plan_create(const pano_index* idx, const float* queries, int64_t nq
   PANO_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   // kernel attributes and occupancy are settled by one eager search first
   pano_search_opts o{};
-  o.mode = mode;
+  if (opts) o = *opts;
+  o.collect_stats = 0;
+  o.collect_timing = 0;
   o.synchronize = 1;
   int rc = search(idx, queries, nq, nprobe, nprobe_scalar, k, k_scalar, k_max, out_ids,
                   out_dists, cs, &o);
@@ -256,25 +268,44 @@ int panorama_autotune(const pano_transform* t, const float* X, int64_t n, const 
     pano_index* idx = nullptr;
     if (build_ivf(t, X, n, nlist, &o, st, &idx)) continue;  // not buildable: +inf
     if (cent.empty()) cent = idx->centroids;
-    std::vector<float> times;
-    for (int r = 0; r <= repeats && rc == PANO_OK; ++r) {
-      cudaEventRecord(e0, st);
-      rc = search(idx, queries, nq, nullptr, nprobe, nullptr, k, k, ids, dists, st, nullptr);
-      cudaEventRecord(e1, st);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (r > 0) times.push_back(ms);  // the first search warms up
+    // the bound-test schedules: every level (Algorithm 1), every other,
+    // every fourth, the last level only
+    std::vector<uint64_t> seen;  // tested-level masks already timed
+    for (int te : {1, 2, 4, (int)tr.n_levels}) {
+      uint64_t mask = 1ull << (tr.n_levels - 1);
+      for (int l = 0; l < tr.n_levels; ++l)
+        if ((l + 1) % te == 0) mask |= 1ull << l;
+      if (std::find(seen.begin(), seen.end(), mask) != seen.end()) continue;
+      seen.push_back(mask);
+      pano_search_opts so{};
+      so.synchronize = 1;
+      so.test_every = te;
+      std::vector<float> times;
+      for (int r = 0; r <= repeats && rc == PANO_OK; ++r) {
+        cudaEventRecord(e0, st);
+        rc = search(idx, queries, nq, nullptr, nprobe, nullptr, k, k, ids, dists, st, &so);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) times.push_back(ms);  // the first search warms up
+      }
+      if (rc) break;
+      std::sort(times.begin(), times.end());
+      if (times[times.size() / 2] < tr.ms) {
+        tr.ms = times[times.size() / 2];
+        tr.test_every = te;
+      }
     }
     delete idx;
     if (rc == PANO_EINVAL) {  // a split the search cannot stage: not a candidate
       rc = PANO_OK;
       clear_error();
+      tr.ms = INFINITY;
+      tr.test_every = 0;
       continue;
     }
     if (rc) break;
-    std::sort(times.begin(), times.end());
-    tr.ms = times[times.size() / 2];
     if (tr.ms < best_ms) {
       best_ms = tr.ms;
       *best = (int32_t)c;

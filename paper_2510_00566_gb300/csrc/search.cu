@@ -607,6 +607,7 @@ struct VerifyArgs {
   float lb_scale;  // (1 - 8u) / (1 + eta): lower bound in T~ space -> original
   float ub_scale;  // (1 + 8u) / (1 - eta): upper bound in T~ space -> original
   int prune;       // 0: plain scan (prune only after the last level)
+  int test_every;  // with prune: test at level l when (l + 1) % test_every == 0 (and the last)
   int collect;
   int phase;        // 0: phase A (its dims are also counted apart)
   float eps;        // Eq. 4: the query tail term of the pruning test is scaled by eps
@@ -1164,7 +1165,7 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
             }
           }
           // bound update and pruning (Eq. 3 with rounding margins)
-          if (a.prune || l == L - 1) {
+          if ((a.prune && (l + 1) % a.test_every == 0) || l == L - 1) {
             const float4 sx = *reinterpret_cast<const float4*>(xb + w * CH);
             const float sxv[4] = {sx.x, sx.y, sx.z, sx.w};
             float4 ct[4];
@@ -1579,6 +1580,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
   const int mode = opts ? opts->mode : 0;
   // Eq. 4: LB_eps = A - 2 eps C (0 and 1 mean the exact Eq. 3)
   const float eps = (opts && opts->epsilon > 0.f && opts->epsilon < 1.f) ? opts->epsilon : 1.f;
+  const int test_every = (opts && opts->test_every > 1) ? opts->test_every : 1;
   const bool timing = opts ? opts->collect_timing != 0 : false;
   const bool sync = (opts ? opts->synchronize != 0 : true) || timing;
   const bool collect = opts ? opts->collect_stats != 0 : false;
@@ -1769,6 +1771,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
       ta.lb_scale = (float)((1.0 - 8.0 * kU32) / (1.0 + I.eta));
       ta.ub_scale = (float)((1.0 + 8.0 * kU32) / (1.0 - I.eta) * (1.0 + 1e-7));
       ta.prune = mode == 0 ? 1 : 0;
+      ta.test_every = test_every;
       ta.eps = eps;
       ta.collect = collect ? 1 : 0;
       for (int l = 0; l <= L; ++l) ta.level_off[l] = I.offs[l];
@@ -1818,6 +1821,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     }
     va.ub_scale = (float)((1.0 + 8.0 * kU32) / (1.0 - I.eta) * (1.0 + 1e-7));
     va.prune = mode == 0 ? 1 : 0;
+    va.test_every = test_every;
     va.eps = eps;
     va.collect = collect ? 1 : 0;
     for (int l = 0; l <= L; ++l) va.level_off[l] = I.offs[l];

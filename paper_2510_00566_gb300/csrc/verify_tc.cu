@@ -630,7 +630,9 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     section(0);
     for (int l = 0; l < L; ++l) {
       const int w = a.level_off[l + 1] - a.level_off[l];
-      const bool test = a.prune || l == L - 1;
+      // the bound is tested at the levels of the schedule (every level by
+      // default, as Algorithm 1) and always at the last
+      const bool test = (a.prune && (l + 1) % a.test_every == 0) || l == L - 1;
       const bool has_next = l + 1 < L;
       uint32_t live_mask = 0;
       for (int c = 0; c < nch; ++c)

@@ -37,6 +37,7 @@ struct VerifyTCArgs {
   float lb_scale;  // (1 - 8u) / (1 + eta)
   float ub_scale;  // (1 + 8u) / (1 - eta)
   int prune;
+  int test_every;  // the bound is tested at level l when (l + 1) % test_every == 0 (and the last)
   int collect;
   int phase;  // 0: phase A (its dims are also counted apart)
   float eps;  // Eq. 4: the query tail term of the pruning test is scaled by eps

@@ -104,3 +104,40 @@ def test_bf16_rejects_unsupported_widths():
     with pytest.raises(pano.LibraryError):
         pano.panorama_build_ivf(t, w.X.to(DEV), nlist=1, level_widths=[48, 80],
                                 precision=pano.PANO_BF16)
+
+
+@pytest.mark.parametrize("precision", [pano.PANO_BF16, pano.PANO_FP32])
+def test_test_schedule_keeps_the_exact_answer(precision):
+    """The bound-test schedule (test_every: which levels test Eq. 3, the last
+    always) changes the work, never the answer: every schedule returns the
+    oracle's exact top-k, the same ids and distances bit for bit, and no
+    schedule reads more coordinates than testing only the last level."""
+    s = synth.scaled(3, n=20_000, n_queries=80, nlist=16)
+    w = synth.generate(s)
+    X, Q = w.X.numpy(), w.Q.numpy()
+    C = synth.initial_centroids(w.X, 16, seed=3013).numpy()
+    t = pano.panorama_fit_transform(X, n_levels=12)
+    idx = pano.panorama_build_ivf(t, w.X.to(DEV), nlist=16, level_widths=[64] * 12,
+                                  precision=precision, centroids=C)
+    q = torch.from_numpy(Q).to(DEV)
+    lists, _ = oracle.assign(X, C)
+    ref = oracle.ivf_search(X, Q, C, 4, 10, lists_of_vector=lists)
+    keep = ref["probe_gap"] >= 1e-6
+    G = gamma_of(lists, ref["probes"])
+    first = None
+    dims = []
+    for te in (1, 2, 5, 12, 100):
+        ids, d = idx.search(q, 4, 10, test_every=te, collect_stats=True)
+        dims.append(pano.last_stats().dims_scanned)
+        ids, d = ids.cpu().numpy(), d.cpu().numpy()
+        check_topk(X, Q[keep], ids[keep], d[keep], ref["ids"][keep], ref["dists"][keep], 10,
+                   gamma_rows=[G[i] for i in np.nonzero(keep)[0]])
+        if first is None:
+            first = (ids, d)
+        else:
+            assert np.array_equal(first[0], ids) and np.array_equal(first[1], d), te
+    # testing only at the last level reads every coordinate of every pair
+    # (the same for any test_every >= L); any schedule reads at most that
+    pairs = pano.last_stats().pairs
+    assert dims[3] == dims[4] == pairs * 768
+    assert all(x <= dims[3] for x in dims)
