@@ -769,7 +769,8 @@ def secondary(args, timer, dev, world, check_oracle, pk, pk_kind):
     """The 960-d FP32 workload (N = 1M from a 1,024-cluster mixture, nlist
     1024, nprobe 32, 10k queries, 16 x 60 levels, k = 10): pruned FP32
     search, the plain FP32 scan, the FP32 verify roofline, a parity sample,
-    the epsilon sweep of Eq. 4, point-centric refine and IVFPQ."""
+    the same data in BF16 storage against its plain tensor-core scan, the
+    epsilon sweep of Eq. 4, point-centric refine and IVFPQ."""
     import numpy as np
     import torch
     import paper_2510_00566_gb300 as pano
@@ -824,6 +825,28 @@ def secondary(args, timer, dev, world, check_oracle, pk, pk_kind):
         gp = pano.panorama_probe(idx, Q[torch.from_numpy(prow).to(dev)], s.nprobe).cpu().numpy()
         res["parity"] = parity_report(osd, prow, s.nprobe, k, out[0].cpu().numpy()[prow],
                                       out[1].cpu().numpy()[prow], gp, idx.assignment())
+    # the same data in BF16 storage (15 levels of 64, same transform basis and
+    # centroids): pruned search and the plain tensor-core scan
+    if not args.no_fp8:
+        ixb = pano.panorama_build_ivf(t, X, nlist=s.nlist, level_widths=[64] * (s.d // 64),
+                                      precision=pano.PANO_BF16, centroids=C)
+        ob = ixb.search(Q, s.nprobe, k)
+        msb, _, _ = timer.run(lambda: ixb.search(Q, s.nprobe, k), args.steps, args.warmup)
+        scb, _, _ = timer.run(lambda: ixb.search(Q, s.nprobe, k, mode=1), args.scan_steps, 1)
+        ixb.search(Q, s.nprobe, k, collect_stats=True)
+        stb = pano.last_stats().as_dict()
+        res["bf16_pruned"] = {
+            "storage": "bf16", "levels": f"{s.d // 64}x64", "ms_per_step": msb,
+            "qps": nq * world / (msb / 1e3), "value": stb["pairs"] * world / (msb / 1e3),
+            "dims_scanned_frac": stb["dims_scanned"] / max(1, stb["pairs"] * s.d),
+            "plain_tc_scan": {"ms_per_step": scb, "speedup_of_pruned": scb / msb},
+            "speedup_vs_plain_fp32_scan": scan_ms / msb}
+        if osd is not None:
+            gp = pano.panorama_probe(ixb, Q[torch.from_numpy(prow).to(dev)], s.nprobe).cpu().numpy()
+            res["bf16_pruned"]["parity"] = parity_report(
+                osd, prow, s.nprobe, k, ob[0].cpu().numpy()[prow], ob[1].cpu().numpy()[prow], gp,
+                ixb.assignment())
+        del ixb, ob
     # Eq. 4 / Proposition 5.3: epsilon-relaxed pruning; recall@k against the
     # oracle's exact top-k on the parity sample, dims read against the model
     # E[cost_eps] / E[cost_1] = 1 + ln(eps) (valid for eps > 1/e)
