@@ -22,6 +22,7 @@
 #include "gemm.h"
 #include "internal.h"
 #include "kernels_common.cuh"
+#include "probe_tc.h"
 #include "search.h"
 #include "verify_tc.h"
 
@@ -1671,12 +1672,23 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     mark(1);
     if (nlist > 1) {
       float* pd = (float*)P(o_pd);
-      PANO_CUDA(gemm_nt(kDist, (int)nq, nlist, d, queries, d, nullptr, I.cent.as<float>(), d, pd,
-                        nlist, qn2, I.cent_n2.as<float>(), st));
+      // query x centroid distances: tensor cores (bf16 hi/lo) where d allows,
+      // with the wider error band they need; the band is re-scored exactly
+      float gerr;
+      if (probe_tc_supported(d)) {
+        int r = launch_probe_tc(queries, nq, I.cent.as<float>(), nlist, d, qn2,
+                                I.cent_n2.as<float>(), pd, err, st);
+        if (r) return r;
+        gerr = (float)probe_tc_gerr(d);
+        if ((double)gerr < probe_tc_gerr(d)) gerr = std::nextafter(gerr, INFINITY);
+      } else {
+        PANO_CUDA(gemm_nt(kDist, (int)nq, nlist, d, queries, d, nullptr, I.cent.as<float>(), d,
+                          pd, nlist, qn2, I.cent_n2.as<float>(), st));
+        gerr = (float)(2.0 * gamma_n(gemm_rounds(d) + 4));
+      }
       const float cmax = I.cmax;
       size_t psm = (size_t)nlist * 4;
       PANO_CUDA(allow_dynamic_smem((const void*)probe_select_kernel));
-      float gerr = (float)(2.0 * gamma_n(gemm_rounds(d) + 4));
       probe_select_kernel<<<(unsigned)nq, NT, psm, st>>>(pd, nlist, queries, I.cent.as<float>(), d,
                                                          qn2, cmax, gerr, npq, stride, probes, err);
       PANO_CUDA(cudaGetLastError());
@@ -1943,11 +1955,20 @@ int probe_only(const pano_index* ip, const float* queries, int64_t nq, int32_t n
     prep_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(nq, nullptr, nprobe, nlist, nullptr,
                                                               0, 1, npq, npq + nq, err);
     row_sqnorm_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(queries, nq, d, qn2);
-    PANO_CUDA(gemm_nt(kDist, (int)nq, nlist, d, queries, d, nullptr, I.cent.as<float>(), d, pd,
-                      nlist, qn2, I.cent_n2.as<float>(), st));
+    float gerr;
+    if (probe_tc_supported(d)) {
+      int r = launch_probe_tc(queries, nq, I.cent.as<float>(), nlist, d, qn2,
+                              I.cent_n2.as<float>(), pd, err, st);
+      if (r) return r;
+      gerr = (float)probe_tc_gerr(d);
+      if ((double)gerr < probe_tc_gerr(d)) gerr = std::nextafter(gerr, INFINITY);
+    } else {
+      PANO_CUDA(gemm_nt(kDist, (int)nq, nlist, d, queries, d, nullptr, I.cent.as<float>(), d,
+                        pd, nlist, qn2, I.cent_n2.as<float>(), st));
+      gerr = (float)(2.0 * gamma_n(gemm_rounds(d) + 4));
+    }
     size_t psm = (size_t)nlist * 4;
     PANO_CUDA(allow_dynamic_smem((const void*)probe_select_kernel));
-    float gerr = (float)(2.0 * gamma_n(gemm_rounds(d) + 4));
     probe_select_kernel<<<(unsigned)nq, NT, psm, st>>>(pd, nlist, queries, I.cent.as<float>(), d,
                                                        qn2, I.cmax, gerr, npq, nprobe, out, err);
     PANO_CUDA(cudaGetLastError());
