@@ -246,8 +246,8 @@ int panorama_search_ex(const pano_index* idx, const float* queries,
  * loads the library until the process exits) instead of cudaMallocAsync;
  * a call whose workspace would exceed it fails with PANO_EINVAL before any
  * work is queued (the workspace grows with nq x (d + nlist + nprobe + k_max)).
- * The array's device address is looked up on the first call on each device
- * (make that call before any stream capture).  The call returns once the
+ * The array's device address is looked up on the first call on each device.
+ * The call returns once the
  * search has finished: it synchronizes the stream and reads the device
  * error word, like panorama_search.  Every call reuses the same array, so
  * calls that overlap on the GPU race; serialise them on one stream. */

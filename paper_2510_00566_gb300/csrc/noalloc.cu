@@ -12,11 +12,10 @@
 // library reserves it until the process exits.  In host code its name is
 // only a host-side stand-in, so the device address is fetched with
 // cudaGetSymbolAddress, once per device, with that device current, on the
-// first call made on the device (make that first call before any stream
-// capture).  All calls share the array, and it keeps the last call's
-// contents: the search clears what must start at zero on its stream, and
-// calls whose work overlaps on the GPU (different streams, or devices
-// sharing a context) race on the array.
+// first call made on the device.  All calls share the array, and it keeps
+// the last call's contents: the search clears what must start at zero on
+// its stream, and calls whose work overlaps on the GPU (different streams,
+// or devices sharing a context) race on the array.
 #include <mutex>
 
 #include "internal.h"
