@@ -126,28 +126,35 @@ __global__ void prep_kernel(int64_t nq, const int32_t* __restrict__ nprobe, int 
 
 // ------------------------------------------------------ a2: probe selection
 // One CTA per query.  The nprobe-th smallest expansion distance v is found by
-// an 8-bit radix select on order-preserving keys; every centroid whose
-// expansion distance is within twice the expansion's rounding bound of v (or
-// below) is re-scored with the compensated difference form and the first
-// nprobe by (exact distance, list id) are written in ascending order.
+// an 8-bit radix select on order-preserving keys.  With e the expansion's
+// rounding bound (|expansion - exact| <= e for every centroid), the nprobe-th
+// smallest exact distance D* lies in [v - e, v + e]: a centroid whose
+// expansion is above v + 2e is beyond D*, and one below v - 2e is strictly
+// inside it, so only the band [v - 2e, v + 2e] needs the compensated
+// difference form, and the probe set is the centroids below the band plus
+// the band's first ones by (exact distance, list id).  exact_order: every
+// centroid up to v + 2e is re-scored and the nprobe are written in ascending
+// (exact distance, list id) order; otherwise the ones below the band come
+// first, by (expansion distance, list id), then the band's.
 constexpr int kBandCap = 1024;
 
 __global__ void __launch_bounds__(NT) probe_select_kernel(
     const float* __restrict__ pdist, int nlist, const float* __restrict__ q,
     const float* __restrict__ cent, int d, const float* __restrict__ qn2, float cmax,
     float gerr, const int32_t* __restrict__ npq, int nprobe_stride,
-    int32_t* __restrict__ probes, int* __restrict__ err) {
+    int32_t* __restrict__ probes, int* __restrict__ err, int exact_order) {
   extern __shared__ uint32_t keys[];  // nlist
   __shared__ int hist[256];
   __shared__ int s_bin, s_below;
-  __shared__ int band_n;
+  // below the band: [0, n_in); the band: [kBandCap - n_band, kBandCap)
+  __shared__ int n_in, n_band;
   __shared__ int band_id[kBandCap];
   __shared__ float band_d[kBandCap];
   const int64_t row = blockIdx.x;
   const int m = npq[row];
   const float* pd = pdist + row * (int64_t)nlist;
   for (int i = threadIdx.x; i < nlist; i += NT) keys[i] = float_ordered(pd[i]);
-  if (threadIdx.x == 0) band_n = 0;
+  if (threadIdx.x == 0) n_in = n_band = 0;
   uint32_t prefix = 0, mask = 0;
   int remaining = m;
   for (int shift = 24; shift >= 0; shift -= 8) {
@@ -200,38 +207,64 @@ __global__ void __launch_bounds__(NT) probe_select_kernel(
     remaining -= s_below;
     __syncthreads();
   }
-  // decode v and form the band
+  // decode v and split the centroids up to v + 2e into "below the band" and
+  // "in the band"
   uint32_t u = (prefix & 0x80000000u) ? (prefix & 0x7fffffffu) : ~prefix;
   float v = __uint_as_float(u);
   float s = sqrtf(qn2[row]) + cmax;
-  float hi = v + 2.f * gerr * s * s;
+  const float e2 = 2.f * gerr * s * s;
+  float hi = v + e2;
+  const float lo = exact_order ? -INFINITY : v - e2;
   for (int i = threadIdx.x; i < nlist; i += NT) {
-    if (pd[i] <= hi) {
-      int pos = atomicAdd(&band_n, 1);
-      if (pos < kBandCap) band_id[pos] = i;
+    const float di = pd[i];
+    if (di <= hi) {
+      if (di < lo) {
+        const int pos = atomicAdd(&n_in, 1);
+        if (pos < kBandCap) {
+          band_id[pos] = i;
+          band_d[pos] = di;
+        }
+      } else {
+        const int pos = atomicAdd(&n_band, 1);
+        if (pos < kBandCap) band_id[kBandCap - 1 - pos] = i;
+      }
     }
   }
   __syncthreads();
-  const int nb = min(band_n, kBandCap);
-  if (threadIdx.x == 0 && band_n > kBandCap) atomicOr(err, kErrOverflow);
+  const bool over = n_in + n_band > kBandCap;
+  if (threadIdx.x == 0 && over) atomicOr(err, kErrOverflow);
+  const int ni = over ? 0 : n_in;
+  const int nb = over ? min(n_band, kBandCap) : n_band;
+  const int b0 = kBandCap - nb;  // the band occupies [b0, kBandCap)
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-  for (int b = warp; b < nb; b += NT / 32) {
+  for (int b = b0 + warp; b < kBandCap; b += NT / 32) {
     float e = exact_sqdist_warp(q + row * d, cent + (int64_t)band_id[b] * d, d);
     if (lane == 0) band_d[b] = e;
   }
   __syncthreads();
+  // ranks: below the band among themselves, the band among itself after them
   int32_t* out = probes + row * (int64_t)nprobe_stride;
-  for (int b = threadIdx.x; b < nb; b += NT) {
-    float db = band_d[b];
-    int ib = band_id[b];
+  for (int b = threadIdx.x; b < ni; b += NT) {
+    const float db = band_d[b];
+    const int ib = band_id[b];
     int rank = 0;
-    for (int o = 0; o < nb; ++o) {
-      float dd = band_d[o];
+    for (int o = 0; o < ni; ++o) {
+      const float dd = band_d[o];
       rank += (dd < db) || (dd == db && band_id[o] < ib);
     }
     if (rank < m) out[rank] = ib;
   }
-  for (int r = nb + threadIdx.x; r < m; r += NT) out[r] = -1;  // unreachable unless nlist < m
+  for (int b = b0 + threadIdx.x; b < kBandCap; b += NT) {
+    const float db = band_d[b];
+    const int ib = band_id[b];
+    int rank = ni;
+    for (int o = b0; o < kBandCap; ++o) {
+      const float dd = band_d[o];
+      rank += (dd < db) || (dd == db && band_id[o] < ib);
+    }
+    if (rank < m) out[rank] = ib;
+  }
+  for (int r = ni + nb + threadIdx.x; r < m; r += NT) out[r] = -1;  // unreachable unless nlist < m
 }
 
 // ------------------------------------------------------- a3: work inversion
@@ -1690,7 +1723,8 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
       size_t psm = (size_t)nlist * 4;
       PANO_CUDA(allow_dynamic_smem((const void*)probe_select_kernel));
       probe_select_kernel<<<(unsigned)nq, NT, psm, st>>>(pd, nlist, queries, I.cent.as<float>(), d,
-                                                         qn2, cmax, gerr, npq, stride, probes, err);
+                                                         qn2, cmax, gerr, npq, stride, probes, err,
+                                                         0);
       PANO_CUDA(cudaGetLastError());
     } else {
       PANO_CUDA(cudaMemsetAsync(probes, 0, (size_t)nq * stride * 4, st));
@@ -1970,7 +2004,7 @@ int probe_only(const pano_index* ip, const float* queries, int64_t nq, int32_t n
     size_t psm = (size_t)nlist * 4;
     PANO_CUDA(allow_dynamic_smem((const void*)probe_select_kernel));
     probe_select_kernel<<<(unsigned)nq, NT, psm, st>>>(pd, nlist, queries, I.cent.as<float>(), d,
-                                                       qn2, I.cmax, gerr, npq, nprobe, out, err);
+                                                       qn2, I.cmax, gerr, npq, nprobe, out, err, 1);
     PANO_CUDA(cudaGetLastError());
     PANO_CUDA(cudaStreamSynchronize(st));
     return PANO_OK;
