@@ -46,9 +46,10 @@ FALLBACK_HBM_GBS, FALLBACK_BF16_TFS = 6800.0, 1900.0
 # null instead of a stale figure.
 TRAFFIC = {
     # verify_tc_kernel<BF16>, phase B of the pruned search (whole-tile copies,
-    # issue warp, alive masks laid out by query half): 20.60 GB read + 0.059 GB written
+    # issue warp, one CTA barrier per level, chunk-wise test schedule):
+    # 20.63 GB read + 0.046 GB written
     "ivf-10m-d768-bf16: N=10,000,000 d=768 BF16, nlist=4096, nprobe=64, 10,000 queries, "
-    "12x64 levels, k=10": 20.60e9 + 58.93e6,
+    "12x64 levels, k=10": 20.63e9 + 45.70e6,
 }
 PQ_TRAFFIC = {}
 EPSILONS = (1.0, 0.9, 0.8, 0.6, 0.5, 0.4)
@@ -380,7 +381,7 @@ class Timer:
         return t.item() / steps, extra, c
 
 
-def e2e_time(idx, Q, npa, ka, k, steps, timer, test_every=1):
+def e2e_time(idx, Q, npa, ka, k, steps, timer, test_every=0):
     """Per-step time of the public API call with HOST buffers: pinned H2D of
     the queries (and per-query nprobe / k), search, D2H of ids and
     distances, all inside the events."""
@@ -461,7 +462,10 @@ def main():
     k = int(w.k.max()) if not isinstance(s.k, int) else s.k  # k_max
     npmax = int(w.nprobe.max())
     widths, tune = None, None
-    test_every = 1  # the bound tested at every level (Algorithm 1) unless tuned
+    # the bound-test schedule: the library's default for the storage format
+    # (FP32 every level as Algorithm 1; BF16 / FP8 every 4th level and nearly
+    # dead chunks at every level) unless tuned
+    test_every = 0
     if per_query:
         # storage precision and level split chosen by the autotuner: median
         # search time of each (precision, split) pair on a query sample,
@@ -522,7 +526,8 @@ def main():
     scan_ms, _, _ = timer.run(lambda: idx.search(Q, npa, ka, k_max=k, mode=1),
                               args.scan_steps, 1)
     # the bound-test schedule (which levels test Eq. 3): every level as in
-    # Algorithm 1, every other, every fourth, the last level only
+    # Algorithm 1, every other, every fourth, the first and last levels only
+    # (the tensor-core formats also test nearly dead chunks at every level)
     schedule_sweep = None
     if not per_query and not args.no_eps:
         schedule_sweep = []
@@ -701,7 +706,7 @@ def main():
         "parity": parity,
         "epsilon_sweep": eps_sweep,
         "test_schedule_sweep": schedule_sweep,
-        "test_every": test_every,
+        "test_every": test_every if test_every > 0 else (1 if s.precision == "fp32" else 4),
         "fp8_pruned": fp8,
         "fp32": fp32,
         "speedup_vs_plain_fp32_scan": (fp32["plain_scan"]["ms_per_step"] / ms_per_step

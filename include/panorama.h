@@ -103,12 +103,16 @@ typedef struct {
                              2 eps C prunes more and may lose true
                              neighbours (returned distances stay exact)    */
   int32_t test_every;     /* levels whose bound is tested (mode 0): level l
-                             when (l + 1) % test_every == 0, and always the
-                             last level.  0 or 1 (default) = every level,
-                             as Algorithm 1; larger values test less often,
-                             which can be faster where the work is per tile
-                             and tiles seldom die (panorama_autotune times
-                             it).  The result is exact whatever the value. */
+                             when l % test_every == 0, and always the last
+                             level; with BF16 / FP8 storage a chunk of 128
+                             candidates with at most 16 live rows is also
+                             tested at every level (only a test that leaves
+                             it no live row saves its copies and MMAs).
+                             1 = every level, as Algorithm 1.  0 (default)
+                             = the format's default: FP32 every level,
+                             BF16 / FP8 every 4th.  panorama_autotune times
+                             several.  The result is exact whatever the
+                             value; only the work changes.               */
 } pano_search_opts;
 
 /* Counters of the most recent search through this index from this thread
@@ -372,7 +376,8 @@ int panorama_autotune_levels(const pano_transform* t, const float* X, int64_t n,
  *   pair in precision-major order, with its median search time over
  *   `repeats` timed searches (after one warm-up) at the fastest of the
  *   bound-test schedules test_every = 1, 2, 4 and n_levels (every level,
- *   every other, every fourth, the last only), and that schedule, or +inf
+ *   every other, every fourth, the first and last only), and that
+ *   schedule, or +inf
  *   when the pair cannot be built or staged; *n_trials and *best (index of
  *   the fastest) are written.  k-means runs once; every candidate is built with its
  *   centroids.  Errors: PANO_EINVAL for bad arguments, more pairs than

@@ -252,15 +252,17 @@ def panorama_build_ivf(t: "Transform", X, nlist: int, n_levels=8,
 def panorama_search_ex(idx: "Index", queries, nprobe, k, k_max=None,
                        mode=0, collect_stats=False, synchronize=True,
                        stream=None, out=None, collect_timing=False,
-                       single_phase=None, epsilon=1.0, test_every=1):
+                       single_phase=None, epsilon=1.0, test_every=0):
     """Returns (ids int64 [nq, k_max], dists float32 [nq, k_max]) on the GPU.
 
     nprobe / k: python ints, or CUDA int32 tensors with one value per query.
     single_phase: None = the library chooses, True = one pass, False = each
     query's nearest list first.  epsilon < 1: Eq. 4's relaxed pruning
     (approximate; exact distances for what is returned).  test_every: the
-    bound is tested at level l when (l + 1) % test_every == 0 and at the
-    last level (1 = every level; the result is exact either way).
+    bound is tested at level l when l % test_every == 0 and at the last
+    level, and (BF16 / FP8) at every level for chunks with at most 16 live
+    rows; 1 = every level, 0 = the format's default (FP32 1, BF16 / FP8 4).
+    The result is exact whatever the schedule.
     """
     import torch
     q = queries.contiguous()
@@ -520,7 +522,7 @@ class Plan:
     nprobe / k when they are tensors) in place, call ``launch()``, then read
     ``ids`` / ``dists``."""
 
-    def __init__(self, idx: "Index", queries, nprobe, k, k_max=None, mode=0, test_every=1,
+    def __init__(self, idx: "Index", queries, nprobe, k, k_max=None, mode=0, test_every=0,
                  epsilon=1.0):
         import torch
         self.idx = idx

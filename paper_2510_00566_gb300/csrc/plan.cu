@@ -269,12 +269,13 @@ int panorama_autotune(const pano_transform* t, const float* X, int64_t n, const 
     if (build_ivf(t, X, n, nlist, &o, st, &idx)) continue;  // not buildable: +inf
     if (cent.empty()) cent = idx->centroids;
     // the bound-test schedules: every level (Algorithm 1), every other,
-    // every fourth, the last level only
+    // every fourth, the first and last levels only (the tensor-core formats
+    // also test nearly dead chunks at every level)
     std::vector<uint64_t> seen;  // tested-level masks already timed
     for (int te : {1, 2, 4, (int)tr.n_levels}) {
       uint64_t mask = 1ull << (tr.n_levels - 1);
       for (int l = 0; l < tr.n_levels; ++l)
-        if ((l + 1) % te == 0) mask |= 1ull << l;
+        if (l % te == 0) mask |= 1ull << l;
       if (std::find(seen.begin(), seen.end(), mask) != seen.end()) continue;
       seen.push_back(mask);
       pano_search_opts so{};

@@ -641,7 +641,7 @@ struct VerifyArgs {
   float lb_scale;  // (1 - 8u) / (1 + eta): lower bound in T~ space -> original
   float ub_scale;  // (1 + 8u) / (1 - eta): upper bound in T~ space -> original
   int prune;       // 0: plain scan (prune only after the last level)
-  int test_every;  // with prune: test at level l when (l + 1) % test_every == 0 (and the last)
+  int test_every;  // with prune: test at level l when l % test_every == 0 (and the last)
   int collect;
   int phase;        // 0: phase A (its dims are also counted apart)
   float eps;        // Eq. 4: the query tail term of the pruning test is scaled by eps
@@ -1199,7 +1199,7 @@ __global__ void __launch_bounds__(NTH, 2) verify_fp32_kernel(const VerifyArgs a)
             }
           }
           // bound update and pruning (Eq. 3 with rounding margins)
-          if ((a.prune && (l + 1) % a.test_every == 0) || l == L - 1) {
+          if ((a.prune && l % a.test_every == 0) || l == L - 1) {
             const float4 sx = *reinterpret_cast<const float4*>(xb + w * CH);
             const float sxv[4] = {sx.x, sx.y, sx.z, sx.w};
             float4 ct[4];
@@ -1614,7 +1614,11 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
   const int mode = opts ? opts->mode : 0;
   // Eq. 4: LB_eps = A - 2 eps C (0 and 1 mean the exact Eq. 3)
   const float eps = (opts && opts->epsilon > 0.f && opts->epsilon < 1.f) ? opts->epsilon : 1.f;
-  const int test_every = (opts && opts->test_every > 1) ? opts->test_every : 1;
+  // bound-test schedule: 0 = the storage format's default (FP32 every level;
+  // tensor-core formats every kTcTestEvery-th level plus nearly dead chunks)
+  const int te_opt = (opts && opts->test_every > 0) ? opts->test_every : 0;
+  const int test_every =
+      te_opt > 0 ? te_opt : (I.precision == PANO_FP32 ? 1 : kTcTestEvery);
   const bool timing = opts ? opts->collect_timing != 0 : false;
   const bool sync = (opts ? opts->synchronize != 0 : true) || timing;
   const bool collect = opts ? opts->collect_stats != 0 : false;

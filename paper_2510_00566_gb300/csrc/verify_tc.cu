@@ -228,10 +228,15 @@ __global__ void __launch_bounds__(256) pack_fp8_kernel(
 // that stays live has its next level's tile staged into its buffer while the
 // other chunks are still tested.  The next level's query slices, tail norms
 // and threshold terms are loaded into the epilogue threads' registers at the
-// start of a level and written to shared memory at its end (a CTA barrier).
+// start of a level and written to shared memory at its end: for BF16 by each
+// epilogue warp once its own tests are done, before the level's one CTA
+// barrier; for FP8 after that barrier, with a second one.
 constexpr int TMEM_COLS = S * QG;  // 256: two CTAs share an SM's tensor memory
 constexpr int AW = (QG + 31) / 32;  // alive-mask words per candidate row
 constexpr int PF_CHUNKS = 2;        // 16-byte query chunks prefetched per thread
+// a chunk with at most this many live rows is tested at every level: only a
+// test that leaves no live row retires the chunk's copies and MMAs
+constexpr int kTestRows = 16;
 static_assert(QG == 64 && AW == 2 && TMEM_COLS <= 256, "two query halves; two CTAs per SM");
 
 struct Smem {
@@ -251,9 +256,9 @@ struct Smem {
     off_b_hi = S * abytes;
     off_b_lo = off_b_hi + bbytes;
     off_alive = off_b_lo + bbytes;                   // [S][AW][CH] u32 (a warp's rows: consecutive words)
-    off_cand = off_alive + S * CH * AW * 4;  // 6 x [S][CH] (Hx, rx, ex, id, sx, FP8 factor)
-    off_q = off_cand + 6 * S * CH * 4;       // [QG] float4 + 6 x [QG]
-    total = off_q + 10 * QG * 4;
+    off_cand = off_alive + S * CH * AW * 4;  // 7 x [S][CH] (Hx, rx, ex, id, sx, FP8 factor, sx')
+    off_q = off_cand + 7 * S * CH * 4;       // 2 x [QG] float4 + 6 x [QG]
+    total = off_q + 14 * QG * 4;
   }
 };
 
@@ -370,8 +375,20 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   float* csx = reinterpret_cast<float*>(cid + S * CH);
   float* cfr = csx + S * CH;  // FP8: s_x / group scale, the accumulator's factor
   // per-query terms of the separable test: (E, g*rq, sq, H)
-  float4* qterm = reinterpret_cast<float4*>(base + lay.off_q);  // [QG]
-  int32_t* qid = reinterpret_cast<int32_t*>(qterm + QG);
+  float4* qterm = reinterpret_cast<float4*>(base + lay.off_q);  // [2][QG]
+  int32_t* qid = reinterpret_cast<int32_t*>(qterm + 2 * QG);
+  // BF16: each epilogue warp writes the next level's B tiles, tail norms and
+  // query terms as soon as its own tests of the level are done (the level's
+  // MMAs have completed by then), into a second tail / query-term buffer
+  // chosen by level parity, so one CTA barrier per level suffices.  FP8 (its
+  // three-term B tiles) measured faster with the writes after the level's
+  // barrier and a second barrier.
+  constexpr bool kEarly = !FP8;
+  // level l's tail norms and query terms (two buffers by level parity when
+  // the next level's are written while this level is still being tested)
+  float* const csx1 = cfr + S * CH;
+  auto csx_of = [&](int l) { return (kEarly && (l & 1)) ? csx1 : csx; };
+  auto qterm_of = [&](int l) { return (kEarly && (l & 1)) ? qterm + QG : qterm; };
   int32_t* qk = qid + QG;
   float* qnq = reinterpret_cast<float*>(qk + QG);
   float* qrq = qnq + QG;
@@ -398,6 +415,12 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   __shared__ unsigned int s_qmax;
   __shared__ float s_qs, s_cunder;
   __shared__ uint32_t rowlive[S][NE / 32];  // per epilogue warp: its rows live in its half
+  // the chunks live at level l and the chunks whose bound is tested there
+  // (bit c), by level parity: written by the issue warp from the liveness
+  // words it has acquired (before the CTA barrier that ends the previous
+  // level), so every thread reads the same masks even while fast warps
+  // already update rowlive for level l
+  __shared__ uint32_t s_live[2], s_test[2];
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
   const int row = tid & (CH - 1), half = tid / CH;
@@ -444,13 +467,13 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   constexpr float kEval = 32.f * 5.9604645e-08f;  // evaluation slack of the separable test
 
   // threshold -> per-query terms of the separable test (thread g < QG)
-  auto set_query_terms = [&](int g, float tau, float sq) {
+  auto set_query_terms = [&](int g, float tau, float sq, float4* qt) {
     const float st = tau == INFINITY ? 1e18f : fminf(__fsqrt_ru(__fdiv_ru(tau, a.lb_scale)), 1e18f);
     const float E = __fadd_ru(qeq[g], st);
     const float nq = qnq[g], rq = qrq[g];
     // FP8: the query split's underflow error (at most s_cunder |x|_2 on the
     // partial product) joins the g rq coefficient of rx
-    qterm[g] = make_float4(E, FP8 ? fmaf(g_slack, rq, s_cunder) : g_slack * rq, sq,
+    qt[g] = make_float4(E, FP8 ? fmaf(g_slack, rq, s_cunder) : g_slack * rq, sq,
                            0.5f * (nq - g_slack * nq - E * E - kEval * (rq + E) * (rq + E)));
     qtau[g] = tau;
   };
@@ -537,6 +560,32 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       }
     };
 
+    // the next level's B tiles, tail norms and query terms from the values
+    // prefetched into registers at the start of level l (epilogue threads)
+    auto next_level_setup = [&](int l, int w1, const float4 (&pf)[2 * PF_CHUNKS],
+                                const float (&tail_pf)[S * CH / NE], unsigned long long key_pf,
+                                float seed_pf, float sq_pf) {
+#pragma unroll
+      for (int i = 0; i < PF_CHUNKS; ++i) {
+        const int e = tid + i * NE;
+        if (e < Npad * (w1 / 8)) {
+          const int g = e / (w1 / 8), c8 = e % (w1 / 8);
+          const float f[8] = {pf[2 * i].x,     pf[2 * i].y,     pf[2 * i].z,     pf[2 * i].w,
+                              pf[2 * i + 1].x, pf[2 * i + 1].y, pf[2 * i + 1].z, pf[2 * i + 1].w};
+          store_b(g, c8, w1, f);
+        }
+      }
+      if (Npad * (w1 / 8) > PF_CHUNKS * NE) build_b(l + 1, PF_CHUNKS);  // wide levels
+      float* const cs = csx_of(l + 1);
+#pragma unroll
+      for (int u = 0; u < S * CH / NE; ++u) cs[tid + u * NE] = tail_pf[u];
+      if (tid < QG && qid[tid] >= 0 && qk[tid] > 0) {
+        const float tau = key_pf == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key_pf), 1.000001f);
+        set_query_terms(tid, fminf(tau, seed_pf), sq_pf, qterm_of(l + 1));
+      }
+      fence_proxy_async_smem();
+    };
+
     // ---- item prologue: group, candidates, liveness, level-0 tiles
     if (tid < QG) {
       int q = tid < G ? a.bucket[it.z + tid] : -1;
@@ -600,18 +649,27 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       }
     }
     __syncthreads();
-    if (warp == kIssuer)
+    if (warp == kIssuer) {
+      uint32_t m = 0;
       for (int c = 0; c < nch; ++c)
-        if (chunk_live(c)) issue_load(c, 0);
+        if (chunk_live(c)) {
+          issue_load(c, 0);
+          m |= 1u << c;
+        }
+      if (lane == 0) {
+        s_live[0] = m;
+        s_test[0] = (a.prune || L == 1) ? m : 0u;  // level 0: a test level of every schedule
+      }
+    }
     if (tid < QG) {
       const int q = qid[tid];
       if (q >= 0 && qk[tid] > 0) {
         unsigned long long key = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + qk[tid] - 1);
         float tau = key == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key), 1.000001f);
         set_query_terms(tid, fminf(tau, __ldcg(a.tau_seed + q)),
-                        a.eps * a.qtail[(int64_t)q * (L + 1) + 1]);
+                        a.eps * a.qtail[(int64_t)q * (L + 1) + 1], qterm);
       } else {
-        qterm[tid] = make_float4(0.f, 0.f, 0.f, -INFINITY);
+        qterm[tid] = qterm[QG + tid] = make_float4(0.f, 0.f, 0.f, -INFINITY);
         qtau[tid] = -1.f;
       }
     }
@@ -630,13 +688,11 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     section(0);
     for (int l = 0; l < L; ++l) {
       const int w = a.level_off[l + 1] - a.level_off[l];
-      // the bound is tested at the levels of the schedule (every level by
-      // default, as Algorithm 1) and always at the last
-      const bool test = (a.prune && (l + 1) % a.test_every == 0) || l == L - 1;
       const bool has_next = l + 1 < L;
-      uint32_t live_mask = 0;
-      for (int c = 0; c < nch; ++c)
-        if (chunk_live(c)) live_mask |= 1u << c;
+      const float* const csx_l = csx_of(l);
+      const float4* const qterm_l = qterm_of(l);
+      const uint32_t live_mask = s_live[l & 1];
+      const uint32_t test_mask = s_test[l & 1];
       if (!live_mask) {
         completed = false;
         break;
@@ -689,6 +745,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       // chunk c's test (epilogue warps): its accumulator once its MMAs are
       // done, then its liveness for the issue warp
       auto epilogue = [&](int c) {
+        const bool test = (test_mask >> c) & 1u;
         const bool ok = wait_phase(&mma_bar[c], mma_bits, c, &s_fail);
         tc::fence_after_sync();
         uint32_t wm = alive[(c * AW + half) * CH + row];
@@ -704,14 +761,14 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         // changes no liveness: its accumulator is not read
         const bool any_warp = test && any_live && __all_sync(0xffffffffu, ok);
         if (any_warp) {
-          const float sx = csx[c * CH + row], rx = crx[c * CH + row], exv = cex[c * CH + row];
+          const float sx = csx_l[c * CH + row], rx = crx[c * CH + row], exv = cex[c * CH + row];
           const float Hx = cHx[c * CH + row];
           const float fr = FP8 ? cfr[c * CH + row] : 1.f;
           if (Npad <= 16) {  // a group of <= 16 queries: 16 columns (half 0 only)
             float v[16];
             tc::tmem_ld16(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
             if (test && wm) {
-              const float4* qt = qterm + 32 * half;
+              const float4* qt = qterm_l + 32 * half;
               uint32_t pruned = 0;
 #pragma unroll
               for (int g = 0; g < 16; ++g) {
@@ -726,7 +783,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
             float v[32];
             tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
             if (test && wm) {  // every slot is tested (no branches); dead ones stay dead
-              const float4* qt = qterm + 32 * half;
+              const float4* qt = qterm_l + 32 * half;
               uint32_t pruned = 0;
 #pragma unroll
               for (int g = 0; g < 32; ++g) {
@@ -789,7 +846,8 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         __syncwarp();
         // ... then each chunk that stays live gets its next level's tile as
         // soon as every epilogue warp has read its accumulator
-        if (has_next)
+        if (has_next) {
+          uint32_t next_live = 0, next_test = 0;
           for (int c = 0; c < nch; ++c) {
             if (!((live_mask >> c) & 1u)) continue;
             int ok = 1;
@@ -798,48 +856,47 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
             // lane 0 (which acquired the chunk's liveness words) decides for
             // the warp (s_fail may change under it)
             const int go = __shfl_sync(0xffffffffu, (ok && !s_fail && chunk_live(c)) ? 1 : 0, 0);
-            if (go) issue_load(c, l + 1);
+            if (go) {
+              issue_load(c, l + 1);
+              next_live |= 1u << c;
+              // the bound-test schedule: chunk c is tested at level l + 1 if
+              // that is a level of the schedule or the last, or if at most
+              // kTestRows of its rows are still live
+              int n = 0;
+              for (int q = 0; q < 4; ++q) n += __popc(rowlive[c][q] | rowlive[c][q + 4]);
+              if (l + 1 == L - 1 ||
+                  (a.prune && ((l + 1) % a.test_every == 0 || n <= kTestRows)))
+                next_test |= 1u << c;
+            }
           }
+          if (lane == 0) {
+            s_live[(l + 1) & 1] = next_live;
+            s_test[(l + 1) & 1] = next_test;
+          }
+        }
       } else {
         for (int c = 0; c < nch; ++c)
           if ((live_mask >> c) & 1u) epilogue(c);
+        // every MMA of the level has completed (this warp saw the last live
+        // chunk's commit), so its B tiles are free: the next level's B
+        // tiles, tails and thresholds go in now, into the other tail and
+        // query-term buffers, while other warps may still be testing
+        if (kEarly && has_next) next_level_setup(l, w1, pf, tail_pf, key_pf, seed_pf, sq_pf);
       }
       // the level's accumulators have been read, its B tiles are free and
-      // the next level's tiles are on their way
+      // the next level's tiles are on their way; a failed wait anywhere ends
+      // the item for every thread alike
       tc::fence_before_sync();
-      __syncthreads();
+      const int failed = __syncthreads_or(s_fail != 0);
       tc::fence_after_sync();
       if (a.collect && tid == 0) s_stat[2] += __popc(live_mask);
       section(2);
-      if (s_fail) {
+      if (failed) {
         completed = false;
         break;
       }
-      if (has_next) {
-        if (epi) {
-          // next level's B tiles, tails and thresholds from the prefetch
-#pragma unroll
-          for (int i = 0; i < PF_CHUNKS; ++i) {
-            const int e = tid + i * NE;
-            if (e < Npad * (w1 / 8)) {
-              const int g = e / (w1 / 8), c8 = e % (w1 / 8);
-              const float f[8] = {pf[2 * i].x, pf[2 * i].y, pf[2 * i].z, pf[2 * i].w,
-                                  pf[2 * i + 1].x, pf[2 * i + 1].y, pf[2 * i + 1].z,
-                                  pf[2 * i + 1].w};
-              store_b(g, c8, w1, f);
-            }
-          }
-          if (Npad * (w1 / 8) > PF_CHUNKS * NE) build_b(l + 1, PF_CHUNKS);  // wide levels
-#pragma unroll
-          for (int u = 0; u < S * CH / NE; ++u) csx[tid + u * NE] = tail_pf[u];
-          if (tid < QG) {
-            if (qid[tid] >= 0 && qk[tid] > 0) {
-              float tau = key_pf == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key_pf), 1.000001f);
-              set_query_terms(tid, fminf(tau, seed_pf), sq_pf);
-            }
-          }
-          fence_proxy_async_smem();
-        }
+      if (!kEarly && has_next) {
+        if (epi) next_level_setup(l, w1, pf, tail_pf, key_pf, seed_pf, sq_pf);
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
@@ -895,7 +952,8 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       }
     }
     epi_sync();
-    if (tid < G && qk[tid] > 0) set_query_terms(tid, qtau[tid], 0.f);
+    float4* const qterm_last = qterm_of(L - 1);
+    if (tid < G && qk[tid] > 0) set_query_terms(tid, qtau[tid], 0.f, qterm_last);
     tc::fence_before_sync();
     epi_sync();
     tc::fence_after_sync();
@@ -913,7 +971,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         const float fr = FP8 ? cfr[c * CH + row] : 1.f;
         float v[32];
         tc::tmem_ld32(tbase + lane_base + (uint32_t)(c * QG + 32 * half), v);
-        const float4* qt = qterm + 32 * half;
+        const float4* qt = qterm_last + 32 * half;
         uint32_t pruned = 0;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {

@@ -8,6 +8,9 @@ namespace pano {
 constexpr int TC_CHUNK = 128;  // vectors per chunk (MMA M)
 constexpr int TC_QG = 64;      // queries per group (MMA N, padded to 16)
 constexpr int TC_SEG = 4;      // chunks per work-item segment
+// the tensor-core formats' default bound-test schedule: every chunk at the
+// levels l % 4 == 0 and the last, nearly dead chunks at every level
+constexpr int kTcTestEvery = 4;
 
 struct VerifyTCArgs {
   const uint8_t* slices;
@@ -37,7 +40,9 @@ struct VerifyTCArgs {
   float lb_scale;  // (1 - 8u) / (1 + eta)
   float ub_scale;  // (1 + 8u) / (1 - eta)
   int prune;
-  int test_every;  // the bound is tested at level l when (l + 1) % test_every == 0 (and the last)
+  // a live chunk's bound is tested at level l when l % test_every == 0, at
+  // the last level, and at every level once at most 16 of its rows are live
+  int test_every;
   int collect;
   int phase;  // 0: phase A (its dims are also counted apart)
   float eps;  // Eq. 4: the query tail term of the pruning test is scaled by eps

@@ -55,8 +55,9 @@ def test_bf16_768d_single_gaussian(mode):
     if mode == 1:
         assert st.dims_scanned == st.pairs * 768
         return
-    # pruning at least about as effective as the oracle's Algorithm 1
-    idx.search(torch.from_numpy(Q[:20]).to(DEV), 4, 10, collect_stats=True)
+    # pruning at least about as effective as the oracle's Algorithm 1 (the
+    # bound tested at every level, as there)
+    idx.search(torch.from_numpy(Q[:20]).to(DEV), 4, 10, collect_stats=True, test_every=1)
     st = pano.last_stats()
     frac = st.dims_scanned / (st.pairs * 768)
     lists, _ = oracle.assign(X, C)
@@ -109,9 +110,10 @@ def test_bf16_rejects_unsupported_widths():
 @pytest.mark.parametrize("precision", [pano.PANO_BF16, pano.PANO_FP32])
 def test_test_schedule_keeps_the_exact_answer(precision):
     """The bound-test schedule (test_every: which levels test Eq. 3, the last
-    always) changes the work, never the answer: every schedule returns the
-    oracle's exact top-k, the same ids and distances bit for bit, and no
-    schedule reads more coordinates than testing only the last level."""
+    always; 0 = the format's default) changes the work, never the answer:
+    every schedule returns the oracle's exact top-k, the same ids and
+    distances bit for bit, and none reads more coordinates than the plain
+    scan (the test at the last level only)."""
     s = synth.scaled(3, n=20_000, n_queries=80, nlist=16)
     w = synth.generate(s)
     X, Q = w.X.numpy(), w.Q.numpy()
@@ -126,7 +128,7 @@ def test_test_schedule_keeps_the_exact_answer(precision):
     G = gamma_of(lists, ref["probes"])
     first = None
     dims = []
-    for te in (1, 2, 5, 12, 100):
+    for te in (1, 2, 5, 12, 100, 0):
         ids, d = idx.search(q, 4, 10, test_every=te, collect_stats=True)
         dims.append(pano.last_stats().dims_scanned)
         ids, d = ids.cpu().numpy(), d.cpu().numpy()
@@ -136,8 +138,11 @@ def test_test_schedule_keeps_the_exact_answer(precision):
             first = (ids, d)
         else:
             assert np.array_equal(first[0], ids) and np.array_equal(first[1], d), te
-    # testing only at the last level reads every coordinate of every pair
-    # (the same for any test_every >= L); any schedule reads at most that
-    pairs = pano.last_stats().pairs
-    assert dims[3] == dims[4] == pairs * 768
-    assert all(x <= dims[3] for x in dims)
+    # the plain scan reads every coordinate of every pair; no schedule reads
+    # more, and testing every level reads less (how much less depends on the
+    # thresholds of the moment, which the order of the work items decides)
+    idx.search(q, 4, 10, mode=1, collect_stats=True)
+    st = pano.last_stats()
+    assert st.dims_scanned == st.pairs * 768
+    assert all(x <= st.dims_scanned for x in dims), (dims, st.dims_scanned)
+    assert dims[0] < st.dims_scanned

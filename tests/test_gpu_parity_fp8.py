@@ -60,7 +60,10 @@ def test_fp8_768d_single_gaussian(mode):
     if mode == 1:
         assert st.dims_scanned == st.pairs * 768
         return
-    # the bounds still prune (E4M3 loosens them by its quantisation error)
+    # the bounds still prune (E4M3 loosens them by its quantisation error):
+    # with the bound tested at every level, as the oracle's Algorithm 1
+    idx.search(torch.from_numpy(Q).to(DEV), 4, 10, collect_stats=True, test_every=1)
+    st = pano.last_stats()
     frac = st.dims_scanned / (st.pairs * 768)
     lists, _ = oracle.assign(X, C)
     ref = oracle_dims_fraction(X, Q[:20], C, lists, 4, [64] * 12, 10)
