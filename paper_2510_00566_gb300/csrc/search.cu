@@ -1819,6 +1819,14 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
                          : (float)(std::ldexp(1.0, -16) + (d / 8.0) * std::ldexp(1.0, -20) +
                                    2.0 * gamma_n(L + 8));
       ta.lb_scale = (float)((1.0 - 8.0 * kU32) / (1.0 + I.eta));
+      {
+        // inv is the double nearest 1 / lb_scale: a float at or below it
+        // moves up one step, so f exceeds the exact reciprocal
+        const double inv = 1.0 / (double)ta.lb_scale;
+        float f = (float)inv;
+        if ((double)f <= inv) f = std::nextafter(f, INFINITY);
+        ta.inv_lb_up = f;
+      }
       ta.ub_scale = (float)((1.0 + 8.0 * kU32) / (1.0 - I.eta) * (1.0 + 1e-7));
       ta.prune = mode == 0 ? 1 : 0;
       ta.test_every = test_every;
@@ -1866,7 +1874,7 @@ int search(const pano_index* ip, const float* queries, int64_t nq, const int32_t
     {
       const double inv = 1.0 / (double)va.lb_scale;
       float f = (float)inv;
-      if ((double)f < inv) f = std::nextafter(f, INFINITY);
+      if ((double)f <= inv) f = std::nextafter(f, INFINITY);
       va.inv_lb_up = f;
     }
     va.ub_scale = (float)((1.0 + 8.0 * kU32) / (1.0 - I.eta) * (1.0 + 1e-7));

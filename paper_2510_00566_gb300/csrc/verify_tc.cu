@@ -233,7 +233,6 @@ __global__ void __launch_bounds__(256) pack_fp8_kernel(
 // barrier; for FP8 after that barrier, with a second one.
 constexpr int TMEM_COLS = S * QG;  // 256: two CTAs share an SM's tensor memory
 constexpr int AW = (QG + 31) / 32;  // alive-mask words per candidate row
-constexpr int PF_CHUNKS = 2;        // 16-byte query chunks prefetched per thread
 // a chunk with at most this many live rows is tested at every level: only a
 // test that leaves no live row retires the chunk's copies and MMAs
 constexpr int kTestRows = 16;
@@ -468,7 +467,9 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
 
   // threshold -> per-query terms of the separable test (thread g < QG)
   auto set_query_terms = [&](int g, float tau, float sq, float4* qt) {
-    const float st = tau == INFINITY ? 1e18f : fminf(__fsqrt_ru(__fdiv_ru(tau, a.lb_scale)), 1e18f);
+    // sqrt(tau / lb_scale), rounded up (a product by the rounded-up
+    // reciprocal, itself rounded up, bounds the quotient from above)
+    const float st = tau == INFINITY ? 1e18f : fminf(__fsqrt_ru(__fmul_ru(tau, a.inv_lb_up)), 1e18f);
     const float E = __fadd_ru(qeq[g], st);
     const float nq = qnq[g], rq = qrq[g];
     // FP8: the query split's underflow error (at most s_cunder |x|_2 on the
@@ -560,22 +561,12 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       }
     };
 
-    // the next level's B tiles, tail norms and query terms from the values
-    // prefetched into registers at the start of level l (epilogue threads)
-    auto next_level_setup = [&](int l, int w1, const float4 (&pf)[2 * PF_CHUNKS],
-                                const float (&tail_pf)[S * CH / NE], unsigned long long key_pf,
-                                float seed_pf, float sq_pf) {
-#pragma unroll
-      for (int i = 0; i < PF_CHUNKS; ++i) {
-        const int e = tid + i * NE;
-        if (e < Npad * (w1 / 8)) {
-          const int g = e / (w1 / 8), c8 = e % (w1 / 8);
-          const float f[8] = {pf[2 * i].x,     pf[2 * i].y,     pf[2 * i].z,     pf[2 * i].w,
-                              pf[2 * i + 1].x, pf[2 * i + 1].y, pf[2 * i + 1].z, pf[2 * i + 1].w};
-          store_b(g, c8, w1, f);
-        }
-      }
-      if (Npad * (w1 / 8) > PF_CHUNKS * NE) build_b(l + 1, PF_CHUNKS);  // wide levels
+    // the next level's B tiles (query slices read from global memory here:
+    // holding them in registers since the level's start cost more in spills
+    // than the load latency), tail norms and query terms (epilogue threads)
+    auto next_level_setup = [&](int l, const float (&tail_pf)[S * CH / NE],
+                                unsigned long long key_pf, float seed_pf, float sq_pf) {
+      build_b(l + 1, 0);
       float* const cs = csx_of(l + 1);
 #pragma unroll
       for (int u = 0; u < S * CH / NE; ++u) cs[tid + u * NE] = tail_pf[u];
@@ -705,27 +696,11 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           for (int q = 0; q < 4; ++q) n += __popc(rowlive[c][q] | rowlive[c][q + 4]);
         s_stat[5] += n * (unsigned long long)(w * EB + 4);
       }
-      // prefetch the next level's query slices, tails and thresholds
-      float4 pf[2 * PF_CHUNKS];
+      // prefetch the next level's tails and thresholds
       float tail_pf[S * CH / NE];
       unsigned long long key_pf = kEmptyKey;
       float seed_pf = INFINITY, sq_pf = 0.f;
-      int m1 = 0, w1 = 16;
       if (has_next && epi) {
-        m1 = a.level_off[l + 1];
-        w1 = a.level_off[l + 2] - m1;
-#pragma unroll
-        for (int i = 0; i < PF_CHUNKS; ++i) {
-          const int e = tid + i * NE;
-          const int g = e / (w1 / 8), c8 = e % (w1 / 8);
-          if (e < Npad * (w1 / 8) && g < G) {
-            const float* src = a.qt + (int64_t)qid[g] * d + m1 + c8 * 8;
-            pf[2 * i] = *reinterpret_cast<const float4*>(src);
-            pf[2 * i + 1] = *reinterpret_cast<const float4*>(src + 4);
-          } else {
-            pf[2 * i] = pf[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-          }
-        }
 #pragma unroll
         for (int u = 0; u < S * CH / NE; ++u) {
           const int e = tid + u * NE;
@@ -881,7 +856,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         // chunk's commit), so its B tiles are free: the next level's B
         // tiles, tails and thresholds go in now, into the other tail and
         // query-term buffers, while other warps may still be testing
-        if (kEarly && has_next) next_level_setup(l, w1, pf, tail_pf, key_pf, seed_pf, sq_pf);
+        if (kEarly && has_next) next_level_setup(l, tail_pf, key_pf, seed_pf, sq_pf);
       }
       // the level's accumulators have been read, its B tiles are free and
       // the next level's tiles are on their way; a failed wait anywhere ends
@@ -896,7 +871,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         break;
       }
       if (!kEarly && has_next) {
-        if (epi) next_level_setup(l, w1, pf, tail_pf, key_pf, seed_pf, sq_pf);
+        if (epi) next_level_setup(l, tail_pf, key_pf, seed_pf, sq_pf);
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();

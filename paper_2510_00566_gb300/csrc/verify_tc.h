@@ -38,6 +38,7 @@ struct VerifyTCArgs {
   int d, L, max_w, k_max;
   float gslack;    // |computed - exact| terms of the bound <= gslack (|q~|+|x^|)^2
   float lb_scale;  // (1 - 8u) / (1 + eta)
+  float inv_lb_up;  // 1 / lb_scale rounded up
   float ub_scale;  // (1 + 8u) / (1 - eta)
   int prune;
   // a live chunk's bound is tested at level l when l % test_every == 0, at
