@@ -35,6 +35,15 @@ int panorama_debug_tc_gemm(const void* A, const void* B, int32_t N, int32_t K,
 int panorama_debug_tc_gemm_fp8(const void* A, const void* B, int32_t N, int32_t K,
                                float* D, void* stream);
 
+/* panorama_debug_sqrt_up -- out[i] = the verify kernels' rounded-up square
+ * root of x[i] (x[i] >= 0): the approximate square root times 1 + 2^-18,
+ * rounded up, which the upper bounds of the last level use.  The paper has
+ * no counterpart: it lets a test check that the result bounds the exact
+ * root from above.
+ *   x, out: device, n floats.
+ * Errors: PANO_EINVAL (n < 0, null pointers with n > 0), PANO_ECUDA. */
+int panorama_debug_sqrt_up(const float* x, int64_t n, float* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -147,6 +147,7 @@ SIGNATURES = {
     "panorama_pq_export": (ctypes.c_int, [_P, _P, _P, _P]),
     "panorama_debug_pq_encode": (ctypes.c_int, [_P, _I64, _I32, _I32, _P, _P, _P]),
     "panorama_debug_tc_gemm_fp8": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _P]),
+    "panorama_debug_sqrt_up": (ctypes.c_int, [_P, _I64, _P, _P]),
     "panorama_plan_create": (ctypes.c_int, [_P, _P, _I64, _P, _I32, _P, _I32, _I32,
                                             _P, _P, _I32, _P]),
     "panorama_plan_create_ex": (ctypes.c_int, [_P, _P, _I64, _P, _I32, _P, _I32, _I32,
@@ -382,6 +383,17 @@ def panorama_debug_tc_gemm_fp8(A, B, stream=None):
     _check(lib().panorama_debug_tc_gemm_fp8(A.data_ptr(), B.data_ptr(), N, K,
                                             D.data_ptr(), _stream_ptr(stream)))
     return D
+
+
+def panorama_debug_sqrt_up(x, stream=None):
+    """The verify kernels' rounded-up square root of each element of x (a
+    float32 CUDA tensor of non-negative values)."""
+    import torch
+    x = x.contiguous()
+    out = torch.empty_like(x)
+    _check(lib().panorama_debug_sqrt_up(x.data_ptr(), x.numel(), out.data_ptr(),
+                                        _stream_ptr(stream)))
+    return out
 
 
 # ------------------------------------------------------------------ IVFPQ

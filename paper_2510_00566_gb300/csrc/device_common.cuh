@@ -167,6 +167,20 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// sqrt(x) rounded up, for x >= 0 where only an upper bound is needed: the
+// approximate square root (sqrt.approx.f32, whose relative error is a few
+// units of 2^-23) times 1 + 2^-18, rounded up.  One multiply on top of the
+// approximation, against the longer sequence of the IEEE directed-rounding
+// square root.  Inputs below 2^-126 (zero and subnormals) are raised to it,
+// so the result there is 2^-63 (times 1 + 2^-18), still an upper bound.
+// panorama_debug_sqrt_up exposes it so that a test checks the bound against
+// FP64 over the whole range.
+__device__ __forceinline__ float sqrt_up(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(fmaxf(x, 0x1p-126f)));
+  return __fmul_ru(r, 1.0f + 0x1p-18f);
+}
+
 // Order-preserving map of any FP32 value to uint32.
 __device__ __forceinline__ uint32_t float_ordered(float f) {
   uint32_t u = __float_as_uint(f);

@@ -130,3 +130,24 @@ extern "C" int panorama_debug_tc_gemm_fp8(const void* A, const void* B, int32_t 
                                           float* D, void* stream) {
   return pano::run_tc_selftest(true, A, B, N, K, D, stream);
 }
+
+namespace pano {
+namespace {
+__global__ void sqrt_up_kernel(const float* __restrict__ x, int64_t n, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = sqrt_up(x[i]);
+}
+}  // namespace
+}  // namespace pano
+
+extern "C" int panorama_debug_sqrt_up(const float* x, int64_t n, float* out, void* stream) {
+  using namespace pano;
+  clear_error();
+  PANO_CHECK(n >= 0 && (n == 0 || (x && out)), PANO_EINVAL, "bad arguments");
+  if (n == 0) return PANO_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  sqrt_up_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, n, out);
+  PANO_CUDA(cudaGetLastError());
+  PANO_CUDA(cudaStreamSynchronize(st));
+  return PANO_OK;
+}

@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       for (int u = 0; u < S * CH / NE; ++u) cs[tid + u * NE] = tail_pf[u];
       if (tid < QG && qid[tid] >= 0 && qk[tid] > 0) {
         const float tau = key_pf == kEmptyKey ? INFINITY : __fmul_ru(key_dist(key_pf), 1.000001f);
-        set_query_terms(tid, fminf(tau, seed_pf), sq_pf, qterm_of(l + 1));
+        set_query_terms(tid, fminf(tau, seed_pf), a.eps * sq_pf, qterm_of(l + 1));
       }
       fence_proxy_async_smem();
     };
@@ -696,7 +696,9 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           for (int q = 0; q < 4; ++q) n += __popc(rowlive[c][q] | rowlive[c][q + 4]);
         s_stat[5] += n * (unsigned long long)(w * EB + 4);
       }
-      // prefetch the next level's tails and thresholds
+      // prefetch the next level's tails and thresholds (raw loads: no
+      // arithmetic on them here, so no thread waits for them before its
+      // tests)
       float tail_pf[S * CH / NE];
       unsigned long long key_pf = kEmptyKey;
       float seed_pf = INFINITY, sq_pf = 0.f;
@@ -704,16 +706,15 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
 #pragma unroll
         for (int u = 0; u < S * CH / NE; ++u) {
           const int e = tid + u * NE;
-          tail_pf[u] = e < nch * CH
-                           ? a.tails[((ch0 + e / CH) * (L + 1) + l + 2) * CH + (e % CH)]
-                           : 0.f;
+          tail_pf[u] = 0.f;
+          if (e < nch * CH) tail_pf[u] = a.tails[((ch0 + e / CH) * (L + 1) + l + 2) * CH + (e % CH)];
         }
         if (tid < QG) {
           const int q = qid[tid];
           if (q >= 0 && qk[tid] > 0) {
             key_pf = ld_volatile_u64(a.topk + (int64_t)q * a.k_max + qk[tid] - 1);
             seed_pf = __ldcg(a.tau_seed + q);
-            sq_pf = a.eps * a.qtail[(int64_t)q * (L + 1) + l + 2];
+            sq_pf = a.qtail[(int64_t)q * (L + 1) + l + 2];
           }
         }
       }
@@ -906,7 +907,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           if ((wm >> j) & 1u) {
             const float A = qnq[g] + nx2 - 2.f * (FP8 ? v[j] * fr : v[j]);
             const float Ss = qrq[g] + rx;
-            const float r = __fadd_ru(__fsqrt_ru(fmaxf(A + fmaf(g_slack * Ss, Ss, under), 0.f)),
+            const float r = __fadd_ru(sqrt_up(fmaxf(A + fmaf(g_slack * Ss, Ss, under), 0.f)),
                                       qeq[g] + exv);
             u = __bfloat16_as_ushort(__float2bfloat16_ru(__fmul_ru(__fmul_ru(r, r), a.ub_scale)));
           }
@@ -992,7 +993,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
           pq[np + s] = qid[g];
           pid[np + s] = cid[c * CH + r];
           plb[np + s] = lr > 0.f ? lr * lr * a.lb_scale : 0.f;
-          const float ru = __fadd_ru(__fsqrt_ru(fmaxf(A + slack, 0.f)), qeq[g] + exv);
+          const float ru = __fadd_ru(sqrt_up(fmaxf(A + slack, 0.f)), qeq[g] + exv);
           pub[np + s] = __fmul_ru(__fmul_ru(ru, ru), a.ub_scale);
         }
         np += nb;

@@ -94,3 +94,27 @@ def test_tc_gemm_fp8_wide_range_and_cancellation():
     b = torch.ones(32, 128)
     b[:, 1::2] = 1.125
     assert _fp8_check(a.to(E4M3), b.to(E4M3)) == 0.0
+
+
+def test_sqrt_up_bounds_the_root_from_above():
+    """The last level's upper bounds take square roots with the approximate
+    square root times 1 + 2^-18, rounded up: on every binade of FP32 (zero,
+    subnormals, normals up to 2^127) and many mantissas it must be at least
+    the exact root, within 2^-17 of it for normal inputs, and at most 2^-62
+    below 2^-126 (where the input is raised to 2^-126)."""
+    g = torch.Generator().manual_seed(11)
+    exps = torch.arange(-149, 128, dtype=torch.float64)
+    mant = 1.0 + torch.rand(exps.numel(), 64, generator=g, dtype=torch.float64)
+    x = (mant * torch.pow(2.0, exps)[:, None]).reshape(-1)
+    x = torch.cat([x, torch.tensor([0.0, 2.0 ** -149, 2.0 ** -126, 1.0, 4.0,
+                                    float(torch.finfo(torch.float32).max)],
+                                   dtype=torch.float64)])
+    x32 = x.to(torch.float32)
+    x32 = x32[torch.isfinite(x32)]
+    r = pano.panorama_debug_sqrt_up(x32.to("cuda:0")).cpu().double()
+    exact = x32.double().sqrt()
+    assert torch.all(r >= exact)
+    normal = x32.double() >= 2.0 ** -126
+    assert torch.all(r[normal] <= exact[normal] * (1 + 2.0 ** -17)), \
+        float((r[normal] / exact[normal]).max())
+    assert torch.all(r[~normal] <= 2.0 ** -62)
