@@ -21,8 +21,9 @@
 // row t is owned by two epilogue threads (warps w and w + 4 read the same
 // TMEM lane quarter), one per half of the query group, each reading its 32
 // accumulators with tcgen05.ld and applying the separable form of the
-// margined Eq. 3 test (three FMAs and a compare per (candidate, query) pair).
-// A chunk whose rows are all dead is neither copied nor multiplied again.
+// margined Eq. 3 test (three FMAs and a compare per (candidate, query) pair)
+// at the levels of the bound-test schedule.  A chunk whose rows are all dead
+// is neither copied nor multiplied again.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -226,11 +227,14 @@ __global__ void __launch_bounds__(256) pack_fp8_kernel(
 // the chunks in order as their accumulators complete and tell the issue warp
 // (an mbarrier per chunk) when all of them have read one, whereupon a chunk
 // that stays live has its next level's tile staged into its buffer while the
-// other chunks are still tested.  The next level's query slices, tail norms
-// and threshold terms are loaded into the epilogue threads' registers at the
-// start of a level and written to shared memory at its end: for BF16 by each
+// other chunks are still tested.  The next level's tail norms and threshold
+// terms are loaded into the epilogue threads' registers at the start of a
+// level; they and the next level's B tiles (built from the query slices in
+// global memory) are written to shared memory at its end: for BF16 by each
 // epilogue warp once its own tests are done, before the level's one CTA
-// barrier; for FP8 after that barrier, with a second one.
+// barrier; for FP8 after that barrier, with a second one.  A live chunk's
+// bound is tested at the levels of the schedule (l % test_every == 0), at the
+// last level, and at every level once it is nearly dead.
 constexpr int TMEM_COLS = S * QG;  // 256: two CTAs share an SM's tensor memory
 constexpr int AW = (QG + 31) / 32;  // alive-mask words per candidate row
 // a chunk with at most this many live rows is tested at every level: only a
