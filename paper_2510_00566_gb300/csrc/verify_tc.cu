@@ -424,6 +424,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
   // level), so every thread reads the same masks even while fast warps
   // already update rowlive for level l
   __shared__ uint32_t s_live[2], s_test[2];
+  __shared__ uint32_t s_gm[2];  // the group's queries with k > 0 (two halves)
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
   const int row = tid & (CH - 1), half = tid / CH;
@@ -582,20 +583,29 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     };
 
     // ---- item prologue: group, candidates, liveness, level-0 tiles
+    // the level-0 tiles of every chunk are staged first, so that their copies
+    // overlap the rest of the prologue (the previous item's last-level work,
+    // which used the A buffers, ended at the barrier above)
+    if (warp == kIssuer)
+      for (int c = 0; c < nch; ++c) issue_load(c, 0);
     if (tid < QG) {
       int q = tid < G ? a.bucket[it.z + tid] : -1;
       qid[tid] = q;
+      int kk = 0;
       if (q >= 0) {
         float4 inf = a.qinfo[q];
         qnq[tid] = inf.x;
         qrq[tid] = inf.y;
         qeq[tid] = inf.z;
-        qk[tid] = a.kq[q];
+        kk = a.kq[q];
         if (FP8) atomicMax(&s_qmax, __float_as_uint(inf.w));  // inf.w = max_j |q~_j| >= 0
       } else {
         qnq[tid] = qrq[tid] = qeq[tid] = 0.f;
-        qk[tid] = 0;
       }
+      qk[tid] = kk;
+      // the group's queries with k > 0: warp 0 holds queries 0-31, warp 1 32-63
+      const unsigned b = __ballot_sync(0xffffffffu, kk > 0);
+      if (lane == 0) s_gm[warp] = b;
     }
     for (int e = tid; e < S * CH; e += NT) {
       const int c = e / CH;
@@ -629,13 +639,7 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
       s_cunder = __fmul_ru(ldexpf(1.f, e - 10), __fsqrt_ru((float)d));
     }
     if (epi) {
-      uint32_t gm0 = 0, gm1 = 0;
-      for (int g = 0; g < G; ++g)
-        if (qk[g] > 0) {
-          if (g < 32) gm0 |= 1u << g;
-          else gm1 |= 1u << (g - 32);
-        }
-      const uint32_t gm = half ? gm1 : gm0;
+      const uint32_t gm = s_gm[half];
       for (int c = 0; c < S; ++c) {
         const bool v = c < nch && cid[c * CH + row] >= 0;
         alive[(c * AW + half) * CH + row] = v ? gm : 0u;
@@ -645,12 +649,16 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
     }
     __syncthreads();
     if (warp == kIssuer) {
+      // a chunk with no live row at level 0 (no valid row, or no query with
+      // k > 0) is not multiplied: its copy is waited for here instead
       uint32_t m = 0;
-      for (int c = 0; c < nch; ++c)
+      for (int c = 0; c < nch; ++c) {
         if (chunk_live(c)) {
-          issue_load(c, 0);
           m |= 1u << c;
+        } else if (lane == 0) {
+          wait_phase(&load_bar[c], load_bits, c, &s_fail);
         }
+      }
       if (lane == 0) {
         s_live[0] = m;
         s_test[0] = (a.prune || L == 1) ? m : 0u;  // level 0: a test level of every schedule
