@@ -472,9 +472,9 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
 
   // threshold -> per-query terms of the separable test (thread g < QG)
   auto set_query_terms = [&](int g, float tau, float sq, float4* qt) {
-    // sqrt(tau / lb_scale), rounded up (a product by the rounded-up
+    // sqrt(tau / lb_scale), bounded from above (a product by the rounded-up
     // reciprocal, itself rounded up, bounds the quotient from above)
-    const float st = tau == INFINITY ? 1e18f : fminf(__fsqrt_ru(__fmul_ru(tau, a.inv_lb_up)), 1e18f);
+    const float st = tau == INFINITY ? 1e18f : fminf(sqrt_up(__fmul_ru(tau, a.inv_lb_up)), 1e18f);
     const float E = __fadd_ru(qeq[g], st);
     const float nq = qnq[g], rq = qrq[g];
     // FP8: the query split's underflow error (at most s_cunder |x|_2 on the
@@ -550,19 +550,34 @@ __global__ void __launch_bounds__(NT, 2) verify_tc_kernel(const VerifyTCArgs a) 
         *reinterpret_cast<uint4*>(blo + off) = *reinterpret_cast<const uint4*>(lo);
       }
     };
+    // (two 8-element groups per thread per round: both loads are in flight
+    // before either is converted)
     auto build_b = [&](int l, int first_chunk) {
       const int m = a.level_off[l], w = a.level_off[l + 1] - m;
-      for (int e = tid + first_chunk * NE; e < Npad * (w / 8); e += NE) {
-        const int g = e / (w / 8), c8 = e % (w / 8);
-        float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (g < G) {
-          const float* src = a.qt + (int64_t)qid[g] * d + m + c8 * 8;
-          const float4 f0 = *reinterpret_cast<const float4*>(src);
-          const float4 f1 = *reinterpret_cast<const float4*>(src + 4);
-          f[0] = f0.x, f[1] = f0.y, f[2] = f0.z, f[3] = f0.w;
-          f[4] = f1.x, f[5] = f1.y, f[6] = f1.z, f[7] = f1.w;
+      const int n8 = w / 8, total = Npad * n8;
+      const bool p2 = (n8 & (n8 - 1)) == 0;  // widths 16, 32, 64, 128, 256: a shift
+      const int sh = __ffs(n8) - 1;
+      for (int e0 = tid + first_chunk * NE; e0 < total; e0 += 2 * NE) {
+        float f[2][8];
+        int gg[2], cc[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int e = e0 + u * NE;
+          gg[u] = p2 ? e >> sh : e / n8;
+          cc[u] = p2 ? e & (n8 - 1) : e % n8;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) f[u][j] = 0.f;
+          if (e < total && gg[u] < G) {
+            const float* src = a.qt + (int64_t)qid[gg[u]] * d + m + cc[u] * 8;
+            const float4 f0 = *reinterpret_cast<const float4*>(src);
+            const float4 f1 = *reinterpret_cast<const float4*>(src + 4);
+            f[u][0] = f0.x, f[u][1] = f0.y, f[u][2] = f0.z, f[u][3] = f0.w;
+            f[u][4] = f1.x, f[u][5] = f1.y, f[u][6] = f1.z, f[u][7] = f1.w;
+          }
         }
-        store_b(g, c8, w, f);
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+          if (e0 + u * NE < total) store_b(gg[u], cc[u], w, f[u]);
       }
     };
 
