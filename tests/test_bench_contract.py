@@ -1,8 +1,9 @@
-"""The benchmark's reference arm on the host (no GPU): `bench.py --impl
-reference` times the CPU oracle on bounded samples of a workload and prints
-one JSON line with the keys every bench line carries; under a multi-rank
-launch only rank 0 runs and prints.  Run on the smallest workload (20,000 x
-128, one list) so that it takes a few seconds."""
+"""Host-side checks of the benchmark (no GPU).  The reference arm
+(`bench.py --impl reference`) times the CPU oracle on bounded samples of a
+workload and prints one JSON line with the keys every bench line carries;
+under a multi-rank launch only rank 0 runs and prints.  It runs here on the
+smallest workload (20,000 x 128, one list), in a few seconds.  The roofline's
+DRAM-traffic table is keyed so that the default line finds its figure."""
 import json
 import os
 import subprocess
@@ -48,3 +49,19 @@ def test_reference_arm_prints_one_bench_line():
 
 def test_reference_arm_other_ranks_exit_quietly():
     assert _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_dram_traffic_figure_is_keyed_by_the_default_workload():
+    """The bench line's roofline traffic comes from a table keyed by the full
+    workload description, so a resized run reports none; the default run's
+    workload (the 10M x 768 BF16 IVF line) must find its figure."""
+    import argparse
+    sys.path.insert(0, ROOT)
+    import bench
+    args = argparse.Namespace(config=3, n=0, queries=0, nlist=0)
+    name = bench.workload_name(bench.workload_spec(args))
+    assert name in bench.TRAFFIC, name
+    assert 1e9 < bench.TRAFFIC[name] < 1e11
+    resized = bench.workload_name(bench.workload_spec(argparse.Namespace(
+        config=3, n=500_000, queries=2000, nlist=256)))
+    assert resized not in bench.TRAFFIC
